@@ -1,0 +1,160 @@
+/*
+ * escg.h -- C ABI of libescg, a GB300 (sm_103a) implementation of the Monte
+ * Carlo step (MCS) of an Evolutionary Spatial Cyclic Game (ESCG) on an L x L
+ * periodic von Neumann lattice (arXiv 2508.16639).
+ *
+ * The model (Section 3.1 "Implementation" of the paper): lattice value 0 is
+ * an empty site, 1..S a species; species a dominates species b iff
+ * digraph[(a-1)*S + (b-1)] == 1 (Alg. 2, "Dominance Check"; the circulant
+ * C(S,K) definition gives RPS = C(3,{1}) and RPSLS = C(5,{1,2})).  One MCS is
+ * N = L*L elementary steps (Alg. 4, "Overall ESCG Loop"); an elementary step
+ * (Alg. 3, "Elementary Step") picks a site and one of its four neighbours
+ * and applies, with probabilities proportional to the rates, exchange
+ * (migration, epsilon), interaction (mu: the dominated one of the pair
+ * becomes empty) or reproduction (sigma: an occupied site fills an empty
+ * neighbour).  epsilon = 2 M N for mobility M (Section 3.1, rate set-up).
+ *
+ * Parallel order.  The N elementary steps of an MCS run in the race-free
+ * order of schedule version 1: the lattice is cut into an even number P of
+ * coarse blocks per axis (about 64 sites wide) coloured 2x2, each block into
+ * fine sub-blocks of 2..4 sites per axis coloured 2x2; the four coarse
+ * colours run one after another in a per-MCS random order, and inside a
+ * block the four fine colours likewise, every sub-block performing all of
+ * its attempts of the MCS in one visit.  Every random choice (colour orders,
+ * cell, direction, action) is a Philox4x32-10 draw keyed by the seed and
+ * counted by (attempt, sub-block, MCS), compared against integer
+ * thresholds.  Results are deterministic: the lattice after m MCS depends
+ * only on (L, S, digraph, rates, seed, initial lattice, m), never on the
+ * device, stream, launch shape or on other lattices in a batch.
+ *
+ * Conventions.
+ *   - All functions except escg_create*, escg_batch_create and the
+ *     escg_server constructors return an escg_status; 0 is success.
+ *   - Host pointers passed in are read during the call only (copied, never
+ *     retained).  Output buffers are caller-owned.
+ *   - Handles are not thread-safe: one thread at a time per handle.
+ *   - escg_last_error() returns a thread-local message for the last failure.
+ *   - Work is enqueued on the handle's CUDA stream; calls that return data
+ *     to the host synchronise that stream first.
+ */
+#ifndef ESCG_H
+#define ESCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ESCG_OK = 0,
+    ESCG_EINVAL = -1,   /* bad argument (message in escg_last_error)      */
+    ESCG_ENOMEM = -2,   /* device or host allocation failed               */
+    ESCG_ECUDA = -3,    /* a CUDA runtime call failed                     */
+    ESCG_ESTATE = -4,   /* call not valid in the handle's current state   */
+    ESCG_ETIMEOUT = -5  /* a bounded device-side wait gave up             */
+} escg_status;
+
+/* Rates by role: interaction (the paper's mu), reproduction (sigma),
+ * exchange (epsilon).  Each >= 0, sum > 0.  Only their ratios matter. */
+typedef struct {
+    double interact;
+    double reproduce;
+    double exchange;
+} escg_rates;
+
+typedef struct {
+    double p_empty;              /* initial empty-site probability, [0,1]      */
+    uint32_t log_every;          /* counts kept every k MCS (0: default 10)    */
+    int32_t stop_at_extinction;  /* stop at the first logged MCS with <= 1
+                                    non-empty species alive (stasis())        */
+    uint32_t schedule_version;   /* 0 or 1 (only version 1 exists)            */
+    int32_t persistent;          /* 1: one persistent dataflow launch per run
+                                    (default); 0: one launch per coarse phase */
+    void* cuda_stream;           /* cudaStream_t to enqueue on, or NULL for a
+                                    stream owned by the handle                */
+    void* device_lattice;        /* optional caller-owned device buffer of
+                                    escg_lattice_bytes(L) bytes (e.g. a torch
+                                    tensor); NULL: the library allocates      */
+} escg_options;
+
+typedef struct escg escg_t;
+
+/* Fills *opt with defaults: p_empty 0, log_every 10, no stop, version 1,
+ * persistent, library-owned stream and memory. */
+void escg_default_options(escg_options* opt);
+
+/* Bytes of device memory a lattice of side L occupies: L rows of pitch
+ * escg_lattice_pitch(L) (L rounded up to 16) bytes. */
+size_t escg_lattice_bytes(int32_t L);
+int32_t escg_lattice_pitch(int32_t L);
+
+/* Creates a lattice of side L (8 <= L <= 16384) with S species
+ * (2 <= S <= 15), dominance digraph (S*S row-major bytes in {0,1}, zero
+ * diagonal), rates, and seed, and initialises it on the device: site i is
+ * empty with probability p_empty, else a uniform species (schedule v1
+ * initialisation).  Returns NULL on error (see escg_last_error). */
+escg_t* escg_create(int32_t L, int32_t S, const uint8_t* digraph, const escg_rates* rates,
+                    uint64_t seed);
+escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_rates* rates,
+                       uint64_t seed, const escg_options* opt);
+
+/* Enqueues n_mcs Monte Carlo steps (N elementary steps each).  Counts are
+ * recorded after every MCS whose absolute number is a multiple of
+ * log_every.  With stop_at_extinction the run ends at the first such MCS at
+ * which at most one non-empty species is alive.  Asynchronous. */
+int escg_run(escg_t* h, uint64_t n_mcs);
+
+/* Waits for all enqueued work; surfaces device-side errors. */
+int escg_sync(escg_t* h);
+
+/* Current species counts out[0..S] (out[0] = empty sites) and the absolute
+ * MCS number of the lattice.  Synchronises. */
+int escg_counts(escg_t* h, uint64_t* out, uint64_t* mcs_out);
+
+/* Logged counts: copies up to cap entries of (S+1) uint64 each, oldest
+ * first, for the MCS numbers written to mcs_out (may be NULL); *n_out gets
+ * the number of entries copied.  Synchronises. */
+int escg_counts_log(escg_t* h, uint64_t* out, uint64_t* mcs_out, int64_t cap, int64_t* n_out);
+
+/* Copies the lattice (L*L bytes, row-major, no padding) to host memory.
+ * Synchronises. */
+int escg_snapshot(escg_t* h, uint8_t* host_out);
+
+/* Replaces the lattice with host_lattice (L*L bytes, values 0..S) at
+ * absolute MCS number mcs; running on from there is bit-exact with a run
+ * that reached this state itself.  Clears the counts log. */
+int escg_restore(escg_t* h, const uint8_t* host_lattice, uint64_t mcs);
+
+/* End-to-end host call: restore(host_in, mcs), run n_mcs, snapshot into
+ * host_out and counts into counts_out (S+1, may be NULL).  host_in and
+ * host_out may alias.  Synchronises. */
+int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_mcs,
+                   uint8_t* host_out, uint64_t* counts_out);
+
+/* Device address of the lattice (row pitch escg_lattice_pitch(L)) and the
+ * handle's stream, for zero-copy interop (e.g. a torch tensor view). */
+void* escg_device_lattice(escg_t* h);
+void* escg_stream(escg_t* h);
+uint64_t escg_current_mcs(escg_t* h);
+
+/* Number of kernel launches this handle has enqueued so far. */
+uint64_t escg_launch_count(escg_t* h);
+
+void escg_destroy(escg_t* h);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* escg_last_error(void);
+
+/* epsilon = 2 M N (Section 3.1, rate initialisation). */
+double escg_exchange_from_mobility(double M, int64_t N);
+
+/* Fills D (S*S) with the circulant dominance digraph C(S,K):
+ * D[i*S+j] = 1 iff (j - i + S) mod S is one of K[0..nK-1]. */
+int escg_circulant(int32_t S, const int32_t* K, int32_t nK, uint8_t* D);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESCG_H */

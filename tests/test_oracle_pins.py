@@ -1,0 +1,193 @@
+"""Pins of the CPU oracle's building blocks against facts fixed outside it.
+
+* Philox4x32-10 against an independent implementation (Triton's, run on the
+  CPU through its interpreter);
+* the elementary-step rule (Alg. 3, Alg. 2) against the paper's worked
+  transitions (tests/golden/rule_cases.txt);
+* the circulant dominance definition against the RPSLS figure's edge list
+  (tests/golden/rpsls_edges.txt);
+* epsilon = 2MN and the integer thresholds against closed forms.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+_TRITON_SNIPPET = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def k(out_ptr, c0_ptr, c1_ptr, c2_ptr, c3_ptr, seed, n: tl.constexpr):
+    i = tl.arange(0, n)
+    c0 = tl.load(c0_ptr + i); c1 = tl.load(c1_ptr + i)
+    c2 = tl.load(c2_ptr + i); c3 = tl.load(c3_ptr + i)
+    a, b, c, d = tl.random.philox(seed, c0, c1, c2, c3, 10)
+    tl.store(out_ptr + 4 * i + 0, a); tl.store(out_ptr + 4 * i + 1, b)
+    tl.store(out_ptr + 4 * i + 2, c); tl.store(out_ptr + 4 * i + 3, d)
+
+req = json.loads(sys.stdin.read())
+ctr = np.array(req["ctr"], dtype=np.uint64).astype(np.uint32)
+n = ctr.shape[0]
+res = {}
+for seed in req["seeds"]:
+    out = torch.zeros(4 * n, dtype=torch.uint32)
+    cs = [torch.from_numpy(ctr[:, j].copy()) for j in range(4)]
+    k[(1,)](out, *cs, seed, n)
+    res[str(seed)] = out.numpy().astype(np.uint64).reshape(n, 4).tolist()
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_independent_implementation():
+    """Our Philox4x32-10 equals Triton's (a separately written library
+    implementation of the same SC'11 generator) on random counters/keys,
+    including counters with all four words nonzero and 64-bit keys."""
+    pytest.importorskip("triton")
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(20250816)
+    n = 64
+    ctr = rng.integers(0, 2**32, (n, 4), dtype=np.uint64)
+    ctr[0] = [0, 0, 0, 0]
+    ctr[1] = [0xFFFFFFFF] * 4
+    seeds = [0, 1, 0x5EED0000, 0x123456789ABCDEF, 2**64 - 1]
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    proc = subprocess.run([sys.executable, "-c", _TRITON_SNIPPET], input=json.dumps(
+        {"ctr": ctr.tolist(), "seeds": seeds}), capture_output=True, text=True, env=env, timeout=600)
+    if proc.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + proc.stderr.strip().splitlines()[-1])
+    ref = json.loads(proc.stdout)
+    for seed in seeds:
+        key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
+        mine = O.philox(ctr.astype(np.uint32), key)
+        assert np.array_equal(mine.astype(np.uint64), np.array(ref[str(seed)], dtype=np.uint64)), seed
+
+
+def test_philox_avalanche_and_uniformity():
+    """Sanity of the generator's output (not a pin by itself): flipping one
+    counter bit changes ~half the output bits; output bytes are uniform."""
+    n = 4096
+    ctr = np.zeros((n, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(n)
+    out = O.philox(ctr, [7, 9])
+    flipped = ctr.copy()
+    flipped[:, 2] ^= 1
+    out2 = O.philox(flipped, [7, 9])
+    diff = np.unpackbits((out ^ out2).view(np.uint8)).mean()
+    assert 0.48 < diff < 0.52
+    hist = np.bincount(out.view(np.uint8).ravel(), minlength=256)
+    from scipy.stats import chisquare
+    assert chisquare(hist).pvalue > 1e-4
+
+
+def _rule_cases():
+    cases = []
+    with open(os.path.join(GOLDEN, "rule_cases.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            lhs, rhs = line.split("->")
+            S, K, act, a, b = lhs.split()
+            a2, b2 = rhs.split()
+            cases.append((int(S), [int(k) for k in K.split(",")], {"X": O.EXCHANGE, "I": O.INTERACT,
+                                                                   "P": O.REPRODUCE}[act],
+                          int(a), int(b), int(a2), int(b2)))
+    return cases
+
+
+@pytest.mark.parametrize("case", _rule_cases())
+def test_rule_worked_transitions(case):
+    S, K, act, a, b, a2, b2 = case
+    D = O.circulant(S, K)
+    assert O.rule(act, a, b, D) == (a2, b2)
+
+
+def test_rule_cases_file_covers_the_paper_examples():
+    assert len(_rule_cases()) >= 20
+
+
+def test_circulant_rps_and_rpsls_match_figure():
+    # RPS = C(3,{1}): each species dominates exactly the next one.
+    D3 = O.circulant(3, [1])
+    assert D3.tolist() == [[0, 1, 0], [0, 0, 1], [1, 0, 0]]
+    names = ["Rock", "Scissors", "Lizard", "Paper", "Spock"]
+    edges = set()
+    with open(os.path.join(GOLDEN, "rpsls_edges.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                w, l = line.split()
+                edges.add((names.index(w), names.index(l)))
+    D5 = O.circulant(5, [1, 2])
+    got = {(i, j) for i in range(5) for j in range(5) if D5[i, j]}
+    assert got == edges
+    # every species beats exactly two others and loses to two
+    assert (D5.sum(1) == 2).all() and (D5.sum(0) == 2).all()
+
+
+def test_dominates_alg2():
+    D = O.circulant(3, [1])
+    assert not O.dominates(0, 1, D) and not O.dominates(1, 0, D) and not O.dominates(0, 0, D)
+    assert O.dominates(1, 2, D) and O.dominates(2, 3, D) and O.dominates(3, 1, D)
+    assert not O.dominates(2, 1, D) and not O.dominates(1, 1, D)
+
+
+def test_rule_exhaustive_properties():
+    """For every (a, b, action) of RPS and RPSLS: exchange is a swap, the
+    other actions never create a species that was not in the pair, empties
+    only ever appear through interaction, and at most one site changes."""
+    for S, K in [(3, [1]), (5, [1, 2])]:
+        D = O.circulant(S, K)
+        for a in range(S + 1):
+            for b in range(S + 1):
+                assert O.rule(O.EXCHANGE, a, b, D) == (b, a)
+                ai, bi = O.rule(O.INTERACT, a, b, D)
+                assert (ai, bi) in {(a, b), (0, b), (a, 0)}
+                if a and b and a != b:
+                    # a tournament: exactly one of the two dies
+                    assert (ai, bi) == ((a, 0) if D[a - 1, b - 1] else (0, b))
+                ar, br = O.rule(O.REPRODUCE, a, b, D)
+                if a and not b:
+                    assert (ar, br) == (a, a)
+                elif b and not a:
+                    assert (ar, br) == (b, b)
+                else:
+                    assert (ar, br) == (a, b)
+
+
+def test_exchange_from_mobility_closed_form():
+    # epsilon = 2 M N (Section 3.1, rate initialisation)
+    assert O.exchange_from_mobility(1e-4, 800 * 800) == pytest.approx(128.0, rel=1e-15)
+    for M, X in [(1e-5, 204.8), (1e-4, 2048.0), (1e-3, 20480.0)]:
+        assert O.exchange_from_mobility(M, 3200 * 3200) == pytest.approx(X, rel=1e-14)
+
+
+def test_thresholds_closed_forms():
+    two32 = 1 << 32
+    assert O.thresholds(1, 0, 0) == (0, two32)            # competition only
+    assert O.thresholds(0, 1, 0) == (0, 0)                # reproduction only
+    assert O.thresholds(0, 0, 1) == (two32, two32)        # exchange only
+    assert O.thresholds(1, 1, 2) == (two32 // 2, 3 * two32 // 4)
+    assert O.thresholds(1, 1, 0) == (0, two32 // 2)
+    tx, txi = O.thresholds(1, 1, 128.0)
+    assert abs(tx / two32 - 128 / 130) < 2**-32 and abs(txi / two32 - 129 / 130) < 2**-32
+    with pytest.raises(ValueError):
+        O.thresholds(0, 0, 0)
+    with pytest.raises(ValueError):
+        O.thresholds(-1, 1, 1)
+
+
+def test_counts_histogram():
+    lat = np.array([[0, 1, 2], [3, 3, 3], [0, 0, 1]], dtype=np.uint8)
+    assert O.counts(lat, 3).tolist() == [3, 2, 1, 3]
+    with pytest.raises(ValueError):
+        O.counts(np.array([[4]], dtype=np.uint8), 3)
