@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Benchmark of the ESCG Monte Carlo step on GB300.
+
+Metric: site-updates/s (one update = one elementary-step attempt, no-ops
+included; N = L^2 per MCS) of a single L = 3200 RPS lattice with empty sites
+(S = 3, C(3,{1}), uniform initial states, interaction = reproduction = 1,
+exchange = 2 M N with M = 1e-4), counts logged every 10 MCS.  One step =
+10 MCS = one log interval, i.e. one pass of every row of the hot path
+(coloured-phase lattice update, counts, log).
+
+  value     device time (CUDA events on the library's stream) of K steps,
+            L2 flushed (256 MiB write) before every timed step, lattice
+            resident in HBM;
+  e2e       the same metric through the C ABI with host buffers
+            (escg_step_host: pinned host lattice in, K x 10 MCS, lattice and
+            counts out, copies inside the timed region);
+  roofline  the dominant kernel (persistent_kernel): algorithmic integer
+            instructions per launch / its event-timed launch duration
+            against the GPU's integer-issue peak;
+  cpu_baseline  the CPU replay oracle (single thread) on a bounded sample.
+
+`--impl reference` times the CPU oracle itself (the reference arm of this
+tier) on the same metric and workload.  Multi-GPU (torchrun): replicas only,
+one independent lattice per rank (weak scaling), max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-updates/s at L=3200 vs roofline; ensemble runs/s and p50/p99 latency"
+UNIT = "site-updates/s"
+
+# Algorithmic integer instructions of one elementary step (schedule v1,
+# 2x2 sub-blocks): Philox4x32-10 = 10 rounds x (2 wide multiplies + 2
+# three-input XORs) per 4 attempts = 10; split of the 32-bit word into
+# cell/direction and action draw (1 wide multiply) = 1; cell and neighbour
+# tile offsets = 6; two threshold compares and the action select = 3;
+# transition-table index = 2; unpacking the new pair = 2; the four
+# shared-memory accesses (load a, load b, store a', store b') and the
+# table lookup are memory instructions and not counted.
+ALG_INT_INSTR_PER_ATTEMPT = 24
+
+# DRAM traffic of persistent_kernel from one ncu capture (bytes per launch of
+# a 10-MCS chunk at L = 3200), valid only for the kernel sources it was taken
+# from (hash of csrc/*); None when not measured for the current sources.
+NCU_TRAFFIC = {"sources_sha1": None, "bytes_per_launch": None, "profile": None}
+
+
+def _sources_sha1() -> str:
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2508_16639_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()
+
+
+def _parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mobility", type=float, default=1e-4)
+    ap.add_argument("--mcs-per-step", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--persistent", type=int, default=1)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _workload(M: float):
+    from paper_2508_16639_gb300 import workloads as W
+    if M in W.CFG3:
+        return W.CFG3[M]
+    import dataclasses
+    return dataclasses.replace(W.CFG3[1e-4], name=f"rps-L3200-M{M:g}", mobility=M)
+
+
+def _cpu_oracle_rate(w, seconds: float):
+    """Replay oracle (single-threaded C) on the seeded initial lattice: whole
+    MCS until `seconds` have passed; returns (site-updates/s, MCS done)."""
+    import oracle as O
+    X = O.exchange_from_mobility(w.mobility, w.L * w.L)
+    D = O.circulant(w.S, w.K)
+    lat = O.init(w.L, w.S, w.p_empty, w.seed)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        lat, att = O.replay_run(lat, D, w.interact, w.reproduce, X, w.seed, 1, mcs_begin=done)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return done * w.L * w.L / el, done, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    w = _workload(args.mobility)
+    X = O.exchange_from_mobility(w.mobility, w.L * w.L)
+    D = O.circulant(w.S, w.K)
+    lat = O.init(w.L, w.S, w.p_empty, w.seed)
+    m = 0
+    for _ in range(args.warmup):
+        lat, _ = O.replay_run(lat, D, w.interact, w.reproduce, X, w.seed, 1, mcs_begin=m)
+        m += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lat, _ = O.replay_run(lat, D, w.interact, w.reproduce, X, w.seed, 1, mcs_begin=m)
+        m += 1
+    el = time.perf_counter() - t0
+    value = args.steps * w.L * w.L / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": _config(w, 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"schedule-v1 replay oracle, 1 MCS of the L={w.L} lattice per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(w, mcs_per_step):
+    return {"workload": w.name, "L": w.L, "S": w.S, "digraph": f"C({w.S},{set(w.K)})",
+            "mobility": w.mobility, "p_empty": w.p_empty, "interact": w.interact,
+            "reproduce": w.reproduce, "mcs_per_step": mcs_per_step, "log_every": w.log_every,
+            "l2": "flushed before every timed step (256 MiB write); lattice 10.24 MB",
+            "parallelism": "replicas (one independent lattice per GPU)"}
+
+
+def main():
+    args = _parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2508_16639_gb300 as E
+
+    w = _workload(args.mobility)
+    N = w.L * w.L
+    X = E.exchange_from_mobility(w.mobility, N)
+    stream = torch.cuda.Stream()
+    g = E.Lattice(w.L, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X), w.seed + rank,
+                  p_empty=w.p_empty, log_every=w.log_every, stream=stream, time_kernels=True,
+                  persistent=bool(args.persistent))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K, Wm, mps = args.steps, args.warmup, args.mcs_per_step
+
+    for _ in range(Wm):
+        g.run(mps)
+    g.sync()
+    g.kernel_time(reset=True)
+    launches0 = g.launches
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        g.run(mps)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    g.sync()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    kernel_ms, kernel_n = g.kernel_time()
+    gpu_launches = g.launches - launches0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    attempts = K * mps * N * world
+    value = attempts / (ms * 1e-3)
+
+    # roofline of the dominant kernel
+    ops_s, ops_sm_clk = E.int_throughput()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    lanes = 64 if ops_sm_clk < 96 else 128
+    sm_max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * lanes * sm_max_mhz * 1e6  # integer instructions/s
+    per_launch_attempts = mps * N  # one persistent launch = one 10-MCS chunk
+    avg_launch_s = (kernel_ms * 1e-3) / max(1, kernel_n)
+    achieved = per_launch_attempts * ALG_INT_INSTR_PER_ATTEMPT / avg_launch_s
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sources_sha1"] == _sources_sha1() else None
+    roofline = {"bound": "alu", "kernel": "persistent_kernel" if args.persistent else "phase_kernel",
+                "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tinstr/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "alg_int_instr_per_attempt": ALG_INT_INSTR_PER_ATTEMPT,
+                "attempts_per_launch": per_launch_attempts,
+                "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": kernel_n,
+                "peak_derivation": f"{sms} SMs x {lanes} int32 lanes x {sm_max_mhz:.0f} MHz",
+                "probe_int_instr_per_s": ops_s, "probe_int_instr_per_sm_clk": ops_sm_clk,
+                "l2_lattice_gbs": 2.0 * per_launch_attempts / avg_launch_s / 1e9}
+
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(g.snapshot()).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        a, b = host_in.numpy(), host_out.numpy()
+        m0 = g.mcs
+        g.step_host(a, m0, mps, out=b)  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K):
+            g.step_host(a, m0, mps, out=b)
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": K * mps * N * world / el, "unit": UNIT, "h2d_bytes_per_step": N,
+               "d2h_bytes_per_step": N + 8 * (w.S + 1), "ms_per_step": 1e3 * el / K,
+               "api": "escg_step_host (restore + run + snapshot + counts), pinned host buffers"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, nmcs, el = _cpu_oracle_rate(w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"schedule-v1 replay oracle, first {nmcs} MCS of the L={w.L} lattice "
+                         f"({el:.1f} s, single thread)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": _config(w, mps), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": gpu_launches, "clocks": clocks,
+                "context": {"paper_cuda_ms_L3200_site_updates_per_s": 2.45e8,
+                            "paper_hardware": "RTX A2000 (not a target)"}}
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

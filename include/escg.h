@@ -77,6 +77,9 @@ typedef struct {
     void* device_lattice;        /* optional caller-owned device buffer of
                                     escg_lattice_bytes(L) bytes (e.g. a torch
                                     tensor); NULL: the library allocates      */
+    int32_t time_kernels;        /* 1: bracket every lattice-update launch with
+                                    CUDA events on the handle's stream (read
+                                    back with escg_kernel_time)               */
 } escg_options;
 
 typedef struct escg escg_t;
@@ -141,6 +144,11 @@ uint64_t escg_current_mcs(escg_t* h);
 
 /* Number of kernel launches this handle has enqueued so far. */
 uint64_t escg_launch_count(escg_t* h);
+
+/* With time_kernels set: total device time (ms, CUDA events on the
+ * handle's stream) and number of lattice-update launches (persistent or
+ * phase kernels) since the last reset.  Synchronises. */
+int escg_kernel_time(escg_t* h, double* ms_total, uint64_t* n_launches, int reset);
 
 void escg_destroy(escg_t* h);
 

@@ -1,0 +1,40 @@
+/*
+ * escg_diag.h -- diagnostics of libescg that are not part of the model: a
+ * measurement of the GPU's integer-issue rate (the denominator of the
+ * Monte Carlo kernels' roofline; the paper has no counterpart) and a
+ * host-controlled stall used to test the bounded device-side waits of the
+ * persistent kernel without hanging or faulting the GPU.
+ */
+#ifndef ESCG_DIAG_H
+#define ESCG_DIAG_H
+
+#include <stdint.h>
+
+#include "escg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Runs a kernel of independent integer chains on every SM of the current
+ * device -- each step one 32x32+32->64-bit multiply-add and one
+ * three-input XOR, the two instruction kinds of a Philox round -- and
+ * reports the achieved rate in thread-level integer instructions per second
+ * (*ops_per_s) and per SM per SM clock cycle (*ops_per_sm_clk, may be NULL).
+ * Allocates and frees a small device buffer; synchronises. */
+int escg_diag_int_throughput(double* ops_per_s, double* ops_per_sm_clk);
+
+/* Test hook: the next persistent launches of h never publish the epoch of
+ * coarse block `block` (0 <= block < P*P), so its neighbours' waits run out
+ * after `spin_limit` polls; escg_sync then returns ESCG_ETIMEOUT and the
+ * handle refuses to run until escg_restore.  block < 0 clears the hook;
+ * spin_limit 0 restores the default limit. */
+int escg_debug_stall_block(escg_t* h, int32_t block, uint32_t spin_limit);
+
+/* Coarse blocks per axis (P) of the handle's schedule-v1 partition. */
+int32_t escg_coarse_blocks(escg_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESCG_DIAG_H */

@@ -1,0 +1,189 @@
+"""GB300-native Monte Carlo step of the Evolutionary Spatial Cyclic Game
+(arXiv 2508.16639): Python binding of libescg.
+
+The binding only marshals arguments into the C ABI (include/escg.h); every
+step of the lattice update runs in the library's CUDA kernels.  PyTorch, when
+used, supplies device memory (a uint8 tensor passed as the lattice buffer)
+and the CUDA stream.  There is no CPU fallback: a missing library or device
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import EscgError, Options, Rates, check, load
+
+__all__ = ["Lattice", "circulant", "exchange_from_mobility", "lattice_pitch", "lattice_bytes",
+           "int_throughput", "EscgError", "load"]
+
+
+def _u8(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+def circulant(S: int, K) -> np.ndarray:
+    """Dominance digraph of the circulant graph C(S, K) (S x S uint8)."""
+    K = np.ascontiguousarray(np.asarray(list(K), dtype=np.int32))
+    D = np.zeros((S, S), dtype=np.uint8)
+    check(load().escg_circulant(S, K.ctypes.data_as(C.POINTER(C.c_int32)), len(K), _u8(D)))
+    return D
+
+
+def exchange_from_mobility(M: float, N: int) -> float:
+    """epsilon = 2 M N."""
+    return float(load().escg_exchange_from_mobility(M, N))
+
+
+def int_throughput():
+    """Measured integer-instruction issue rate of the current GPU:
+    (instructions/s, instructions per SM per clock)."""
+    a, b = C.c_double(), C.c_double()
+    check(load().escg_diag_int_throughput(C.byref(a), C.byref(b)))
+    return float(a.value), float(b.value)
+
+
+def lattice_pitch(L: int) -> int:
+    return int(load().escg_lattice_pitch(L))
+
+
+def lattice_bytes(L: int) -> int:
+    return int(load().escg_lattice_bytes(L))
+
+
+class Lattice:
+    """One L x L lattice resident on the GPU (a handle of the C ABI).
+
+    rates: (interact, reproduce, exchange).  device_buffer: optional torch
+    uint8 CUDA tensor of at least lattice_bytes(L) bytes used as the lattice
+    storage; stream: optional torch.cuda.Stream (or raw cudaStream_t int)."""
+
+    def __init__(self, L: int, S: int, digraph, rates, seed: int, p_empty: float = 0.0,
+                 log_every: int = 10, stop_at_extinction: bool = False, persistent: bool = True,
+                 stream=None, device_buffer=None, time_kernels: bool = False):
+        lib = load()
+        self.L, self.S = int(L), int(S)
+        D = np.ascontiguousarray(np.asarray(digraph, dtype=np.uint8).reshape(S, S))
+        r = Rates(*[float(x) for x in rates])
+        opt = Options()
+        lib.escg_default_options(C.byref(opt))
+        opt.p_empty = float(p_empty)
+        opt.log_every = int(log_every)
+        opt.stop_at_extinction = int(bool(stop_at_extinction))
+        opt.persistent = int(bool(persistent))
+        opt.time_kernels = int(bool(time_kernels))
+        if stream is not None:
+            opt.cuda_stream = int(getattr(stream, "cuda_stream", stream))
+        self._buffer = device_buffer  # keep the torch tensor alive
+        if device_buffer is not None:
+            if device_buffer.numel() * device_buffer.element_size() < lattice_bytes(L):
+                raise ValueError("device_buffer is smaller than lattice_bytes(L)")
+            opt.device_lattice = int(device_buffer.data_ptr())
+        h = lib.escg_create_ex(self.L, self.S, _u8(D), C.byref(r), C.c_uint64(seed & (2**64 - 1)),
+                               C.byref(opt))
+        if not h:
+            raise EscgError(-1, lib.escg_last_error().decode(errors="replace"))
+        self._h = C.c_void_p(h)
+        self.pitch = lattice_pitch(L)
+
+    # -- life cycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().escg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- operations -----------------------------------------------------------
+    def run(self, n_mcs: int):
+        check(load().escg_run(self._h, int(n_mcs)))
+        return self
+
+    def sync(self):
+        check(load().escg_sync(self._h))
+
+    def counts(self):
+        out = np.zeros(self.S + 1, dtype=np.uint64)
+        mcs = C.c_uint64()
+        check(load().escg_counts(self._h, out.ctypes.data_as(C.POINTER(C.c_uint64)), C.byref(mcs)))
+        return out, int(mcs.value)
+
+    def counts_log(self, cap: int = 4096):
+        out = np.zeros((cap, self.S + 1), dtype=np.uint64)
+        ms = np.zeros(cap, dtype=np.uint64)
+        n = C.c_int64()
+        check(load().escg_counts_log(self._h, out.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                     ms.ctypes.data_as(C.POINTER(C.c_uint64)), cap, C.byref(n)))
+        return ms[:n.value].astype(np.int64), out[:n.value]
+
+    def snapshot(self) -> np.ndarray:
+        out = np.empty((self.L, self.L), dtype=np.uint8)
+        check(load().escg_snapshot(self._h, _u8(out)))
+        return out
+
+    def restore(self, lattice: np.ndarray, mcs: int):
+        lat = np.ascontiguousarray(lattice, dtype=np.uint8)
+        if lat.shape != (self.L, self.L):
+            raise ValueError("lattice shape mismatch")
+        check(load().escg_restore(self._h, _u8(lat), int(mcs)))
+
+    def step_host(self, lattice_in: np.ndarray, mcs: int, n_mcs: int, out: np.ndarray | None = None):
+        """End-to-end host call: lattice in, n_mcs on the GPU, lattice and
+        counts out (host buffers, copies included)."""
+        lat = np.ascontiguousarray(lattice_in, dtype=np.uint8)
+        out = np.empty_like(lat) if out is None else out
+        counts = np.zeros(self.S + 1, dtype=np.uint64)
+        check(load().escg_step_host(self._h, _u8(lat), int(mcs), int(n_mcs), _u8(out),
+                                    counts.ctypes.data_as(C.POINTER(C.c_uint64))))
+        return out, counts
+
+    def kernel_time(self, reset: bool = False):
+        """(total ms, launches) of the lattice-update kernels, measured with
+        CUDA events on the handle's stream (needs time_kernels=True)."""
+        ms, n = C.c_double(), C.c_uint64()
+        check(load().escg_kernel_time(self._h, C.byref(ms), C.byref(n), int(bool(reset))))
+        return float(ms.value), int(n.value)
+
+    def debug_stall_block(self, block: int, spin_limit: int = 0):
+        """Test hook: never publish the epoch of one coarse block so that the
+        persistent kernel's bounded waits run out (block < 0 clears it)."""
+        check(load().escg_debug_stall_block(self._h, int(block), int(spin_limit)))
+
+    @property
+    def coarse_blocks(self) -> int:
+        return int(load().escg_coarse_blocks(self._h))
+
+    @property
+    def mcs(self) -> int:
+        return int(load().escg_current_mcs(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(load().escg_launch_count(self._h))
+
+    @property
+    def device_ptr(self) -> int:
+        return int(load().escg_device_lattice(self._h))
+
+    @property
+    def stream_ptr(self) -> int:
+        return int(load().escg_stream(self._h) or 0)
+
+    def as_tensor(self):
+        """torch view of the device lattice (L x pitch uint8), when the
+        lattice lives in a torch-allocated buffer."""
+        if self._buffer is None:
+            raise RuntimeError("lattice storage is library-owned; pass device_buffer= to get a view")
+        return self._buffer.view(-1)[: self.L * self.pitch].view(self.L, self.pitch)

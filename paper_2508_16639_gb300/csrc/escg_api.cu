@@ -1,0 +1,658 @@
+// escg_api.cu -- the C ABI of libescg (include/escg.h): handle life cycle,
+// host-side set-up (partition tables, integer thresholds, transition table;
+// SURVEY rows A1/A2) and run orchestration on the handle's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "escg.h"
+#include "escg_diag.h"
+#include "escg_internal.h"
+
+using namespace escg_impl;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+#define CUDA_TRY(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      set_err("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return ESCG_ECUDA;                                                                \
+    }                                                                                   \
+  } while (0)
+
+constexpr uint32_t kDefaultSpinLimit = 2000000;  // polls of ~1 us: a few seconds
+
+std::mutex g_init_mu;
+bool g_perm_uploaded[64] = {};
+
+int ensure_device_tables(int dev) {
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (dev < 0 || dev >= 64) return ESCG_EINVAL;
+  if (!g_perm_uploaded[dev]) {
+    upload_perm_table();
+    CUDA_TRY(cudaGetLastError());
+    g_perm_uploaded[dev] = true;
+  }
+  return ESCG_OK;
+}
+
+// Schedule v1 partition of one axis (both axes are identical).
+struct Partition {
+  int P = 0, GQ = 0;
+  std::vector<int32_t> cs, fs, fc;
+};
+
+void split_even(int n, int parts, int32_t* start) {
+  const int q = n / parts, r = n % parts;
+  start[0] = 0;
+  for (int k = 0; k < parts; ++k) start[k + 1] = start[k] + q + (k < r ? 1 : 0);
+}
+
+Partition make_partition(int L) {
+  Partition p;
+  const int h = (L + 64) / 128;
+  p.P = 2 * (h < 1 ? 1 : h);
+  p.cs.resize(p.P + 1);
+  split_even(L, p.P, p.cs.data());
+  p.fc.resize(p.P + 1);
+  for (int k = 0; k < p.P; ++k) {
+    const int w = p.cs[k + 1] - p.cs[k];
+    const int Q = 2 * (w / 4);
+    std::vector<int32_t> loc(Q + 1);
+    split_even(w, Q, loc.data());
+    p.fc[k] = (int)p.fs.size();
+    for (int q = 0; q < Q; ++q) p.fs.push_back(p.cs[k] + loc[q]);
+  }
+  p.GQ = (int)p.fs.size();
+  p.fc[p.P] = p.GQ;
+  p.fs.push_back(L);
+  return p;
+}
+
+bool partition_fits(const Partition& p) {
+  for (int k = 0; k < p.P; ++k) {
+    if (p.cs[k + 1] - p.cs[k] > kMaxBlock) return false;
+    if (p.fc[k + 1] - p.fc[k] > kMaxFine) return false;
+  }
+  return true;
+}
+
+bool thresholds(const escg_rates* r, uint64_t* tx, uint64_t* txi) {
+  const double I = r->interact, Pr = r->reproduce, X = r->exchange;
+  if (!(I >= 0.0) || !(Pr >= 0.0) || !(X >= 0.0)) return false;
+  const double R = (X + I) + Pr;
+  if (!(R > 0.0) || std::isinf(R)) return false;
+  *tx = (uint64_t)std::floor(std::ldexp(X / R, 32) + 0.5);
+  *txi = (uint64_t)std::floor(std::ldexp((X + I) / R, 32) + 0.5);
+  return true;
+}
+
+// Transition table of Alg. 3 for every (action, selected a, neighbour b):
+// exchange swaps distinct values; interaction empties the dominated one
+// (selected site tested first; empty sites never dominate, Alg. 2);
+// reproduction fills an empty site of the pair with the other's species.
+void build_trans(int S, const uint8_t* D, std::vector<uint8_t>& t) {
+  const int s1 = S + 1;
+  t.assign(3 * s1 * s1, 0);
+  auto dom = [&](int a, int b) { return a != 0 && b != 0 && D[(a - 1) * S + (b - 1)] == 1; };
+  for (int act = 0; act < 3; ++act)
+    for (int a = 0; a < s1; ++a)
+      for (int b = 0; b < s1; ++b) {
+        int na = a, nb = b;
+        if (a != b) {
+          if (act == 0) {
+            na = b;
+            nb = a;
+          } else if (act == 1) {
+            if (dom(a, b))
+              nb = 0;
+            else if (dom(b, a))
+              na = 0;
+          } else {
+            if (b == 0)
+              nb = a;
+            else if (a == 0)
+              na = b;
+          }
+        }
+        t[(act * s1 + a) * s1 + b] = (uint8_t)(na | (nb << 4));
+      }
+}
+
+}  // namespace
+
+struct escg {
+  int device = 0;
+  int L = 0, S = 0, pitch = 0;
+  uint64_t seed = 0;
+  escg_options opt{};
+  Partition part;
+  LatticeDesc desc{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false, own_lattice = false;
+  uint8_t* lattice = nullptr;
+  int32_t* d_tables = nullptr;   // cs | fs | fc
+  uint8_t* d_trans = nullptr;
+  RunState* d_state = nullptr;
+  unsigned long long* d_log = nullptr;
+  uint32_t* d_log_mcs = nullptr;
+  uint32_t* d_done = nullptr;    // P*P epoch counters of the persistent kernel
+  uint64_t mcs_enq = 0;          // MCS number after all enqueued work
+  uint64_t launches = 0;
+  uint64_t T_empty = 0;
+  int grid = 0;
+  uint32_t spin_limit = kDefaultSpinLimit;
+  int stall_block = -1;
+  bool failed = false;
+  RunState* d_scratch = nullptr;  // accumulator for on-demand counts
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+  double kernel_ms = 0.0;
+  uint64_t kernel_launches = 0;
+};
+
+namespace {
+
+int enqueue_log(escg* h, uint32_t m_end, bool log) {
+  if (log) {
+    CUDA_TRY(launch_count(h->desc, h->d_state, h->stream));
+    h->launches++;
+  }
+  CUDA_TRY(launch_finalize(h->desc, h->d_state, h->d_log, h->d_log_mcs, m_end, log ? 1 : 0,
+                           h->opt.stop_at_extinction, h->stream));
+  h->launches++;
+  return ESCG_OK;
+}
+
+// Optional CUDA-event bracketing of the lattice-update launches.
+cudaError_t timing_begin(escg* h) {
+  if (!h->opt.time_kernels) return cudaSuccess;
+  if (h->ev_free.empty()) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return e;
+    h->ev_free.emplace_back(a, b);
+  }
+  h->ev_used.push_back(h->ev_free.back());
+  h->ev_free.pop_back();
+  return cudaEventRecord(h->ev_used.back().first, h->stream);
+}
+
+cudaError_t timing_end(escg* h) {
+  if (!h->opt.time_kernels) return cudaSuccess;
+  return cudaEventRecord(h->ev_used.back().second, h->stream);
+}
+
+int reset_state(escg* h, uint64_t mcs) {
+  RunState st{};
+  st.mcs = (uint32_t)mcs;
+  CUDA_TRY(cudaMemcpyAsync(h->d_state, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+  h->mcs_enq = mcs;
+  h->failed = false;
+  if (mcs % h->opt.log_every == 0) return enqueue_log(h, (uint32_t)mcs, true);
+  return ESCG_OK;
+}
+
+void free_handle(escg* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->own_lattice && h->lattice) cudaFree(h->lattice);
+  cudaFree(h->d_tables);
+  cudaFree(h->d_trans);
+  cudaFree(h->d_state);
+  cudaFree(h->d_log);
+  cudaFree(h->d_log_mcs);
+  cudaFree(h->d_done);
+  cudaFree(h->d_scratch);
+  for (auto& e : h->ev_used) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  for (auto& e : h->ev_free) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int check_inputs(int32_t L, int32_t S, const uint8_t* D, const escg_rates* rates) {
+  if (L < 8 || L > 16384) {
+    set_err("L=%d out of range [8, 16384]", L);
+    return ESCG_EINVAL;
+  }
+  if (S < 2 || S > 15) {
+    set_err("S=%d out of range [2, 15]", S);
+    return ESCG_EINVAL;
+  }
+  if (!D || !rates) {
+    set_err("digraph and rates must not be NULL");
+    return ESCG_EINVAL;
+  }
+  for (int i = 0; i < S; ++i)
+    for (int j = 0; j < S; ++j) {
+      if (D[i * S + j] > 1) {
+        set_err("digraph[%d][%d]=%d is not 0 or 1", i, j, D[i * S + j]);
+        return ESCG_EINVAL;
+      }
+      if (i == j && D[i * S + j]) {
+        set_err("digraph has a nonzero diagonal at %d", i);
+        return ESCG_EINVAL;
+      }
+    }
+  uint64_t tx, txi;
+  if (!thresholds(rates, &tx, &txi)) {
+    set_err("rates must be finite, >= 0 and not all zero");
+    return ESCG_EINVAL;
+  }
+  return ESCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void escg_default_options(escg_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof *opt);
+  opt->p_empty = 0.0;
+  opt->log_every = 10;
+  opt->stop_at_extinction = 0;
+  opt->schedule_version = 1;
+  opt->persistent = 1;
+}
+
+int32_t escg_lattice_pitch(int32_t L) { return L <= 0 ? 0 : ((L + 15) / 16) * 16; }
+
+size_t escg_lattice_bytes(int32_t L) { return L <= 0 ? 0 : (size_t)L * escg_lattice_pitch(L); }
+
+const char* escg_last_error(void) { return g_err; }
+
+double escg_exchange_from_mobility(double M, int64_t N) { return 2.0 * M * (double)N; }
+
+int escg_circulant(int32_t S, const int32_t* K, int32_t nK, uint8_t* D) {
+  if (S < 1 || nK < 0 || (nK > 0 && !K) || !D) {
+    set_err("bad circulant arguments");
+    return ESCG_EINVAL;
+  }
+  for (int i = 0; i < S; ++i)
+    for (int j = 0; j < S; ++j) {
+      const int off = ((j - i) % S + S) % S;
+      uint8_t v = 0;
+      for (int k = 0; k < nK; ++k) v |= (uint8_t)(off == K[k]);
+      D[i * S + j] = v;
+    }
+  return ESCG_OK;
+}
+
+escg_t* escg_create(int32_t L, int32_t S, const uint8_t* digraph, const escg_rates* rates, uint64_t seed) {
+  escg_options o;
+  escg_default_options(&o);
+  return escg_create_ex(L, S, digraph, rates, seed, &o);
+}
+
+escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_rates* rates,
+                       uint64_t seed, const escg_options* opt) {
+  g_err[0] = 0;
+  if (check_inputs(L, S, digraph, rates) != ESCG_OK) return nullptr;
+  escg_options o;
+  escg_default_options(&o);
+  if (opt) o = *opt;
+  if (o.log_every == 0) o.log_every = 10;
+  if (o.schedule_version != 0 && o.schedule_version != 1) {
+    set_err("schedule_version %u is not supported (only 1)", o.schedule_version);
+    return nullptr;
+  }
+  if (!(o.p_empty >= 0.0 && o.p_empty <= 1.0)) {
+    set_err("p_empty=%g outside [0, 1]", o.p_empty);
+    return nullptr;
+  }
+  escg* h = new (std::nothrow) escg;
+  if (!h) {
+    set_err("host allocation failed");
+    return nullptr;
+  }
+  h->L = L;
+  h->S = S;
+  h->seed = seed;
+  h->opt = o;
+  h->pitch = escg_lattice_pitch(L);
+  h->part = make_partition(L);
+  if (!partition_fits(h->part)) {
+    set_err("internal: partition of L=%d exceeds the kernel's block limits", L);
+    delete h;
+    return nullptr;
+  }
+  h->T_empty = (uint64_t)std::floor(std::ldexp(o.p_empty, 32) + 0.5);
+
+  auto fail = [&](int code) -> escg_t* {
+    (void)code;
+    free_handle(h);
+    return nullptr;
+  };
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+    set_err("no CUDA device available (libescg has no CPU fallback)");
+    return fail(ESCG_ECUDA);
+  }
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    set_err("cudaGetDevice failed");
+    return fail(ESCG_ECUDA);
+  }
+  if (ensure_device_tables(h->device) != ESCG_OK) return fail(ESCG_ECUDA);
+
+  cudaError_t e = cudaSuccess;
+  if (o.cuda_stream) {
+    h->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    h->own_stream = true;
+  }
+  const size_t nbytes = escg_lattice_bytes(L);
+  if (e == cudaSuccess) {
+    if (o.device_lattice) {
+      h->lattice = (uint8_t*)o.device_lattice;
+    } else {
+      e = cudaMalloc(&h->lattice, nbytes);
+      h->own_lattice = true;
+    }
+  }
+  const Partition& p = h->part;
+  const size_t ntab = p.cs.size() + p.fs.size() + p.fc.size();
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_tables, ntab * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_trans, 3 * kMaxStates * kMaxStates);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_state, sizeof(RunState));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_log, sizeof(unsigned long long) * kLogCap * kMaxStates);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_log_mcs, sizeof(uint32_t) * kLogCap);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_done, sizeof(uint32_t) * p.P * p.P);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, sizeof(RunState));
+  if (e != cudaSuccess) {
+    set_err("device allocation failed: %s", cudaGetErrorString(e));
+    return fail(ESCG_ENOMEM);
+  }
+  std::vector<int32_t> tab;
+  tab.insert(tab.end(), p.cs.begin(), p.cs.end());
+  tab.insert(tab.end(), p.fs.begin(), p.fs.end());
+  tab.insert(tab.end(), p.fc.begin(), p.fc.end());
+  std::vector<uint8_t> trans;
+  build_trans(S, digraph, trans);
+  uint64_t tx = 0, txi = 0;
+  thresholds(rates, &tx, &txi);
+  if (cudaMemcpyAsync(h->d_tables, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_trans, trans.data(), trans.size(), cudaMemcpyHostToDevice, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    set_err("upload of lattice tables failed");
+    return fail(ESCG_ECUDA);
+  }
+  LatticeDesc& d = h->desc;
+  d.lat = h->lattice;
+  d.L = L;
+  d.pitch = h->pitch;
+  d.P = p.P;
+  d.GQ = p.GQ;
+  d.cs = h->d_tables;
+  d.fs = h->d_tables + p.cs.size();
+  d.fc = h->d_tables + p.cs.size() + p.fs.size();
+  d.trans = h->d_trans;
+  d.key0 = (uint32_t)seed;
+  d.key1 = (uint32_t)(seed >> 32);
+  d.tx = (uint32_t)tx;
+  d.tx_all = tx >> 32 ? 1u : 0u;
+  d.txi = (uint32_t)txi;
+  d.txi_all = txi >> 32 ? 1u : 0u;
+  d.S = S;
+  bool uni = true;
+  for (int k = 0; k < p.P; ++k) uni = uni && (p.cs[k + 1] - p.cs[k] == 64);
+  for (int k = 0; k < p.GQ; ++k) uni = uni && (p.fs[k + 1] - p.fs[k] == 2);
+  d.uniform64 = (uni && h->pitch % 16 == 0) ? 1 : 0;
+  h->grid = persistent_grid(h->device);
+
+  if (launch_init(d, h->T_empty, h->stream) != cudaSuccess) {
+    set_err("init kernel launch failed");
+    return fail(ESCG_ECUDA);
+  }
+  h->launches++;
+  if (reset_state(h, 0) != ESCG_OK) return fail(ESCG_ECUDA);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    set_err("initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(ESCG_ECUDA);
+  }
+  return h;
+}
+
+int escg_run(escg_t* h, uint64_t n_mcs) {
+  if (!h) {
+    set_err("NULL handle");
+    return ESCG_EINVAL;
+  }
+  if (h->failed) {
+    set_err("handle is in an error state; restore a lattice first");
+    return ESCG_ESTATE;
+  }
+  const uint64_t target = h->mcs_enq + n_mcs;
+  if (target > 0xFFFFFFFFull) {
+    set_err("MCS number would exceed 2^32-1");
+    return ESCG_EINVAL;
+  }
+  const uint32_t k = h->opt.log_every;
+  while (h->mcs_enq < target) {
+    const uint64_t next_log = (h->mcs_enq / k + 1) * k;
+    uint64_t end = next_log < target ? next_log : target;
+    // the persistent kernel numbers work items with 32-bit tickets
+    const uint64_t per_mcs = (uint64_t)h->part.P * h->part.P;
+    const uint64_t max_chunk = ((1ull << 31) - (uint64_t)h->grid) / per_mcs;
+    if (end - h->mcs_enq > max_chunk) end = h->mcs_enq + max_chunk;
+    const uint32_t m0 = (uint32_t)h->mcs_enq, n = (uint32_t)(end - h->mcs_enq);
+    if (h->opt.persistent) {
+      CUDA_TRY(cudaMemsetAsync(h->d_done, 0, sizeof(uint32_t) * h->part.P * h->part.P, h->stream));
+      CUDA_TRY(cudaMemsetAsync(&h->d_state->ticket, 0, sizeof(uint32_t), h->stream));
+      const uint64_t items = (uint64_t)n * h->part.P * h->part.P;
+      const int grid = (int)(items < (uint64_t)h->grid ? items : (uint64_t)h->grid);
+      CUDA_TRY(timing_begin(h));
+      CUDA_TRY(launch_persistent(h->desc, h->d_state, h->d_done, m0, n, grid, h->spin_limit,
+                                 h->stall_block, h->stream));
+      CUDA_TRY(timing_end(h));
+      h->launches++;
+    } else {
+      for (uint32_t m = m0; m < m0 + n; ++m)
+        for (int slot = 0; slot < 4; ++slot) {
+          CUDA_TRY(timing_begin(h));
+          CUDA_TRY(launch_phase(h->desc, h->d_state, m, slot, h->stream));
+          CUDA_TRY(timing_end(h));
+          h->launches++;
+        }
+    }
+    h->mcs_enq = end;
+    const int rc = enqueue_log(h, (uint32_t)end, end % k == 0);
+    if (rc != ESCG_OK) return rc;
+  }
+  return ESCG_OK;
+}
+
+int escg_sync(escg_t* h) {
+  if (!h) {
+    set_err("NULL handle");
+    return ESCG_EINVAL;
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  RunState st;
+  CUDA_TRY(cudaMemcpy(&st, h->d_state, sizeof st, cudaMemcpyDeviceToHost));
+  if (st.error & kErrTimeout) {
+    h->failed = true;
+    set_err("a bounded device-side wait timed out; the lattice is inconsistent until restored");
+    return ESCG_ETIMEOUT;
+  }
+  return ESCG_OK;
+}
+
+int escg_counts(escg_t* h, uint64_t* out, uint64_t* mcs_out) {
+  if (!h || !out) {
+    set_err("NULL argument");
+    return ESCG_EINVAL;
+  }
+  int rc = escg_sync(h);
+  if (rc != ESCG_OK) return rc;
+  // separate scratch state so the run's accumulator is untouched
+  RunState* tmp = h->d_scratch;
+  cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(RunState), h->stream);
+  if (e == cudaSuccess) e = launch_count(h->desc, tmp, h->stream);
+  h->launches++;
+  RunState st{}, cur{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&cur, tmp, sizeof cur, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, h->d_state, sizeof st, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    set_err("count failed: %s", cudaGetErrorString(e));
+    return ESCG_ECUDA;
+  }
+  for (int v = 0; v <= h->S; ++v) out[v] = cur.cur[v];
+  if (mcs_out) *mcs_out = st.mcs;
+  return ESCG_OK;
+}
+
+int escg_counts_log(escg_t* h, uint64_t* out, uint64_t* mcs_out, int64_t cap, int64_t* n_out) {
+  if (!h || (!out && cap > 0) || cap < 0) {
+    set_err("bad arguments");
+    return ESCG_EINVAL;
+  }
+  int rc = escg_sync(h);
+  if (rc != ESCG_OK) return rc;
+  RunState st;
+  CUDA_TRY(cudaMemcpy(&st, h->d_state, sizeof st, cudaMemcpyDeviceToHost));
+  const int64_t have = st.n_log < (uint32_t)kLogCap ? st.n_log : kLogCap;
+  const int64_t n = have < cap ? have : cap;
+  std::vector<unsigned long long> buf((size_t)kLogCap * kMaxStates);
+  std::vector<uint32_t> ms(kLogCap);
+  CUDA_TRY(cudaMemcpy(buf.data(), h->d_log, buf.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(ms.data(), h->d_log_mcs, ms.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  const uint32_t first = st.n_log - (uint32_t)have;  // oldest retained entry
+  for (int64_t i = 0; i < n; ++i) {
+    const uint32_t idx = (first + (uint32_t)i) % (uint32_t)kLogCap;
+    for (int v = 0; v <= h->S; ++v) out[i * (h->S + 1) + v] = buf[(size_t)idx * kMaxStates + v];
+    if (mcs_out) mcs_out[i] = ms[idx];
+  }
+  if (n_out) *n_out = n;
+  return ESCG_OK;
+}
+
+int escg_snapshot(escg_t* h, uint8_t* host_out) {
+  if (!h || !host_out) {
+    set_err("NULL argument");
+    return ESCG_EINVAL;
+  }
+  int rc = escg_sync(h);
+  if (rc != ESCG_OK) return rc;
+  CUDA_TRY(cudaMemcpy2DAsync(host_out, h->L, h->lattice, h->pitch, h->L, h->L, cudaMemcpyDeviceToHost,
+                             h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return ESCG_OK;
+}
+
+int escg_restore(escg_t* h, const uint8_t* host_lattice, uint64_t mcs) {
+  if (!h || !host_lattice) {
+    set_err("NULL argument");
+    return ESCG_EINVAL;
+  }
+  if (mcs > 0xFFFFFFFFull) {
+    set_err("mcs exceeds 2^32-1");
+    return ESCG_EINVAL;
+  }
+  const size_t N = (size_t)h->L * h->L;
+  for (size_t i = 0; i < N; ++i)
+    if (host_lattice[i] > h->S) {
+      set_err("lattice value %d at %zu exceeds S=%d", host_lattice[i], i, h->S);
+      return ESCG_EINVAL;
+    }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  CUDA_TRY(cudaMemcpy2DAsync(h->lattice, h->pitch, host_lattice, h->L, h->L, h->L, cudaMemcpyHostToDevice,
+                             h->stream));
+  const int rc = reset_state(h, mcs);
+  if (rc != ESCG_OK) return rc;
+  return ESCG_OK;
+}
+
+int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_mcs, uint8_t* host_out,
+                   uint64_t* counts_out) {
+  if (!h || !host_in || !host_out) {
+    set_err("NULL argument");
+    return ESCG_EINVAL;
+  }
+  int rc = escg_restore(h, host_in, mcs);
+  if (rc == ESCG_OK) rc = escg_run(h, n_mcs);
+  if (rc == ESCG_OK) rc = escg_snapshot(h, host_out);
+  if (rc == ESCG_OK && counts_out) rc = escg_counts(h, counts_out, nullptr);
+  return rc;
+}
+
+void* escg_device_lattice(escg_t* h) { return h ? (void*)h->lattice : nullptr; }
+void* escg_stream(escg_t* h) { return h ? (void*)h->stream : nullptr; }
+uint64_t escg_launch_count(escg_t* h) { return h ? h->launches : 0; }
+
+uint64_t escg_current_mcs(escg_t* h) {
+  if (!h) return 0;
+  if (escg_sync(h) != ESCG_OK) return 0;
+  RunState st;
+  if (cudaMemcpy(&st, h->d_state, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+  return st.mcs;
+}
+
+int escg_kernel_time(escg_t* h, double* ms_total, uint64_t* n_launches, int reset) {
+  if (!h) {
+    set_err("NULL handle");
+    return ESCG_EINVAL;
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (auto& e : h->ev_used) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e.first, e.second));
+    h->kernel_ms += ms;
+    h->kernel_launches++;
+    h->ev_free.push_back(e);
+  }
+  h->ev_used.clear();
+  if (ms_total) *ms_total = h->kernel_ms;
+  if (n_launches) *n_launches = h->kernel_launches;
+  if (reset) {
+    h->kernel_ms = 0.0;
+    h->kernel_launches = 0;
+  }
+  return ESCG_OK;
+}
+
+int escg_debug_stall_block(escg_t* h, int32_t block, uint32_t spin_limit) {
+  if (!h) {
+    set_err("NULL handle");
+    return ESCG_EINVAL;
+  }
+  if (block >= h->part.P * h->part.P) {
+    set_err("block %d out of range", block);
+    return ESCG_EINVAL;
+  }
+  h->stall_block = block < 0 ? -1 : block;
+  h->spin_limit = spin_limit ? spin_limit : kDefaultSpinLimit;
+  return ESCG_OK;
+}
+
+int32_t escg_coarse_blocks(escg_t* h) { return h ? h->part.P : 0; }
+
+void escg_destroy(escg_t* h) { free_handle(h); }
+
+}  // extern "C"

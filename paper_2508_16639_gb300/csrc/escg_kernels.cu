@@ -1,0 +1,250 @@
+// escg_kernels.cu -- CUDA kernels of the ESCG Monte Carlo step (sm_103a)
+// and their host-side launchers.
+//
+//   init_kernel        site-parallel Philox initialisation (schedule v1)
+//   count_kernel       species histogram (warp-reduced, one atomic per warp
+//                      per state), the densities() of Alg. 4
+//   finalize_kernel    appends a logged count vector, stasis() check
+//   phase_kernel       one coarse colour phase: one CTA per active block
+//   persistent_kernel  many MCS in one launch: CTAs take (MCS, phase, block)
+//                      work items in schedule order from a ticket counter and
+//                      start a block once its 8 neighbours have reached the
+//                      required epoch (bounded spin; gives up with an error
+//                      status instead of hanging)
+#include <cstdio>
+
+#include "escg_device.cuh"
+#include "escg_internal.h"
+
+namespace escg_impl {
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void init_kernel(LatticeDesc d, uint64_t T_empty) {
+  const int L = d.L, pitch = d.pitch;
+  const size_t total = (size_t)L * pitch;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(k / pitch), col = (int)(k % pitch);
+    uint8_t v = 0;
+    if (col < L) {
+      const uint32_t i = (uint32_t)row * (uint32_t)L + (uint32_t)col;
+      const uint4 x = philox10(make_uint4(i, 0u, 0u, kTagInit), d.key0, d.key1);
+      v = ((uint64_t)x.x < T_empty) ? 0 : (uint8_t)(1u + __umulhi(x.y, (uint32_t)d.S));
+    }
+    d.lat[k] = v;
+  }
+}
+
+// Number of bytes of w equal to v (v < 128): zero-byte count of w ^ v*0x01010101.
+__device__ __forceinline__ uint32_t bytes_equal(uint32_t w, uint32_t v) {
+  const uint32_t t = w ^ (v * 0x01010101u);
+  const uint32_t z = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t | 0x7F7F7F7Fu);
+  return __popc(z);
+}
+
+__global__ void count_kernel(LatticeDesc d, RunState* st) {
+  if (ld_volatile(&st->stopped)) return;
+  const int L = d.L, pitch = d.pitch, S = d.S;
+  const int vec_per_row = pitch / 16;
+  const size_t total = (size_t)L * vec_per_row;
+  uint32_t c[kMaxStates];
+#pragma unroll
+  for (int v = 0; v < kMaxStates; ++v) c[v] = 0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(k / vec_per_row), q = (int)(k % vec_per_row);
+    uint4 w = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)row * pitch) + q);
+    const int col = 16 * q;
+    if (col + 16 > L) {  // mask padding bytes with 0xFF (never a state)
+      uint32_t* p = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int valid = L - (col + 4 * e);
+        if (valid <= 0)
+          p[e] = 0xFFFFFFFFu;
+        else if (valid < 4)
+          p[e] |= 0xFFFFFFFFu << (8 * valid);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kMaxStates; ++v)
+      if (v <= S) c[v] += bytes_equal(w.x, v) + bytes_equal(w.y, v) + bytes_equal(w.z, v) +
+                         bytes_equal(w.w, v);
+  }
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < kMaxStates; ++v) {
+    if (v <= S) {
+      const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, c[v]);
+      if (lane == 0 && s) atomicAdd(&st->cur[v], (unsigned long long)s);
+    }
+  }
+}
+
+__global__ void finalize_kernel(RunState* st, int S, unsigned long long* log_counts, uint32_t* log_mcs,
+                                uint32_t m_end, int log, int stop_at_extinction) {
+  if (st->stopped) return;
+  st->mcs = m_end;
+  if (!log) return;
+  const uint32_t idx = st->n_log % (uint32_t)kLogCap;
+  int alive = 0;
+  for (int v = 0; v < kMaxStates; ++v) {
+    const unsigned long long c = (v <= S) ? st->cur[v] : 0ull;
+    log_counts[(size_t)idx * kMaxStates + v] = c;
+    if (v >= 1 && v <= S && c > 0) ++alive;
+    st->cur[v] = 0;
+  }
+  log_mcs[idx] = m_end;
+  st->n_log += 1;
+  if (stop_at_extinction && alive <= 1) st->stopped = 1;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st, uint32_t m, int slot) {
+  if (ld_volatile(&st->stopped)) return;
+  __shared__ VisitSmem sm;
+  load_trans(d, sm.trans);
+  const uint4 x = philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1);
+  const int colour = order_at(colour_order(x.x), slot);
+  const int half = d.P >> 1, j = blockIdx.x;
+  const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
+  visit_block(d, bx, by, m, sm);
+}
+
+// ---------------------------------------------------------------------------
+constexpr int kPersistentThreads = 256;
+
+__global__ void __launch_bounds__(kPersistentThreads, 4)
+    persistent_kernel(LatticeDesc d, RunState* st, uint32_t* done, uint32_t m_begin, uint32_t n_mcs,
+                      uint32_t spin_limit, int stall_block) {
+  __shared__ VisitSmem sm;
+  __shared__ uint32_t s_item, s_ord, s_quit;
+  if (ld_volatile(&st->stopped)) return;
+  load_trans(d, sm.trans);
+  const int P = d.P, half = P >> 1;
+  const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
+  const uint64_t total = (uint64_t)n_mcs * nb;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      const uint32_t t = atomicAdd(&st->ticket, 1u);
+      s_item = t;
+      uint32_t quit = ((uint64_t)t >= total) || ld_volatile(&st->abort);
+      if (!quit) {
+        const uint32_t m = m_begin + t / nb;
+        s_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x);
+      }
+      s_quit = quit;
+    }
+    __syncthreads();
+    if (s_quit) break;
+    const uint32_t t = s_item, ord = s_ord;
+    const uint32_t mi = t / nb, rem = t - mi * nb;
+    const int k = (int)(rem / per), j = (int)(rem - (uint32_t)k * per);
+    const int colour = order_at(ord, k);
+    const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
+    if (tid < 9) {
+      const int dx = tid % 3 - 1, dy = tid / 3 - 1;
+      const int nx = (bx + dx + P) % P, ny = (by + dy + P) % P;
+      const int ncol = 2 * (ny & 1) + (nx & 1);
+      const uint32_t need = (tid == 4) ? mi : (slot_of(ord, ncol) < k ? mi + 1u : mi);
+      const uint32_t* flag = done + ny * P + nx;
+      uint32_t spins = 0;
+      while (ld_acquire(flag) < need) {
+        if (ld_volatile(&st->abort)) break;
+        if (++spins > spin_limit) {
+          atomicOr(&st->error, kErrTimeout);
+          atomicExch(&st->abort, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __syncthreads();
+    if (ld_volatile(&st->abort)) break;
+    visit_block(d, bx, by, m_begin + mi, sm);
+    __syncthreads();
+    if (tid == 0 && by * P + bx != stall_block) {
+      __threadfence();
+      st_release(done + by * P + bx, mi + 1u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+static inline int blocks_for(size_t n, int threads, int cap) {
+  size_t b = (n + threads - 1) / threads;
+  if (b > (size_t)cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+void upload_perm_table() {
+  uint8_t perms[24];
+  int n = 0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int c = 0; c < 4; ++c)
+        for (int e = 0; e < 4; ++e) {
+          if (a == b || a == c || a == e || b == c || b == e || c == e) continue;
+          perms[n++] = (uint8_t)(a | (b << 2) | (c << 4) | (e << 6));
+        }
+  cudaMemcpyToSymbol(c_perm24, perms, sizeof(perms));
+}
+
+cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream) {
+  const size_t n = (size_t)d.L * d.pitch;
+  init_kernel<<<blocks_for(n, 256, 152 * 32), 256, 0, stream>>>(d, T_empty);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream) {
+  const size_t n = (size_t)d.L * (d.pitch / 16);
+  count_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const LatticeDesc& d, RunState* st, unsigned long long* log_counts,
+                            uint32_t* log_mcs, uint32_t m_end, int log, int stop_at_extinction,
+                            cudaStream_t stream) {
+  finalize_kernel<<<1, 1, 0, stream>>>(st, d.S, log_counts, log_mcs, m_end, log, stop_at_extinction);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase(const LatticeDesc& d, RunState* st, uint32_t m, int slot, cudaStream_t stream) {
+  const int nblocks = (d.P * d.P) / 4;
+  phase_kernel<<<nblocks, 256, 0, stream>>>(d, st, m, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_persistent(const LatticeDesc& d, RunState* st, uint32_t* done, uint32_t m_begin,
+                              uint32_t n_mcs, int grid, uint32_t spin_limit, int stall_block,
+                              cudaStream_t stream) {
+  persistent_kernel<<<grid, kPersistentThreads, 0, stream>>>(d, st, done, m_begin, n_mcs, spin_limit,
+                                                             stall_block);
+  return cudaGetLastError();
+}
+
+int persistent_grid(int device) {
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, kPersistentThreads, 0);
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+int persistent_block_threads() { return kPersistentThreads; }
+
+}  // namespace escg_impl

@@ -1,0 +1,38 @@
+// escg_types.h -- plain data types and constants shared by the host and
+// device code of libescg (no device functions here).
+#pragma once
+
+#include <cstdint>
+
+namespace escg_impl {
+
+// Philox counter tags (word 3 of the counter).
+constexpr uint32_t kTagInit = 1, kTagOrder = 2, kTagFineOrder = 3, kTagStep = 4;
+
+// Largest coarse block edge the partition rule produces (L in [64,192) gives
+// two blocks of up to 96 sites), the tile's column offset of the block
+// interior (keeps interior rows 8-byte aligned), and the largest tile pitch.
+constexpr int kMaxBlock = 96;
+constexpr int kColOff = 8;
+constexpr int kMaxTilePitch = 112;   // round_up(kColOff + kMaxBlock + 1, 16)
+constexpr int kMaxTileRows = kMaxBlock + 2;
+constexpr int kMaxFine = kMaxBlock / 2;  // fine segments per block axis
+constexpr int kMaxStates = 16;           // S <= 15
+
+// Everything a kernel needs to know about one lattice.
+struct LatticeDesc {
+  uint8_t* lat;         // L rows of `pitch` bytes, values 0..S
+  int32_t L, pitch;
+  int32_t P, GQ;        // coarse segments per axis, fine segments per axis
+  const int32_t* cs;    // [P+1] coarse segment starts
+  const int32_t* fs;    // [GQ+1] fine segment starts (global coordinates)
+  const int32_t* fc;    // [P+1] first global fine index of each coarse segment
+  const uint8_t* trans; // [3][S+1][S+1]: new (a | b << 4) for (action, a, b)
+  uint32_t key0, key1;  // Philox key (seed)
+  uint32_t tx, txi;     // thresholds, low 32 bits
+  uint32_t tx_all, txi_all;  // 1 when the threshold is 2^32 (always)
+  int32_t S;
+  int32_t uniform64;    // all blocks 64x64 and all sub-blocks 2x2
+};
+
+}  // namespace escg_impl

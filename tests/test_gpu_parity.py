@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA path (through the C ABI) against the schedule-v1
+replay oracle, bit-exact (integer lattice work), after every MCS.
+
+Covers small and ragged lattices (odd L, non-uniform partitions, several
+tiles), the three benchmark lattices at their full sizes in the launch
+configuration the benchmark times (persistent kernel, default grid), both
+launch modes, counts and the count log, stasis, exact resume, the
+end-to-end host call and torch memory/stream interop.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2508_16639_gb300 as E
+from paper_2508_16639_gb300 import workloads as W
+from paper_2508_16639_gb300.build import build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _x(L, mobility, exchange):
+    return O.exchange_from_mobility(mobility, L * L) if mobility is not None else exchange
+
+
+def _pair(L, S, K, p_empty, I, P, X, seed, **kw):
+    D = O.circulant(S, K)
+    g = E.Lattice(L, S, E.circulant(S, K), (I, P, X), seed, p_empty=p_empty, **kw)
+    o = O.init(L, S, p_empty, seed)
+    return g, o, D
+
+
+@pytest.mark.parametrize("L,S,p_empty,seed", [(8, 3, 0.0, 1), (13, 5, 0.2, 2), (64, 3, 0.25, 3),
+                                              (100, 5, 1 / 6, 4), (333, 7, 0.5, 5), (800, 5, 0.2, 6),
+                                              (3200, 3, 0.25, W.SEED0), (16, 3, 1.0, 7)])
+def test_init_matches_oracle(L, S, p_empty, seed):
+    g, o, _ = _pair(L, S, [1], p_empty, 1.0, 1.0, 1.0, seed)
+    assert np.array_equal(g.snapshot(), o)
+    c, m = g.counts()
+    assert m == 0 and np.array_equal(c, O.counts(o, S))
+
+
+SMALL = [  # (L, S, K, p_empty, I, P, X, n_mcs)
+    (8, 3, (1,), 0.25, 1.0, 1.0, 1.0, 12),
+    (9, 3, (1,), 0.25, 1.0, 1.0, 0.3, 10),
+    (12, 5, (1, 2), 0.2, 1.0, 1.0, 2.0, 10),
+    (13, 3, (1,), 0.0, 1.0, 0.0, 0.0, 10),
+    (31, 5, (1, 2), 1 / 6, 0.5, 1.5, 4.0, 8),
+    (50, 3, (1,), 0.25, 1.0, 1.0, 0.5, 8),
+    (64, 3, (1,), 0.25, 1.0, 1.0, 0.8192, 8),
+    (77, 5, (1, 2), 0.2, 1.0, 1.0, 11.86, 6),
+    (100, 3, (1,), 0.25, 1.0, 1.0, 2.0, 6),
+    (131, 4, (1,), 0.1, 1.0, 2.0, 1.0, 5),
+    (191, 3, (1,), 0.25, 1.0, 1.0, 7.3, 4),
+    (200, 5, (1, 2), 0.2, 1.0, 1.0, 8.0, 4),
+    (257, 3, (1,), 0.25, 0.0, 0.0, 1.0, 3),
+]
+
+
+@pytest.mark.parametrize("persistent", [True, False], ids=["persistent", "phase"])
+@pytest.mark.parametrize("case", SMALL, ids=[f"L{c[0]}" for c in SMALL])
+def test_replay_parity_every_mcs(case, persistent):
+    L, S, K, p_empty, I, P, X, n = case
+    seed = 1000 + L
+    g, o, D = _pair(L, S, K, p_empty, I, P, X, seed, persistent=persistent, log_every=3)
+    for m in range(n):
+        g.run(1)
+        o, att = O.replay_run(o, D, I, P, X, seed, 1, mcs_begin=m)
+        assert att == L * L
+        got = g.snapshot()
+        assert np.array_equal(got, o), f"L={L} mismatch after MCS {m + 1}: " \
+                                       f"{int((got != o).sum())} sites differ"
+    c, mcs = g.counts()
+    assert mcs == n and np.array_equal(c, O.counts(o, S))
+
+
+def test_cfg1_competition_only_L64():
+    w = W.CFG1
+    g, o, D = _pair(w.L, w.S, w.K, w.p_empty, w.interact, w.reproduce, w.exchange, w.seed)
+    for m in range(w.n_mcs):
+        g.run(1)
+        o, _ = O.replay_run(o, D, w.interact, w.reproduce, w.exchange, w.seed, 1, mcs_begin=m)
+        assert np.array_equal(g.snapshot(), o), m
+
+
+def test_cfg2_rpsls_L800_every_mcs():
+    w = W.CFG2
+    X = _x(w.L, w.mobility, w.exchange)
+    assert X == E.exchange_from_mobility(w.mobility, w.L * w.L) == pytest.approx(128.0)
+    g, o, D = _pair(w.L, w.S, w.K, w.p_empty, w.interact, w.reproduce, X, w.seed)
+    for m in range(w.n_mcs):
+        g.run(1)
+        o, _ = O.replay_run(o, D, w.interact, w.reproduce, X, w.seed, 1, mcs_begin=m)
+        if m < 20 or m % 25 == 24 or m == w.n_mcs - 1:
+            assert np.array_equal(g.snapshot(), o), m
+    assert np.array_equal(g.snapshot(), o)
+
+
+@pytest.mark.parametrize("M", [1e-5, 1e-4, 1e-3])
+def test_cfg3_L3200_full_size(M):
+    """Full-size lattice in the benchmark's launch configuration (persistent
+    kernel, chunks ending at log points every 10 MCS)."""
+    w = W.CFG3[M]
+    X = _x(w.L, w.mobility, w.exchange)
+    g, o, D = _pair(w.L, w.S, w.K, w.p_empty, w.interact, w.reproduce, X, w.seed,
+                    log_every=w.log_every)
+    checkpoints = [1, 2, 10] if M == 1e-4 else [1, 3]
+    m = 0
+    for c in checkpoints:
+        g.run(c - m)
+        o, _ = O.replay_run(o, D, w.interact, w.reproduce, X, w.seed, c - m, mcs_begin=m)
+        m = c
+        assert np.array_equal(g.snapshot(), o), (M, c)
+    ms, log = g.counts_log()
+    assert list(ms) == [k for k in (0, 10) if k <= m]
+    assert np.array_equal(log[-1] if m == 10 else O.counts(o, w.S), O.counts(o, w.S))
+
+
+def test_counts_log_matches_oracle():
+    L, S, K, I, P, X, seed = 40, 5, (1, 2), 1.0, 1.0, 3.0, 77
+    g, o, D = _pair(L, S, K, 0.2, I, P, X, seed, log_every=4)
+    g.run(10).run(9)
+    lat, log, mend = O.run_observed(o, D, I, P, X, seed, 19, log_every=4)
+    ms, glog = g.counts_log()
+    assert list(ms) == [0, 4, 8, 12, 16] and mend == 19
+    assert np.array_equal(glog, log)
+    assert np.array_equal(g.snapshot(), lat)
+
+
+@pytest.mark.parametrize("persistent", [True, False], ids=["persistent", "phase"])
+def test_stop_at_extinction_matches_oracle(persistent):
+    L, S, K, I, P, seed = 16, 3, (1,), 1.0, 1.0, 5
+    X = O.exchange_from_mobility(0.1, L * L)
+    g, o, D = _pair(L, S, K, 0.25, I, P, X, seed, log_every=10, stop_at_extinction=True,
+                    persistent=persistent)
+    g.run(3000)
+    lat, log, mend = O.run_observed(o, D, I, P, X, seed, 3000, log_every=10, stop_at_extinction=True)
+    assert mend < 3000
+    assert g.mcs == mend
+    assert np.array_equal(g.snapshot(), lat)
+    ms, glog = g.counts_log()
+    assert np.array_equal(glog, log) and ms[-1] == mend
+
+
+def test_restore_resume_exact():
+    L, S, K, I, P, X, seed = 100, 3, (1,), 1.0, 1.0, 2.0, 9
+    g, o, D = _pair(L, S, K, 0.25, I, P, X, seed, log_every=10)
+    g.run(7)
+    snap7 = g.snapshot()
+    g.run(6)
+    full = g.snapshot()
+    h = E.Lattice(L, S, E.circulant(S, K), (I, P, X), seed, p_empty=0.25, log_every=10)
+    h.restore(snap7, 7)
+    assert h.mcs == 7
+    h.run(6)
+    assert np.array_equal(h.snapshot(), full)
+    ref, _ = O.replay_run(snap7, D, I, P, X, seed, 6, mcs_begin=7)
+    assert np.array_equal(full, ref)
+
+
+def test_step_host_end_to_end():
+    L, S, K, I, P, X, seed = 64, 5, (1, 2), 1.0, 1.0, 1.5, 21
+    g, o, D = _pair(L, S, K, 0.2, I, P, X, seed)
+    out, counts = g.step_host(o, 0, 5)
+    ref, _ = O.replay_run(o, D, I, P, X, seed, 5)
+    assert np.array_equal(out, ref)
+    assert np.array_equal(counts, O.counts(ref, S))
+    out2, _ = g.step_host(out, 5, 3)
+    ref2, _ = O.replay_run(ref, D, I, P, X, seed, 3, mcs_begin=5)
+    assert np.array_equal(out2, ref2)
+
+
+def test_torch_buffer_and_stream_interop():
+    import torch
+    L, S, K, I, P, X, seed = 96, 3, (1,), 1.0, 1.0, 1.0, 33
+    buf = torch.zeros(E.lattice_bytes(L), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    g = E.Lattice(L, S, E.circulant(S, K), (I, P, X), seed, p_empty=0.25, stream=stream,
+                  device_buffer=buf)
+    g.run(4)
+    g.sync()
+    view = g.as_tensor()[:, :L].cpu().numpy()
+    o, _ = O.replay_run(O.init(L, S, 0.25, seed), O.circulant(S, K), I, P, X, seed, 4)
+    assert np.array_equal(view, o)
+    assert np.array_equal(g.snapshot(), o)
+    assert g.stream_ptr == stream.cuda_stream
+
+
+def test_launch_modes_agree_and_chunking_is_invisible():
+    L, S, K, I, P, X, seed = 150, 5, (1, 2), 1.0, 1.0, 5.0, 55
+    a = E.Lattice(L, S, E.circulant(S, K), (I, P, X), seed, p_empty=0.2, persistent=True, log_every=7)
+    b = E.Lattice(L, S, E.circulant(S, K), (I, P, X), seed, p_empty=0.2, persistent=False, log_every=5)
+    a.run(3).run(11).run(1)
+    b.run(15)
+    assert np.array_equal(a.snapshot(), b.snapshot())
+    assert a.launches > 0 and b.launches > a.launches
+
+
+def test_bounded_wait_times_out_with_status():
+    """A block whose epoch is never published (host-controlled hook: the
+    flag nothing sets) makes its neighbours' bounded waits run out; the
+    kernel returns, escg_sync reports ESCG_ETIMEOUT and the handle refuses
+    to run until a lattice is restored.  No hang, no fault."""
+    L, S = 256, 3
+    g = E.Lattice(L, S, E.circulant(S, [1]), (1.0, 1.0, 1.0), 3, p_empty=0.25)
+    ref = g.snapshot()
+    g.debug_stall_block(0, spin_limit=2000)
+    g.run(3)
+    with pytest.raises(E.EscgError) as ei:
+        g.sync()
+    assert ei.value.status == -5
+    with pytest.raises(E.EscgError) as ei2:
+        g.run(1)
+    assert ei2.value.status == -4
+    g.debug_stall_block(-1)
+    g.restore(ref, 0)
+    g.run(2)
+    o, _ = O.replay_run(ref, O.circulant(S, [1]), 1.0, 1.0, 1.0, 3, 2)
+    assert np.array_equal(g.snapshot(), o)
+
+
+def test_kernel_timing_counts_launches():
+    g = E.Lattice(64, 3, E.circulant(3, [1]), (1.0, 1.0, 1.0), 3, time_kernels=True)
+    g.run(25)
+    ms, n = g.kernel_time()
+    assert n == 3 and ms > 0
+    assert E.int_throughput()[0] > 1e12
