@@ -108,7 +108,7 @@ bool thresholds(const escg_rates* r, uint64_t* tx, uint64_t* txi) {
 // reproduction fills an empty site of the pair with the other's species.
 void build_trans(int S, const uint8_t* D, std::vector<uint8_t>& t) {
   const int s1 = S + 1;
-  t.assign(3 * s1 * s1, 0);
+  t.assign(4 * s1 * s1, 0);
   auto dom = [&](int a, int b) { return a != 0 && b != 0 && D[(a - 1) * S + (b - 1)] == 1; };
   for (int act = 0; act < 3; ++act)
     for (int a = 0; a < s1; ++a)
@@ -130,7 +130,7 @@ void build_trans(int S, const uint8_t* D, std::vector<uint8_t>& t) {
               na = b;
           }
         }
-        t[(act * s1 + a) * s1 + b] = (uint8_t)(na | (nb << 4));
+        t[(a * s1 + b) * 4 + act] = (uint8_t)(na | (nb << 4));
       }
 }
 
@@ -151,13 +151,14 @@ struct escg {
   RunState* d_state = nullptr;
   unsigned long long* d_log = nullptr;
   uint32_t* d_log_mcs = nullptr;
-  uint32_t* d_done = nullptr;    // P*P epoch counters of the persistent kernel
+  uint32_t* d_done = nullptr;    // P*P absolute epochs of the persistent kernel
   uint64_t mcs_enq = 0;          // MCS number after all enqueued work
   uint64_t launches = 0;
   uint64_t T_empty = 0;
   int grid = 0;
   uint32_t spin_limit = kDefaultSpinLimit;
   int stall_block = -1;
+  uint32_t log_num0_host = 0;
   bool failed = false;
   RunState* d_scratch = nullptr;  // accumulator for on-demand counts
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -167,12 +168,14 @@ struct escg {
 
 namespace {
 
+LogBuffers log_buffers(escg* h) { return LogBuffers{h->d_log, h->d_log_mcs}; }
+
 int enqueue_log(escg* h, uint32_t m_end, bool log) {
   if (log) {
     CUDA_TRY(launch_count(h->desc, h->d_state, h->stream));
     h->launches++;
   }
-  CUDA_TRY(launch_finalize(h->desc, h->d_state, h->d_log, h->d_log_mcs, m_end, log ? 1 : 0,
+  CUDA_TRY(launch_finalize(h->desc, h->d_state, log_buffers(h), m_end, h->opt.log_every, log ? 1 : 0,
                            h->opt.stop_at_extinction, h->stream));
   h->launches++;
   return ESCG_OK;
@@ -200,9 +203,19 @@ cudaError_t timing_end(escg* h) {
 }
 
 int reset_state(escg* h, uint64_t mcs) {
-  RunState st{};
-  st.mcs = (uint32_t)mcs;
-  CUDA_TRY(cudaMemcpyAsync(h->d_state, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+  static RunState zero{};  // RunState is large; fill on the device
+  (void)zero;
+  CUDA_TRY(cudaMemsetAsync(h->d_state, 0, sizeof(RunState), h->stream));
+  uint32_t head[2] = {(uint32_t)mcs, 0u};
+  const uint32_t le = h->opt.log_every;
+  const uint32_t num0 = (uint32_t)((mcs + le - 1) / le);
+  CUDA_TRY(cudaMemcpyAsync(&h->d_state->mcs, &head[0], sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream));
+  h->log_num0_host = num0;
+  CUDA_TRY(cudaMemcpyAsync(&h->d_state->log_num0, &h->log_num0_host, sizeof(uint32_t),
+                           cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(launch_fill_u32(h->d_done, h->part.P * h->part.P, (uint32_t)mcs, h->stream));
+  h->launches++;
+  CUDA_TRY(cudaStreamSynchronize(h->stream));  // the host values above are stack/handle-owned
   h->mcs_enq = mcs;
   h->failed = false;
   if (mcs % h->opt.log_every == 0) return enqueue_log(h, (uint32_t)mcs, true);
@@ -376,7 +389,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   const Partition& p = h->part;
   const size_t ntab = p.cs.size() + p.fs.size() + p.fc.size();
   if (e == cudaSuccess) e = cudaMalloc(&h->d_tables, ntab * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_trans, 3 * kMaxStates * kMaxStates);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_trans, 4 * kMaxStates * kMaxStates);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_state, sizeof(RunState));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_log, sizeof(unsigned long long) * kLogCap * kMaxStates);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_log_mcs, sizeof(uint32_t) * kLogCap);
@@ -414,16 +427,16 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   d.trans = h->d_trans;
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);
-  d.tx = (uint32_t)tx;
-  d.tx_all = tx >> 32 ? 1u : 0u;
-  d.txi = (uint32_t)txi;
-  d.txi_all = txi >> 32 ? 1u : 0u;
+  // 2^32 ("always") becomes 0xFFFFFFFF: exact, since every action draw u
+  // is a multiple of 4 and so never equals 0xFFFFFFFF
+  d.tx = tx >> 32 ? 0xFFFFFFFFu : (uint32_t)tx;
+  d.txi = txi >> 32 ? 0xFFFFFFFFu : (uint32_t)txi;
   d.S = S;
   bool uni = true;
   for (int k = 0; k < p.P; ++k) uni = uni && (p.cs[k + 1] - p.cs[k] == 64);
   for (int k = 0; k < p.GQ; ++k) uni = uni && (p.fs[k + 1] - p.fs[k] == 2);
   d.uniform64 = (uni && h->pitch % 16 == 0) ? 1 : 0;
-  h->grid = persistent_grid(h->device);
+  h->grid = persistent_grid(h->device, d.uniform64 != 0);
 
   if (launch_init(d, h->T_empty, h->stream) != cudaSuccess) {
     set_err("init kernel launch failed");
@@ -454,23 +467,41 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
   }
   const uint32_t k = h->opt.log_every;
   while (h->mcs_enq < target) {
-    const uint64_t next_log = (h->mcs_enq / k + 1) * k;
-    uint64_t end = next_log < target ? next_log : target;
+    uint64_t end;
+    if (h->opt.persistent && !h->opt.stop_at_extinction) {
+      // one launch may leave up to kPendRing log points open
+      const uint64_t lim = (h->mcs_enq / k + kPendRing) * k;
+      end = lim < target ? lim : target;
+    } else {
+      // stasis is decided at log points: a launch ends there
+      const uint64_t next_log = (h->mcs_enq / k + 1) * k;
+      end = next_log < target ? next_log : target;
+    }
     // the persistent kernel numbers work items with 32-bit tickets
     const uint64_t per_mcs = (uint64_t)h->part.P * h->part.P;
     const uint64_t max_chunk = ((1ull << 31) - (uint64_t)h->grid) / per_mcs;
     if (end - h->mcs_enq > max_chunk) end = h->mcs_enq + max_chunk;
     const uint32_t m0 = (uint32_t)h->mcs_enq, n = (uint32_t)(end - h->mcs_enq);
     if (h->opt.persistent) {
-      CUDA_TRY(cudaMemsetAsync(h->d_done, 0, sizeof(uint32_t) * h->part.P * h->part.P, h->stream));
-      CUDA_TRY(cudaMemsetAsync(&h->d_state->ticket, 0, sizeof(uint32_t), h->stream));
-      const uint64_t items = (uint64_t)n * h->part.P * h->part.P;
+      const uint64_t items = (uint64_t)n * per_mcs;
       const int grid = (int)(items < (uint64_t)h->grid ? items : (uint64_t)h->grid);
+      PersistentArgs a{};
+      a.d = h->desc;
+      a.st = h->d_state;
+      a.done = h->d_done;
+      a.lb = log_buffers(h);
+      a.m_begin = m0;
+      a.n_mcs = n;
+      a.log_every = k;
+      a.stop_at_extinction = h->opt.stop_at_extinction;
+      a.spin_limit = h->spin_limit;
+      a.stall_block = h->stall_block;
       CUDA_TRY(timing_begin(h));
-      CUDA_TRY(launch_persistent(h->desc, h->d_state, h->d_done, m0, n, grid, h->spin_limit,
-                                 h->stall_block, h->stream));
+      CUDA_TRY(launch_persistent(a, grid, h->stream));
       CUDA_TRY(timing_end(h));
       h->launches++;
+      h->mcs_enq = end;
+      continue;  // counts of log points and the MCS number are written in-kernel
     } else {
       for (uint32_t m = m0; m < m0 + n; ++m)
         for (int slot = 0; slot < 4; ++slot) {

@@ -1,7 +1,7 @@
 // escg_device.cuh -- device-side building blocks of the ESCG Monte Carlo
-// step on sm_103a: Philox4x32-10, the per-lattice parameter block, the
-// elementary step on a shared-memory tile, and the visit of one coarse block
-// (load block + 1-site rim, four fine colour phases, write back).
+// step on sm_103a: Philox4x32-10, the elementary step on a shared-memory
+// tile, the visit of one coarse block (load block + 1-site rim, four fine
+// colour phases, write back) and the fused species count of a visit.
 //
 // The schedule implemented here (version 1) is the coloured two-level
 // sublattice decomposition of the lattice: coarse blocks coloured 2x2, fine
@@ -19,7 +19,6 @@
 #include "escg_types.h"
 
 namespace escg_impl {
-
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64-bit multiplies; the high halves are mixed with the other two
@@ -55,18 +54,33 @@ __device__ __forceinline__ int slot_of(uint32_t ord, int colour) {
 // Per-CTA shared state of a block visit.
 struct VisitSmem {
   uint8_t tile[kMaxTileRows * kMaxTilePitch];
-  uint8_t trans[3 * kMaxStates * kMaxStates];
+  uint32_t trans[kMaxStates * kMaxStates];   // word (a*(S+1)+b), byte = action
   int16_t fsx[kMaxFine + 1], fsy[kMaxFine + 1];   // block-local fine starts
   uint32_t forder;
+  uint32_t hist[kMaxStates];
 };
 
-// One elementary step (Alg. 3) on the tile.  w: the attempt's 32-bit Philox
-// word; n4 = 4 * cells of the sub-block; base: tile index of the sub-block's
-// first cell; wx: sub-block width; inv_wx = ceil(65536 / wx).
+// Transition of the pair (a, b) under the action drawn by u: byte
+// (a*(S+1)+b)*4 + action of the table, action = [u >= T_X] + [u >= T_XI]
+// (0 exchange, 1 interaction, 2 reproduction); new a in the low nibble, new b
+// in the high nibble.  Thresholds of 2^32 are stored as 0xFFFFFFFF, which is
+// exact because u is always a multiple of 4.
+__device__ __forceinline__ void apply_rule(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
+                                           int ti, int tj, uint32_t u, uint32_t tx, uint32_t txi,
+                                           uint32_t s1) {
+  const uint32_t a = tile[ti], b = tile[tj];
+  const uint32_t act = (u >= tx ? 1u : 0u) + (u >= txi ? 1u : 0u);
+  const uint32_t nn = trans[(a * s1 + b) * 4u + act];
+  tile[ti] = (uint8_t)(nn & 15u);
+  tile[tj] = (uint8_t)(nn >> 4);
+}
+
+// One elementary step (Alg. 3) of a generic sub-block.  w: the attempt's
+// 32-bit Philox word; n4 = 4 * cells of the sub-block; base: tile index of
+// the sub-block's first cell; wx: its width; inv_wx = ceil(65536 / wx).
 __device__ __forceinline__ void attempt(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
                                         uint32_t w, uint32_t n4, int base, int wx, uint32_t inv_wx,
-                                        int sp, uint32_t tx, uint32_t txi, uint32_t tx_all,
-                                        uint32_t txi_all, uint32_t s1, uint32_t ts) {
+                                        int sp, uint32_t tx, uint32_t txi, uint32_t s1) {
   const uint32_t hi = __umulhi(w, n4);
   const uint32_t u = w * n4;
   const uint32_t site = hi >> 2, dir = hi & 3u;
@@ -75,135 +89,155 @@ __device__ __forceinline__ void attempt(uint8_t* __restrict__ tile, const uint8_
   const int ti = base + (int)r * sp + (int)c;
   const int mag = (dir & 2u) ? 1 : sp;
   const int tj = ti + ((dir & 1u) ? mag : -mag);
-  const uint32_t a = tile[ti], b = tile[tj];
-  const bool ex = tx_all | (u < tx);
-  const bool in = txi_all | (u < txi);
-  const uint32_t idx = (ex ? 0u : (in ? ts : 2u * ts)) + a * s1 + b;
-  const uint32_t nn = trans[idx];
-  tile[ti] = (uint8_t)(nn & 15u);
-  tile[tj] = (uint8_t)(nn >> 4);
+  apply_rule(tile, trans, ti, tj, u, tx, txi, s1);
 }
 
 // Tile index of block-local (row r, col c), r, c in [-1, B].
 __device__ __forceinline__ int tidx(int r, int c, int sp) { return (r + 1) * sp + c + kColOff; }
-
+__device__ __forceinline__ int tile_pitch(int bw) { return ((kColOff + bw + 1) + 15) & ~15; }
 __device__ __forceinline__ int wrap(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+// Uniform geometry: 64x64 blocks, 2x2 sub-blocks, one thread per 2x2 pair of
+// sub-blocks ("quad"), 256 threads.
+constexpr int kUniB = 64;
+constexpr int kUniSP = 80;   // tile_pitch(64)
+constexpr int kUniThreads = 256;
+
+// One elementary step on a 2x2 sub-block: 4*n_k = 16, so the high 4 bits of
+// w are (row, col, dir) and u = w << 4.
+__device__ __forceinline__ void attempt_uni(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
+                                            uint32_t w, int base, uint32_t tx, uint32_t txi, uint32_t s1) {
+  const uint32_t u = w << 4;
+  const int row80 = ((int32_t)w >> 31) & kUniSP;
+  const int col = (int)((w >> 30) & 1u);
+  const int ti = base + row80 + col;
+  const int mag = (w & (1u << 29)) ? 1 : kUniSP;
+  const int tj = ti + ((w & (1u << 28)) ? mag : -mag);
+  apply_rule(tile, trans, ti, tj, u, tx, txi, s1);
+}
 
 // Loads block interior + the four 1-site rim strips (no corners) into the
 // tile through L2 (ld.global.cg: data written by other CTAs of the same
 // launch must not be served from a stale L1 line).
-__device__ __forceinline__ void load_tile(const LatticeDesc& d, int x0, int y0, int bw, int bh,
-                                          uint8_t* tile, int sp) {
-  const int L = d.L, pitch = d.pitch;
-  const uint8_t* lat = d.lat;
-  const int nthr = blockDim.x;
-  if (d.uniform64) {
-    // interior: 64 rows x 64 bytes as 16-byte loads; rows 16-byte aligned
-    for (int k = threadIdx.x; k < 64 * 4; k += nthr) {
-      const int r = k >> 2, q = k & 3;
-      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(lat + (size_t)(y0 + r) * pitch + x0) + q);
-      uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, sp));
-      dst[0] = make_uint2(v.x, v.y);
-      dst[1] = make_uint2(v.z, v.w);
-    }
-    // top / bottom rim rows: 2 x 4 x 16 bytes
-    for (int k = threadIdx.x; k < 8; k += nthr) {
-      const int top = k < 4, q = k & 3;
-      const int r = top ? -1 : 64;
-      const int gy = wrap(y0 + r, L);
-      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(lat + (size_t)gy * pitch + x0) + q);
-      uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, sp));
-      dst[0] = make_uint2(v.x, v.y);
-      dst[1] = make_uint2(v.z, v.w);
-    }
-    // left / right rim columns
-    for (int k = threadIdx.x; k < 128; k += nthr) {
-      const int left = k < 64, r = k & 63;
-      const int c = left ? -1 : 64;
-      const int gx = wrap(x0 + c, L);
-      tile[tidx(r, c, sp)] = __ldcg(lat + (size_t)(y0 + r) * pitch + gx);
-    }
-    return;
-  }
-  const int W = bw + 2, H = bh + 2;
-  for (int k = threadIdx.x; k < W * H; k += nthr) {
+__device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
+                                                  uint8_t* tile, int sp) {
+  const int L = d.L, pitch = d.pitch, W = bw + 2, H = bh + 2;
+  for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
     const int r = k / W - 1, c = k % W - 1;
-    const bool corner = (r < 0 || r >= bh) && (c < 0 || c >= bw);
-    if (corner) continue;
-    const int gy = wrap(y0 + r, L), gx = wrap(x0 + c, L);
-    tile[tidx(r, c, sp)] = __ldcg(lat + (size_t)gy * pitch + gx);
+    if ((r < 0 || r >= bh) && (c < 0 || c >= bw)) continue;   // corners
+    tile[tidx(r, c, sp)] = __ldcg(d.lat + (size_t)wrap(y0 + r, L) * pitch + wrap(x0 + c, L));
   }
 }
 
 // Writes back the block interior and its four rim strips (never the
 // corners, which belong to diagonal blocks that may be updated meanwhile).
-__device__ __forceinline__ void store_tile(const LatticeDesc& d, int x0, int y0, int bw, int bh,
-                                           const uint8_t* tile, int sp) {
-  const int L = d.L, pitch = d.pitch;
-  uint8_t* lat = d.lat;
-  const int nthr = blockDim.x;
-  if (d.uniform64) {
-    for (int k = threadIdx.x; k < 64 * 4; k += nthr) {
-      const int r = k >> 2, q = k & 3;
-      const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, sp));
-      const uint2 a = src[0], b = src[1];
-      reinterpret_cast<uint4*>(lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
-    }
-    for (int k = threadIdx.x; k < 8; k += nthr) {
-      const int top = k < 4, q = k & 3;
-      const int r = top ? -1 : 64;
-      const int gy = wrap(y0 + r, L);
-      const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, sp));
-      const uint2 a = src[0], b = src[1];
-      reinterpret_cast<uint4*>(lat + (size_t)gy * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
-    }
-    for (int k = threadIdx.x; k < 128; k += nthr) {
-      const int left = k < 64, r = k & 63;
-      const int c = left ? -1 : 64;
-      const int gx = wrap(x0 + c, L);
-      lat[(size_t)(y0 + r) * pitch + gx] = tile[tidx(r, c, sp)];
-    }
-    return;
-  }
-  const int W = bw + 2, H = bh + 2;
-  for (int k = threadIdx.x; k < W * H; k += nthr) {
+__device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
+                                                   const uint8_t* tile, int sp) {
+  const int L = d.L, pitch = d.pitch, W = bw + 2, H = bh + 2;
+  for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
     const int r = k / W - 1, c = k % W - 1;
-    const bool corner = (r < 0 || r >= bh) && (c < 0 || c >= bw);
-    if (corner) continue;
-    const int gy = wrap(y0 + r, L), gx = wrap(x0 + c, L);
-    lat[(size_t)gy * pitch + gx] = tile[tidx(r, c, sp)];
+    if ((r < 0 || r >= bh) && (c < 0 || c >= bw)) continue;
+    d.lat[(size_t)wrap(y0 + r, L) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, sp)];
   }
 }
 
-__device__ __forceinline__ int tile_pitch(int bw) { return ((kColOff + bw + 1) + 15) & ~15; }
-
-// Loads the transition table of a lattice into shared memory.
-__device__ __forceinline__ void load_trans(const LatticeDesc& d, uint8_t* trans) {
-  const int n = 3 * (d.S + 1) * (d.S + 1);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) trans[k] = d.trans[k];
+__device__ __forceinline__ void load_tile_uni(const LatticeDesc& d, int x0, int y0, uint8_t* tile) {
+  const int L = d.L, pitch = d.pitch, t = threadIdx.x;
+  {  // interior: 64 rows x 4 x 16 bytes, one 16-byte load per thread
+    const int r = t >> 2, q = t & 3;
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q);
+    uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    dst[0] = make_uint2(v.x, v.y);
+    dst[1] = make_uint2(v.z, v.w);
+  }
+  if (t < 8) {  // top / bottom rim rows
+    const int r = (t < 4) ? -1 : kUniB, q = t & 3;
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, L) * pitch + x0) + q);
+    uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    dst[0] = make_uint2(v.x, v.y);
+    dst[1] = make_uint2(v.z, v.w);
+  } else if (t >= 128) {  // left / right rim columns
+    const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
+    tile[tidx(r, c, kUniSP)] = __ldcg(d.lat + (size_t)(y0 + r) * pitch + wrap(x0 + c, L));
+  }
 }
 
-// One visit of coarse block (bx, by) in MCS m: stage, four fine colour
-// phases, write back.  Must be called by all threads of the CTA; begins and
-// ends with the tile free for reuse.  trans must already be in sm.trans.
-__device__ void visit_block(const LatticeDesc& d, int bx, int by, uint32_t m, VisitSmem& sm) {
+__device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int y0, const uint8_t* tile) {
+  const int L = d.L, pitch = d.pitch, t = threadIdx.x;
+  {
+    const int r = t >> 2, q = t & 3;
+    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    const uint2 a = src[0], b = src[1];
+    reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
+  }
+  if (t < 8) {
+    const int r = (t < 4) ? -1 : kUniB, q = t & 3;
+    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    const uint2 a = src[0], b = src[1];
+    reinterpret_cast<uint4*>(d.lat + (size_t)wrap(y0 + r, L) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
+  } else if (t >= 128) {
+    const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
+    d.lat[(size_t)(y0 + r) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, kUniSP)];
+  }
+}
+
+// Loads the transition table (built on the host) and the fine order.
+__device__ __forceinline__ void load_trans(const LatticeDesc& d, uint32_t* trans) {
+  const int n = (d.S + 1) * (d.S + 1);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) trans[k] = reinterpret_cast<const uint32_t*>(d.trans)[k];
+}
+
+// Visit of coarse block (bx, by) in MCS m, uniform geometry.  Must be called
+// by all 256 threads; the tile is free for reuse after the caller's next
+// __syncthreads().
+__device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int by, uint32_t m,
+                                              VisitSmem& sm) {
+  const int x0 = bx * kUniB, y0 = by * kUniB;
+  const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
+  if (t == 0) {
+    const uint4 x = philox10(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.key0, d.key1);
+    sm.forder = colour_order(x.x);
+  }
+  load_tile_uni(d, x0, y0, sm.tile);
+  __syncthreads();
+  const uint32_t ord = sm.forder, s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
+  const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
+  const uint32_t gx0 = (uint32_t)(bx * (kUniB / 2) + 2 * qx), gy0 = (uint32_t)(by * (kUniB / 2) + 2 * qy);
+#pragma unroll 1
+  for (int fi = 0; fi < 4; ++fi) {
+    const int fcol = order_at(ord, fi);
+    const int cx = fcol & 1, cy = fcol >> 1;
+    const uint32_t g = (gy0 + (uint32_t)cy) * (uint32_t)d.GQ + gx0 + (uint32_t)cx;
+    const int base = tidx(4 * qy + 2 * cy, 4 * qx + 2 * cx, kUniSP);
+    const uint4 x = philox10(make_uint4(0u, g, m, kTagStep), d.key0, d.key1);
+    attempt_uni(sm.tile, trans, x.x, base, tx, txi, s1);
+    attempt_uni(sm.tile, trans, x.y, base, tx, txi, s1);
+    attempt_uni(sm.tile, trans, x.z, base, tx, txi, s1);
+    attempt_uni(sm.tile, trans, x.w, base, tx, txi, s1);
+    __syncthreads();
+  }
+  store_tile_uni(d, x0, y0, sm.tile);
+}
+
+// Visit of coarse block (bx, by) in MCS m, any geometry of the partition.
+__device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int by, uint32_t m,
+                                              VisitSmem& sm) {
   const int x0 = d.cs[bx], bw = d.cs[bx + 1] - x0;
   const int y0 = d.cs[by], bh = d.cs[by + 1] - y0;
   const int fx0 = d.fc[bx], Qx = d.fc[bx + 1] - fx0;
   const int fy0 = d.fc[by], Qy = d.fc[by + 1] - fy0;
   const int sp = tile_pitch(bw);
   const int tid = threadIdx.x, nthr = blockDim.x;
-
   for (int k = tid; k <= Qx; k += nthr) sm.fsx[k] = (int16_t)(d.fs[fx0 + k] - x0);
   for (int k = tid; k <= Qy; k += nthr) sm.fsy[k] = (int16_t)(d.fs[fy0 + k] - y0);
   if (tid == 0) {
     const uint4 x = philox10(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.key0, d.key1);
     sm.forder = colour_order(x.x);
   }
-  load_tile(d, x0, y0, bw, bh, sm.tile, sp);
+  load_tile_generic(d, x0, y0, bw, bh, sm.tile, sp);
   __syncthreads();
-
-  const uint32_t s1 = (uint32_t)d.S + 1u, ts = s1 * s1;
+  const uint32_t s1 = (uint32_t)d.S + 1u;
+  const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
   const int hx = Qx >> 1, nquads = hx * (Qy >> 1);
   const uint32_t ord = sm.forder;
   for (int fi = 0; fi < 4; ++fi) {
@@ -224,13 +258,109 @@ __device__ void visit_block(const LatticeDesc& d, int bx, int by, uint32_t m, Vi
 #pragma unroll
         for (int e = 0; e < 4; ++e)
           if (4u * j + (uint32_t)e < nk)
-            attempt(sm.tile, sm.trans, wv[e], n4, base, wx, inv_wx, sp, d.tx, d.txi, d.tx_all,
-                    d.txi_all, s1, ts);
+            attempt(sm.tile, trans, wv[e], n4, base, wx, inv_wx, sp, d.tx, d.txi, s1);
       }
     }
     __syncthreads();
   }
-  store_tile(d, x0, y0, bw, bh, sm.tile, sp);
+  store_tile_generic(d, x0, y0, bw, bh, sm.tile, sp);
+}
+
+// ---------------------------------------------------------------------------
+// Fused species count of one visit.  After MCS m every site must be counted
+// once, by the last block to touch it in that MCS: a site of block X is
+// touched by X and by the edge neighbours whose rim strip covers it.  The
+// vertical neighbours of a block all have colour c^2, the horizontal ones
+// c^1 and the diagonal ones c^3, so the order of the four coarse phases
+// decides: a block with slot k counts
+//   - its interior sites, except edge rows when the vertical neighbours come
+//     later (sV > k) and edge columns when the horizontal ones do (sH > k);
+//   - its top/bottom rim sites when sV < k, the end cells also needing
+//     sD < k (the diagonal block's rim touches them too);
+//   - its left/right rim sites when sH < k, the end cells also needing sD < k.
+// The counts are added to sm.hist (zeroed by the caller).
+
+// Number of bytes of w equal to v (v < 128).
+__device__ __forceinline__ uint32_t bytes_equal(uint32_t w, uint32_t v) {
+  const uint32_t t = w ^ (v * 0x01010101u);
+  const uint32_t z = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t | 0x7F7F7F7Fu);
+  return __popc(z);
+}
+
+__device__ __forceinline__ void hist_add_words(VisitSmem& sm, int S, uint32_t w0, uint32_t w1, uint32_t w2,
+                                               uint32_t w3) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < kMaxStates; ++v) {
+    if (v <= S) {
+      const uint32_t c = bytes_equal(w0, v) + bytes_equal(w1, v) + bytes_equal(w2, v) + bytes_equal(w3, v);
+      const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, c);
+      if (lane == 0 && s) atomicAdd(&sm.hist[v], s);
+    }
+  }
+}
+
+// Uniform geometry: every thread takes one 16-byte piece of the interior and
+// at most one rim piece; excluded bytes are set to 0xFF (never a state).
+__device__ __forceinline__ void count_visit_uni(VisitSmem& sm, int S, int k, int sV, int sH, int sD) {
+  const int t = threadIdx.x;
+  const uint8_t* tile = sm.tile;
+  uint32_t w[4];
+  {
+    const int r = t >> 2, q = t & 3;
+    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    const uint2 a = src[0], b = src[1];
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+    if ((r == 0 || r == kUniB - 1) && sV > k) w[0] = w[1] = w[2] = w[3] = 0xFFFFFFFFu;
+    if (q == 0 && sH > k) w[0] |= 0xFFu;
+    if (q == 3 && sH > k) w[3] |= 0xFF000000u;
+  }
+  hist_add_words(sm, S, w[0], w[1], w[2], w[3]);
+  // rim pieces: threads 0..7 top/bottom rows (4 x 16 bytes each), threads
+  // 8..23 left/right columns (8 x 8 cells each)
+  uint32_t x[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+  if (t < 8 && sV < k) {
+    const int r = (t < 4) ? -1 : kUniB, q = t & 3;
+    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    const uint2 a = src[0], b = src[1];
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    if (q == 0 && sD > k) x[0] |= 0xFFu;
+    if (q == 3 && sD > k) x[3] |= 0xFF000000u;
+  } else if (t >= 8 && t < 24 && sH < k) {
+    const int j = t - 8, c = (j < 8) ? -1 : kUniB, r0 = (j & 7) * 8;
+    uint32_t p[2] = {0u, 0u};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int r = r0 + e;
+      uint32_t v = tile[tidx(r, c, kUniSP)];
+      if ((r == 0 || r == kUniB - 1) && sD > k) v = 0xFFu;
+      p[e >> 2] |= v << (8 * (e & 3));
+    }
+    x[0] = p[0];
+    x[1] = p[1];
+  }
+  hist_add_words(sm, S, x[0], x[1], x[2], x[3]);
+}
+
+// Any geometry: one site per thread iteration, shared-memory atomics.
+__device__ __forceinline__ void count_visit_generic(const LatticeDesc& d, int bx, int by, VisitSmem& sm,
+                                                    int k, int sV, int sH, int sD) {
+  const int bw = d.cs[bx + 1] - d.cs[bx], bh = d.cs[by + 1] - d.cs[by];
+  const int sp = tile_pitch(bw), W = bw + 2, H = bh + 2;
+  for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
+    const int r = e / W - 1, c = e % W - 1;
+    const bool rim_r = (r < 0 || r >= bh), rim_c = (c < 0 || c >= bw);
+    if (rim_r && rim_c) continue;
+    const bool end_r = (r == 0 || r == bh - 1), end_c = (c == 0 || c == bw - 1);
+    bool count;
+    if (rim_r)
+      count = sV < k && (!end_c || sD < k);
+    else if (rim_c)
+      count = sH < k && (!end_r || sD < k);
+    else
+      count = !(end_r && sV > k) && !(end_c && sH > k);
+    if (count) atomicAdd(&sm.hist[sm.tile[tidx(r, c, sp)]], 1u);
+  }
 }
 
 }  // namespace escg_impl

@@ -9,43 +9,61 @@
 
 namespace escg_impl {
 
+constexpr int kLogCap = 4096;   // ring of logged count vectors per lattice
+constexpr int kPendRing = 64;   // log points a persistent launch may have open
+
 // Device-side run state of one lattice (lives in device memory).
 struct RunState {
   uint32_t mcs;        // absolute MCS number the lattice has reached
   uint32_t stopped;    // stasis reached with stop_at_extinction
   uint32_t error;      // error bits (kErrTimeout, ...)
   uint32_t abort;      // set by a CTA that gave up; others leave quickly
-  uint32_t n_log;      // number of count-log entries written so far
+  uint32_t n_log;      // count-log entries written (entry i = log number log_num0 + i)
+  uint32_t log_num0;   // log number (MCS / log_every) of entry 0
   uint32_t ticket;     // work-item dispenser of the persistent kernel
-  uint32_t pad[2];
-  unsigned long long cur[kMaxStates];  // counts being accumulated
+  uint32_t exited;     // CTAs of the current persistent launch that have left
+  unsigned long long cur[kMaxStates];             // counts being accumulated
+  unsigned long long acc[kPendRing][kMaxStates];  // open log points (fused counts)
+  uint32_t pend[kPendRing];                       // blocks done per open log point
 };
 
 constexpr uint32_t kErrTimeout = 1u;
-constexpr int kLogCap = 4096;  // ring of logged count vectors per lattice
+
+struct LogBuffers {
+  unsigned long long* counts;  // [kLogCap][kMaxStates]
+  uint32_t* mcs;               // [kLogCap]
+};
 
 // Host-side launchers (all asynchronous on `stream`).
 void upload_perm_table();  // once per process/device
 cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream);
+cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t stream);
 // Accumulates the lattice histogram into st->cur (which must be zero).
 cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream);
-// After a chunk ending at MCS m_end: st->mcs = m_end (unless stopped); if
-// `log` appends st->cur to the ring (entry n_log, MCS m_end) and, with
-// stop_at_extinction, sets st->stopped when <= 1 species is alive.
-cudaError_t launch_finalize(const LatticeDesc& d, RunState* st, unsigned long long* log_counts,
-                            uint32_t* log_mcs, uint32_t m_end, int log, int stop_at_extinction,
-                            cudaStream_t stream);
+// After work ending at MCS m_end: st->mcs = m_end (unless stopped); if `log`
+// appends st->cur as the entry of MCS m_end and, with stop_at_extinction,
+// sets st->stopped when <= 1 species is alive.
+cudaError_t launch_finalize(const LatticeDesc& d, RunState* st, LogBuffers lb, uint32_t m_end,
+                            uint32_t log_every, int log, int stop_at_extinction, cudaStream_t stream);
 // One coarse phase (slot 0..3 of MCS m): one CTA per active block.
 cudaError_t launch_phase(const LatticeDesc& d, RunState* st, uint32_t m, int slot,
                          cudaStream_t stream);
-// MCS [m_begin, m_begin + n_mcs) in one persistent dataflow launch.
-// done: P*P epoch counters, zeroed by the caller together with st->ticket.
-// stall_block >= 0 (test hook) never publishes that block's epoch.
-cudaError_t launch_persistent(const LatticeDesc& d, RunState* st, uint32_t* done, uint32_t m_begin,
-                              uint32_t n_mcs, int grid, uint32_t spin_limit, int stall_block,
-                              cudaStream_t stream);
-// Occupancy-derived grid size of the persistent kernel.
-int persistent_grid(int device);
-int persistent_block_threads();
+
+struct PersistentArgs {
+  LatticeDesc d;
+  RunState* st;
+  uint32_t* done;        // [P*P] absolute MCS count each block has completed
+  LogBuffers lb;
+  uint32_t m_begin, n_mcs;
+  uint32_t log_every;
+  int32_t stop_at_extinction;
+  uint32_t spin_limit;
+  int32_t stall_block;   // test hook: never publish this block's epoch (-1: off)
+};
+// MCS [m_begin, m_begin + n_mcs) in one persistent dataflow launch, counts
+// of log points fused in.
+cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream);
+// Occupancy-derived grid size of the persistent kernel for a lattice.
+int persistent_grid(int device, bool uniform);
 
 }  // namespace escg_impl

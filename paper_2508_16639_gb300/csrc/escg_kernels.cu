@@ -10,7 +10,8 @@
 //                      work items in schedule order from a ticket counter and
 //                      start a block once its 8 neighbours have reached the
 //                      required epoch (bounded spin; gives up with an error
-//                      status instead of hanging)
+//                      status instead of hanging); species counts of log
+//                      points are fused into the visits
 #include <cstdio>
 
 #include "escg_device.cuh"
@@ -48,11 +49,8 @@ __global__ void init_kernel(LatticeDesc d, uint64_t T_empty) {
   }
 }
 
-// Number of bytes of w equal to v (v < 128): zero-byte count of w ^ v*0x01010101.
-__device__ __forceinline__ uint32_t bytes_equal(uint32_t w, uint32_t v) {
-  const uint32_t t = w ^ (v * 0x01010101u);
-  const uint32_t z = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t | 0x7F7F7F7Fu);
-  return __popc(z);
+__global__ void fill_u32_kernel(uint32_t* p, int n, uint32_t value) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) p[k] = value;
 }
 
 __global__ void count_kernel(LatticeDesc d, RunState* st) {
@@ -94,22 +92,33 @@ __global__ void count_kernel(LatticeDesc d, RunState* st) {
   }
 }
 
-__global__ void finalize_kernel(RunState* st, int S, unsigned long long* log_counts, uint32_t* log_mcs,
-                                uint32_t m_end, int log, int stop_at_extinction) {
+// Writes the log entry of MCS m_end from counts c[0..S]; stasis check.
+__device__ void write_log_entry(RunState* st, LogBuffers lb, int S, uint32_t m_end, uint32_t log_every,
+                                const unsigned long long* c, int stop_at_extinction) {
+  const uint32_t idx = m_end / log_every - st->log_num0;
+  const uint32_t slot = idx % (uint32_t)kLogCap;
+  int alive = 0;
+  for (int v = 0; v < kMaxStates; ++v) {
+    const unsigned long long x = (v <= S) ? c[v] : 0ull;
+    lb.counts[(size_t)slot * kMaxStates + v] = x;
+    if (v >= 1 && v <= S && x > 0) ++alive;
+  }
+  lb.mcs[slot] = m_end;
+  atomicMax(&st->n_log, idx + 1u);
+  if (stop_at_extinction && alive <= 1) st->stopped = 1;
+}
+
+__global__ void finalize_kernel(RunState* st, int S, LogBuffers lb, uint32_t m_end, uint32_t log_every,
+                                int log, int stop_at_extinction) {
   if (st->stopped) return;
   st->mcs = m_end;
   if (!log) return;
-  const uint32_t idx = st->n_log % (uint32_t)kLogCap;
-  int alive = 0;
+  unsigned long long c[kMaxStates];
   for (int v = 0; v < kMaxStates; ++v) {
-    const unsigned long long c = (v <= S) ? st->cur[v] : 0ull;
-    log_counts[(size_t)idx * kMaxStates + v] = c;
-    if (v >= 1 && v <= S && c > 0) ++alive;
+    c[v] = st->cur[v];
     st->cur[v] = 0;
   }
-  log_mcs[idx] = m_end;
-  st->n_log += 1;
-  if (stop_at_extinction && alive <= 1) st->stopped = 1;
+  write_log_entry(st, lb, S, m_end, log_every, c, stop_at_extinction);
 }
 
 // ---------------------------------------------------------------------------
@@ -121,65 +130,120 @@ __global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st,
   const int colour = order_at(colour_order(x.x), slot);
   const int half = d.P >> 1, j = blockIdx.x;
   const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
-  visit_block(d, bx, by, m, sm);
+  if (d.uniform64)
+    visit_uniform(d, bx, by, m, sm);
+  else
+    visit_generic(d, bx, by, m, sm);
 }
 
 // ---------------------------------------------------------------------------
 constexpr int kPersistentThreads = 256;
+constexpr int kUniMinBlocks = 6;
 
-__global__ void __launch_bounds__(kPersistentThreads, 4)
-    persistent_kernel(LatticeDesc d, RunState* st, uint32_t* done, uint32_t m_begin, uint32_t n_mcs,
-                      uint32_t spin_limit, int stall_block) {
+template <bool UNI>
+__global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
+    persistent_kernel(PersistentArgs a) {
   __shared__ VisitSmem sm;
-  __shared__ uint32_t s_item, s_ord, s_quit;
-  if (ld_volatile(&st->stopped)) return;
-  load_trans(d, sm.trans);
-  const int P = d.P, half = P >> 1;
-  const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
-  const uint64_t total = (uint64_t)n_mcs * nb;
+  __shared__ uint32_t s_item, s_ord, s_quit, s_abort;
+  const LatticeDesc& d = a.d;
+  RunState* st = a.st;
   const int tid = threadIdx.x;
-  for (;;) {
-    if (tid == 0) {
-      const uint32_t t = atomicAdd(&st->ticket, 1u);
-      s_item = t;
-      uint32_t quit = ((uint64_t)t >= total) || ld_volatile(&st->abort);
-      if (!quit) {
-        const uint32_t m = m_begin + t / nb;
-        s_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x);
-      }
-      s_quit = quit;
-    }
-    __syncthreads();
-    if (s_quit) break;
-    const uint32_t t = s_item, ord = s_ord;
-    const uint32_t mi = t / nb, rem = t - mi * nb;
-    const int k = (int)(rem / per), j = (int)(rem - (uint32_t)k * per);
-    const int colour = order_at(ord, k);
-    const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
-    if (tid < 9) {
-      const int dx = tid % 3 - 1, dy = tid / 3 - 1;
-      const int nx = (bx + dx + P) % P, ny = (by + dy + P) % P;
-      const int ncol = 2 * (ny & 1) + (nx & 1);
-      const uint32_t need = (tid == 4) ? mi : (slot_of(ord, ncol) < k ? mi + 1u : mi);
-      const uint32_t* flag = done + ny * P + nx;
-      uint32_t spins = 0;
-      while (ld_acquire(flag) < need) {
-        if (ld_volatile(&st->abort)) break;
-        if (++spins > spin_limit) {
-          atomicOr(&st->error, kErrTimeout);
-          atomicExch(&st->abort, 1u);
-          break;
+  const bool run = !ld_volatile(&st->stopped);
+  if (run) {
+    load_trans(d, sm.trans);
+    const int P = d.P, half = P >> 1;
+    const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
+    const uint64_t total = (uint64_t)a.n_mcs * nb;
+    for (;;) {
+      if (tid == 0) {
+        const uint32_t t = atomicAdd(&st->ticket, 1u);
+        s_item = t;
+        uint32_t quit = ((uint64_t)t >= total) || ld_volatile(&st->abort);
+        if (!quit) {
+          const uint32_t m = a.m_begin + t / nb;
+          s_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x);
         }
-        __nanosleep(64);
+        s_quit = quit;
+        s_abort = 0;
+      }
+      if (tid < kMaxStates) sm.hist[tid] = 0;
+      __syncthreads();
+      if (s_quit) break;
+      const uint32_t t = s_item, ord = s_ord;
+      const uint32_t mi = t / nb, rem = t - mi * nb;
+      const uint32_t m = a.m_begin + mi;
+      const int k = (int)(rem / per), j = (int)(rem - (uint32_t)k * per);
+      const int colour = order_at(ord, k);
+      const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
+      // Wait until the 8 neighbours (and the block itself) have completed
+      // every visit that precedes this one in schedule order.
+      if (tid < 9) {
+        const int dx = tid % 3 - 1, dy = tid / 3 - 1;
+        const int nx = (bx + dx + P) % P, ny = (by + dy + P) % P;
+        const int ncol = colour ^ ((dx & 1) | ((dy & 1) << 1));
+        const uint32_t need = (tid == 4) ? m : (slot_of(ord, ncol) < k ? m + 1u : m);
+        const uint32_t* flag = a.done + ny * P + nx;
+        uint32_t spins = 0;
+        while (ld_acquire(flag) < need) {
+          if (ld_volatile(&st->abort)) {
+            s_abort = 1;
+            break;
+          }
+          if (++spins > a.spin_limit) {
+            atomicOr(&st->error, kErrTimeout);
+            atomicExch(&st->abort, 1u);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __syncthreads();
+      if (s_abort) break;  // uniform across the CTA
+      if (UNI)
+        visit_uniform(d, bx, by, m, sm);
+      else
+        visit_generic(d, bx, by, m, sm);
+      const bool log_point = ((m + 1u) % a.log_every) == 0u;
+      if (log_point) {
+        const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1),
+                  sD = slot_of(ord, colour ^ 3);
+        if (UNI)
+          count_visit_uni(sm, d.S, k, sV, sH, sD);
+        else
+          count_visit_generic(d, bx, by, sm, k, sV, sH, sD);
+      }
+      __syncthreads();
+      if (log_point) {
+        const uint32_t ring = ((m + 1u) / a.log_every) % (uint32_t)kPendRing;
+        if (tid <= d.S && sm.hist[tid]) atomicAdd(&st->acc[ring][tid], (unsigned long long)sm.hist[tid]);
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          if (atomicAdd(&st->pend[ring], 1u) == nb - 1u) {
+            // last block of this log point: every contribution is in acc
+            __threadfence();
+            unsigned long long c[kMaxStates];
+            for (int v = 0; v < kMaxStates; ++v) c[v] = atomicExch(&st->acc[ring][v], 0ull);
+            st->pend[ring] = 0;
+            write_log_entry(st, a.lb, d.S, m + 1u, a.log_every, c, a.stop_at_extinction);
+          }
+        }
+      }
+      if (tid == 0 && by * P + bx != a.stall_block) {
+        __threadfence();
+        st_release(a.done + by * P + bx, m + 1u);
       }
     }
-    __syncthreads();
-    if (ld_volatile(&st->abort)) break;
-    visit_block(d, bx, by, m_begin + mi, sm);
-    __syncthreads();
-    if (tid == 0 && by * P + bx != stall_block) {
-      __threadfence();
-      st_release(done + by * P + bx, mi + 1u);
+  }
+  // The last CTA to leave publishes the MCS number and resets the
+  // dispensers for the next launch on this stream.
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&st->exited, 1u) == gridDim.x - 1u) {
+      st->exited = 0;
+      st->ticket = 0;
+      if (!st->stopped && !st->abort) st->mcs = a.m_begin + a.n_mcs;
     }
   }
 }
@@ -210,16 +274,20 @@ cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t str
   return cudaGetLastError();
 }
 
+cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t stream) {
+  fill_u32_kernel<<<blocks_for((size_t)n, 256, 152 * 4), 256, 0, stream>>>(p, n, value);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream) {
   const size_t n = (size_t)d.L * (d.pitch / 16);
   count_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const LatticeDesc& d, RunState* st, unsigned long long* log_counts,
-                            uint32_t* log_mcs, uint32_t m_end, int log, int stop_at_extinction,
-                            cudaStream_t stream) {
-  finalize_kernel<<<1, 1, 0, stream>>>(st, d.S, log_counts, log_mcs, m_end, log, stop_at_extinction);
+cudaError_t launch_finalize(const LatticeDesc& d, RunState* st, LogBuffers lb, uint32_t m_end,
+                            uint32_t log_every, int log, int stop_at_extinction, cudaStream_t stream) {
+  finalize_kernel<<<1, 1, 0, stream>>>(st, d.S, lb, m_end, log_every, log, stop_at_extinction);
   return cudaGetLastError();
 }
 
@@ -229,22 +297,23 @@ cudaError_t launch_phase(const LatticeDesc& d, RunState* st, uint32_t m, int slo
   return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(const LatticeDesc& d, RunState* st, uint32_t* done, uint32_t m_begin,
-                              uint32_t n_mcs, int grid, uint32_t spin_limit, int stall_block,
-                              cudaStream_t stream) {
-  persistent_kernel<<<grid, kPersistentThreads, 0, stream>>>(d, st, done, m_begin, n_mcs, spin_limit,
-                                                             stall_block);
+cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream) {
+  if (a.d.uniform64)
+    persistent_kernel<true><<<grid, kPersistentThreads, 0, stream>>>(a);
+  else
+    persistent_kernel<false><<<grid, kPersistentThreads, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
-int persistent_grid(int device) {
+int persistent_grid(int device, bool uniform) {
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, kPersistentThreads, 0);
+  if (uniform)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<true>, kPersistentThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<false>, kPersistentThreads, 0);
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;
 }
-
-int persistent_block_threads() { return kPersistentThreads; }
 
 }  // namespace escg_impl

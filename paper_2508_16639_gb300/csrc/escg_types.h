@@ -27,10 +27,11 @@ struct LatticeDesc {
   const int32_t* cs;    // [P+1] coarse segment starts
   const int32_t* fs;    // [GQ+1] fine segment starts (global coordinates)
   const int32_t* fc;    // [P+1] first global fine index of each coarse segment
-  const uint8_t* trans; // [3][S+1][S+1]: new (a | b << 4) for (action, a, b)
+  const uint8_t* trans; // [(S+1)*(S+1)][4]: byte (a*(S+1)+b)*4 + action holds
+                        // the new pair (a' | b' << 4)
   uint32_t key0, key1;  // Philox key (seed)
-  uint32_t tx, txi;     // thresholds, low 32 bits
-  uint32_t tx_all, txi_all;  // 1 when the threshold is 2^32 (always)
+  uint32_t tx, txi;     // thresholds; 2^32 stored as 0xFFFFFFFF (exact: the
+                        // action draw u is always a multiple of 4)
   int32_t S;
   int32_t uniform64;    // all blocks 64x64 and all sub-blocks 2x2
 };

@@ -133,10 +133,29 @@ def test_counts_log_matches_oracle():
     assert np.array_equal(g.snapshot(), lat)
 
 
-@pytest.mark.parametrize("persistent", [True, False], ids=["persistent", "phase"])
-def test_stop_at_extinction_matches_oracle(persistent):
-    L, S, K, I, P, seed = 16, 3, (1,), 1.0, 1.0, 5
-    X = O.exchange_from_mobility(0.1, L * L)
+@pytest.mark.parametrize("L,S,log_every", [(128, 3, 1), (128, 5, 7), (192, 3, 3), (256, 5, 2),
+                                           (67, 3, 5)])
+def test_fused_counts_log_matches_oracle(L, S, log_every):
+    """Counts of log points fused into the persistent kernel (each site
+    counted by the last block that touches it in the MCS) equal the
+    oracle's histogram after that MCS; uniform (L=128, 256) and non-uniform
+    partitions, several log points open in one launch."""
+    K, I, P, X, seed = ((1,) if S == 3 else (1, 2)), 1.0, 1.0, 2.0 + L / 64, 4242 + L
+    g, o, D = _pair(L, S, K, 0.2, I, P, X, seed, log_every=log_every)
+    n = 6 * log_every + 1
+    g.run(n)
+    lat, log, mend = O.run_observed(o, D, I, P, X, seed, n, log_every=log_every)
+    ms, glog = g.counts_log()
+    assert list(ms) == list(range(0, n + 1, log_every))
+    assert np.array_equal(glog, log)
+    assert np.array_equal(g.snapshot(), lat)
+    assert g.mcs == n
+
+
+@pytest.mark.parametrize("L,persistent", [(16, True), (16, False), (128, True)])
+def test_stop_at_extinction_matches_oracle(L, persistent):
+    S, K, I, P, seed = 3, (1,), 1.0, 1.0, 5
+    X = O.exchange_from_mobility(0.1 if L == 16 else 0.02, L * L)
     g, o, D = _pair(L, S, K, 0.25, I, P, X, seed, log_every=10, stop_at_extinction=True,
                     persistent=persistent)
     g.run(3000)
