@@ -154,8 +154,9 @@ def test_fused_counts_log_matches_oracle(L, S, log_every):
 
 @pytest.mark.parametrize("L,persistent", [(16, True), (16, False), (128, True)])
 def test_stop_at_extinction_matches_oracle(L, persistent):
-    S, K, I, P, seed = 3, (1,), 1.0, 1.0, 5
-    X = O.exchange_from_mobility(0.1 if L == 16 else 0.02, L * L)
+    S, K, I, P = 3, (1,), 1.0, 1.0
+    seed = 5 if L == 16 else 6   # both go extinct within the budget
+    X = O.exchange_from_mobility(0.1 if L == 16 else 3e-4, L * L)
     g, o, D = _pair(L, S, K, 0.25, I, P, X, seed, log_every=10, stop_at_extinction=True,
                     persistent=persistent)
     g.run(3000)
