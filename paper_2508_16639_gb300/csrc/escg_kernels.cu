@@ -105,7 +105,10 @@ __device__ void write_log_entry(RunState* st, LogBuffers lb, int S, uint32_t m_e
   }
   lb.mcs[slot] = m_end;
   atomicMax(&st->n_log, idx + 1u);
-  if (stop_at_extinction && alive <= 1) st->stopped = 1;
+  if (stop_at_extinction && alive <= 1) {
+    st->mcs = m_end;
+    st->stopped = 1;
+  }
 }
 
 __global__ void finalize_kernel(RunState* st, int S, LogBuffers lb, uint32_t m_end, uint32_t log_every,
