@@ -606,17 +606,23 @@ int escg_restore(escg_t* h, const uint8_t* host_lattice, uint64_t mcs) {
     set_err("mcs exceeds 2^32-1");
     return ESCG_EINVAL;
   }
-  const size_t N = (size_t)h->L * h->L;
-  for (size_t i = 0; i < N; ++i)
-    if (host_lattice[i] > h->S) {
-      set_err("lattice value %d at %zu exceeds S=%d", host_lattice[i], i, h->S);
-      return ESCG_EINVAL;
-    }
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   CUDA_TRY(cudaMemcpy2DAsync(h->lattice, h->pitch, host_lattice, h->L, h->L, h->L, cudaMemcpyHostToDevice,
                              h->stream));
+  // values are checked on the device (reset_state synchronises)
+  uint32_t* bad = &h->d_scratch->error;
+  CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(uint32_t), h->stream));
+  CUDA_TRY(launch_validate(h->desc, bad, h->stream));
+  h->launches++;
   const int rc = reset_state(h, mcs);
   if (rc != ESCG_OK) return rc;
+  uint32_t flag = 0;
+  CUDA_TRY(cudaMemcpy(&flag, bad, sizeof flag, cudaMemcpyDeviceToHost));
+  if (flag) {
+    h->failed = true;
+    set_err("restored lattice holds a value outside 0..S=%d; restore a valid lattice", h->S);
+    return ESCG_EINVAL;
+  }
   return ESCG_OK;
 }
 

@@ -38,6 +38,8 @@ struct LogBuffers {
 void upload_perm_table();  // once per process/device
 cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream);
 cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t stream);
+// Sets *bad = 1 if any lattice byte is outside 0..S.
+cudaError_t launch_validate(const LatticeDesc& d, uint32_t* bad, cudaStream_t stream);
 // Accumulates the lattice histogram into st->cur (which must be zero).
 cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream);
 // After work ending at MCS m_end: st->mcs = m_end (unless stopped); if `log`

@@ -49,6 +49,31 @@ __global__ void init_kernel(LatticeDesc d, uint64_t T_empty) {
   }
 }
 
+// Flags (*bad = 1) any lattice byte outside 0..S (padding bytes excluded).
+__global__ void validate_kernel(LatticeDesc d, uint32_t* bad) {
+  const int L = d.L, pitch = d.pitch, vec_per_row = pitch / 16;
+  const uint32_t lim = 0x7Fu - (uint32_t)d.S;  // byte + lim has bit 7 set iff byte > S (byte < 128)
+  const size_t total = (size_t)L * vec_per_row;
+  uint32_t any = 0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(k / vec_per_row), q = (int)(k % vec_per_row);
+    uint4 w = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)row * pitch) + q);
+    uint32_t* p = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int valid = L - (16 * q + 4 * e);
+      uint32_t x = p[e];
+      if (valid <= 0)
+        x = 0;
+      else if (valid < 4)
+        x &= 0xFFFFFFFFu >> (8 * (4 - valid));
+      any |= (x | ((x & 0x7F7F7F7Fu) + lim * 0x01010101u)) & 0x80808080u;
+    }
+  }
+  if (__any_sync(0xFFFFFFFFu, any != 0) && (threadIdx.x & 31) == 0) atomicExch(bad, 1u);
+}
+
 __global__ void fill_u32_kernel(uint32_t* p, int n, uint32_t value) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) p[k] = value;
 }
@@ -279,6 +304,12 @@ cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t str
 
 cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t stream) {
   fill_u32_kernel<<<blocks_for((size_t)n, 256, 152 * 4), 256, 0, stream>>>(p, n, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const LatticeDesc& d, uint32_t* bad, cudaStream_t stream) {
+  const size_t n = (size_t)d.L * (d.pitch / 16);
+  validate_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, bad);
   return cudaGetLastError();
 }
 

@@ -251,3 +251,20 @@ def test_kernel_timing_counts_launches():
     ms, n = g.kernel_time()
     assert n == 3 and ms > 0
     assert E.int_throughput()[0] > 1e12
+
+
+def test_restore_rejects_values_outside_states():
+    L, S = 40, 3
+    g = E.Lattice(L, S, E.circulant(S, [1]), (1.0, 1.0, 1.0), 3, p_empty=0.25)
+    good = g.snapshot()
+    bad = good.copy()
+    bad[L - 1, L - 1] = S + 1
+    with pytest.raises(E.EscgError) as ei:
+        g.restore(bad, 0)
+    assert ei.value.status == -1
+    with pytest.raises(E.EscgError):
+        g.run(1)
+    g.restore(good, 0)
+    g.run(2)
+    o, _ = O.replay_run(good, O.circulant(S, [1]), 1.0, 1.0, 1.0, 3, 2)
+    assert np.array_equal(g.snapshot(), o)
