@@ -70,8 +70,10 @@ typedef struct {
     int32_t stop_at_extinction;  /* stop at the first logged MCS with <= 1
                                     non-empty species alive (stasis())        */
     uint32_t schedule_version;   /* 0 or 1 (only version 1 exists)            */
-    int32_t persistent;          /* 1: one persistent dataflow launch per run
-                                    (default); 0: one launch per coarse phase */
+    int32_t persistent;          /* 1: persistent dataflow launches (default;
+                                    tiles staged by TMA where the partition is
+                                    uniform 64x64); 2: persistent with plain
+                                    loads; 0: one launch per coarse phase     */
     void* cuda_stream;           /* cudaStream_t to enqueue on, or NULL for a
                                     stream owned by the handle                */
     void* device_lattice;        /* optional caller-owned device buffer of

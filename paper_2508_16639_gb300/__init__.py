@@ -72,7 +72,7 @@ class Lattice:
         opt.p_empty = float(p_empty)
         opt.log_every = int(log_every)
         opt.stop_at_extinction = int(bool(stop_at_extinction))
-        opt.persistent = int(bool(persistent))
+        opt.persistent = int(persistent)
         opt.time_kernels = int(bool(time_kernels))
         if stream is not None:
             opt.cuda_stream = int(getattr(stream, "cuda_stream", stream))

@@ -1,6 +1,8 @@
 // escg_api.cu -- the C ABI of libescg (include/escg.h): handle life cycle,
 // host-side set-up (partition tables, integer thresholds, transition table;
 // SURVEY rows A1/A2) and run orchestration on the handle's stream.
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -84,6 +86,29 @@ Partition make_partition(int L) {
   return p;
 }
 
+// 2-D uint8 tensor map of a lattice for the TMA tile loads: dims L x L
+// (columns beyond L are out of bounds and read as zero), row stride pitch,
+// box 112 x 66 bytes.
+bool make_tensor_map(CUtensorMap* map, uint8_t* lattice, int L, int pitch) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)L, (cuuint64_t)L};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+  const cuuint32_t box[2] = {112u, 66u};
+  const cuuint32_t elem[2] = {1u, 1u};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, lattice, dims, strides, box, elem,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool partition_fits(const Partition& p) {
   for (int k = 0; k < p.P; ++k) {
     if (p.cs[k + 1] - p.cs[k] > kMaxBlock) return false;
@@ -156,6 +181,8 @@ struct escg {
   uint64_t launches = 0;
   uint64_t T_empty = 0;
   int grid = 0;
+  bool use_tma = false;
+  CUtensorMap tmap{};
   uint32_t spin_limit = kDefaultSpinLimit;
   int stall_block = -1;
   uint32_t log_num0_host = 0;
@@ -427,6 +454,10 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   d.trans = h->d_trans;
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    d.rk[2 * r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
+    d.rk[2 * r + 1] = d.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   // 2^32 ("always") becomes 0xFFFFFFFF: exact, since every action draw u
   // is a multiple of 4 and so never equals 0xFFFFFFFF
   d.tx = tx >> 32 ? 0xFFFFFFFFu : (uint32_t)tx;
@@ -437,6 +468,14 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   for (int k = 0; k < p.GQ; ++k) uni = uni && (p.fs[k + 1] - p.fs[k] == 2);
   d.uniform64 = (uni && h->pitch % 16 == 0) ? 1 : 0;
   h->grid = persistent_grid(h->device, d.uniform64 != 0);
+  if (d.uniform64 && o.persistent == 1) {
+    if (!make_tensor_map(&h->tmap, h->lattice, L, h->pitch)) {
+      set_err("cuTensorMapEncodeTiled failed for L=%d", L);
+      return fail(ESCG_ECUDA);
+    }
+    h->use_tma = true;
+    h->grid = persistent_tma_grid(h->device);
+  }
 
   if (launch_init(d, h->T_empty, h->stream) != cudaSuccess) {
     set_err("init kernel launch failed");
@@ -497,7 +536,14 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
       a.spin_limit = h->spin_limit;
       a.stall_block = h->stall_block;
       CUDA_TRY(timing_begin(h));
-      CUDA_TRY(launch_persistent(a, grid, h->stream));
+      if (h->use_tma) {
+        TmaArgs ta{};
+        ta.map = h->tmap;
+        ta.p = a;
+        CUDA_TRY(launch_persistent_tma(ta, grid, h->stream));
+      } else {
+        CUDA_TRY(launch_persistent(a, grid, h->stream));
+      }
       CUDA_TRY(timing_end(h));
       h->launches++;
       h->mcs_enq = end;

@@ -36,6 +36,20 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// Same, with the ten round keys precomputed (rk[2r], rk[2r+1] = key + r *
+// Weyl constants); rk points into the kernel's parameter space, so the keys
+// are constant-bank operands of the XORs rather than per-thread additions.
+__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t* __restrict__ rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * r + 1], (uint32_t)p0);
+  }
+  return c;
+}
+
 // The 24 orders of the four colours, lexicographic; entry = 4 x 2-bit
 // colours, first colour in the lowest bits.
 __device__ __constant__ uint8_t c_perm24[24];
@@ -103,18 +117,24 @@ constexpr int kUniB = 64;
 constexpr int kUniSP = 80;   // tile_pitch(64)
 constexpr int kUniThreads = 256;
 
-// One elementary step on a 2x2 sub-block: 4*n_k = 16, so the high 4 bits of
-// w are (row, col, dir) and u = w << 4.
+// One elementary step on a 2x2 sub-block of a tile with row pitch SP (a
+// value < 128 whose bits the sign mask can select): 4*n_k = 16, so the high
+// 4 bits of w are (row, col, dir) and u = w << 4.
+template <int SP>
 __device__ __forceinline__ void attempt_uni(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
                                             uint32_t w, int base, uint32_t tx, uint32_t txi, uint32_t s1) {
+  static_assert(SP < 128, "row offset is selected with a sign mask");
   const uint32_t u = w << 4;
-  const int row80 = ((int32_t)w >> 31) & kUniSP;
+  const int rowoff = ((int32_t)w >> 31) & SP;
   const int col = (int)((w >> 30) & 1u);
-  const int ti = base + row80 + col;
-  const int mag = (w & (1u << 29)) ? 1 : kUniSP;
+  const int ti = base + rowoff + col;
+  const int mag = (w & (1u << 29)) ? 1 : SP;
   const int tj = ti + ((w & (1u << 28)) ? mag : -mag);
   apply_rule(tile, trans, ti, tj, u, tx, txi, s1);
 }
+
+template <int SP, int COFF>
+__device__ __forceinline__ int tidx_u(int r, int c) { return (r + 1) * SP + c + COFF; }
 
 // Loads block interior + the four 1-site rim strips (no corners) into the
 // tile through L2 (ld.global.cg: data written by other CTAs of the same
@@ -195,7 +215,7 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
   const int x0 = bx * kUniB, y0 = by * kUniB;
   const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
   if (t == 0) {
-    const uint4 x = philox10(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.key0, d.key1);
+    const uint4 x = philox10_rk(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.rk);
     sm.forder = colour_order(x.x);
   }
   load_tile_uni(d, x0, y0, sm.tile);
@@ -209,11 +229,11 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
     const int cx = fcol & 1, cy = fcol >> 1;
     const uint32_t g = (gy0 + (uint32_t)cy) * (uint32_t)d.GQ + gx0 + (uint32_t)cx;
     const int base = tidx(4 * qy + 2 * cy, 4 * qx + 2 * cx, kUniSP);
-    const uint4 x = philox10(make_uint4(0u, g, m, kTagStep), d.key0, d.key1);
-    attempt_uni(sm.tile, trans, x.x, base, tx, txi, s1);
-    attempt_uni(sm.tile, trans, x.y, base, tx, txi, s1);
-    attempt_uni(sm.tile, trans, x.z, base, tx, txi, s1);
-    attempt_uni(sm.tile, trans, x.w, base, tx, txi, s1);
+    const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
+    attempt_uni<kUniSP>(sm.tile, trans, x.x, base, tx, txi, s1);
+    attempt_uni<kUniSP>(sm.tile, trans, x.y, base, tx, txi, s1);
+    attempt_uni<kUniSP>(sm.tile, trans, x.z, base, tx, txi, s1);
+    attempt_uni<kUniSP>(sm.tile, trans, x.w, base, tx, txi, s1);
     __syncthreads();
   }
   store_tile_uni(d, x0, y0, sm.tile);
@@ -231,7 +251,7 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
   for (int k = tid; k <= Qx; k += nthr) sm.fsx[k] = (int16_t)(d.fs[fx0 + k] - x0);
   for (int k = tid; k <= Qy; k += nthr) sm.fsy[k] = (int16_t)(d.fs[fy0 + k] - y0);
   if (tid == 0) {
-    const uint4 x = philox10(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.key0, d.key1);
+    const uint4 x = philox10_rk(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.rk);
     sm.forder = colour_order(x.x);
   }
   load_tile_generic(d, x0, y0, bw, bh, sm.tile, sp);
@@ -253,7 +273,7 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
       const uint32_t inv_wx = (65536u + (uint32_t)wx - 1u) / (uint32_t)wx;
       const int base = tidx(sy, sx, sp);
       for (uint32_t j = 0; 4u * j < nk; ++j) {
-        const uint4 x = philox10(make_uint4(j, g, m, kTagStep), d.key0, d.key1);
+        const uint4 x = philox10_rk(make_uint4(j, g, m, kTagStep), d.rk);
         const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e)
@@ -287,7 +307,7 @@ __device__ __forceinline__ uint32_t bytes_equal(uint32_t w, uint32_t v) {
   return __popc(z);
 }
 
-__device__ __forceinline__ void hist_add_words(VisitSmem& sm, int S, uint32_t w0, uint32_t w1, uint32_t w2,
+__device__ __forceinline__ void hist_add_words(uint32_t* hist, int S, uint32_t w0, uint32_t w1, uint32_t w2,
                                                uint32_t w3) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -295,33 +315,35 @@ __device__ __forceinline__ void hist_add_words(VisitSmem& sm, int S, uint32_t w0
     if (v <= S) {
       const uint32_t c = bytes_equal(w0, v) + bytes_equal(w1, v) + bytes_equal(w2, v) + bytes_equal(w3, v);
       const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, c);
-      if (lane == 0 && s) atomicAdd(&sm.hist[v], s);
+      if (lane == 0 && s) atomicAdd(&hist[v], s);
     }
   }
 }
 
-// Uniform geometry: every thread takes one 16-byte piece of the interior and
-// at most one rim piece; excluded bytes are set to 0xFF (never a state).
-__device__ __forceinline__ void count_visit_uni(VisitSmem& sm, int S, int k, int sV, int sH, int sD) {
+// Uniform geometry (64x64 blocks, 256 threads): every thread takes one
+// 16-byte piece of the interior and at most one rim piece; excluded bytes are
+// set to 0xFF (never a state).  hist: per-CTA histogram in shared memory.
+template <int SP, int COFF>
+__device__ __forceinline__ void count_visit_uni(const uint8_t* tile, uint32_t* hist, int S, int k, int sV,
+                                                int sH, int sD) {
   const int t = threadIdx.x;
-  const uint8_t* tile = sm.tile;
   uint32_t w[4];
   {
     const int r = t >> 2, q = t & 3;
-    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx_u<SP, COFF>(r, 16 * q));
     const uint2 a = src[0], b = src[1];
     w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
     if ((r == 0 || r == kUniB - 1) && sV > k) w[0] = w[1] = w[2] = w[3] = 0xFFFFFFFFu;
     if (q == 0 && sH > k) w[0] |= 0xFFu;
     if (q == 3 && sH > k) w[3] |= 0xFF000000u;
   }
-  hist_add_words(sm, S, w[0], w[1], w[2], w[3]);
+  hist_add_words(hist, S, w[0], w[1], w[2], w[3]);
   // rim pieces: threads 0..7 top/bottom rows (4 x 16 bytes each), threads
   // 8..23 left/right columns (8 x 8 cells each)
   uint32_t x[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
   if (t < 8 && sV < k) {
     const int r = (t < 4) ? -1 : kUniB, q = t & 3;
-    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx_u<SP, COFF>(r, 16 * q));
     const uint2 a = src[0], b = src[1];
     x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
     if (q == 0 && sD > k) x[0] |= 0xFFu;
@@ -332,14 +354,14 @@ __device__ __forceinline__ void count_visit_uni(VisitSmem& sm, int S, int k, int
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int r = r0 + e;
-      uint32_t v = tile[tidx(r, c, kUniSP)];
+      uint32_t v = tile[tidx_u<SP, COFF>(r, c)];
       if ((r == 0 || r == kUniB - 1) && sD > k) v = 0xFFu;
       p[e >> 2] |= v << (8 * (e & 3));
     }
     x[0] = p[0];
     x[1] = p[1];
   }
-  hist_add_words(sm, S, x[0], x[1], x[2], x[3]);
+  hist_add_words(hist, S, x[0], x[1], x[2], x[3]);
 }
 
 // Any geometry: one site per thread iteration, shared-memory atomics.

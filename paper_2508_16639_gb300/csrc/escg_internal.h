@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "escg_types.h"
@@ -67,5 +68,15 @@ struct PersistentArgs {
 cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream);
 // Occupancy-derived grid size of the persistent kernel for a lattice.
 int persistent_grid(int device, bool uniform);
+
+// Uniform geometry (64x64 blocks): TMA-staged, warp-specialised variant.
+// map: 2-D uint8 tensor map of the lattice (dims L x L, row stride pitch,
+// box 112 x 66).
+struct alignas(64) TmaArgs {
+  CUtensorMap map;
+  PersistentArgs p;
+};
+cudaError_t launch_persistent_tma(const TmaArgs& a, int grid, cudaStream_t stream);
+int persistent_tma_grid(int device);
 
 }  // namespace escg_impl

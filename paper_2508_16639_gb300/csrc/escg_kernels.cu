@@ -16,6 +16,7 @@
 
 #include "escg_device.cuh"
 #include "escg_internal.h"
+#include "escg_tma.cuh"
 
 namespace escg_impl {
 
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
         const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1),
                   sD = slot_of(ord, colour ^ 3);
         if (UNI)
-          count_visit_uni(sm, d.S, k, sV, sH, sD);
+          count_visit_uni<kUniSP, kColOff>(sm.tile, sm.hist, d.S, k, sV, sH, sD);
         else
           count_visit_generic(d, bx, by, sm, k, sV, sH, sD);
       }
@@ -272,6 +273,272 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
       st->exited = 0;
       st->ticket = 0;
       if (!st->stopped && !st->abort) st->mcs = a.m_begin + a.n_mcs;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised persistent kernel for the uniform geometry (64x64 blocks,
+// 2x2 sub-blocks).  Warp 8 is the producer: it takes the next work item from
+// the ticket counter, waits for the block's 8 neighbours, and stages the
+// block + rim into one of two shared-memory tiles with a single TMA box load
+// (112 x 66 bytes from (x0-16, y0-1); the wrap-around rim cells of blocks on
+// the lattice edge, which the box fills with zeros, are patched afterwards
+// with plain loads).  Warps 0..7 (the consumers) run the four fine colour
+// phases on the other tile, write the block back, count log points and
+// publish the block's epoch.  The producer's waits and copies overlap the
+// consumers' arithmetic.
+constexpr int kTmaSP = 112, kTmaColOff = 16, kTmaRows = kUniB + 2;
+constexpr uint32_t kTmaBoxBytes = (uint32_t)(kTmaSP * kTmaRows);   // 7392
+constexpr int kTmaTileStride = 7424;                               // 128-byte multiple
+constexpr int kTmaConsumers = 256, kTmaThreads = kTmaConsumers + 32;
+constexpr uint32_t kMbarLimit = 1u << 26;
+
+struct TmaItem {
+  uint32_t m, ord, forder, quit;
+  int32_t k, bx, by, colour;
+};
+
+struct TmaSmem {
+  alignas(128) uint8_t tile[2][kTmaTileStride];
+  uint32_t trans[kMaxStates * kMaxStates];
+  alignas(8) uint64_t full[2], empty[2], tma[2];
+  TmaItem item[2];
+  uint32_t hist[kMaxStates];
+};
+
+__device__ __forceinline__ int tix(int r, int c) { return tidx_u<kTmaSP, kTmaColOff>(r, c); }
+
+__device__ __forceinline__ void tma_fail(RunState* st) {
+  atomicOr(&st->error, kErrTimeout);
+  atomicExch(&st->abort, 1u);
+}
+
+__device__ void tma_producer(const TmaArgs& a, TmaSmem& sm) {
+  const PersistentArgs& p = a.p;
+  const LatticeDesc& d = p.d;
+  RunState* st = p.st;
+  const int lane = threadIdx.x & 31;
+  const int P = d.P, half = P >> 1, L = d.L, pitch = d.pitch;
+  const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
+  const uint64_t total = (uint64_t)p.n_mcs * nb;
+  for (uint32_t n = 0;; ++n) {
+    const int b = (int)(n & 1u);
+    const uint32_t use = n >> 1;
+    uint32_t t = 0, quit = 0;
+    if (lane == 0) {
+      t = atomicAdd(&st->ticket, 1u);
+      quit = ((uint64_t)t >= total) || ld_volatile(&st->abort);
+      // the consumers must have released this buffer
+      if (!mbar_wait(&sm.empty[b], (use & 1u) ^ 1u, kMbarLimit)) {
+        tma_fail(st);
+        quit = 1;
+      }
+    }
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    quit = __shfl_sync(0xFFFFFFFFu, quit, 0);
+    uint32_t m = 0, ord = 0, forder = 0;
+    int k = 0, colour = 0, bx = 0, by = 0;
+    if (!quit) {
+      const uint32_t mi = t / nb, rem = t - mi * nb;
+      m = p.m_begin + mi;
+      k = (int)(rem / per);
+      const int j = (int)(rem - (uint32_t)k * per);
+      ord = colour_order(philox10_rk(make_uint4(0u, 0u, m, kTagOrder), d.rk).x);
+      colour = order_at(ord, k);
+      bx = 2 * (j % half) + (colour & 1);
+      by = 2 * (j / half) + (colour >> 1);
+      // wait until the 8 neighbours (and the block itself) have completed
+      // every visit that precedes this one in schedule order
+      uint32_t fail = 0;
+      if (lane < 9) {
+        const int dx = lane % 3 - 1, dy = lane / 3 - 1;
+        const int nx = (bx + dx + P) % P, ny = (by + dy + P) % P;
+        const int ncol = colour ^ ((dx & 1) | ((dy & 1) << 1));
+        const uint32_t need = (lane == 4) ? m : (slot_of(ord, ncol) < k ? m + 1u : m);
+        const uint32_t* flag = p.done + ny * P + nx;
+        uint32_t spins = 0;
+        while (ld_acquire(flag) < need) {
+          if (ld_volatile(&st->abort)) {
+            fail = 1;
+            break;
+          }
+          if (++spins > p.spin_limit) {
+            tma_fail(st);
+            fail = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+        // what was acquired above is read next through the async proxy
+        fence_proxy_async_global();
+      }
+      quit = __any_sync(0xFFFFFFFFu, fail != 0);
+      if (lane == 1)
+        forder = colour_order(
+            philox10_rk(make_uint4(0u, (uint32_t)(by * P + bx), m, kTagFineOrder), d.rk).x);
+      forder = __shfl_sync(0xFFFFFFFFu, forder, 1);
+    }
+    if (!quit) {
+      const int x0 = bx * kUniB, y0 = by * kUniB;
+      uint8_t* tile = sm.tile[b];
+      uint32_t ok = 1;
+      if (lane == 0) {
+        fence_proxy_async_smem();  // the consumers' writes to this tile precede the TMA's
+        mbar_arrive_expect_tx(&sm.tma[b], kTmaBoxBytes);
+        tma_load_2d(tile, &a.map, x0 - kTmaColOff, y0 - 1, &sm.tma[b]);
+        if (!mbar_wait(&sm.tma[b], use & 1u, kMbarLimit)) {
+          tma_fail(st);
+          // do not leave a copy in flight into this CTA's shared memory
+          ok = mbar_wait(&sm.tma[b], use & 1u, kMbarLimit) ? 0u : 2u;
+        }
+      }
+      ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+      if (ok != 1u) {
+        quit = 1;
+      } else {
+        // wrap-around rim cells the box filled with zeros
+        if (by == 0 && lane < 4) {
+          const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(L - 1) * pitch + x0) + lane);
+          *reinterpret_cast<uint4*>(tile + tix(-1, 16 * lane)) = v;
+        }
+        if (by == P - 1 && lane >= 4 && lane < 8) {
+          const int q = lane - 4;
+          const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + x0) + q);
+          *reinterpret_cast<uint4*>(tile + tix(kUniB, 16 * q)) = v;
+        }
+        if (bx == 0) {
+          tile[tix(lane, -1)] = __ldcg(d.lat + (size_t)(y0 + lane) * pitch + (L - 1));
+          tile[tix(lane + 32, -1)] = __ldcg(d.lat + (size_t)(y0 + lane + 32) * pitch + (L - 1));
+        }
+        if (bx == P - 1) {
+          tile[tix(lane, kUniB)] = __ldcg(d.lat + (size_t)(y0 + lane) * pitch);
+          tile[tix(lane + 32, kUniB)] = __ldcg(d.lat + (size_t)(y0 + lane + 32) * pitch);
+        }
+        if (lane == 0) {
+          TmaItem& it = sm.item[b];
+          it.m = m; it.ord = ord; it.forder = forder; it.quit = 0;
+          it.k = k; it.bx = bx; it.by = by; it.colour = colour;
+        }
+      }
+    }
+    if (quit && lane == 0) sm.item[b].quit = 1;
+    __syncwarp();
+    mbar_arrive(&sm.full[b]);   // 32 arrivals complete the phase
+    if (quit) break;
+  }
+}
+
+__device__ void tma_consumer(const TmaArgs& a, TmaSmem& sm) {
+  const PersistentArgs& p = a.p;
+  const LatticeDesc& d = p.d;
+  RunState* st = p.st;
+  const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
+  const int P = d.P, L = d.L, pitch = d.pitch;
+  const uint32_t nb = (uint32_t)(P * P), s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
+  const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
+  for (uint32_t n = 0;; ++n) {
+    const int b = (int)(n & 1u);
+    const uint32_t use = n >> 1;
+    if (!mbar_wait(&sm.full[b], use & 1u, kMbarLimit)) {
+      if (t == 0) tma_fail(st);
+      break;
+    }
+    const TmaItem it = sm.item[b];
+    if (it.quit) break;
+    uint8_t* tile = sm.tile[b];
+    if (t < kMaxStates) sm.hist[t] = 0;
+    const uint32_t gx0 = (uint32_t)(it.bx * (kUniB / 2) + 2 * qx);
+    const uint32_t gy0 = (uint32_t)(it.by * (kUniB / 2) + 2 * qy);
+#pragma unroll 1
+    for (int fi = 0; fi < 4; ++fi) {
+      const int fcol = order_at(it.forder, fi);
+      const int cx = fcol & 1, cy = fcol >> 1;
+      const uint32_t g = (gy0 + (uint32_t)cy) * (uint32_t)d.GQ + gx0 + (uint32_t)cx;
+      const int base = tix(4 * qy + 2 * cy, 4 * qx + 2 * cx);
+      const uint4 x = philox10_rk(make_uint4(0u, g, it.m, kTagStep), d.rk);
+      attempt_uni<kTmaSP>(tile, trans, x.x, base, tx, txi, s1);
+      attempt_uni<kTmaSP>(tile, trans, x.y, base, tx, txi, s1);
+      attempt_uni<kTmaSP>(tile, trans, x.z, base, tx, txi, s1);
+      attempt_uni<kTmaSP>(tile, trans, x.w, base, tx, txi, s1);
+      bar_sync_consumers(kTmaConsumers);
+    }
+    const bool log_point = ((it.m + 1u) % p.log_every) == 0u;
+    if (log_point) {
+      const int sV = slot_of(it.ord, it.colour ^ 2), sH = slot_of(it.ord, it.colour ^ 1),
+                sD = slot_of(it.ord, it.colour ^ 3);
+      count_visit_uni<kTmaSP, kTmaColOff>(tile, sm.hist, d.S, it.k, sV, sH, sD);
+    }
+    // write back interior and rim strips (never the corners)
+    const int x0 = it.bx * kUniB, y0 = it.by * kUniB;
+    {
+      const int r = t >> 2, q = t & 3;
+      const uint4 v = *reinterpret_cast<const uint4*>(tile + tix(r, 16 * q));
+      reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = v;
+    }
+    if (t < 8) {
+      const int r = (t < 4) ? -1 : kUniB, q = t & 3;
+      const uint4 v = *reinterpret_cast<const uint4*>(tile + tix(r, 16 * q));
+      reinterpret_cast<uint4*>(d.lat + (size_t)wrap(y0 + r, L) * pitch + x0)[q] = v;
+    } else if (t >= 128) {
+      const int kk = t - 128, c = (kk < 64) ? -1 : kUniB, r = kk & 63;
+      d.lat[(size_t)(y0 + r) * pitch + wrap(x0 + c, L)] = tile[tix(r, c)];
+    }
+    bar_sync_consumers(kTmaConsumers);
+    if (log_point) {
+      const uint32_t ring = ((it.m + 1u) / p.log_every) % (uint32_t)kPendRing;
+      if (t <= d.S && sm.hist[t]) atomicAdd(&st->acc[ring][t], (unsigned long long)sm.hist[t]);
+      bar_sync_consumers(kTmaConsumers);
+      if (t == 0) {
+        __threadfence();
+        if (atomicAdd(&st->pend[ring], 1u) == nb - 1u) {
+          __threadfence();
+          unsigned long long c[kMaxStates];
+          for (int v = 0; v < kMaxStates; ++v) c[v] = atomicExch(&st->acc[ring][v], 0ull);
+          st->pend[ring] = 0;
+          write_log_entry(st, p.lb, d.S, it.m + 1u, p.log_every, c, p.stop_at_extinction);
+        }
+      }
+    }
+    if (t == 0) {
+      if (it.by * P + it.bx != p.stall_block) {
+        __threadfence();
+        st_release(p.done + it.by * P + it.bx, it.m + 1u);
+      }
+      mbar_arrive(&sm.empty[b]);   // the tile may be refilled
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTmaThreads, 4) persistent_tma_kernel(const __grid_constant__ TmaArgs a) {
+  __shared__ TmaSmem sm;
+  RunState* st = a.p.st;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.full[b], 32);
+      mbar_init(&sm.empty[b], 1);
+      mbar_init(&sm.tma[b], 1);
+    }
+    fence_mbar_init();
+  }
+  load_trans(a.p.d, sm.trans);
+  __syncthreads();
+  if (!ld_volatile(&st->stopped)) {
+    if (tid >= kTmaConsumers)
+      tma_producer(a, sm);
+    else
+      tma_consumer(a, sm);
+  }
+  __syncthreads();
+  // The last CTA to leave publishes the MCS number and resets the
+  // dispensers for the next launch on this stream.
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&st->exited, 1u) == gridDim.x - 1u) {
+      st->exited = 0;
+      st->ticket = 0;
+      if (!st->stopped && !st->abort) st->mcs = a.p.m_begin + a.p.n_mcs;
     }
   }
 }
@@ -329,6 +596,19 @@ cudaError_t launch_phase(const LatticeDesc& d, RunState* st, uint32_t m, int slo
   const int nblocks = (d.P * d.P) / 4;
   phase_kernel<<<nblocks, 256, 0, stream>>>(d, st, m, slot);
   return cudaGetLastError();
+}
+
+cudaError_t launch_persistent_tma(const TmaArgs& a, int grid, cudaStream_t stream) {
+  persistent_tma_kernel<<<grid, kTmaThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+int persistent_tma_grid(int device) {
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_tma_kernel, kTmaThreads, 0);
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
 }
 
 cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream) {

@@ -30,6 +30,8 @@ struct LatticeDesc {
   const uint8_t* trans; // [(S+1)*(S+1)][4]: byte (a*(S+1)+b)*4 + action holds
                         // the new pair (a' | b' << 4)
   uint32_t key0, key1;  // Philox key (seed)
+  uint32_t rk[20];      // Philox round keys: rk[2r] = key0 + r*0x9E3779B9,
+                        // rk[2r+1] = key1 + r*0xBB67AE85
   uint32_t tx, txi;     // thresholds; 2^32 stored as 0xFFFFFFFF (exact: the
                         // action draw u is always a multiple of 4)
   int32_t S;

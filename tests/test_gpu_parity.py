@@ -60,10 +60,13 @@ SMALL = [  # (L, S, K, p_empty, I, P, X, n_mcs)
     (191, 3, (1,), 0.25, 1.0, 1.0, 7.3, 4),
     (200, 5, (1, 2), 0.2, 1.0, 1.0, 8.0, 4),
     (257, 3, (1,), 0.25, 0.0, 0.0, 1.0, 3),
+    (128, 3, (1,), 0.25, 1.0, 1.0, 3.3, 5),      # uniform 64x64 blocks, P = 2
+    (256, 5, (1, 2), 0.2, 1.0, 1.0, 13.1, 4),    # uniform, P = 4
+    (384, 3, (1,), 0.25, 1.0, 1.0, 29.5, 3),     # uniform, P = 6
 ]
 
 
-@pytest.mark.parametrize("persistent", [True, False], ids=["persistent", "phase"])
+@pytest.mark.parametrize("persistent", [1, 2, 0], ids=["persistent", "persistent-plain", "phase"])
 @pytest.mark.parametrize("case", SMALL, ids=[f"L{c[0]}" for c in SMALL])
 def test_replay_parity_every_mcs(case, persistent):
     L, S, K, p_empty, I, P, X, n = case
@@ -249,7 +252,11 @@ def test_kernel_timing_counts_launches():
     g = E.Lattice(64, 3, E.circulant(3, [1]), (1.0, 1.0, 1.0), 3, time_kernels=True)
     g.run(25)
     ms, n = g.kernel_time()
-    assert n == 3 and ms > 0
+    assert n == 1 and ms > 0     # one persistent launch (counts fused, no stop)
+    h = E.Lattice(64, 3, E.circulant(3, [1]), (1.0, 1.0, 1.0), 3, time_kernels=True,
+                  stop_at_extinction=True)
+    h.run(25)
+    assert h.kernel_time()[1] == 3   # stasis is decided at each log point
     assert E.int_throughput()[0] > 1e12
 
 
