@@ -219,7 +219,7 @@ def main():
     stream = torch.cuda.Stream()
     g = E.Lattice(w.L, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X), w.seed + rank,
                   p_empty=w.p_empty, log_every=w.log_every, stream=stream, time_kernels=True,
-                  persistent=bool(args.persistent))
+                  persistent=args.persistent)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     K, Wm, mps = args.steps, args.warmup, args.mcs_per_step
 

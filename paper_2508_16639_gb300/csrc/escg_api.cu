@@ -230,8 +230,6 @@ cudaError_t timing_end(escg* h) {
 }
 
 int reset_state(escg* h, uint64_t mcs) {
-  static RunState zero{};  // RunState is large; fill on the device
-  (void)zero;
   CUDA_TRY(cudaMemsetAsync(h->d_state, 0, sizeof(RunState), h->stream));
   uint32_t head[2] = {(uint32_t)mcs, 0u};
   const uint32_t le = h->opt.log_every;

@@ -72,7 +72,7 @@ int persistent_grid(int device, bool uniform);
 // Uniform geometry (64x64 blocks): TMA-staged, warp-specialised variant.
 // map: 2-D uint8 tensor map of the lattice (dims L x L, row stride pitch,
 // box 112 x 66).
-struct alignas(64) TmaArgs {
+struct TmaArgs {   // aligned like CUtensorMap
   CUtensorMap map;
   PersistentArgs p;
 };

@@ -293,6 +293,7 @@ constexpr uint32_t kTmaBoxBytes = (uint32_t)(kTmaSP * kTmaRows);   // 7392
 constexpr int kTmaTileStride = 7424;                               // 128-byte multiple
 constexpr int kTmaConsumers = 256, kTmaThreads = kTmaConsumers + 32;
 constexpr uint32_t kMbarLimit = 1u << 26;
+constexpr int kLookahead = 3;   // work items a producer holds (9 lanes poll each)
 
 struct TmaItem {
   uint32_t m, ord, forder, quit;
@@ -314,6 +315,19 @@ __device__ __forceinline__ void tma_fail(RunState* st) {
   atomicExch(&st->abort, 1u);
 }
 
+// Producer with a lookahead window: it holds up to kLookahead work items
+// (taken from the ticket counter in schedule order) and dispatches whichever
+// is ready first, oldest first among the ready ones.  An item is ready when
+// its 8 neighbours (and the block itself) have completed every visit that
+// precedes it in schedule order.  Progress is guaranteed: the oldest
+// unfinished item of the whole launch has all its dependencies done, and
+// the producer holding it dispatches it as soon as it polls it.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ void tma_producer(const TmaArgs& a, TmaSmem& sm) {
   const PersistentArgs& p = a.p;
   const LatticeDesc& d = p.d;
@@ -322,110 +336,166 @@ __device__ void tma_producer(const TmaArgs& a, TmaSmem& sm) {
   const int P = d.P, half = P >> 1, L = d.L, pitch = d.pitch;
   const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
   const uint64_t total = (uint64_t)p.n_mcs * nb;
+  // held items: ticket (0xFFFFFFFF = empty slot) and decoded fields
+  uint32_t h_t = 0xFFFFFFFFu, h_m = 0, h_ord = 0;
+  int h_k = 0, h_bx = 0, h_by = 0, h_col = 0;   // lane j < kLookahead holds slot j
+  bool exhausted = false, failed = false;
   for (uint32_t n = 0;; ++n) {
     const int b = (int)(n & 1u);
     const uint32_t use = n >> 1;
-    uint32_t t = 0, quit = 0;
-    if (lane == 0) {
-      t = atomicAdd(&st->ticket, 1u);
-      quit = ((uint64_t)t >= total) || ld_volatile(&st->abort);
-      // the consumers must have released this buffer
-      if (!mbar_wait(&sm.empty[b], (use & 1u) ^ 1u, kMbarLimit)) {
-        tma_fail(st);
-        quit = 1;
-      }
-    }
-    t = __shfl_sync(0xFFFFFFFFu, t, 0);
-    quit = __shfl_sync(0xFFFFFFFFu, quit, 0);
-    uint32_t m = 0, ord = 0, forder = 0;
-    int k = 0, colour = 0, bx = 0, by = 0;
-    if (!quit) {
-      const uint32_t mi = t / nb, rem = t - mi * nb;
-      m = p.m_begin + mi;
-      k = (int)(rem / per);
-      const int j = (int)(rem - (uint32_t)k * per);
-      ord = colour_order(philox10_rk(make_uint4(0u, 0u, m, kTagOrder), d.rk).x);
-      colour = order_at(ord, k);
-      bx = 2 * (j % half) + (colour & 1);
-      by = 2 * (j / half) + (colour >> 1);
-      // wait until the 8 neighbours (and the block itself) have completed
-      // every visit that precedes this one in schedule order
-      uint32_t fail = 0;
-      if (lane < 9) {
-        const int dx = lane % 3 - 1, dy = lane / 3 - 1;
-        const int nx = (bx + dx + P) % P, ny = (by + dy + P) % P;
-        const int ncol = colour ^ ((dx & 1) | ((dy & 1) << 1));
-        const uint32_t need = (lane == 4) ? m : (slot_of(ord, ncol) < k ? m + 1u : m);
-        const uint32_t* flag = p.done + ny * P + nx;
-        uint32_t spins = 0;
-        while (ld_acquire(flag) < need) {
-          if (ld_volatile(&st->abort)) {
-            fail = 1;
-            break;
+    // refill empty slots with new tickets
+    if (!exhausted && !failed) {
+      const bool want = lane < kLookahead && h_t == 0xFFFFFFFFu;
+      const uint32_t need_mask = __ballot_sync(0xFFFFFFFFu, want);
+      if (need_mask) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&st->ticket, (uint32_t)__popc(need_mask));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (want) {
+          const uint32_t t = base + (uint32_t)__popc(need_mask & ((1u << lane) - 1u));
+          if ((uint64_t)t < total) {
+            h_t = t;
+            const uint32_t mi = t / nb, rem = t - mi * nb;
+            h_m = p.m_begin + mi;
+            h_k = (int)(rem / per);
+            const int j = (int)(rem - (uint32_t)h_k * per);
+            h_ord = colour_order(philox10_rk(make_uint4(0u, 0u, h_m, kTagOrder), d.rk).x);
+            h_col = order_at(h_ord, h_k);
+            h_bx = 2 * (j % half) + (h_col & 1);
+            h_by = 2 * (j / half) + (h_col >> 1);
           }
-          if (++spins > p.spin_limit) {
-            tma_fail(st);
-            fail = 1;
-            break;
-          }
-          __nanosleep(64);
         }
-        // what was acquired above is read next through the async proxy
-        fence_proxy_async_global();
+        // a ticket past the end means every later one is too
+        exhausted = __any_sync(0xFFFFFFFFu, want && h_t == 0xFFFFFFFFu);
       }
-      quit = __any_sync(0xFFFFFFFFu, fail != 0);
-      if (lane == 1)
-        forder = colour_order(
-            philox10_rk(make_uint4(0u, (uint32_t)(by * P + bx), m, kTagFineOrder), d.rk).x);
-      forder = __shfl_sync(0xFFFFFFFFu, forder, 1);
     }
+    const uint32_t held = __ballot_sync(0xFFFFFFFFu, lane < kLookahead && h_t != 0xFFFFFFFFu);
+    bool quit = failed || held == 0u;
+    // the consumers must have released this buffer
     if (!quit) {
-      const int x0 = bx * kUniB, y0 = by * kUniB;
-      uint8_t* tile = sm.tile[b];
       uint32_t ok = 1;
-      if (lane == 0) {
-        fence_proxy_async_smem();  // the consumers' writes to this tile precede the TMA's
-        mbar_arrive_expect_tx(&sm.tma[b], kTmaBoxBytes);
-        tma_load_2d(tile, &a.map, x0 - kTmaColOff, y0 - 1, &sm.tma[b]);
-        if (!mbar_wait(&sm.tma[b], use & 1u, kMbarLimit)) {
-          tma_fail(st);
-          // do not leave a copy in flight into this CTA's shared memory
-          ok = mbar_wait(&sm.tma[b], use & 1u, kMbarLimit) ? 0u : 2u;
-        }
+      if (lane == 0 && !mbar_wait(&sm.empty[b], (use & 1u) ^ 1u, kMbarLimit)) {
+        tma_fail(st);
+        ok = 0;
       }
-      ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
-      if (ok != 1u) {
-        quit = 1;
-      } else {
-        // wrap-around rim cells the box filled with zeros
-        if (by == 0 && lane < 4) {
-          const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(L - 1) * pitch + x0) + lane);
-          *reinterpret_cast<uint4*>(tile + tix(-1, 16 * lane)) = v;
+      quit = __shfl_sync(0xFFFFFFFFu, ok, 0) == 0u;
+    }
+    // poll the held items until one is ready: lane 9j+f checks neighbour f
+    // of slot j
+    int pick = -1;
+    if (!quit) {
+      const int j = lane / 9, f = lane % 9;
+      const bool mine = lane < 9 * kLookahead;
+      const uint32_t jt = __shfl_sync(0xFFFFFFFFu, h_t, mine ? j : 0);
+      const uint32_t jm = __shfl_sync(0xFFFFFFFFu, h_m, mine ? j : 0);
+      const uint32_t jord = __shfl_sync(0xFFFFFFFFu, h_ord, mine ? j : 0);
+      const int jk = __shfl_sync(0xFFFFFFFFu, h_k, mine ? j : 0);
+      const int jbx = __shfl_sync(0xFFFFFFFFu, h_bx, mine ? j : 0);
+      const int jby = __shfl_sync(0xFFFFFFFFu, h_by, mine ? j : 0);
+      const int jcol = __shfl_sync(0xFFFFFFFFu, h_col, mine ? j : 0);
+      const uint32_t* flag = p.done;
+      uint32_t need = 0;
+      const bool active = mine && jt != 0xFFFFFFFFu;
+      if (active) {
+        const int dx = f % 3 - 1, dy = f / 3 - 1;
+        const int nx = (jbx + dx + P) % P, ny = (jby + dy + P) % P;
+        const int ncol = jcol ^ ((dx & 1) | ((dy & 1) << 1));
+        need = (f == 4) ? jm : (slot_of(jord, ncol) < jk ? jm + 1u : jm);
+        flag = p.done + ny * P + nx;
+      }
+      for (uint32_t spins = 0;; ++spins) {
+        const bool not_ready = active && ld_relaxed(flag) < need;
+        const uint32_t nr = __ballot_sync(0xFFFFFFFFu, not_ready);
+        // slot j is ready when it is held and none of its 9 lanes is waiting
+        uint32_t best_t = 0xFFFFFFFFu;
+        for (int jj = 0; jj < kLookahead; ++jj) {
+          const uint32_t tj = __shfl_sync(0xFFFFFFFFu, h_t, jj);
+          const bool ready = tj != 0xFFFFFFFFu && ((nr >> (9 * jj)) & 0x1FFu) == 0u;
+          if (ready && tj < best_t) {
+            best_t = tj;
+            pick = jj;
+          }
         }
-        if (by == P - 1 && lane >= 4 && lane < 8) {
-          const int q = lane - 4;
-          const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + x0) + q);
-          *reinterpret_cast<uint4*>(tile + tix(kUniB, 16 * q)) = v;
+        if (pick >= 0) break;
+        const uint32_t ab = __shfl_sync(0xFFFFFFFFu, lane == 0 ? ld_volatile(&st->abort) : 0u, 0);
+        if (ab) {   // uniform across the warp
+          quit = true;
+          break;
         }
-        if (bx == 0) {
-          tile[tix(lane, -1)] = __ldcg(d.lat + (size_t)(y0 + lane) * pitch + (L - 1));
-          tile[tix(lane + 32, -1)] = __ldcg(d.lat + (size_t)(y0 + lane + 32) * pitch + (L - 1));
+        if (spins > p.spin_limit) {
+          if (lane == 0) tma_fail(st);
+          quit = true;
+          break;
         }
-        if (bx == P - 1) {
-          tile[tix(lane, kUniB)] = __ldcg(d.lat + (size_t)(y0 + lane) * pitch);
-          tile[tix(lane + 32, kUniB)] = __ldcg(d.lat + (size_t)(y0 + lane + 32) * pitch);
-        }
-        if (lane == 0) {
-          TmaItem& it = sm.item[b];
-          it.m = m; it.ord = ord; it.forder = forder; it.quit = 0;
-          it.k = k; it.bx = bx; it.by = by; it.colour = colour;
-        }
+        __nanosleep(32);
+      }
+      // acquire what the neighbours published, for the async proxy too
+      __threadfence();
+      fence_proxy_async_global();
+    }
+    if (quit) {
+      failed = true;
+      if (lane == 0) sm.item[b].quit = 1;
+      __syncwarp();
+      mbar_arrive(&sm.full[b]);
+      break;
+    }
+    const uint32_t m = __shfl_sync(0xFFFFFFFFu, h_m, pick);
+    const uint32_t ord = __shfl_sync(0xFFFFFFFFu, h_ord, pick);
+    const int k = __shfl_sync(0xFFFFFFFFu, h_k, pick);
+    const int bx = __shfl_sync(0xFFFFFFFFu, h_bx, pick);
+    const int by = __shfl_sync(0xFFFFFFFFu, h_by, pick);
+    const int colour = __shfl_sync(0xFFFFFFFFu, h_col, pick);
+    if (lane == pick) h_t = 0xFFFFFFFFu;   // slot freed
+    uint32_t forder = 0;
+    if (lane == 1)
+      forder = colour_order(philox10_rk(make_uint4(0u, (uint32_t)(by * P + bx), m, kTagFineOrder), d.rk).x);
+    forder = __shfl_sync(0xFFFFFFFFu, forder, 1);
+    const int x0 = bx * kUniB, y0 = by * kUniB;
+    uint8_t* tile = sm.tile[b];
+    uint32_t ok = 1;
+    if (lane == 0) {
+      fence_proxy_async_smem();  // the consumers' writes to this tile precede the TMA's
+      mbar_arrive_expect_tx(&sm.tma[b], kTmaBoxBytes);
+      tma_load_2d(tile, &a.map, x0 - kTmaColOff, y0 - 1, &sm.tma[b]);
+      if (!mbar_wait(&sm.tma[b], use & 1u, kMbarLimit)) {
+        tma_fail(st);
+        // do not leave a copy in flight into this CTA's shared memory
+        ok = mbar_wait(&sm.tma[b], use & 1u, kMbarLimit) ? 0u : 2u;
       }
     }
-    if (quit && lane == 0) sm.item[b].quit = 1;
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    if (ok == 1u) {
+      // wrap-around rim cells the box filled with zeros
+      if (by == 0 && lane < 4) {
+        const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(L - 1) * pitch + x0) + lane);
+        *reinterpret_cast<uint4*>(tile + tix(-1, 16 * lane)) = v;
+      }
+      if (by == P - 1 && lane >= 4 && lane < 8) {
+        const int q = lane - 4;
+        const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + x0) + q);
+        *reinterpret_cast<uint4*>(tile + tix(kUniB, 16 * q)) = v;
+      }
+      if (bx == 0) {
+        tile[tix(lane, -1)] = __ldcg(d.lat + (size_t)(y0 + lane) * pitch + (L - 1));
+        tile[tix(lane + 32, -1)] = __ldcg(d.lat + (size_t)(y0 + lane + 32) * pitch + (L - 1));
+      }
+      if (bx == P - 1) {
+        tile[tix(lane, kUniB)] = __ldcg(d.lat + (size_t)(y0 + lane) * pitch);
+        tile[tix(lane + 32, kUniB)] = __ldcg(d.lat + (size_t)(y0 + lane + 32) * pitch);
+      }
+      if (lane == 0) {
+        TmaItem& it = sm.item[b];
+        it.m = m; it.ord = ord; it.forder = forder; it.quit = 0;
+        it.k = k; it.bx = bx; it.by = by; it.colour = colour;
+      }
+    } else {
+      failed = true;
+      if (lane == 0) sm.item[b].quit = 1;
+    }
     __syncwarp();
     mbar_arrive(&sm.full[b]);   // 32 arrivals complete the phase
-    if (quit) break;
+    if (failed) break;
   }
 }
 
@@ -502,6 +572,8 @@ __device__ void tma_consumer(const TmaArgs& a, TmaSmem& sm) {
     }
     if (t == 0) {
       if (it.by * P + it.bx != p.stall_block) {
+        // release: the consumers' stores (ordered before by the named
+        // barrier) become visible before the new epoch
         __threadfence();
         st_release(p.done + it.by * P + it.bx, it.m + 1u);
       }
