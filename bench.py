@@ -78,6 +78,7 @@ def _parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--persistent", type=int, default=1)
+    ap.add_argument("--L", type=int, default=3200, help="lattice side (3200 is the benchmark)")
     return ap.parse_args()
 
 
@@ -128,12 +129,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _workload(M: float):
+def _workload(M: float, L: int = 3200):
     from paper_2508_16639_gb300 import workloads as W
-    if M in W.CFG3:
-        return W.CFG3[M]
     import dataclasses
-    return dataclasses.replace(W.CFG3[1e-4], name=f"rps-L3200-M{M:g}", mobility=M)
+    w = W.CFG3[M] if M in W.CFG3 else dataclasses.replace(W.CFG3[1e-4], name=f"rps-L3200-M{M:g}",
+                                                          mobility=M)
+    if L != w.L:
+        w = dataclasses.replace(w, name=w.name.replace("L3200", f"L{L}"), L=L)
+    return w
 
 
 def _cpu_oracle_rate(w, seconds: float):
@@ -189,7 +192,7 @@ def _config(w, mcs_per_step):
     return {"workload": w.name, "L": w.L, "S": w.S, "digraph": f"C({w.S},{set(w.K)})",
             "mobility": w.mobility, "p_empty": w.p_empty, "interact": w.interact,
             "reproduce": w.reproduce, "mcs_per_step": mcs_per_step, "log_every": w.log_every,
-            "l2": "flushed before every timed step (256 MiB write); lattice 10.24 MB",
+            "l2": f"flushed before every timed step (256 MiB write); lattice {w.L * w.L / 1e6:.2f} MB",
             "parallelism": "replicas (one independent lattice per GPU)"}
 
 
@@ -213,7 +216,7 @@ def main():
     __graft_entry__.build()
     import paper_2508_16639_gb300 as E
 
-    w = _workload(args.mobility)
+    w = _workload(args.mobility, args.L)
     N = w.L * w.L
     X = E.exchange_from_mobility(w.mobility, N)
     stream = torch.cuda.Stream()

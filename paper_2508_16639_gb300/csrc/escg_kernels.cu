@@ -293,7 +293,10 @@ constexpr uint32_t kTmaBoxBytes = (uint32_t)(kTmaSP * kTmaRows);   // 7392
 constexpr int kTmaTileStride = 7424;                               // 128-byte multiple
 constexpr int kTmaConsumers = 256, kTmaThreads = kTmaConsumers + 32;
 constexpr uint32_t kMbarLimit = 1u << 26;
-constexpr int kLookahead = 3;   // work items a producer holds (9 lanes poll each)
+// Work items a producer holds (9 lanes poll each).  Measured at L = 3200: a
+// window of 3 was slower than 1 -- dispatching a newer ready item delays the
+// globally oldest one behind a whole visit and lengthens the critical path.
+constexpr int kLookahead = 1;
 
 struct TmaItem {
   uint32_t m, ord, forder, quit;
