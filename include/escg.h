@@ -70,10 +70,10 @@ typedef struct {
     int32_t stop_at_extinction;  /* stop at the first logged MCS with <= 1
                                     non-empty species alive (stasis())        */
     uint32_t schedule_version;   /* 0 or 1 (only version 1 exists)            */
-    int32_t persistent;          /* 1: persistent dataflow launches (default;
-                                    tiles staged by TMA where the partition is
-                                    uniform 64x64); 2: persistent with plain
-                                    loads; 0: one launch per coarse phase     */
+    int32_t persistent;          /* 1: persistent dataflow launches (default);
+                                    2: same, uniform 64x64 partitions staged by
+                                    a TMA producer warp (warp-specialised);
+                                    0: one launch per coarse phase            */
     void* cuda_stream;           /* cudaStream_t to enqueue on, or NULL for a
                                     stream owned by the handle                */
     void* device_lattice;        /* optional caller-owned device buffer of
@@ -156,6 +156,66 @@ void escg_destroy(escg_t* h);
 
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* escg_last_error(void);
+
+/* ---- Batched ensembles ------------------------------------------------
+ * Many independent replicas (the paper runs its trials one after another;
+ * here they share one GPU): each replica is a lattice with its own L, S,
+ * digraph, rates, seed, initial empty fraction and MCS budget, and runs until
+ * its budget is spent or -- with stop_at_extinction -- until the first log
+ * point at which at most one non-empty species is alive.  The replicas' work
+ * items share persistent launches of log_every MCS each; a device-side
+ * compaction step between launches retires finished replicas, so the whole
+ * run is enqueued (and captured in a CUDA graph) without host round trips.
+ * A replica's lattice and counts are bit-identical to running it alone with
+ * escg_create_ex/escg_run with the same parameters. */
+typedef struct {
+    int32_t L, S;                 /* as escg_create                              */
+    const uint8_t* digraph;       /* S*S bytes, read during escg_batch_create    */
+    escg_rates rates;
+    uint64_t seed;
+    double p_empty;
+    uint64_t max_mcs;             /* budget (absolute MCS number to stop at)     */
+    int32_t stop_at_extinction;
+} escg_replica_spec;
+
+typedef struct {
+    uint32_t log_every;           /* stasis checks / counts every k MCS (0: 10)  */
+    int32_t threads;              /* CTA size 64, 128 or 256; 0: autotune        */
+    int32_t use_graph;            /* capture chunk sequences in a CUDA graph     */
+    void* cuda_stream;            /* cudaStream_t or NULL (library-owned)        */
+} escg_batch_options;
+
+typedef struct escg_batch escg_batch_t;
+
+void escg_batch_default_options(escg_batch_options* opt);
+
+/* Creates n replicas (n >= 1), allocates one device arena for all of them
+ * and initialises every lattice.  Returns NULL on error. */
+escg_batch_t* escg_batch_create(int32_t n, const escg_replica_spec* specs,
+                                const escg_batch_options* opt);
+
+/* Enqueues work until every replica is finished or has advanced max_mcs
+ * more MCS (0: until every replica is finished).  Asynchronous. */
+int escg_batch_run(escg_batch_t* b, uint64_t max_mcs);
+int escg_batch_sync(escg_batch_t* b);
+
+/* Per replica: MCS reached, 1 if stopped by extinction, and the counts
+ * (S+1 values, padded to 16 per replica) at its last log point.  Any output
+ * pointer may be NULL.  Synchronises. */
+int escg_batch_status(escg_batch_t* b, uint64_t* mcs_out, int32_t* extinct_out,
+                      uint64_t* counts16_out);
+
+/* Number of replicas still running (synchronises). */
+int32_t escg_batch_active(escg_batch_t* b);
+
+/* Copies replica i's lattice (L*L bytes) to host memory.  Synchronises. */
+int escg_batch_snapshot(escg_batch_t* b, int32_t i, uint8_t* host_out);
+
+/* CTA size in use (after autotuning) and kernel launches so far. */
+int32_t escg_batch_threads(escg_batch_t* b);
+uint64_t escg_batch_launch_count(escg_batch_t* b);
+
+void escg_batch_destroy(escg_batch_t* b);
 
 /* epsilon = 2 M N (Section 3.1, rate initialisation). */
 double escg_exchange_from_mobility(double M, int64_t N);

@@ -14,9 +14,9 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import EscgError, Options, Rates, check, load
+from ._lib import BatchOptions, EscgError, Options, Rates, ReplicaSpec, check, load
 
-__all__ = ["Lattice", "circulant", "exchange_from_mobility", "lattice_pitch", "lattice_bytes",
+__all__ = ["Lattice", "Batch", "circulant", "exchange_from_mobility", "lattice_pitch", "lattice_bytes",
            "int_throughput", "EscgError", "load"]
 
 
@@ -187,3 +187,87 @@ class Lattice:
         if self._buffer is None:
             raise RuntimeError("lattice storage is library-owned; pass device_buffer= to get a view")
         return self._buffer.view(-1)[: self.L * self.pitch].view(self.L, self.pitch)
+
+
+class Batch:
+    """An ensemble of independent replicas run together on the GPU (a batch
+    handle of the C ABI).  specs: sequence of dicts with keys L, S, digraph,
+    rates (interact, reproduce, exchange), seed, p_empty, max_mcs,
+    stop_at_extinction.  threads: CTA size (64/128/256) or 0 to autotune."""
+
+    def __init__(self, specs, log_every: int = 10, threads: int = 0, use_graph: bool = True,
+                 stream=None):
+        lib = load()
+        self.n = len(specs)
+        self._digraphs = [np.ascontiguousarray(np.asarray(sp["digraph"], dtype=np.uint8))
+                          for sp in specs]
+        arr = (ReplicaSpec * self.n)()
+        self.L, self.S = [], []
+        for i, sp in enumerate(specs):
+            r = arr[i]
+            r.L, r.S = int(sp["L"]), int(sp["S"])
+            r.digraph = _u8(self._digraphs[i])
+            r.rates = Rates(*[float(x) for x in sp["rates"]])
+            r.seed = int(sp["seed"]) & (2**64 - 1)
+            r.p_empty = float(sp.get("p_empty", 0.0))
+            r.max_mcs = int(sp["max_mcs"])
+            r.stop_at_extinction = int(bool(sp.get("stop_at_extinction", False)))
+            self.L.append(r.L)
+            self.S.append(r.S)
+        opt = BatchOptions()
+        lib.escg_batch_default_options(C.byref(opt))
+        opt.log_every = int(log_every)
+        opt.threads = int(threads)
+        opt.use_graph = int(bool(use_graph))
+        if stream is not None:
+            opt.cuda_stream = int(getattr(stream, "cuda_stream", stream))
+        h = lib.escg_batch_create(self.n, arr, C.byref(opt))
+        if not h:
+            raise EscgError(-1, lib.escg_last_error().decode(errors="replace"))
+        self._h = C.c_void_p(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().escg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, max_mcs: int = 0):
+        check(load().escg_batch_run(self._h, int(max_mcs)))
+        return self
+
+    def sync(self):
+        check(load().escg_batch_sync(self._h))
+
+    def status(self):
+        """(mcs[n], extinct[n], counts[n, 16]) -- counts at each replica's
+        last log point."""
+        mcs = np.zeros(self.n, dtype=np.uint64)
+        ext = np.zeros(self.n, dtype=np.int32)
+        cnt = np.zeros((self.n, 16), dtype=np.uint64)
+        check(load().escg_batch_status(self._h, mcs.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                       ext.ctypes.data_as(C.POINTER(C.c_int32)),
+                                       cnt.ctypes.data_as(C.POINTER(C.c_uint64))))
+        return mcs.astype(np.int64), ext.astype(bool), cnt
+
+    def snapshot(self, i: int) -> np.ndarray:
+        out = np.empty((self.L[i], self.L[i]), dtype=np.uint8)
+        check(load().escg_batch_snapshot(self._h, int(i), _u8(out)))
+        return out
+
+    @property
+    def active(self) -> int:
+        return int(load().escg_batch_active(self._h))
+
+    @property
+    def threads(self) -> int:
+        return int(load().escg_batch_threads(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(load().escg_batch_launch_count(self._h))

@@ -26,6 +26,17 @@ class Options(C.Structure):
                 ("device_lattice", C.c_void_p), ("time_kernels", C.c_int32)]
 
 
+class ReplicaSpec(C.Structure):
+    _fields_ = [("L", C.c_int32), ("S", C.c_int32), ("digraph", C.POINTER(C.c_uint8)),
+                ("rates", Rates), ("seed", C.c_uint64), ("p_empty", C.c_double),
+                ("max_mcs", C.c_uint64), ("stop_at_extinction", C.c_int32)]
+
+
+class BatchOptions(C.Structure):
+    _fields_ = [("log_every", C.c_uint32), ("threads", C.c_int32), ("use_graph", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
 _u8p = C.POINTER(C.c_uint8)
 _u64p = C.POINTER(C.c_uint64)
 _i32p = C.POINTER(C.c_int32)
@@ -55,6 +66,16 @@ SIGNATURES = {
     "escg_exchange_from_mobility": (C.c_double, [C.c_double, C.c_int64]),
     "escg_circulant": (C.c_int, [C.c_int32, _i32p, C.c_int32, _u8p]),
     "escg_kernel_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), _u64p, C.c_int]),
+    "escg_batch_default_options": (None, [C.POINTER(BatchOptions)]),
+    "escg_batch_create": (C.c_void_p, [C.c_int32, C.POINTER(ReplicaSpec), C.POINTER(BatchOptions)]),
+    "escg_batch_run": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "escg_batch_sync": (C.c_int, [C.c_void_p]),
+    "escg_batch_status": (C.c_int, [C.c_void_p, _u64p, _i32p, _u64p]),
+    "escg_batch_active": (C.c_int32, [C.c_void_p]),
+    "escg_batch_snapshot": (C.c_int, [C.c_void_p, C.c_int32, _u8p]),
+    "escg_batch_threads": (C.c_int32, [C.c_void_p]),
+    "escg_batch_launch_count": (C.c_uint64, [C.c_void_p]),
+    "escg_batch_destroy": (None, [C.c_void_p]),
     # include/escg_diag.h
     "escg_diag_int_throughput": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "escg_debug_stall_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint32]),

@@ -28,6 +28,17 @@ void set_err(const char* fmt, ...) {
   va_end(ap);
 }
 
+}  // namespace
+
+void escg_impl::set_last_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+namespace {
+
 #define CUDA_TRY(expr)                                                                  \
   do {                                                                                  \
     cudaError_t e_ = (expr);                                                            \
@@ -38,20 +49,6 @@ void set_err(const char* fmt, ...) {
   } while (0)
 
 constexpr uint32_t kDefaultSpinLimit = 2000000;  // polls of ~1 us: a few seconds
-
-std::mutex g_init_mu;
-bool g_perm_uploaded[64] = {};
-
-int ensure_device_tables(int dev) {
-  std::lock_guard<std::mutex> lk(g_init_mu);
-  if (dev < 0 || dev >= 64) return ESCG_EINVAL;
-  if (!g_perm_uploaded[dev]) {
-    upload_perm_table();
-    CUDA_TRY(cudaGetLastError());
-    g_perm_uploaded[dev] = true;
-  }
-  return ESCG_OK;
-}
 
 // Schedule v1 partition of one axis (both axes are identical).
 struct Partition {
@@ -393,7 +390,6 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     set_err("cudaGetDevice failed");
     return fail(ESCG_ECUDA);
   }
-  if (ensure_device_tables(h->device) != ESCG_OK) return fail(ESCG_ECUDA);
 
   cudaError_t e = cudaSuccess;
   if (o.cuda_stream) {
@@ -461,12 +457,13 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   d.tx = tx >> 32 ? 0xFFFFFFFFu : (uint32_t)tx;
   d.txi = txi >> 32 ? 0xFFFFFFFFu : (uint32_t)txi;
   d.S = S;
+  fill_perm24(d.perm24);
   bool uni = true;
   for (int k = 0; k < p.P; ++k) uni = uni && (p.cs[k + 1] - p.cs[k] == 64);
   for (int k = 0; k < p.GQ; ++k) uni = uni && (p.fs[k + 1] - p.fs[k] == 2);
   d.uniform64 = (uni && h->pitch % 16 == 0) ? 1 : 0;
   h->grid = persistent_grid(h->device, d.uniform64 != 0);
-  if (d.uniform64 && o.persistent == 1) {
+  if (d.uniform64 && o.persistent == 2) {
     if (!make_tensor_map(&h->tmap, h->lattice, L, h->pitch)) {
       set_err("cuTensorMapEncodeTiled failed for L=%d", L);
       return fail(ESCG_ECUDA);

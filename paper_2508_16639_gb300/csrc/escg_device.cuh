@@ -50,12 +50,11 @@ __device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t* __restrict
   return c;
 }
 
-// The 24 orders of the four colours, lexicographic; entry = 4 x 2-bit
-// colours, first colour in the lowest bits.
-__device__ __constant__ uint8_t c_perm24[24];
-
-__device__ __forceinline__ uint32_t colour_order(uint32_t x0) {
-  return c_perm24[__umulhi(x0, 24u)];
+// Colour order drawn by x0: entry floor(x0 * 24 / 2^32) of the 24 orders of
+// the four colours (lexicographic; d.perm24 holds them as 4 x 2-bit colours,
+// first colour in the lowest bits).
+__device__ __forceinline__ uint32_t colour_order(uint32_t x0, const uint8_t* perm24) {
+  return perm24[__umulhi(x0, 24u)];
 }
 __device__ __forceinline__ int order_at(uint32_t ord, int k) { return (ord >> (2 * k)) & 3; }
 __device__ __forceinline__ int slot_of(uint32_t ord, int colour) {
@@ -216,7 +215,7 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
   const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
   if (t == 0) {
     const uint4 x = philox10_rk(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.rk);
-    sm.forder = colour_order(x.x);
+    sm.forder = colour_order(x.x, d.perm24);
   }
   load_tile_uni(d, x0, y0, sm.tile);
   __syncthreads();
@@ -252,7 +251,7 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
   for (int k = tid; k <= Qy; k += nthr) sm.fsy[k] = (int16_t)(d.fs[fy0 + k] - y0);
   if (tid == 0) {
     const uint4 x = philox10_rk(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.rk);
-    sm.forder = colour_order(x.x);
+    sm.forder = colour_order(x.x, d.perm24);
   }
   load_tile_generic(d, x0, y0, bw, bh, sm.tile, sp);
   __syncthreads();

@@ -35,8 +35,10 @@ struct LogBuffers {
   uint32_t* mcs;               // [kLogCap]
 };
 
+// Sets the thread-local message returned by escg_last_error().
+void set_last_error(const char* fmt, ...);
+
 // Host-side launchers (all asynchronous on `stream`).
-void upload_perm_table();  // once per process/device
 cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream);
 cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t stream);
 // Sets *bad = 1 if any lattice byte is outside 0..S.

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st,
   __shared__ VisitSmem sm;
   load_trans(d, sm.trans);
   const uint4 x = philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1);
-  const int colour = order_at(colour_order(x.x), slot);
+  const int colour = order_at(colour_order(x.x, d.perm24), slot);
   const int half = d.P >> 1, j = blockIdx.x;
   const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
   if (d.uniform64)
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
         uint32_t quit = ((uint64_t)t >= total) || ld_volatile(&st->abort);
         if (!quit) {
           const uint32_t m = a.m_begin + t / nb;
-          s_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x);
+          s_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
         }
         s_quit = quit;
         s_abort = 0;
@@ -362,7 +362,7 @@ __device__ void tma_producer(const TmaArgs& a, TmaSmem& sm) {
             h_m = p.m_begin + mi;
             h_k = (int)(rem / per);
             const int j = (int)(rem - (uint32_t)h_k * per);
-            h_ord = colour_order(philox10_rk(make_uint4(0u, 0u, h_m, kTagOrder), d.rk).x);
+            h_ord = colour_order(philox10_rk(make_uint4(0u, 0u, h_m, kTagOrder), d.rk).x, d.perm24);
             h_col = order_at(h_ord, h_k);
             h_bx = 2 * (j % half) + (h_col & 1);
             h_by = 2 * (j / half) + (h_col >> 1);
@@ -452,7 +452,7 @@ __device__ void tma_producer(const TmaArgs& a, TmaSmem& sm) {
     if (lane == pick) h_t = 0xFFFFFFFFu;   // slot freed
     uint32_t forder = 0;
     if (lane == 1)
-      forder = colour_order(philox10_rk(make_uint4(0u, (uint32_t)(by * P + bx), m, kTagFineOrder), d.rk).x);
+      forder = colour_order(philox10_rk(make_uint4(0u, (uint32_t)(by * P + bx), m, kTagFineOrder), d.rk).x, d.perm24);
     forder = __shfl_sync(0xFFFFFFFFu, forder, 1);
     const int x0 = bx * kUniB, y0 = by * kUniB;
     uint8_t* tile = sm.tile[b];
@@ -623,19 +623,6 @@ static inline int blocks_for(size_t n, int threads, int cap) {
   size_t b = (n + threads - 1) / threads;
   if (b > (size_t)cap) b = cap;
   return b < 1 ? 1 : (int)b;
-}
-
-void upload_perm_table() {
-  uint8_t perms[24];
-  int n = 0;
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b)
-      for (int c = 0; c < 4; ++c)
-        for (int e = 0; e < 4; ++e) {
-          if (a == b || a == c || a == e || b == c || b == e || c == e) continue;
-          perms[n++] = (uint8_t)(a | (b << 2) | (c << 4) | (e << 6));
-        }
-  cudaMemcpyToSymbol(c_perm24, perms, sizeof(perms));
 }
 
 cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream) {

@@ -36,6 +36,20 @@ struct LatticeDesc {
                         // action draw u is always a multiple of 4)
   int32_t S;
   int32_t uniform64;    // all blocks 64x64 and all sub-blocks 2x2
+  uint8_t perm24[24];   // the 24 colour orders, lexicographic (4 x 2 bits)
 };
+
+// Fills perm24 with the 24 orders of the colours {0,1,2,3} in lexicographic
+// order, each packed as 4 x 2 bits (first colour in the lowest bits).
+inline void fill_perm24(uint8_t* perm24) {
+  int n = 0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int c = 0; c < 4; ++c)
+        for (int e = 0; e < 4; ++e) {
+          if (a == b || a == c || a == e || b == c || b == e || c == e) continue;
+          perm24[n++] = (uint8_t)(a | (b << 2) | (c << 4) | (e << 6));
+        }
+}
 
 }  // namespace escg_impl

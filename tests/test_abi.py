@@ -90,3 +90,15 @@ def test_no_cpu_fallback_without_device(lib):
         pytest.skip("a CUDA device is present")
     with pytest.raises(E.EscgError, match="no CUDA device"):
         E.Lattice(64, 3, O.circulant(3, [1]), (1, 0, 0), 1)
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (dict(L=7), "bad L"), (dict(S=1), "bad L"), (dict(rates=(0, 0, 0)), "bad rates"),
+    (dict(p_empty=1.5), "bad rates"), (dict(max_mcs=2**33), "bad rates"),
+])
+def test_batch_create_rejects_bad_specs(lib, bad, msg):
+    spec = dict(L=64, S=3, digraph=O.circulant(3, [1]), rates=(1, 1, 1), seed=1, p_empty=0.25,
+                max_mcs=100, stop_at_extinction=True)
+    spec.update(bad)
+    with pytest.raises(E.EscgError, match=msg):
+        E.Batch([spec, dict(spec, L=64, S=3, rates=(1, 1, 1), p_empty=0.0, max_mcs=10)])

@@ -66,7 +66,7 @@ SMALL = [  # (L, S, K, p_empty, I, P, X, n_mcs)
 ]
 
 
-@pytest.mark.parametrize("persistent", [1, 2, 0], ids=["persistent", "persistent-plain", "phase"])
+@pytest.mark.parametrize("persistent", [1, 2, 0], ids=["persistent", "persistent-tma", "phase"])
 @pytest.mark.parametrize("case", SMALL, ids=[f"L{c[0]}" for c in SMALL])
 def test_replay_parity_every_mcs(case, persistent):
     L, S, K, p_empty, I, P, X, n = case
