@@ -217,6 +217,52 @@ uint64_t escg_batch_launch_count(escg_batch_t* b);
 
 void escg_batch_destroy(escg_batch_t* b);
 
+/* ---- Serving ------------------------------------------------------------
+ * A request loop with continuous batching: runs (replica specs) are
+ * submitted as they arrive and queue in FIFO order; escg_server_step admits
+ * queued runs into free slots while the device arena has room for them,
+ * advances every resident run by chunks_per_step * log_every MCS in shared
+ * persistent launches, and retires the runs that went extinct or spent their
+ * budget (their memory is freed for the next admissions).  A run's result is
+ * bit-identical to running it alone, whatever else shares the GPU. */
+typedef struct {
+    uint64_t arena_bytes;         /* device memory for resident runs             */
+    int32_t max_slots;            /* runs resident at once                       */
+    uint32_t log_every;           /* 0: 10                                       */
+    int32_t threads;              /* CTA size 64/128/256, 0: autotune            */
+    uint32_t chunks_per_step;     /* chunks of log_every MCS per step (0: 4)     */
+    int32_t keep_lattice;         /* 1: copy each finished lattice to the host   */
+    void* cuda_stream;
+} escg_server_options;
+
+typedef struct escg_server escg_server_t;
+
+void escg_server_default_options(escg_server_options* opt);
+escg_server_t* escg_server_create(const escg_server_options* opt);
+
+/* Queues a run; returns its id (>= 0) or a negative escg_status.  The spec's
+ * digraph is copied.  Runs larger than the whole arena are rejected. */
+int64_t escg_server_submit(escg_server_t* s, const escg_replica_spec* spec);
+
+/* Admits, advances and retires (see above); synchronises at its end.
+ * *finished_out (may be NULL) receives the number of runs retired. */
+int escg_server_step(escg_server_t* s, int32_t* finished_out);
+
+/* Ids of runs finished since the previous poll (up to cap). */
+int escg_server_poll(escg_server_t* s, int64_t* ids_out, int32_t cap, int32_t* n_out);
+
+/* Result of a finished run: MCS reached, extinct flag, counts at its last
+ * log point (16 values), and -- with keep_lattice -- its lattice (L*L bytes;
+ * lattice_out may be NULL).  ESCG_ESTATE if the run has not finished. */
+int escg_server_result(escg_server_t* s, int64_t id, uint64_t* mcs_out, int32_t* extinct_out,
+                       uint64_t* counts16_out, uint8_t* lattice_out);
+
+/* Runs resident, runs queued, arena bytes in use. */
+int escg_server_stats(escg_server_t* s, int32_t* resident, int32_t* queued, uint64_t* bytes_in_use);
+int32_t escg_server_threads(escg_server_t* s);
+uint64_t escg_server_launch_count(escg_server_t* s);
+void escg_server_destroy(escg_server_t* s);
+
 /* epsilon = 2 M N (Section 3.1, rate initialisation). */
 double escg_exchange_from_mobility(double M, int64_t N);
 

@@ -14,9 +14,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import BatchOptions, EscgError, Options, Rates, ReplicaSpec, check, load
+from ._lib import (BatchOptions, EscgError, Options, Rates, ReplicaSpec, ServerOptions, check,
+                   load)
 
-__all__ = ["Lattice", "Batch", "circulant", "exchange_from_mobility", "lattice_pitch", "lattice_bytes",
+__all__ = ["Lattice", "Batch", "Server", "circulant", "exchange_from_mobility", "lattice_pitch", "lattice_bytes",
            "int_throughput", "EscgError", "load"]
 
 
@@ -189,6 +190,21 @@ class Lattice:
         return self._buffer.view(-1)[: self.L * self.pitch].view(self.L, self.pitch)
 
 
+def _replica_spec(sp, keep):
+    """Fills a ReplicaSpec from a dict; `keep` holds the digraph array alive."""
+    r = ReplicaSpec()
+    D = np.ascontiguousarray(np.asarray(sp["digraph"], dtype=np.uint8))
+    keep.append(D)
+    r.L, r.S = int(sp["L"]), int(sp["S"])
+    r.digraph = _u8(D)
+    r.rates = Rates(*[float(x) for x in sp["rates"]])
+    r.seed = int(sp["seed"]) & (2**64 - 1)
+    r.p_empty = float(sp.get("p_empty", 0.0))
+    r.max_mcs = int(sp["max_mcs"])
+    r.stop_at_extinction = int(bool(sp.get("stop_at_extinction", False)))
+    return r
+
+
 class Batch:
     """An ensemble of independent replicas run together on the GPU (a batch
     handle of the C ABI).  specs: sequence of dicts with keys L, S, digraph,
@@ -199,21 +215,14 @@ class Batch:
                  stream=None):
         lib = load()
         self.n = len(specs)
-        self._digraphs = [np.ascontiguousarray(np.asarray(sp["digraph"], dtype=np.uint8))
-                          for sp in specs]
+        self._digraphs = []
         arr = (ReplicaSpec * self.n)()
         self.L, self.S = [], []
+        keep = self._digraphs
         for i, sp in enumerate(specs):
-            r = arr[i]
-            r.L, r.S = int(sp["L"]), int(sp["S"])
-            r.digraph = _u8(self._digraphs[i])
-            r.rates = Rates(*[float(x) for x in sp["rates"]])
-            r.seed = int(sp["seed"]) & (2**64 - 1)
-            r.p_empty = float(sp.get("p_empty", 0.0))
-            r.max_mcs = int(sp["max_mcs"])
-            r.stop_at_extinction = int(bool(sp.get("stop_at_extinction", False)))
-            self.L.append(r.L)
-            self.S.append(r.S)
+            arr[i] = _replica_spec(sp, keep)
+            self.L.append(int(sp["L"]))
+            self.S.append(int(sp["S"]))
         opt = BatchOptions()
         lib.escg_batch_default_options(C.byref(opt))
         opt.log_every = int(log_every)
@@ -271,3 +280,83 @@ class Batch:
     @property
     def launches(self) -> int:
         return int(load().escg_batch_launch_count(self._h))
+
+
+class Server:
+    """Continuous-batching request loop (a server handle of the C ABI).
+    submit() queues a run (same dict as Batch specs) and returns its id;
+    step() admits queued runs while slots and device memory allow, advances
+    every resident run by chunks_per_step * log_every MCS, and retires the
+    finished ones; poll() lists runs finished since the last poll."""
+
+    def __init__(self, arena_bytes: int = 256 << 20, max_slots: int = 1024, log_every: int = 10,
+                 threads: int = 0, chunks_per_step: int = 4, keep_lattice: bool = False, stream=None):
+        lib = load()
+        opt = ServerOptions()
+        lib.escg_server_default_options(C.byref(opt))
+        opt.arena_bytes = int(arena_bytes)
+        opt.max_slots = int(max_slots)
+        opt.log_every = int(log_every)
+        opt.threads = int(threads)
+        opt.chunks_per_step = int(chunks_per_step)
+        opt.keep_lattice = int(bool(keep_lattice))
+        if stream is not None:
+            opt.cuda_stream = int(getattr(stream, "cuda_stream", stream))
+        h = lib.escg_server_create(C.byref(opt))
+        if not h:
+            raise EscgError(-1, lib.escg_last_error().decode(errors="replace"))
+        self._h = C.c_void_p(h)
+        self._L = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().escg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, spec) -> int:
+        keep = []
+        r = _replica_spec(spec, keep)
+        rid = int(load().escg_server_submit(self._h, C.byref(r)))
+        if rid < 0:
+            check(rid)
+        self._L[rid] = int(spec["L"])
+        return rid
+
+    def step(self) -> int:
+        n = C.c_int32()
+        check(load().escg_server_step(self._h, C.byref(n)))
+        return int(n.value)
+
+    def poll(self, cap: int = 65536):
+        ids = np.zeros(cap, dtype=np.int64)
+        n = C.c_int32()
+        check(load().escg_server_poll(self._h, ids.ctypes.data_as(C.POINTER(C.c_int64)), cap, C.byref(n)))
+        return [int(x) for x in ids[:n.value]]
+
+    def result(self, rid: int, lattice: bool = False):
+        mcs, ext = C.c_uint64(), C.c_int32()
+        cnt = np.zeros(16, dtype=np.uint64)
+        lat = np.empty((self._L[rid], self._L[rid]), dtype=np.uint8) if lattice else None
+        check(load().escg_server_result(self._h, int(rid), C.byref(mcs), C.byref(ext),
+                                        cnt.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                        _u8(lat) if lattice else None))
+        return int(mcs.value), bool(ext.value), cnt, lat
+
+    def stats(self):
+        r, q, b = C.c_int32(), C.c_int32(), C.c_uint64()
+        check(load().escg_server_stats(self._h, C.byref(r), C.byref(q), C.byref(b)))
+        return int(r.value), int(q.value), int(b.value)
+
+    @property
+    def threads(self) -> int:
+        return int(load().escg_server_threads(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(load().escg_server_launch_count(self._h))

@@ -37,6 +37,12 @@ class BatchOptions(C.Structure):
                 ("cuda_stream", C.c_void_p)]
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("arena_bytes", C.c_uint64), ("max_slots", C.c_int32), ("log_every", C.c_uint32),
+                ("threads", C.c_int32), ("chunks_per_step", C.c_uint32), ("keep_lattice", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
 _u8p = C.POINTER(C.c_uint8)
 _u64p = C.POINTER(C.c_uint64)
 _i32p = C.POINTER(C.c_int32)
@@ -76,6 +82,16 @@ SIGNATURES = {
     "escg_batch_threads": (C.c_int32, [C.c_void_p]),
     "escg_batch_launch_count": (C.c_uint64, [C.c_void_p]),
     "escg_batch_destroy": (None, [C.c_void_p]),
+    "escg_server_default_options": (None, [C.POINTER(ServerOptions)]),
+    "escg_server_create": (C.c_void_p, [C.POINTER(ServerOptions)]),
+    "escg_server_submit": (C.c_int64, [C.c_void_p, C.POINTER(ReplicaSpec)]),
+    "escg_server_step": (C.c_int, [C.c_void_p, _i32p]),
+    "escg_server_poll": (C.c_int, [C.c_void_p, _i64p, C.c_int32, _i32p]),
+    "escg_server_result": (C.c_int, [C.c_void_p, C.c_int64, _u64p, _i32p, _u64p, _u8p]),
+    "escg_server_stats": (C.c_int, [C.c_void_p, _i32p, _i32p, _u64p]),
+    "escg_server_threads": (C.c_int32, [C.c_void_p]),
+    "escg_server_launch_count": (C.c_uint64, [C.c_void_p]),
+    "escg_server_destroy": (None, [C.c_void_p]),
     # include/escg_diag.h
     "escg_diag_int_throughput": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "escg_debug_stall_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint32]),

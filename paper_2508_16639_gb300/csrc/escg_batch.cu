@@ -23,8 +23,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "escg.h"
@@ -320,8 +324,6 @@ using namespace escg_impl;
 
 namespace {
 
-#define bset_err set_last_error
-
 struct BPartition {
   int P = 0, GQ = 0;
   std::vector<int32_t> cs, fs, fc;
@@ -355,15 +357,110 @@ BPartition bpartition(int L) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-}  // namespace
+// First-fit allocator of 256-byte-aligned regions of the device arena, with
+// coalescing of freed neighbours.
+class Arena {
+ public:
+  void init(size_t cap) {
+    free_.clear();
+    free_[0] = cap;
+    cap_ = cap;
+    used_ = 0;
+  }
+  bool alloc(size_t n, size_t* off) {
+    n = align_up(n, 256);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < n) continue;
+      *off = it->first;
+      const size_t rem = it->second - n, start = it->first + n;
+      free_.erase(it);
+      if (rem) free_[start] = rem;
+      used_ += n;
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = align_up(n, 256);
+    used_ -= n;
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t used() const { return used_; }
+  size_t capacity() const { return cap_; }
 
-struct escg_batch {
-  int n = 0;
+ private:
+  std::map<size_t, size_t> free_;
+  size_t cap_ = 0, used_ = 0;
+};
+
+// A replica's footprint in the arena: lattice | tables | transitions | epochs.
+struct SlotPlan {
+  BPartition part;
+  size_t lat = 0, tab = 0, trans = 0, done = 0, bytes = 0;
+  uint64_t TE = 0;
+};
+
+int plan_slot(const escg_replica_spec& sp, SlotPlan* pl, int idx) {
+  if (sp.L < 8 || sp.L > 16384 || sp.S < 2 || sp.S > 15 || !sp.digraph) {
+    set_last_error("replica %d: bad L=%d / S=%d / digraph", idx, sp.L, sp.S);
+    return ESCG_EINVAL;
+  }
+  for (int a = 0; a < sp.S * sp.S; ++a)
+    if (sp.digraph[a] > 1 || (a / sp.S == a % sp.S && sp.digraph[a])) {
+      set_last_error("replica %d: digraph must be 0/1 with a zero diagonal", idx);
+      return ESCG_EINVAL;
+    }
+  const double I = sp.rates.interact, Pr = sp.rates.reproduce, X = sp.rates.exchange;
+  if (!(I >= 0 && Pr >= 0 && X >= 0) || !((X + I) + Pr > 0) || std::isinf((X + I) + Pr) ||
+      !(sp.p_empty >= 0.0 && sp.p_empty <= 1.0) || sp.max_mcs > 0xFFFFFFFFull) {
+    set_last_error("replica %d: bad rates / p_empty / max_mcs", idx);
+    return ESCG_EINVAL;
+  }
+  pl->part = bpartition(sp.L);
+  for (int k = 0; k < pl->part.P; ++k)
+    if (pl->part.cs[k + 1] - pl->part.cs[k] > kMaxBlock) {
+      set_last_error("replica %d: partition exceeds block limits", idx);
+      return ESCG_EINVAL;
+    }
+  const BPartition& p = pl->part;
+  size_t off = 0;
+  pl->lat = off;
+  off = align_up(off + (size_t)sp.L * escg_lattice_pitch(sp.L), 256);
+  pl->tab = off;
+  off = align_up(off + 4 * (p.cs.size() + p.fs.size() + p.fc.size()), 256);
+  pl->trans = off;
+  off = align_up(off + 4 * (size_t)(sp.S + 1) * (sp.S + 1), 256);
+  pl->done = off;
+  off = align_up(off + 4 * (size_t)p.P * p.P, 256);
+  pl->bytes = off;
+  pl->TE = (uint64_t)std::floor(std::ldexp(sp.p_empty, 32) + 0.5);
+  return ESCG_OK;
+}
+
+// Shared machinery of batches and servers: a pool of replica slots over one
+// device arena, and the chunked persistent execution.
+struct Engine {
   int device = 0;
-  escg_batch_options opt{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  uint8_t* arena = nullptr;
+  uint32_t log_every = 10;
+  int threads = 0;          // CTA size in use (0: autotune on the first chunks)
+  bool use_graph = true;
+  int max_slots = 0;
+  uint8_t* arena_mem = nullptr;
+  Arena arena;
   SlotDesc* d_slots = nullptr;
   SlotState* d_states = nullptr;
   BatchCtl* d_ctl = nullptr;
@@ -371,78 +468,366 @@ struct escg_batch {
   uint32_t* d_active_tmp = nullptr;
   uint32_t* d_table = nullptr;
   uint32_t* d_admit = nullptr;
+  uint32_t* h_pinned = nullptr;   // pinned host words (admit list staging, counters)
+  size_t table_cap = 0;
   std::vector<SlotDesc> h_slots;
-  std::vector<int> L, S;
-  int threads = 0;          // CTA size in use (0: not tuned yet)
-  int grid[3] = {0, 0, 0};  // persistent grid per CTA size 64/128/256
+  std::vector<size_t> slot_off, slot_bytes;
+  std::vector<uint32_t> pending_admit;
+  int grid[3] = {0, 0, 0};
   uint64_t launches = 0;
-  uint64_t mcs_budget_max = 0;
   cudaGraphExec_t graph = nullptr;
-  int graph_chunks = 0;
-  uint32_t* h_nactive = nullptr;  // pinned
   uint32_t spin_limit = 2000000;
+  static constexpr int kGraphChunks = 16;
 };
-
-namespace {
 
 int tsel(int threads) { return threads == 64 ? 0 : (threads == 128 ? 1 : 2); }
 
-cudaError_t launch_batch_kernel(escg_batch* b, int threads) {
-  BatchArgs a{b->d_slots, b->d_states, b->d_ctl, b->d_table, b->opt.log_every, b->spin_limit};
-  const int g = b->grid[tsel(threads)];
+cudaError_t launch_batch_kernel(Engine* e, int threads) {
+  BatchArgs a{e->d_slots, e->d_states, e->d_ctl, e->d_table, e->log_every, e->spin_limit};
+  const int g = e->grid[tsel(threads)];
   if (threads == 64)
-    batch_kernel<64><<<g, 64, 0, b->stream>>>(a);
+    batch_kernel<64><<<g, 64, 0, e->stream>>>(a);
   else if (threads == 128)
-    batch_kernel<128><<<g, 128, 0, b->stream>>>(a);
+    batch_kernel<128><<<g, 128, 0, e->stream>>>(a);
   else
-    batch_kernel<256><<<g, 256, 0, b->stream>>>(a);
+    batch_kernel<256><<<g, 256, 0, e->stream>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_compact(escg_batch* b) {
-  batch_compact_kernel<<<1, kCompactThreads, 0, b->stream>>>(b->d_slots, b->d_states, b->d_ctl, b->d_active,
-                                                             b->d_active_tmp, b->d_table, b->d_admit,
-                                                             b->opt.log_every);
+cudaError_t launch_compact(Engine* e) {
+  batch_compact_kernel<<<1, kCompactThreads, 0, e->stream>>>(e->d_slots, e->d_states, e->d_ctl, e->d_active,
+                                                             e->d_active_tmp, e->d_table, e->d_admit,
+                                                             e->log_every);
   return cudaGetLastError();
 }
 
-// one chunk: compaction (retire / advance) then the persistent work kernel
-cudaError_t enqueue_chunk(escg_batch* b, int threads) {
-  cudaError_t e = launch_compact(b);
-  if (e != cudaSuccess) return e;
-  b->launches += 2;
-  return launch_batch_kernel(b, threads);
+void engine_free(Engine* e) {
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  if (e->graph) cudaGraphExecDestroy(e->graph);
+  cudaFree(e->arena_mem);
+  cudaFree(e->d_slots);
+  cudaFree(e->d_states);
+  cudaFree(e->d_ctl);
+  cudaFree(e->d_active);
+  cudaFree(e->d_active_tmp);
+  cudaFree(e->d_table);
+  cudaFree(e->d_admit);
+  if (e->h_pinned) cudaFreeHost(e->h_pinned);
+  if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+  e->arena_mem = nullptr;
+  e->stream = nullptr;
 }
 
-void free_batch(escg_batch* b) {
-  if (!b) return;
-  if (b->stream) cudaStreamSynchronize(b->stream);
-  if (b->graph) cudaGraphExecDestroy(b->graph);
-  cudaFree(b->arena);
-  cudaFree(b->d_slots);
-  cudaFree(b->d_states);
-  cudaFree(b->d_ctl);
-  cudaFree(b->d_active);
-  cudaFree(b->d_active_tmp);
-  cudaFree(b->d_table);
-  cudaFree(b->d_admit);
-  if (b->h_nactive) cudaFreeHost(b->h_nactive);
-  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
-  delete b;
-}
-
-int active_count(escg_batch* b, uint32_t* out) {
-  if (cudaMemcpyAsync(b->h_nactive, &b->d_ctl->n_active, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(b->stream) != cudaSuccess) {
-    bset_err("reading the active count failed");
-    return ESCG_ECUDA;
+int engine_init(Engine* e, int max_slots, size_t arena_bytes, size_t table_cap, uint32_t log_every,
+                int threads, bool use_graph, void* stream) {
+  if (threads != 0 && threads != 64 && threads != 128 && threads != 256) {
+    set_last_error("threads must be 0, 64, 128 or 256");
+    return ESCG_EINVAL;
   }
-  *out = *b->h_nactive;
+  e->max_slots = max_slots;
+  e->log_every = log_every ? log_every : 10;
+  e->threads = threads;
+  e->use_graph = use_graph;
+  e->table_cap = table_cap;
+  cudaError_t err = cudaGetDevice(&e->device);
+  if (err == cudaSuccess) {
+    if (stream) {
+      e->stream = (cudaStream_t)stream;
+    } else {
+      err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+      e->own_stream = true;
+    }
+  }
+  if (err == cudaSuccess) err = cudaMalloc(&e->arena_mem, arena_bytes);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_slots, sizeof(SlotDesc) * max_slots);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_states, sizeof(SlotState) * max_slots);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_ctl, sizeof(BatchCtl));
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_active, sizeof(uint32_t) * max_slots);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_active_tmp, sizeof(uint32_t) * max_slots);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_table, sizeof(uint32_t) * table_cap);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_admit, sizeof(uint32_t) * (max_slots + 1));
+  if (err == cudaSuccess) err = cudaMallocHost(&e->h_pinned, sizeof(uint32_t) * (max_slots + 16));
+  if (err == cudaSuccess) err = cudaMemsetAsync(e->d_ctl, 0, sizeof(BatchCtl), e->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(e->d_states, 0, sizeof(SlotState) * max_slots, e->stream);
+  if (err != cudaSuccess) {
+    set_last_error("engine allocation failed: %s", cudaGetErrorString(err));
+    return ESCG_ENOMEM;
+  }
+  e->arena.init(arena_bytes);
+  e->h_slots.assign(max_slots, SlotDesc{});
+  e->slot_off.assign(max_slots, 0);
+  e->slot_bytes.assign(max_slots, 0);
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<64>, 64, 0);
+  e->grid[0] = sms * (per < 1 ? 1 : per);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<128>, 128, 0);
+  e->grid[1] = sms * (per < 1 ? 1 : per);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<256>, 256, 0);
+  e->grid[2] = sms * (per < 1 ? 1 : per);
   return ESCG_OK;
 }
 
+// Places a replica into `slot`: arena memory, tables, initial lattice and
+// counts; it joins the active set at the next chunk.  ESCG_ENOMEM if the
+// arena has no room (nothing is changed then).
+int engine_add(Engine* e, const escg_replica_spec& sp, const SlotPlan& pl, int slot) {
+  size_t off = 0;
+  if (!e->arena.alloc(pl.bytes, &off)) {
+    set_last_error("device arena full");
+    return ESCG_ENOMEM;
+  }
+  uint8_t* base = e->arena_mem + off;
+  const BPartition& p = pl.part;
+  std::vector<uint8_t> img(pl.bytes - pl.tab, 0);   // tables | transitions | epochs
+  int32_t* tab = reinterpret_cast<int32_t*>(img.data());
+  size_t w = 0;
+  for (int32_t v : p.cs) tab[w++] = v;
+  for (int32_t v : p.fs) tab[w++] = v;
+  for (int32_t v : p.fc) tab[w++] = v;
+  const int s1 = sp.S + 1;
+  uint8_t* tr = img.data() + (pl.trans - pl.tab);
+  auto dom = [&](int x, int y) { return x != 0 && y != 0 && sp.digraph[(x - 1) * sp.S + (y - 1)] == 1; };
+  for (int act = 0; act < 3; ++act)
+    for (int x = 0; x < s1; ++x)
+      for (int y = 0; y < s1; ++y) {
+        int nx = x, ny = y;
+        if (x != y) {
+          if (act == 0) {
+            nx = y;
+            ny = x;
+          } else if (act == 1) {
+            if (dom(x, y))
+              ny = 0;
+            else if (dom(y, x))
+              nx = 0;
+          } else {
+            if (y == 0)
+              ny = x;
+            else if (x == 0)
+              nx = y;
+          }
+        }
+        tr[(x * s1 + y) * 4 + act] = (uint8_t)(nx | (ny << 4));
+      }
+  SlotDesc sd;
+  std::memset(&sd, 0, sizeof sd);
+  LatticeDesc& d = sd.d;
+  d.lat = base + pl.lat;
+  d.L = sp.L;
+  d.pitch = escg_lattice_pitch(sp.L);
+  d.P = p.P;
+  d.GQ = p.GQ;
+  d.cs = reinterpret_cast<int32_t*>(base + pl.tab);
+  d.fs = d.cs + p.cs.size();
+  d.fc = d.fs + p.fs.size();
+  d.trans = base + pl.trans;
+  d.key0 = (uint32_t)sp.seed;
+  d.key1 = (uint32_t)(sp.seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    d.rk[2 * r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
+    d.rk[2 * r + 1] = d.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  const double I = sp.rates.interact, Pr = sp.rates.reproduce, X = sp.rates.exchange;
+  const double R = (X + I) + Pr;
+  const uint64_t tx = (uint64_t)std::floor(std::ldexp(X / R, 32) + 0.5);
+  const uint64_t txi = (uint64_t)std::floor(std::ldexp((X + I) / R, 32) + 0.5);
+  d.tx = tx >> 32 ? 0xFFFFFFFFu : (uint32_t)tx;
+  d.txi = txi >> 32 ? 0xFFFFFFFFu : (uint32_t)txi;
+  d.S = sp.S;
+  d.uniform64 = 0;
+  fill_perm24(d.perm24);
+  sd.done = reinterpret_cast<uint32_t*>(base + pl.done);
+  sd.max_mcs = (uint32_t)sp.max_mcs;
+  sd.stop_at_extinction = sp.stop_at_extinction ? 1 : 0;
+  sd.nb4 = p.P * p.P / 4;
+  // the slot is idle on the device, so these synchronous copies race nothing
+  cudaError_t err = cudaMemcpy(base + pl.tab, img.data(), img.size(), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(e->d_slots + slot, &sd, sizeof sd, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemsetAsync(e->d_states + slot, 0, sizeof(SlotState), e->stream);
+  if (err == cudaSuccess) err = launch_init(d, pl.TE, e->stream);
+  if (err == cudaSuccess) {
+    e->h_pinned[0] = (uint32_t)slot;   // consumed by the kernel below before the next use
+    err = cudaMemcpyAsync(e->d_admit + e->max_slots, &e->h_pinned[0], sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, e->stream);
+  }
+  if (err == cudaSuccess) {
+    batch_count_kernel<<<1, 256, 0, e->stream>>>(e->d_slots, e->d_states, e->d_admit + e->max_slots, 1);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+  if (err != cudaSuccess) {
+    e->arena.release(off, pl.bytes);
+    set_last_error("replica set-up failed: %s", cudaGetErrorString(err));
+    return ESCG_ECUDA;
+  }
+  e->launches += 2;
+  e->h_slots[slot] = sd;
+  e->slot_off[slot] = off;
+  e->slot_bytes[slot] = pl.bytes;
+  e->pending_admit.push_back((uint32_t)slot);
+  return ESCG_OK;
+}
+
+void engine_release(Engine* e, int slot) {
+  if (e->slot_bytes[slot]) e->arena.release(e->slot_off[slot], e->slot_bytes[slot]);
+  e->slot_bytes[slot] = 0;
+}
+
+int engine_flush_admits(Engine* e) {
+  const uint32_t n = (uint32_t)e->pending_admit.size();
+  if (!n) return ESCG_OK;
+  // the admit list region [0, max_slots-1) and ctl->n_admit are read only by
+  // the next compaction, which follows these copies on the stream
+  cudaError_t err = cudaStreamSynchronize(e->stream);   // the pinned staging is reused
+  for (uint32_t i = 0; i < n && err == cudaSuccess; ++i) e->h_pinned[i] = e->pending_admit[i];
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(e->d_admit, e->h_pinned, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, e->stream);
+  if (err == cudaSuccess) {
+    e->h_pinned[e->max_slots + 8] = n;
+    err = cudaMemcpyAsync(&e->d_ctl->n_admit, &e->h_pinned[e->max_slots + 8], sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, e->stream);
+  }
+  if (err != cudaSuccess) {
+    set_last_error("admission upload failed: %s", cudaGetErrorString(err));
+    return ESCG_ECUDA;
+  }
+  e->pending_admit.clear();
+  return ESCG_OK;
+}
+
+int engine_chunk(Engine* e, int threads) {
+  if (launch_compact(e) != cudaSuccess || launch_batch_kernel(e, threads) != cudaSuccess) {
+    set_last_error("chunk launch failed");
+    return ESCG_ECUDA;
+  }
+  e->launches += 2;
+  return ESCG_OK;
+}
+
+// Online autotuning of the CTA size: one chunk per candidate, timed with
+// events; the physical mapping never changes the results.
+int engine_autotune(Engine* e, uint64_t* chunks_left) {
+  const int cand[3] = {64, 128, 256};
+  float best = 1e30f;
+  int best_t = 256;
+  for (int c = 0; c < 3 && *chunks_left > 0; ++c) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, e->stream);
+    const int rc = engine_chunk(e, cand[c]);
+    cudaEventRecord(e1, e->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != ESCG_OK) return rc;
+    --*chunks_left;
+    if (ms < best) {
+      best = ms;
+      best_t = cand[c];
+    }
+  }
+  e->threads = best_t;
+  return ESCG_OK;
+}
+
+int engine_build_graph(Engine* e) {
+  if (!e->use_graph || e->graph) return ESCG_OK;
+  cudaGraph_t g;
+  if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    set_last_error("CUDA graph capture failed to start");
+    return ESCG_ECUDA;
+  }
+  for (int c = 0; c < Engine::kGraphChunks; ++c) {
+    launch_compact(e);
+    launch_batch_kernel(e, e->threads);
+  }
+  if (cudaStreamEndCapture(e->stream, &g) != cudaSuccess || cudaGraphInstantiate(&e->graph, g, 0) != cudaSuccess) {
+    set_last_error("CUDA graph capture failed");
+    return ESCG_ECUDA;
+  }
+  cudaGraphDestroy(g);
+  return ESCG_OK;
+}
+
+int engine_active(Engine* e, uint32_t* out) {
+  if (cudaMemcpyAsync(&e->h_pinned[e->max_slots + 9], &e->d_ctl->n_active, sizeof(uint32_t),
+                      cudaMemcpyDeviceToHost, e->stream) != cudaSuccess ||
+      cudaStreamSynchronize(e->stream) != cudaSuccess) {
+    set_last_error("reading the active count failed");
+    return ESCG_ECUDA;
+  }
+  *out = e->h_pinned[e->max_slots + 9];
+  return ESCG_OK;
+}
+
+// Runs up to `chunks` chunks (0: until no replica is active), stopping early
+// when the active set empties; ends with a compaction so that every
+// replica's MCS number and retirement are settled.
+int engine_run(Engine* e, uint64_t chunks, bool until_idle) {
+  int rc = engine_flush_admits(e);
+  if (rc != ESCG_OK) return rc;
+  uint64_t left = chunks;
+  if (e->threads == 0) {
+    rc = engine_autotune(e, &left);
+    if (rc != ESCG_OK) return rc;
+  }
+  rc = engine_build_graph(e);
+  if (rc != ESCG_OK) return rc;
+  const uint64_t G = Engine::kGraphChunks;
+  while (until_idle || left > 0) {
+    if (e->graph && (until_idle || left >= G)) {
+      if (cudaGraphLaunch(e->graph, e->stream) != cudaSuccess) {
+        set_last_error("graph launch failed");
+        return ESCG_ECUDA;
+      }
+      e->launches += 2 * G;
+      left = left >= G ? left - G : 0;
+    } else {
+      rc = engine_chunk(e, e->threads);
+      if (rc != ESCG_OK) return rc;
+      left = left ? left - 1 : 0;
+    }
+    uint32_t n_active = 0;
+    rc = engine_active(e, &n_active);
+    if (rc != ESCG_OK) return rc;
+    if (n_active == 0) break;
+  }
+  if (launch_compact(e) != cudaSuccess) {
+    set_last_error("batch compaction launch failed");
+    return ESCG_ECUDA;
+  }
+  e->launches++;
+  return ESCG_OK;
+}
+
+int engine_check(Engine* e) {
+  if (cudaStreamSynchronize(e->stream) != cudaSuccess) {
+    set_last_error("engine stream failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return ESCG_ECUDA;
+  }
+  BatchCtl ctl;
+  if (cudaMemcpy(&ctl, e->d_ctl, sizeof ctl, cudaMemcpyDeviceToHost) != cudaSuccess) return ESCG_ECUDA;
+  if (ctl.error & kErrTimeout) {
+    set_last_error("a bounded device-side wait timed out");
+    return ESCG_ETIMEOUT;
+  }
+  return ESCG_OK;
+}
+
+size_t table_capacity(int max_slots, size_t arena_bytes) { return (size_t)max_slots + arena_bytes / 4096 + 64; }
+
 }  // namespace
+
+struct escg_batch {
+  Engine e;
+  int n = 0;
+  uint64_t budget_max = 0;
+  std::vector<int> L, S;
+};
 
 extern "C" {
 
@@ -456,303 +841,55 @@ void escg_batch_default_options(escg_batch_options* opt) {
 
 escg_batch_t* escg_batch_create(int32_t n, const escg_replica_spec* specs, const escg_batch_options* opt) {
   if (n < 1 || n > 65535 || !specs) {
-    bset_err("need 1 <= n <= 65535 replicas");
+    set_last_error("need 1 <= n <= 65535 replicas");
     return nullptr;
+  }
+  escg_batch_options o;
+  escg_batch_default_options(&o);
+  if (opt) o = *opt;
+  std::vector<SlotPlan> plans(n);
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    if (plan_slot(specs[i], &plans[i], i) != ESCG_OK) return nullptr;
+    total += plans[i].bytes;
   }
   escg_batch* b = new (std::nothrow) escg_batch;
   if (!b) return nullptr;
   b->n = n;
-  escg_batch_default_options(&b->opt);
-  if (opt) b->opt = *opt;
-  if (b->opt.log_every == 0) b->opt.log_every = 10;
-  if (b->opt.threads != 0 && b->opt.threads != 64 && b->opt.threads != 128 && b->opt.threads != 256) {
-    bset_err("threads must be 0, 64, 128 or 256");
-    free_batch(b);
+  if (engine_init(&b->e, n, total, table_capacity(n, total), o.log_every, o.threads, o.use_graph != 0,
+                  o.cuda_stream) != ESCG_OK) {
+    engine_free(&b->e);
+    delete b;
     return nullptr;
   }
-  b->threads = b->opt.threads;
-  // host image of the arena: per replica lattice | tables | trans | done
-  struct Off { size_t lat, tab, trans, done; BPartition part; uint64_t TE; };
-  std::vector<Off> off(n);
-  size_t total = 0;
   for (int i = 0; i < n; ++i) {
-    const escg_replica_spec& sp = specs[i];
-    // validation (shared rules with escg_create)
-    escg_options o;
-    escg_default_options(&o);
-    if (sp.L < 8 || sp.L > 16384 || sp.S < 2 || sp.S > 15 || !sp.digraph) {
-      bset_err("replica %d: bad L=%d / S=%d / digraph", i, sp.L, sp.S);
-      free_batch(b);
+    if (engine_add(&b->e, specs[i], plans[i], i) != ESCG_OK) {
+      engine_free(&b->e);
+      delete b;
       return nullptr;
     }
-    for (int a = 0; a < sp.S * sp.S; ++a)
-      if (sp.digraph[a] > 1 || (a / sp.S == a % sp.S && sp.digraph[a])) {
-        bset_err("replica %d: digraph must be 0/1 with a zero diagonal", i);
-        free_batch(b);
-        return nullptr;
-      }
-    const double I = sp.rates.interact, Pr = sp.rates.reproduce, X = sp.rates.exchange;
-    if (!(I >= 0 && Pr >= 0 && X >= 0) || !((X + I) + Pr > 0) || std::isinf((X + I) + Pr) ||
-        !(sp.p_empty >= 0.0 && sp.p_empty <= 1.0) || sp.max_mcs > 0xFFFFFFFFull) {
-      bset_err("replica %d: bad rates / p_empty / max_mcs", i);
-      free_batch(b);
-      return nullptr;
-    }
-    Off& f = off[i];
-    f.part = bpartition(sp.L);
-    for (int k = 0; k < f.part.P; ++k)
-      if (f.part.cs[k + 1] - f.part.cs[k] > kMaxBlock) {
-        bset_err("replica %d: partition exceeds block limits", i);
-        free_batch(b);
-        return nullptr;
-      }
-    const int pitch = escg_lattice_pitch(sp.L);
-    f.lat = total;
-    total = align_up(total + (size_t)sp.L * pitch, 256);
-    f.tab = total;
-    total = align_up(total + 4 * (f.part.cs.size() + f.part.fs.size() + f.part.fc.size()), 256);
-    f.trans = total;
-    total = align_up(total + 4 * (size_t)(sp.S + 1) * (sp.S + 1), 256);
-    f.done = total;
-    total = align_up(total + 4 * (size_t)f.part.P * f.part.P, 256);
-    f.TE = (uint64_t)std::floor(std::ldexp(sp.p_empty, 32) + 0.5);
-    b->L.push_back(sp.L);
-    b->S.push_back(sp.S);
-    if (sp.max_mcs > b->mcs_budget_max) b->mcs_budget_max = sp.max_mcs;
+    b->L.push_back(specs[i].L);
+    b->S.push_back(specs[i].S);
+    if (specs[i].max_mcs > b->budget_max) b->budget_max = specs[i].max_mcs;
   }
-  cudaError_t e = cudaGetDevice(&b->device);
-  if (e == cudaSuccess) {
-    if (b->opt.cuda_stream) {
-      b->stream = (cudaStream_t)b->opt.cuda_stream;
-    } else {
-      e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-      b->own_stream = true;
-    }
-  }
-  size_t table_cap = 0;
-  for (int i = 0; i < n; ++i) table_cap += (size_t)off[i].part.P * off[i].part.P / 4;
-  if (e == cudaSuccess) e = cudaMalloc(&b->arena, total);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_slots, sizeof(SlotDesc) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_states, sizeof(SlotState) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_active, sizeof(uint32_t) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_active_tmp, sizeof(uint32_t) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_table, sizeof(uint32_t) * table_cap);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_admit, sizeof(uint32_t) * n);
-  if (e == cudaSuccess) e = cudaMallocHost(&b->h_nactive, sizeof(uint32_t));
-  if (e != cudaSuccess) {
-    bset_err("batch allocation failed: %s", cudaGetErrorString(e));
-    free_batch(b);
-    return nullptr;
-  }
-  std::vector<uint8_t> image(total, 0);
-  b->h_slots.resize(n);
-  for (int i = 0; i < n; ++i) {
-    const escg_replica_spec& sp = specs[i];
-    const Off& f = off[i];
-    const BPartition& p = f.part;
-    int32_t* tab = reinterpret_cast<int32_t*>(image.data() + f.tab);
-    size_t w = 0;
-    for (int32_t v : p.cs) tab[w++] = v;
-    for (int32_t v : p.fs) tab[w++] = v;
-    for (int32_t v : p.fc) tab[w++] = v;
-    // transition table of Alg. 3 (same layout as the single-lattice path)
-    const int s1 = sp.S + 1;
-    uint8_t* tr = image.data() + f.trans;
-    auto dom = [&](int x, int y) { return x != 0 && y != 0 && sp.digraph[(x - 1) * sp.S + (y - 1)] == 1; };
-    for (int act = 0; act < 3; ++act)
-      for (int x = 0; x < s1; ++x)
-        for (int y = 0; y < s1; ++y) {
-          int nx = x, ny = y;
-          if (x != y) {
-            if (act == 0) {
-              nx = y;
-              ny = x;
-            } else if (act == 1) {
-              if (dom(x, y))
-                ny = 0;
-              else if (dom(y, x))
-                nx = 0;
-            } else {
-              if (y == 0)
-                ny = x;
-              else if (x == 0)
-                nx = y;
-            }
-          }
-          tr[(x * s1 + y) * 4 + act] = (uint8_t)(nx | (ny << 4));
-        }
-    SlotDesc& sd = b->h_slots[i];
-    std::memset(&sd, 0, sizeof sd);
-    LatticeDesc& d = sd.d;
-    d.lat = b->arena + f.lat;
-    d.L = sp.L;
-    d.pitch = escg_lattice_pitch(sp.L);
-    d.P = p.P;
-    d.GQ = p.GQ;
-    d.cs = reinterpret_cast<int32_t*>(b->arena + f.tab);
-    d.fs = d.cs + p.cs.size();
-    d.fc = d.fs + p.fs.size();
-    d.trans = b->arena + f.trans;
-    d.key0 = (uint32_t)sp.seed;
-    d.key1 = (uint32_t)(sp.seed >> 32);
-    for (int r = 0; r < 10; ++r) {
-      d.rk[2 * r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
-      d.rk[2 * r + 1] = d.key1 + (uint32_t)r * 0xBB67AE85u;
-    }
-    const double I = sp.rates.interact, Pr = sp.rates.reproduce, X = sp.rates.exchange;
-    const double R = (X + I) + Pr;
-    const uint64_t tx = (uint64_t)std::floor(std::ldexp(X / R, 32) + 0.5);
-    const uint64_t txi = (uint64_t)std::floor(std::ldexp((X + I) / R, 32) + 0.5);
-    d.tx = tx >> 32 ? 0xFFFFFFFFu : (uint32_t)tx;
-    d.txi = txi >> 32 ? 0xFFFFFFFFu : (uint32_t)txi;
-    d.S = sp.S;
-    d.uniform64 = 0;
-    fill_perm24(d.perm24);
-    sd.done = reinterpret_cast<uint32_t*>(b->arena + f.done);
-    sd.max_mcs = (uint32_t)sp.max_mcs;
-    sd.stop_at_extinction = sp.stop_at_extinction ? 1 : 0;
-    sd.nb4 = p.P * p.P / 4;
-  }
-  std::vector<uint32_t> admit(n);
-  for (int i = 0; i < n; ++i) admit[i] = (uint32_t)i;
-  BatchCtl ctl{};
-  ctl.n_admit = (uint32_t)n;
-  e = cudaMemcpyAsync(b->arena, image.data(), total, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_slots, b->h_slots.data(), sizeof(SlotDesc) * n, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_states, 0, sizeof(SlotState) * n, b->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_admit, admit.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, b->stream);
-  for (int i = 0; i < n && e == cudaSuccess; ++i) {
-    e = launch_init(b->h_slots[i].d, off[i].TE, b->stream);
-    b->launches++;
-  }
-  if (e == cudaSuccess) {
-    batch_count_kernel<<<n, 256, 0, b->stream>>>(b->d_slots, b->d_states, nullptr, n);
-    e = cudaGetLastError();
-    b->launches++;
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // image is host stack memory
-  if (e != cudaSuccess) {
-    bset_err("batch initialisation failed: %s", cudaGetErrorString(e));
-    free_batch(b);
-    return nullptr;
-  }
-  int sms = 0, per = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<64>, 64, 0);
-  b->grid[0] = sms * (per < 1 ? 1 : per);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<128>, 128, 0);
-  b->grid[1] = sms * (per < 1 ? 1 : per);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<256>, 256, 0);
-  b->grid[2] = sms * (per < 1 ? 1 : per);
   return b;
 }
 
 int escg_batch_run(escg_batch_t* b, uint64_t max_mcs) {
   if (!b) return ESCG_EINVAL;
-  const uint32_t le = b->opt.log_every;
-  uint64_t chunks_left = max_mcs ? (max_mcs + le - 1) / le : (b->mcs_budget_max + le - 1) / le + 1;
-  // online autotuning of the CTA size: one chunk per candidate, timed with
-  // events; the physical mapping never changes the results
-  if (b->threads == 0) {
-    const int cand[3] = {64, 128, 256};
-    float best = 1e30f;
-    int best_t = 256;
-    for (int c = 0; c < 3 && chunks_left > 0; ++c) {
-      cudaEvent_t e0, e1;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      cudaEventRecord(e0, b->stream);
-      if (enqueue_chunk(b, cand[c]) != cudaSuccess) {
-        bset_err("batch chunk launch failed");
-        return ESCG_ECUDA;
-      }
-      cudaEventRecord(e1, b->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      --chunks_left;
-      if (ms < best) {
-        best = ms;
-        best_t = cand[c];
-      }
-    }
-    b->threads = best_t;
-  }
-  const int G = 16;   // chunks per graph replay
-  if (b->opt.use_graph && !b->graph) {
-    cudaGraph_t g;
-    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      bset_err("CUDA graph capture failed to start");
-      return ESCG_ECUDA;
-    }
-    for (int c = 0; c < G; ++c) {
-      launch_compact(b);
-      launch_batch_kernel(b, b->threads);
-    }
-    if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess ||
-        cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) {
-      bset_err("CUDA graph capture failed");
-      return ESCG_ECUDA;
-    }
-    cudaGraphDestroy(g);
-    b->graph_chunks = G;
-  }
-  while (chunks_left > 0) {
-    if (b->graph && chunks_left >= (uint64_t)G) {
-      if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) {
-        bset_err("graph launch failed");
-        return ESCG_ECUDA;
-      }
-      b->launches += 2 * G;
-      chunks_left -= G;
-    } else {
-      if (enqueue_chunk(b, b->threads) != cudaSuccess) {
-        bset_err("batch chunk launch failed");
-        return ESCG_ECUDA;
-      }
-      chunks_left -= 1;
-    }
-    uint32_t n_active = 0;
-    const int rc = active_count(b, &n_active);
-    if (rc != ESCG_OK) return rc;
-    if (n_active == 0) break;
-  }
-  // settle the MCS numbers and retirements of the last chunk
-  if (launch_compact(b) != cudaSuccess) {
-    bset_err("batch compaction launch failed");
-    return ESCG_ECUDA;
-  }
-  b->launches++;
-  return ESCG_OK;
+  const uint32_t le = b->e.log_every;
+  if (max_mcs == 0) return engine_run(&b->e, (b->budget_max + le - 1) / le + 1, false);
+  return engine_run(&b->e, (max_mcs + le - 1) / le, false);
 }
 
-int escg_batch_sync(escg_batch_t* b) {
-  if (!b) return ESCG_EINVAL;
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
-    bset_err("batch stream failed: %s", cudaGetErrorString(cudaGetLastError()));
-    return ESCG_ECUDA;
-  }
-  BatchCtl ctl;
-  if (cudaMemcpy(&ctl, b->d_ctl, sizeof ctl, cudaMemcpyDeviceToHost) != cudaSuccess) return ESCG_ECUDA;
-  if (ctl.error & kErrTimeout) {
-    bset_err("a bounded device-side wait timed out");
-    return ESCG_ETIMEOUT;
-  }
-  return ESCG_OK;
-}
+int escg_batch_sync(escg_batch_t* b) { return b ? engine_check(&b->e) : ESCG_EINVAL; }
 
 int escg_batch_status(escg_batch_t* b, uint64_t* mcs_out, int32_t* extinct_out, uint64_t* counts16_out) {
   if (!b) return ESCG_EINVAL;
-  int rc = escg_batch_sync(b);
+  int rc = engine_check(&b->e);
   if (rc != ESCG_OK) return rc;
   std::vector<SlotState> st(b->n);
-  if (cudaMemcpy(st.data(), b->d_states, sizeof(SlotState) * b->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpy(st.data(), b->e.d_states, sizeof(SlotState) * b->n, cudaMemcpyDeviceToHost) != cudaSuccess)
     return ESCG_ECUDA;
   for (int i = 0; i < b->n; ++i) {
     if (mcs_out) mcs_out[i] = st[i].mcs;
@@ -766,23 +903,227 @@ int escg_batch_status(escg_batch_t* b, uint64_t* mcs_out, int32_t* extinct_out, 
 int32_t escg_batch_active(escg_batch_t* b) {
   if (!b) return -1;
   uint32_t n = 0;
-  if (active_count(b, &n) != ESCG_OK) return -1;
+  if (engine_active(&b->e, &n) != ESCG_OK) return -1;
   return (int32_t)n;
 }
 
 int escg_batch_snapshot(escg_batch_t* b, int32_t i, uint8_t* host_out) {
   if (!b || i < 0 || i >= b->n || !host_out) return ESCG_EINVAL;
-  int rc = escg_batch_sync(b);
+  int rc = engine_check(&b->e);
   if (rc != ESCG_OK) return rc;
-  const LatticeDesc& d = b->h_slots[i].d;
+  const LatticeDesc& d = b->e.h_slots[i].d;
   if (cudaMemcpy2D(host_out, d.L, d.lat, d.pitch, d.L, d.L, cudaMemcpyDeviceToHost) != cudaSuccess)
     return ESCG_ECUDA;
   return ESCG_OK;
 }
 
-int32_t escg_batch_threads(escg_batch_t* b) { return b ? b->threads : 0; }
-uint64_t escg_batch_launch_count(escg_batch_t* b) { return b ? b->launches : 0; }
+int32_t escg_batch_threads(escg_batch_t* b) { return b ? b->e.threads : 0; }
+uint64_t escg_batch_launch_count(escg_batch_t* b) { return b ? b->e.launches : 0; }
 
-void escg_batch_destroy(escg_batch_t* b) { free_batch(b); }
+void escg_batch_destroy(escg_batch_t* b) {
+  if (!b) return;
+  engine_free(&b->e);
+  delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: a FIFO request queue over the slot engine.
+namespace {
+
+struct Request {
+  int64_t id = 0;
+  escg_replica_spec spec{};
+  std::vector<uint8_t> digraph;   // owned copy
+  SlotPlan plan;
+};
+
+struct Result {
+  uint64_t mcs = 0;
+  int32_t extinct = 0;
+  uint64_t counts[kMaxStates] = {};
+  std::vector<uint8_t> lattice;
+};
+
+}  // namespace
+
+struct escg_server {
+  Engine e;
+  escg_server_options opt{};
+  std::deque<Request> queue;
+  std::vector<int64_t> slot_req;     // request id resident in each slot, -1 free
+  std::vector<int> free_slots;
+  std::vector<int> slot_L;
+  std::unordered_map<int64_t, Result> results;
+  std::vector<int64_t> finished;     // not yet polled
+  int64_t next_id = 0;
+  int resident = 0;
+};
+
+extern "C" {
+
+void escg_server_default_options(escg_server_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof *opt);
+  opt->arena_bytes = 256ull << 20;
+  opt->max_slots = 1024;
+  opt->log_every = 10;
+  opt->threads = 0;
+  opt->chunks_per_step = 4;
+  opt->keep_lattice = 0;
+}
+
+escg_server_t* escg_server_create(const escg_server_options* opt) {
+  escg_server* s = new (std::nothrow) escg_server;
+  if (!s) return nullptr;
+  escg_server_default_options(&s->opt);
+  if (opt) s->opt = *opt;
+  if (s->opt.max_slots < 1 || s->opt.max_slots > 65535 || s->opt.arena_bytes < 4096) {
+    set_last_error("server needs 1 <= max_slots <= 65535 and a non-trivial arena");
+    delete s;
+    return nullptr;
+  }
+  if (s->opt.chunks_per_step == 0) s->opt.chunks_per_step = 4;
+  if (engine_init(&s->e, s->opt.max_slots, s->opt.arena_bytes,
+                  table_capacity(s->opt.max_slots, s->opt.arena_bytes), s->opt.log_every, s->opt.threads,
+                  true, s->opt.cuda_stream) != ESCG_OK) {
+    engine_free(&s->e);
+    delete s;
+    return nullptr;
+  }
+  s->slot_req.assign(s->opt.max_slots, -1);
+  s->slot_L.assign(s->opt.max_slots, 0);
+  for (int i = s->opt.max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+  return s;
+}
+
+int64_t escg_server_submit(escg_server_t* s, const escg_replica_spec* spec) {
+  if (!s || !spec) {
+    set_last_error("NULL argument");
+    return ESCG_EINVAL;
+  }
+  Request r;
+  r.id = s->next_id;
+  if (plan_slot(*spec, &r.plan, (int)r.id) != ESCG_OK) return ESCG_EINVAL;
+  if (r.plan.bytes > s->e.arena.capacity()) {
+    set_last_error("run needs %zu bytes, more than the whole arena", r.plan.bytes);
+    return ESCG_ENOMEM;
+  }
+  r.spec = *spec;
+  r.digraph.assign(spec->digraph, spec->digraph + spec->S * spec->S);
+  r.spec.digraph = r.digraph.data();
+  s->queue.push_back(std::move(r));
+  s->queue.back().spec.digraph = s->queue.back().digraph.data();
+  return s->next_id++;
+}
+
+int escg_server_step(escg_server_t* s, int32_t* finished_out) {
+  if (!s) return ESCG_EINVAL;
+  // 1. admissions, FIFO, while a slot and arena room are free
+  while (!s->queue.empty() && !s->free_slots.empty()) {
+    Request& r = s->queue.front();
+    const int slot = s->free_slots.back();
+    const int rc = engine_add(&s->e, r.spec, r.plan, slot);
+    if (rc == ESCG_ENOMEM) break;   // wait for retirements
+    if (rc != ESCG_OK) return rc;
+    s->free_slots.pop_back();
+    s->slot_req[slot] = r.id;
+    s->slot_L[slot] = r.spec.L;
+    s->resident++;
+    s->queue.pop_front();
+  }
+  int32_t nfin = 0;
+  if (s->resident > 0) {
+    // 2. advance every resident run
+    int rc = engine_run(&s->e, s->opt.chunks_per_step, false);
+    if (rc == ESCG_OK) rc = engine_check(&s->e);
+    if (rc != ESCG_OK) return rc;
+    // 3. retire finished runs
+    std::vector<SlotState> st(s->opt.max_slots);
+    if (cudaMemcpy(st.data(), s->e.d_states, sizeof(SlotState) * s->opt.max_slots, cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
+      set_last_error("reading run states failed");
+      return ESCG_ECUDA;
+    }
+    for (int slot = 0; slot < s->opt.max_slots; ++slot) {
+      if (s->slot_req[slot] < 0) continue;
+      const SlotState& x = st[slot];
+      if (!(x.stopped || x.mcs >= s->e.h_slots[slot].max_mcs)) continue;
+      Result res;
+      res.mcs = x.mcs;
+      res.extinct = (int32_t)x.stopped;
+      for (int v = 0; v < kMaxStates; ++v) res.counts[v] = x.counts[v];
+      if (s->opt.keep_lattice) {
+        const LatticeDesc& d = s->e.h_slots[slot].d;
+        res.lattice.resize((size_t)d.L * d.L);
+        if (cudaMemcpy2D(res.lattice.data(), d.L, d.lat, d.pitch, d.L, d.L, cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+          set_last_error("copying a finished lattice failed");
+          return ESCG_ECUDA;
+        }
+      }
+      const int64_t id = s->slot_req[slot];
+      s->results[id] = std::move(res);
+      s->finished.push_back(id);
+      engine_release(&s->e, slot);
+      s->slot_req[slot] = -1;
+      s->free_slots.push_back(slot);
+      s->resident--;
+      nfin++;
+    }
+  }
+  if (finished_out) *finished_out = nfin;
+  return ESCG_OK;
+}
+
+int escg_server_poll(escg_server_t* s, int64_t* ids_out, int32_t cap, int32_t* n_out) {
+  if (!s || (cap > 0 && !ids_out) || cap < 0) return ESCG_EINVAL;
+  const int32_t n = (int32_t)std::min<size_t>((size_t)cap, s->finished.size());
+  for (int32_t i = 0; i < n; ++i) ids_out[i] = s->finished[i];
+  s->finished.erase(s->finished.begin(), s->finished.begin() + n);
+  if (n_out) *n_out = n;
+  return ESCG_OK;
+}
+
+int escg_server_result(escg_server_t* s, int64_t id, uint64_t* mcs_out, int32_t* extinct_out,
+                       uint64_t* counts16_out, uint8_t* lattice_out) {
+  if (!s) return ESCG_EINVAL;
+  auto it = s->results.find(id);
+  if (it == s->results.end()) {
+    set_last_error("run %lld has not finished", (long long)id);
+    return ESCG_ESTATE;
+  }
+  const Result& r = it->second;
+  if (mcs_out) *mcs_out = r.mcs;
+  if (extinct_out) *extinct_out = r.extinct;
+  if (counts16_out)
+    for (int v = 0; v < kMaxStates; ++v) counts16_out[v] = r.counts[v];
+  if (lattice_out) {
+    if (r.lattice.empty()) {
+      set_last_error("lattices are kept only with keep_lattice");
+      return ESCG_ESTATE;
+    }
+    std::memcpy(lattice_out, r.lattice.data(), r.lattice.size());
+  }
+  return ESCG_OK;
+}
+
+int escg_server_stats(escg_server_t* s, int32_t* resident, int32_t* queued, uint64_t* bytes_in_use) {
+  if (!s) return ESCG_EINVAL;
+  if (resident) *resident = s->resident;
+  if (queued) *queued = (int32_t)s->queue.size();
+  if (bytes_in_use) *bytes_in_use = s->e.arena.used();
+  return ESCG_OK;
+}
+
+int32_t escg_server_threads(escg_server_t* s) { return s ? s->e.threads : 0; }
+uint64_t escg_server_launch_count(escg_server_t* s) { return s ? s->e.launches : 0; }
+
+void escg_server_destroy(escg_server_t* s) {
+  if (!s) return;
+  engine_free(&s->e);
+  delete s;
+}
 
 }  // extern "C"

@@ -1,0 +1,76 @@
+"""Serving with continuous batching: runs submitted while others are on the
+GPU are admitted as slots and memory free up, and every result (MCS reached,
+extinction flag, counts, lattice) is bit-identical to running it alone."""
+import numpy as np
+import pytest
+
+import paper_2508_16639_gb300 as E
+from paper_2508_16639_gb300 import workloads as W
+from paper_2508_16639_gb300.build import build
+from paper_2508_16639_gb300.serve import request_spec, serve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+
+
+def _reqs(n, seed, L_range=(50, 300), budget=(20, 200)):
+    return W.request_stream(n=n, seed=seed, rate_per_s=200.0, L_range=L_range, budget_range=budget)
+
+
+def _alone(sp):
+    g = E.Lattice(sp["L"], sp["S"], sp["digraph"], sp["rates"], sp["seed"], p_empty=sp["p_empty"],
+                  log_every=10, stop_at_extinction=sp["stop_at_extinction"])
+    g.run(sp["max_mcs"])
+    ms, log = g.counts_log()
+    return g.mcs, g.snapshot(), log[-1]
+
+
+@pytest.mark.parametrize("arena_mb,max_slots", [(256, 64), (1, 8)])
+def test_served_runs_match_single_runs(arena_mb, max_slots):
+    reqs = _reqs(24, seed=5)
+    srv = E.Server(arena_bytes=arena_mb << 20, max_slots=max_slots, keep_lattice=True,
+                   chunks_per_step=2)
+    ids = {}
+    queued_seen = 0
+    # arrivals interleaved with steps: 6 submissions, a step, 6 more, ...
+    for k in range(0, len(reqs), 6):
+        for r in reqs[k:k + 6]:
+            ids[srv.submit(request_spec(r))] = r
+        srv.step()
+        queued_seen = max(queued_seen, srv.stats()[1])
+    done = set()
+    for _ in range(10000):
+        done.update(srv.poll())
+        if len(done) == len(reqs):
+            break
+        srv.step()
+    assert len(done) == len(reqs)
+    if arena_mb == 1:
+        assert queued_seen > 0   # memory admission made runs wait
+    for rid, r in ids.items():
+        sp = request_spec(r)
+        mcs, ext, cnt, lat = srv.result(rid, lattice=True)
+        m1, lat1, c1 = _alone(sp)
+        assert mcs == m1, rid
+        assert np.array_equal(lat, lat1), rid
+        assert np.array_equal(cnt[:sp["S"] + 1], c1), rid
+        assert ext == (sp["stop_at_extinction"] and (c1[1:] > 0).sum() <= 1)
+    assert srv.stats() == (0, 0, 0)
+
+
+def test_serve_loop_reports_latency():
+    reqs = _reqs(40, seed=9, L_range=(50, 200), budget=(20, 100))
+    out = serve(reqs, time_scale=0.05, arena_bytes=64 << 20, max_slots=32, chunks_per_step=2)
+    assert out["runs"] == 40 and out["runs_per_s"] > 0
+    assert 0 < out["p50_latency_s"] <= out["p99_latency_s"]
+
+
+def test_submit_rejects_runs_larger_than_the_arena():
+    srv = E.Server(arena_bytes=64 << 10, max_slots=4)
+    r = _reqs(1, seed=1, L_range=(600, 601))[0]
+    with pytest.raises(E.EscgError):
+        srv.submit(request_spec(r))
