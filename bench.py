@@ -79,6 +79,13 @@ def _parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--L", type=int, default=3200, help="lattice side (3200 is the benchmark)")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-replicas", type=int, default=1024)
+    ap.add_argument("--ensemble-baseline-sample", type=int, default=16)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rate", type=float, default=400.0,
+                    help="mean Poisson arrival rate (requests/s); above capacity = saturated")
     return ap.parse_args()
 
 
@@ -196,6 +203,43 @@ def _config(w, mcs_per_step):
             "parallelism": "replicas (one independent lattice per GPU)"}
 
 
+def _ensemble(args, rank):
+    """Batched ensemble: independent replicas (L uniform on {64,100,200,400},
+    RPS/RPSLS, M log-uniform on [1e-5, 1e-3]) each to extinction or 10^4 MCS
+    in shared persistent launches; beside it, a sample of the same runs one
+    at a time through the single-lattice path."""
+    import numpy as np
+    from paper_2508_16639_gb300 import workloads as W
+    from paper_2508_16639_gb300.ensemble import run_batch, run_one_at_a_time
+    reps = W.ensemble(args.ensemble_replicas, seed=1 + rank)
+    out, mcs, ext = run_batch(reps)
+    sample_idx = np.random.default_rng(0).choice(len(reps), min(args.ensemble_baseline_sample, len(reps)),
+                                                 replace=False)
+    base, mcs1 = run_one_at_a_time([reps[i] for i in sample_idx])
+    out["metric"] = "ensemble runs/s"
+    out["config"] = {"workload": f"{len(reps)} replicas, L in {{64,100,200,400}}, S in {{3,5}}, "
+                                 "M log-uniform [1e-5,1e-3], to extinction or 10^4 MCS, log every 10 MCS"}
+    out["per_run_launches"] = dict(base, sample=f"{len(sample_idx)} of the same runs, one at a time",
+                                   identical_mcs=bool(np.array_equal(mcs1, mcs[sample_idx])))
+    out["speedup_vs_per_run"] = out["runs_per_s"] / base["runs_per_s"]
+    return out
+
+
+def _serving(args, rank):
+    """Serving: Poisson arrivals of run requests (L log-uniform [50,1600],
+    S in {3,5}, budgets log-uniform 10^2-10^4 MCS, half stop at extinction),
+    continuous batching with admission by free device memory."""
+    from paper_2508_16639_gb300 import workloads as W
+    from paper_2508_16639_gb300.serve import serve
+    reqs = W.request_stream(n=args.serve_requests, seed=2 + rank, rate_per_s=args.serve_rate)
+    out = serve(reqs, arena_bytes=4 << 30, max_slots=4096, chunks_per_step=4)
+    out["metric"] = "served runs/s and p50/p99 latency (arrival to result)"
+    out["config"] = {"workload": f"{len(reqs)} requests, Poisson rate {args.serve_rate}/s, "
+                                 "L log-uniform [50,1600], S in {3,5}, budget log-uniform [1e2,1e4] MCS, "
+                                 "50% stop at extinction", "arena_bytes": 4 << 30, "max_slots": 4096}
+    return out
+
+
 def main():
     args = _parse()
     if args.impl == "reference":
@@ -300,6 +344,13 @@ def main():
                "d2h_bytes_per_step": N + 8 * (w.S + 1), "ms_per_step": 1e3 * el / K,
                "api": "escg_step_host (restore + run + snapshot + counts), pinned host buffers"}
 
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = _ensemble(args, rank)
+    serving = None
+    if not args.no_serving:
+        serving = _serving(args, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, nmcs, el = _cpu_oracle_rate(w, args.cpu_seconds)
@@ -313,6 +364,7 @@ def main():
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": _config(w, mps), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks,
+                "ensemble": ensemble, "serving": serving,
                 "context": {"paper_cuda_ms_L3200_site_updates_per_s": 2.45e8,
                             "paper_hardware": "RTX A2000 (not a target)"}}
         print(json.dumps(line), flush=True)
