@@ -303,10 +303,7 @@ __global__ void __launch_bounds__(THREADS) batch_kernel(BatchArgs a) {
         }
       }
     }
-    if (tid == 0) {
-      __threadfence();
-      b_st_release(sd.done + by * P + bx, m + 1u);
-    }
+    if (tid == 0) b_st_release(sd.done + by * P + bx, m + 1u);   // release orders the tile stores
   }
   // the last CTA to leave records how far this launch advanced the replicas
   if (tid == 0) {

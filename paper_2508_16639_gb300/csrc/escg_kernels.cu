@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
         }
       }
       if (tid == 0 && by * P + bx != a.stall_block) {
-        __threadfence();
+        // st.release orders the CTA's tile stores (made before the barrier
+        // above) before the new epoch; no separate fence is needed
         st_release(a.done + by * P + bx, m + 1u);
       }
     }
@@ -577,7 +578,6 @@ __device__ void tma_consumer(const TmaArgs& a, TmaSmem& sm) {
       if (it.by * P + it.bx != p.stall_block) {
         // release: the consumers' stores (ordered before by the named
         // barrier) become visible before the new epoch
-        __threadfence();
         st_release(p.done + it.by * P + it.bx, it.m + 1u);
       }
       mbar_arrive(&sm.empty[b]);   // the tile may be refilled
