@@ -87,6 +87,13 @@ Partition make_partition(int L) {
 // (columns beyond L are out of bounds and read as zero), row stride pitch,
 // box 112 x 66 bytes.
 bool make_tensor_map(CUtensorMap* map, uint8_t* lattice, int L, int pitch) {
+  return encode_lattice_map(map, lattice, L, pitch, 112, 66);
+}
+
+}  // namespace
+
+bool escg_impl::encode_lattice_map(CUtensorMap* map, uint8_t* lattice, int L, int pitch, int box_w,
+                                   int box_h) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -99,12 +106,14 @@ bool make_tensor_map(CUtensorMap* map, uint8_t* lattice, int L, int pitch) {
   }
   const cuuint64_t dims[2] = {(cuuint64_t)L, (cuuint64_t)L};
   const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-  const cuuint32_t box[2] = {112u, 66u};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
   const cuuint32_t elem[2] = {1u, 1u};
   return encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, lattice, dims, strides, box, elem,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+namespace {
 
 bool partition_fits(const Partition& p) {
   for (int k = 0; k < p.P; ++k) {

@@ -34,6 +34,7 @@
 #include "escg.h"
 #include "escg_device.cuh"
 #include "escg_internal.h"
+#include "escg_tma.cuh"
 
 namespace escg_impl {
 
@@ -315,6 +316,312 @@ __global__ void __launch_bounds__(THREADS) batch_kernel(BatchArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised variant of the chunk kernel.  The last warp (producer)
+// prepares the next work item in one of two buffers while the CONS consumer
+// threads compute on the other: it takes tickets (skipping items beyond a
+// replica's budget), copies the replica's descriptor, transition table and
+// the block's fine partition into shared memory, waits for the block's 8
+// neighbours, and stages block + rim with one TMA box load through the
+// replica's tensor map (box 144 x 98 bytes from (floor16(x0-1), y0-1); the
+// wrap-around rim cells of blocks on the lattice edge, which the box fills
+// with zeros, are patched afterwards).
+constexpr int kBSP = 144, kBRows = kMaxBlock + 2;
+constexpr uint32_t kBBoxBytes = (uint32_t)(kBSP * kBRows);   // 14112
+constexpr int kBTileStride = 14208;                          // 128-byte multiple
+constexpr uint32_t kBMbarLimit = 1u << 26;
+
+struct BItem {
+  uint32_t m, ord, forder, quit;
+  int32_t slot, k, bx, by, colour, x0, y0, bw, bh, xoff, fx0, fy0, Qx, Qy;
+  int16_t fsx[kMaxFine + 2], fsy[kMaxFine + 2];
+};
+
+struct BatchTmaSmem {
+  alignas(128) uint8_t tile[2][kBTileStride];
+  uint32_t trans[2][kMaxStates * kMaxStates];
+  SlotDesc sd[2];
+  BItem item[2];
+  alignas(8) uint64_t full[2], empty[2], tma[2];
+  uint32_t hist[kMaxStates];
+};
+
+struct BatchTmaArgs {
+  BatchArgs a;
+  const CUtensorMap* maps;   // one per slot
+};
+
+__device__ __forceinline__ void btma_fail(BatchCtl* ctl) {
+  atomicOr(&ctl->error, kErrTimeout);
+  atomicExch(&ctl->abort, 1u);
+}
+
+__device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t total, uint32_t tot4) {
+  const BatchArgs& a = ta.a;
+  BatchCtl* ctl = a.ctl;
+  const int lane = threadIdx.x & 31;
+  for (uint32_t n = 0;; ++n) {
+    const int b = (int)(n & 1u);
+    const uint32_t use = n >> 1;
+    // next ticket whose MCS is within its replica's budget
+    uint32_t quit = 0, slot = 0, j = 0, k = 0, m = 0;
+    if (lane == 0) {
+      for (;;) {
+        const uint32_t t = atomicAdd(&ctl->ticket, 1u);
+        if ((uint64_t)t >= total || b_ld_volatile(&ctl->abort)) {
+          quit = 1;
+          break;
+        }
+        const uint32_t i = t / (4u * tot4), rem = t - i * 4u * tot4;
+        k = rem / tot4;
+        const uint32_t e = a.table[rem - k * tot4];
+        slot = e >> 16;
+        j = e & 0xFFFFu;
+        m = a.states[slot].mcs + i;
+        if (m < a.slots[slot].max_mcs) break;
+      }
+      if (!mbar_wait(&sm.empty[b], (use & 1u) ^ 1u, kBMbarLimit)) {
+        btma_fail(ctl);
+        quit = 1;
+      }
+    }
+    quit = __shfl_sync(0xFFFFFFFFu, quit, 0);
+    if (quit) {
+      if (lane == 0) sm.item[b].quit = 1;
+      __syncwarp();
+      mbar_arrive(&sm.full[b]);
+      return;
+    }
+    slot = __shfl_sync(0xFFFFFFFFu, slot, 0);
+    j = __shfl_sync(0xFFFFFFFFu, j, 0);
+    k = __shfl_sync(0xFFFFFFFFu, k, 0);
+    m = __shfl_sync(0xFFFFFFFFu, m, 0);
+    {  // replica descriptor into this buffer
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(a.slots + slot);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.sd[b]);
+      for (int w = lane; w < (int)(sizeof(SlotDesc) / 4); w += 32) dst[w] = src[w];
+    }
+    __syncwarp();
+    const SlotDesc& sd = sm.sd[b];
+    const LatticeDesc& d = sd.d;
+    const int P = d.P, half = P >> 1;
+    uint32_t ord = 0;
+    if (lane == 0) ord = colour_order(philox10_rk(make_uint4(0u, 0u, m, kTagOrder), d.rk).x, d.perm24);
+    ord = __shfl_sync(0xFFFFFFFFu, ord, 0);
+    const int colour = order_at(ord, (int)k);
+    const int bx = 2 * ((int)j % half) + (colour & 1), by = 2 * ((int)j / half) + (colour >> 1);
+    uint32_t forder = 0;
+    if (lane == 1)
+      forder = colour_order(philox10_rk(make_uint4(0u, (uint32_t)(by * P + bx), m, kTagFineOrder), d.rk).x,
+                            d.perm24);
+    forder = __shfl_sync(0xFFFFFFFFu, forder, 1);
+    const int x0 = d.cs[bx], bw = d.cs[bx + 1] - x0, y0 = d.cs[by], bh = d.cs[by + 1] - y0;
+    const int fx0 = d.fc[bx], Qx = d.fc[bx + 1] - fx0, fy0 = d.fc[by], Qy = d.fc[by + 1] - fy0;
+    BItem& it = sm.item[b];
+    for (int q = lane; q <= Qx; q += 32) it.fsx[q] = (int16_t)(d.fs[fx0 + q] - x0);
+    for (int q = lane; q <= Qy; q += 32) it.fsy[q] = (int16_t)(d.fs[fy0 + q] - y0);
+    {
+      const int nt = (d.S + 1) * (d.S + 1);
+      const uint32_t* tr = reinterpret_cast<const uint32_t*>(d.trans);
+      for (int w = lane; w < nt; w += 32) sm.trans[b][w] = tr[w];
+    }
+    // wait until the 8 neighbours (and the block itself) have completed
+    // every visit that precedes this one in schedule order
+    uint32_t fail = 0;
+    if (lane < 9) {
+      const int dx = lane % 3 - 1, dy = lane / 3 - 1;
+      const int nx = (bx + dx + P) % P, ny = (by + dy + P) % P;
+      const int ncol = colour ^ ((dx & 1) | ((dy & 1) << 1));
+      const uint32_t need = (lane == 4) ? m : (slot_of(ord, ncol) < (int)k ? m + 1u : m);
+      const uint32_t* flag = sd.done + ny * P + nx;
+      uint32_t spins = 0;
+      while (b_ld_acquire(flag) < need) {
+        if (b_ld_volatile(&ctl->abort)) {
+          fail = 1;
+          break;
+        }
+        if (++spins > a.spin_limit) {
+          btma_fail(ctl);
+          fail = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+      fence_proxy_async_global();   // what was acquired is read by the TMA next
+    }
+    const int xal = (x0 - 1) & ~15;   // floor to a 16-byte boundary (x0 - 1 >= -1)
+    uint32_t ok = __any_sync(0xFFFFFFFFu, fail != 0) ? 0u : 1u;
+    if (ok && lane == 0) {
+      fence_proxy_async_smem();   // the consumers' accesses of this tile precede the TMA's
+      mbar_arrive_expect_tx(&sm.tma[b], kBBoxBytes);
+      tma_load_2d(sm.tile[b], ta.maps + slot, xal, y0 - 1, &sm.tma[b]);
+      if (!mbar_wait(&sm.tma[b], use & 1u, kBMbarLimit)) {
+        btma_fail(ctl);
+        mbar_wait(&sm.tma[b], use & 1u, kBMbarLimit);   // no copy left in flight
+        ok = 0;
+      }
+    }
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    if (!ok) {
+      if (lane == 0) it.quit = 1;
+      __syncwarp();
+      mbar_arrive(&sm.full[b]);
+      return;
+    }
+    // wrap-around rim cells (zero-filled by the box) of blocks on the edge
+    uint8_t* tile = sm.tile[b];
+    const int L = d.L, pitch = d.pitch, xoff = x0 - xal;
+    const uint8_t* lat = d.lat;
+    if (by == 0)
+      for (int c = lane; c < bw; c += 32) tile[xoff + c] = __ldcg(lat + (size_t)(L - 1) * pitch + x0 + c);
+    if (by == P - 1)
+      for (int c = lane; c < bw; c += 32) tile[(bh + 1) * kBSP + xoff + c] = __ldcg(lat + x0 + c);
+    if (bx == 0)
+      for (int r = lane; r < bh; r += 32) tile[(r + 1) * kBSP + xoff - 1] = __ldcg(lat + (size_t)(y0 + r) * pitch + L - 1);
+    if (bx == P - 1)
+      for (int r = lane; r < bh; r += 32) tile[(r + 1) * kBSP + xoff + bw] = __ldcg(lat + (size_t)(y0 + r) * pitch);
+    if (lane == 0) {
+      it.m = m; it.ord = ord; it.forder = forder; it.quit = 0;
+      it.slot = (int32_t)slot; it.k = (int32_t)k; it.bx = bx; it.by = by; it.colour = colour;
+      it.x0 = x0; it.y0 = y0; it.bw = bw; it.bh = bh; it.xoff = xoff;
+      it.fx0 = fx0; it.fy0 = fy0; it.Qx = Qx; it.Qy = Qy;
+    }
+    __syncwarp();
+    mbar_arrive(&sm.full[b]);   // 32 arrivals complete the phase
+  }
+}
+
+template <int CONS>
+__device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
+  const BatchArgs& a = ta.a;
+  BatchCtl* ctl = a.ctl;
+  const int tid = threadIdx.x;
+  for (uint32_t n = 0;; ++n) {
+    const int b = (int)(n & 1u);
+    const uint32_t use = n >> 1;
+    if (!mbar_wait(&sm.full[b], use & 1u, kBMbarLimit)) {
+      if (tid == 0) btma_fail(ctl);
+      return;
+    }
+    const BItem& it = sm.item[b];
+    if (it.quit) return;
+    const SlotDesc& sd = sm.sd[b];
+    const LatticeDesc& d = sd.d;
+    uint8_t* tile = sm.tile[b];
+    const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans[b]);
+    const uint32_t m = it.m, ord = it.ord, s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
+    const int xoff = it.xoff, bw = it.bw, bh = it.bh, hx = it.Qx >> 1, nquads = hx * (it.Qy >> 1);
+    if (tid < kMaxStates) sm.hist[tid] = 0;
+    for (int fi = 0; fi < 4; ++fi) {
+      const int fcol = order_at(it.forder, fi);
+      const int cx = fcol & 1, cy = fcol >> 1;
+      for (int q = tid; q < nquads; q += CONS) {
+        const int qy = q / hx, qx = q - qy * hx;
+        const int fx = 2 * qx + cx, fy = 2 * qy + cy;
+        const int sx = it.fsx[fx], wx = it.fsx[fx + 1] - sx;
+        const int sy = it.fsy[fy], wy = it.fsy[fy + 1] - sy;
+        const uint32_t nk = (uint32_t)(wx * wy), n4 = 4u * nk;
+        const uint32_t g = (uint32_t)(it.fy0 + fy) * (uint32_t)d.GQ + (uint32_t)(it.fx0 + fx);
+        const uint32_t inv_wx = (65536u + (uint32_t)wx - 1u) / (uint32_t)wx;
+        const int base = (sy + 1) * kBSP + xoff + sx;
+        for (uint32_t jj = 0; 4u * jj < nk; ++jj) {
+          const uint4 x = philox10_rk(make_uint4(jj, g, m, kTagStep), d.rk);
+          const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (4u * jj + (uint32_t)e < nk) attempt(tile, trans, wv[e], n4, base, wx, inv_wx, kBSP, tx, txi, s1);
+        }
+      }
+      bar_sync_consumers(CONS);
+    }
+    const bool log_point = ((m + 1u) % a.log_every) == 0u;
+    const int W = bw + 2, H = bh + 2;
+    if (log_point) {
+      const int k = it.k, colour = it.colour;
+      const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1), sD = slot_of(ord, colour ^ 3);
+      for (int e = tid; e < W * H; e += CONS) {
+        const int r = e / W - 1, c = e % W - 1;
+        const bool rim_r = (r < 0 || r >= bh), rim_c = (c < 0 || c >= bw);
+        if (rim_r && rim_c) continue;
+        const bool end_r = (r == 0 || r == bh - 1), end_c = (c == 0 || c == bw - 1);
+        bool count;
+        if (rim_r)
+          count = sV < k && (!end_c || sD < k);
+        else if (rim_c)
+          count = sH < k && (!end_r || sD < k);
+        else
+          count = !(end_r && sV > k) && !(end_c && sH > k);
+        if (count) atomicAdd(&sm.hist[tile[(r + 1) * kBSP + xoff + c]], 1u);
+      }
+    }
+    {  // write back block interior and rim strips (never the corners)
+      const int L = d.L, pitch = d.pitch, x0 = it.x0, y0 = it.y0;
+      for (int e = tid; e < W * H; e += CONS) {
+        const int r = e / W - 1, c = e % W - 1;
+        if ((r < 0 || r >= bh) && (c < 0 || c >= bw)) continue;
+        d.lat[(size_t)wrap(y0 + r, L) * pitch + wrap(x0 + c, L)] = tile[(r + 1) * kBSP + xoff + c];
+      }
+    }
+    bar_sync_consumers(CONS);
+    const int P = d.P, slot = it.slot, bx = it.bx, by = it.by;
+    if (log_point) {
+      SlotState* st = a.states + slot;
+      if (tid <= d.S && sm.hist[tid]) atomicAdd(&st->acc[tid], (unsigned long long)sm.hist[tid]);
+      bar_sync_consumers(CONS);
+      if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&st->pend, 1u) == (uint32_t)(P * P) - 1u) {
+          __threadfence();
+          int alive = 0;
+          for (int v = 0; v < kMaxStates; ++v) {
+            const unsigned long long c = atomicExch(&st->acc[v], 0ull);
+            st->counts[v] = c;
+            if (v >= 1 && v <= d.S && c > 0) ++alive;
+          }
+          st->counts_mcs = m + 1u;
+          st->pend = 0;
+          if (sd.stop_at_extinction && alive <= 1) st->stopped = 1;
+        }
+      }
+    }
+    if (tid == 0) {
+      b_st_release(sd.done + by * P + bx, m + 1u);   // release orders the tile stores
+      mbar_arrive(&sm.empty[b]);                     // the buffer may be refilled
+    }
+  }
+}
+
+template <int CONS>
+__global__ void __launch_bounds__(CONS + 32) batch_tma_kernel(const __grid_constant__ BatchTmaArgs ta) {
+  __shared__ BatchTmaSmem sm;
+  BatchCtl* ctl = ta.a.ctl;
+  const int tid = threadIdx.x;
+  const uint32_t tot4 = ctl->tot4, chunk = ctl->chunk;
+  const uint64_t total = (uint64_t)chunk * 4u * tot4;
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.full[b], 32);
+      mbar_init(&sm.empty[b], 1);
+      mbar_init(&sm.tma[b], 1);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid >= CONS)
+    btma_producer(ta, sm, total, tot4);
+  else
+    btma_consumer<CONS>(ta, sm);
+  __syncthreads();
+  // the last CTA to leave records how far this launch advanced the replicas
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl->exited, 1u) == gridDim.x - 1u) {
+      ctl->exited = 0;
+      ctl->last_chunk = chunk;
+    }
+  }
+}
+
 }  // namespace escg_impl
 
 using namespace escg_impl;
@@ -465,6 +772,9 @@ struct Engine {
   uint32_t* d_active_tmp = nullptr;
   uint32_t* d_table = nullptr;
   uint32_t* d_admit = nullptr;
+  CUtensorMap* d_maps = nullptr;  // one TMA tensor map per slot
+  bool tma = true;                // warp-specialised TMA chunk kernel
+  int grid_tma[3] = {0, 0, 0};
   uint32_t* h_pinned = nullptr;   // pinned host words (admit list staging, counters)
   size_t table_cap = 0;
   std::vector<SlotDesc> h_slots;
@@ -481,6 +791,17 @@ int tsel(int threads) { return threads == 64 ? 0 : (threads == 128 ? 1 : 2); }
 
 cudaError_t launch_batch_kernel(Engine* e, int threads) {
   BatchArgs a{e->d_slots, e->d_states, e->d_ctl, e->d_table, e->log_every, e->spin_limit};
+  if (e->tma) {
+    BatchTmaArgs ta{a, e->d_maps};
+    const int g = e->grid_tma[tsel(threads)];
+    if (threads == 64)
+      batch_tma_kernel<64><<<g, 64 + 32, 0, e->stream>>>(ta);
+    else if (threads == 128)
+      batch_tma_kernel<128><<<g, 128 + 32, 0, e->stream>>>(ta);
+    else
+      batch_tma_kernel<256><<<g, 256 + 32, 0, e->stream>>>(ta);
+    return cudaGetLastError();
+  }
   const int g = e->grid[tsel(threads)];
   if (threads == 64)
     batch_kernel<64><<<g, 64, 0, e->stream>>>(a);
@@ -509,6 +830,7 @@ void engine_free(Engine* e) {
   cudaFree(e->d_active_tmp);
   cudaFree(e->d_table);
   cudaFree(e->d_admit);
+  cudaFree(e->d_maps);
   if (e->h_pinned) cudaFreeHost(e->h_pinned);
   if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
   e->arena_mem = nullptr;
@@ -543,6 +865,7 @@ int engine_init(Engine* e, int max_slots, size_t arena_bytes, size_t table_cap, 
   if (err == cudaSuccess) err = cudaMalloc(&e->d_active_tmp, sizeof(uint32_t) * max_slots);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_table, sizeof(uint32_t) * table_cap);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_admit, sizeof(uint32_t) * (max_slots + 1));
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_maps, sizeof(CUtensorMap) * max_slots);
   if (err == cudaSuccess) err = cudaMallocHost(&e->h_pinned, sizeof(uint32_t) * (max_slots + 16));
   if (err == cudaSuccess) err = cudaMemsetAsync(e->d_ctl, 0, sizeof(BatchCtl), e->stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(e->d_states, 0, sizeof(SlotState) * max_slots, e->stream);
@@ -562,6 +885,12 @@ int engine_init(Engine* e, int max_slots, size_t arena_bytes, size_t table_cap, 
   e->grid[1] = sms * (per < 1 ? 1 : per);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<256>, 256, 0);
   e->grid[2] = sms * (per < 1 ? 1 : per);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_tma_kernel<64>, 64 + 32, 0);
+  e->grid_tma[0] = sms * (per < 1 ? 1 : per);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_tma_kernel<128>, 128 + 32, 0);
+  e->grid_tma[1] = sms * (per < 1 ? 1 : per);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_tma_kernel<256>, 256 + 32, 0);
+  e->grid_tma[2] = sms * (per < 1 ? 1 : per);
   return ESCG_OK;
 }
 
@@ -638,8 +967,15 @@ int engine_add(Engine* e, const escg_replica_spec& sp, const SlotPlan& pl, int s
   sd.max_mcs = (uint32_t)sp.max_mcs;
   sd.stop_at_extinction = sp.stop_at_extinction ? 1 : 0;
   sd.nb4 = p.P * p.P / 4;
+  CUtensorMap map;
+  if (!encode_lattice_map(&map, d.lat, d.L, d.pitch, kBSP, kBRows)) {
+    e->arena.release(off, pl.bytes);
+    set_last_error("cuTensorMapEncodeTiled failed for L=%d", sp.L);
+    return ESCG_ECUDA;
+  }
   // the slot is idle on the device, so these synchronous copies race nothing
   cudaError_t err = cudaMemcpy(base + pl.tab, img.data(), img.size(), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(e->d_maps + slot, &map, sizeof map, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(e->d_slots + slot, &sd, sizeof sd, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemsetAsync(e->d_states + slot, 0, sizeof(SlotState), e->stream);
   if (err == cudaSuccess) err = launch_init(d, pl.TE, e->stream);

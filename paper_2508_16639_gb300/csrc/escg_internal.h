@@ -79,6 +79,10 @@ struct TmaArgs {   // aligned like CUtensorMap
   PersistentArgs p;
 };
 cudaError_t launch_persistent_tma(const TmaArgs& a, int grid, cudaStream_t stream);
+
+// 2-D uint8 tensor map of a lattice (dims L x L, row stride pitch, box
+// box_w x box_h bytes; out-of-bounds elements read as zero).
+bool encode_lattice_map(CUtensorMap* map, uint8_t* lattice, int L, int pitch, int box_w, int box_h);
 int persistent_tma_grid(int device);
 
 }  // namespace escg_impl
