@@ -263,6 +263,35 @@ int32_t escg_server_threads(escg_server_t* s);
 uint64_t escg_server_launch_count(escg_server_t* s);
 void escg_server_destroy(escg_server_t* s);
 
+/* ---- Allocation-free entry point ------------------------------------------
+ * The paper has no counterpart of this call.  It exists for callers that
+ * cannot let a library allocate device memory: applications that own a fixed
+ * GPU memory budget (their own pool, a service that reserves all device
+ * memory at start-up) and loops in which a cudaMalloc or cudaFree would
+ * synchronise the device or is not permitted.
+ *
+ * Runs n_mcs Monte Carlo steps (schedule version 1, exactly as escg_run)
+ * from absolute MCS number mcs_begin on the caller's device lattice
+ * d_lattice (L rows of escg_lattice_pitch(L) bytes, values 0..S, updated in
+ * place), then, if d_counts_out is not NULL, writes the species counts
+ * (S+1 uint64 values, device memory) of the final lattice there.  Inputs and
+ * outputs are the caller's; the library allocates nothing, neither device
+ * nor pinned memory.  Its scratch state (run state, block epochs, partition
+ * and transition tables) lives in one fixed 64 KiB device array that every
+ * GPU loading the library keeps until the process exits; L is therefore
+ * limited to 8..4096 (larger lattices are rejected with ESCG_EINVAL and a
+ * message).  Every call clears and rewrites that array, so calls whose work
+ * overlaps on the GPU (from several host threads or streams) race and must
+ * be serialised by the caller.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  digraph and rates are host memory read during
+ * the call; cuda_stream may be NULL (the legacy default stream).  Returns
+ * when the work has finished; ESCG_ETIMEOUT if a bounded device-side wait
+ * gave up.  No counts log, no stop at extinction. */
+int escg_run_noalloc(uint8_t* d_lattice, int32_t L, int32_t S, const uint8_t* digraph,
+                     const escg_rates* rates, uint64_t seed, uint64_t mcs_begin, uint64_t n_mcs,
+                     uint64_t* d_counts_out, void* cuda_stream);
+
 /* epsilon = 2 M N (Section 3.1, rate initialisation). */
 double escg_exchange_from_mobility(double M, int64_t N);
 

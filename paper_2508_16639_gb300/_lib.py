@@ -72,6 +72,8 @@ SIGNATURES = {
     "escg_exchange_from_mobility": (C.c_double, [C.c_double, C.c_int64]),
     "escg_circulant": (C.c_int, [C.c_int32, _i32p, C.c_int32, _u8p]),
     "escg_kernel_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), _u64p, C.c_int]),
+    "escg_run_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _u8p, C.POINTER(Rates),
+                                   C.c_uint64, C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "escg_batch_default_options": (None, [C.POINTER(BatchOptions)]),
     "escg_batch_create": (C.c_void_p, [C.c_int32, C.POINTER(ReplicaSpec), C.POINTER(BatchOptions)]),
     "escg_batch_run": (C.c_int, [C.c_void_p, C.c_uint64]),
