@@ -79,6 +79,7 @@ def _parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--persistent", type=int, default=1)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--L", type=int, default=3200, help="lattice side (3200 is the benchmark)")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-replicas", type=int, default=1024)
@@ -267,7 +268,7 @@ def main():
     stream = torch.cuda.Stream()
     g = E.Lattice(w.L, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X), w.seed + rank,
                   p_empty=w.p_empty, log_every=w.log_every, stream=stream, time_kernels=True,
-                  persistent=args.persistent)
+                  persistent=args.persistent, ctas_per_sm=args.ctas_per_sm)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     K, Wm, mps = args.steps, args.warmup, args.mcs_per_step
 

@@ -82,6 +82,8 @@ typedef struct {
     int32_t time_kernels;        /* 1: bracket every lattice-update launch with
                                     CUDA events on the handle's stream (read
                                     back with escg_kernel_time)               */
+    int32_t ctas_per_sm;         /* persistent CTAs per SM (0: as many as fit);
+                                    physical mapping only, results unchanged  */
 } escg_options;
 
 typedef struct escg escg_t;

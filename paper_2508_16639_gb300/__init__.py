@@ -63,7 +63,7 @@ class Lattice:
 
     def __init__(self, L: int, S: int, digraph, rates, seed: int, p_empty: float = 0.0,
                  log_every: int = 10, stop_at_extinction: bool = False, persistent: bool = True,
-                 stream=None, device_buffer=None, time_kernels: bool = False):
+                 stream=None, device_buffer=None, time_kernels: bool = False, ctas_per_sm: int = 0):
         lib = load()
         self.L, self.S = int(L), int(S)
         D = np.ascontiguousarray(np.asarray(digraph, dtype=np.uint8).reshape(S, S))
@@ -75,6 +75,7 @@ class Lattice:
         opt.stop_at_extinction = int(bool(stop_at_extinction))
         opt.persistent = int(persistent)
         opt.time_kernels = int(bool(time_kernels))
+        opt.ctas_per_sm = int(ctas_per_sm)
         if stream is not None:
             opt.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         self._buffer = device_buffer  # keep the torch tensor alive

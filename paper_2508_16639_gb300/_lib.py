@@ -23,7 +23,8 @@ class Options(C.Structure):
     _fields_ = [("p_empty", C.c_double), ("log_every", C.c_uint32),
                 ("stop_at_extinction", C.c_int32), ("schedule_version", C.c_uint32),
                 ("persistent", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("device_lattice", C.c_void_p), ("time_kernels", C.c_int32)]
+                ("device_lattice", C.c_void_p), ("time_kernels", C.c_int32),
+                ("ctas_per_sm", C.c_int32)]
 
 
 class ReplicaSpec(C.Structure):

@@ -480,6 +480,11 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     h->use_tma = true;
     h->grid = persistent_tma_grid(h->device);
   }
+  if (o.ctas_per_sm > 0) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (sms * o.ctas_per_sm < h->grid) h->grid = sms * o.ctas_per_sm;
+  }
 
   if (launch_init(d, h->T_empty, h->stream) != cudaSuccess) {
     set_err("init kernel launch failed");

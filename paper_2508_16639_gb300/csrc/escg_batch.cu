@@ -1124,10 +1124,12 @@ int engine_run(Engine* e, uint64_t chunks, bool until_idle) {
       if (rc != ESCG_OK) return rc;
       left = left ? left - 1 : 0;
     }
-    uint32_t n_active = 0;
-    rc = engine_active(e, &n_active);
-    if (rc != ESCG_OK) return rc;
-    if (n_active == 0) break;
+    if (until_idle || left == 0 || left % G == 0) {   // host check only between graph-sized groups
+      uint32_t n_active = 0;
+      rc = engine_active(e, &n_active);
+      if (rc != ESCG_OK) return rc;
+      if (n_active == 0) break;
+    }
   }
   if (launch_compact(e) != cudaSuccess) {
     set_last_error("batch compaction launch failed");
