@@ -1112,6 +1112,7 @@ int engine_run(Engine* e, uint64_t chunks, bool until_idle) {
   if (rc != ESCG_OK) return rc;
   const uint64_t G = Engine::kGraphChunks;
   while (until_idle || left > 0) {
+    bool group = false;
     if (e->graph && (until_idle || left >= G)) {
       if (cudaGraphLaunch(e->graph, e->stream) != cudaSuccess) {
         set_last_error("graph launch failed");
@@ -1119,12 +1120,13 @@ int engine_run(Engine* e, uint64_t chunks, bool until_idle) {
       }
       e->launches += 2 * G;
       left = left >= G ? left - G : 0;
+      group = true;
     } else {
       rc = engine_chunk(e, e->threads);
       if (rc != ESCG_OK) return rc;
       left = left ? left - 1 : 0;
     }
-    if (until_idle || left == 0 || left % G == 0) {   // host check only between graph-sized groups
+    if (group || left == 0) {   // the host checks after a graph group or the last chunk
       uint32_t n_active = 0;
       rc = engine_active(e, &n_active);
       if (rc != ESCG_OK) return rc;
