@@ -86,8 +86,8 @@ def _parse():
     ap.add_argument("--ensemble-baseline-sample", type=int, default=16)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=10000)
-    ap.add_argument("--serve-rate", type=float, default=400.0,
-                    help="mean Poisson arrival rate (requests/s); above capacity = saturated")
+    ap.add_argument("--serve-rate", type=float, default=200.0,
+                    help="mean Poisson arrival rate (requests/s); ~ the measured capacity")
     return ap.parse_args()
 
 

@@ -167,7 +167,11 @@ __global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st,
 
 // ---------------------------------------------------------------------------
 constexpr int kPersistentThreads = 256;
-constexpr int kUniMinBlocks = 6;
+// Resident CTAs per SM the uniform persistent kernel is compiled for (and
+// launched with by default).  Measured at L = 3200: 4 per SM beat 2, 3, 5 and
+// 6 -- fewer co-resident visits finish each hop of the colour-phase
+// dependency chain sooner, and 4 still hide most of the memory latency.
+constexpr int kUniMinBlocks = 4;
 
 template <bool UNI>
 __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
@@ -684,9 +688,10 @@ cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t st
 int persistent_grid(int device, bool uniform) {
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  if (uniform)
+  if (uniform) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<true>, kPersistentThreads, 0);
-  else
+    if (per_sm > kUniMinBlocks) per_sm = kUniMinBlocks;
+  } else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<false>, kPersistentThreads, 0);
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;
