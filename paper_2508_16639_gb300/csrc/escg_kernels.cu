@@ -187,14 +187,20 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
     const int P = d.P, half = P >> 1;
     const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
     const uint64_t total = (uint64_t)a.n_mcs * nb;
+    // Thread 0 takes the next ticket while the current visit runs (a CTA
+    // still processes its tickets in increasing order, so the oldest
+    // unfinished ticket of the launch is never a prefetched one).
+    uint32_t t_next = 0;
+    if (tid == 0) t_next = atomicAdd(&st->ticket, 1u);
     for (;;) {
       if (tid == 0) {
-        const uint32_t t = atomicAdd(&st->ticket, 1u);
+        const uint32_t t = t_next;
         s_item = t;
         uint32_t quit = ((uint64_t)t >= total) || ld_volatile(&st->abort);
         if (!quit) {
           const uint32_t m = a.m_begin + t / nb;
           s_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
+          t_next = atomicAdd(&st->ticket, 1u);
         }
         s_quit = quit;
         s_abort = 0;
