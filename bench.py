@@ -249,9 +249,8 @@ def main():
     import numpy as np
     import torch
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2508_16639_gb300 import replicas as R
+    rank, world, local = R.rank_info()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -266,7 +265,7 @@ def main():
     N = w.L * w.L
     X = E.exchange_from_mobility(w.mobility, N)
     stream = torch.cuda.Stream()
-    g = E.Lattice(w.L, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X), w.seed + rank,
+    g = E.Lattice(w.L, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X), R.replica_seed(w.seed, rank),
                   p_empty=w.p_empty, log_every=w.log_every, stream=stream, time_kernels=True,
                   persistent=args.persistent, ctas_per_sm=args.ctas_per_sm)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -298,10 +297,7 @@ def main():
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     kernel_ms, kernel_n = g.kernel_time()
     gpu_launches = g.launches - launches0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = R.max_over_ranks(ms, dist, device="cuda")
     attempts = K * mps * N * world
     value = attempts / (ms * 1e-3)
 
@@ -338,10 +334,7 @@ def main():
         for k in range(K):
             g.step_host(a, m0, mps, out=b)
         el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = R.max_over_ranks(el, dist, device="cuda")
         e2e = {"value": K * mps * N * world / el, "unit": UNIT, "h2d_bytes_per_step": N,
                "d2h_bytes_per_step": N + 8 * (w.S + 1), "ms_per_step": 1e3 * el / K,
                "api": "escg_step_host (restore + run + snapshot + counts), pinned host buffers"}
