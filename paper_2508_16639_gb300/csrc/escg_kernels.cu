@@ -167,11 +167,13 @@ __global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st,
 
 // ---------------------------------------------------------------------------
 constexpr int kPersistentThreads = 256;
-// Resident CTAs per SM the uniform persistent kernel is compiled for (and
-// launched with by default).  Measured at L = 3200: 4 per SM beat 2, 3, 5 and
-// 6 -- fewer co-resident visits finish each hop of the colour-phase
-// dependency chain sooner, and 4 still hide most of the memory latency.
-constexpr int kUniMinBlocks = 4;
+// The uniform persistent kernel is compiled for 6 resident CTAs per SM (40
+// registers) but launched with kUniLaunchPerSM.  Measured at L = 3200: 4 per
+// SM beat 2, 3, 5 and 6 -- fewer co-resident visits finish each hop of the
+// colour-phase dependency chain sooner, and 4 still hide most of the memory
+// latency; the 40-register build was also faster than a 64-register one.
+constexpr int kUniMinBlocks = 6;
+constexpr int kUniLaunchPerSM = 4;
 
 template <bool UNI>
 __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
@@ -187,20 +189,17 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
     const int P = d.P, half = P >> 1;
     const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
     const uint64_t total = (uint64_t)a.n_mcs * nb;
-    // Thread 0 takes the next ticket while the current visit runs (a CTA
-    // still processes its tickets in increasing order, so the oldest
-    // unfinished ticket of the launch is never a prefetched one).
-    uint32_t t_next = 0;
-    if (tid == 0) t_next = atomicAdd(&st->ticket, 1u);
+    // Tickets are taken one at a time, after the previous visit: taking the
+    // next one early was measured slower at L = 3200 (an item that becomes
+    // ready then waits behind a whole visit of its CTA).
     for (;;) {
       if (tid == 0) {
-        const uint32_t t = t_next;
+        const uint32_t t = atomicAdd(&st->ticket, 1u);
         s_item = t;
         uint32_t quit = ((uint64_t)t >= total) || ld_volatile(&st->abort);
         if (!quit) {
           const uint32_t m = a.m_begin + t / nb;
           s_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
-          t_next = atomicAdd(&st->ticket, 1u);
         }
         s_quit = quit;
         s_abort = 0;
@@ -696,7 +695,7 @@ int persistent_grid(int device, bool uniform) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (uniform) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<true>, kPersistentThreads, 0);
-    if (per_sm > kUniMinBlocks) per_sm = kUniMinBlocks;
+    if (per_sm > kUniLaunchPerSM) per_sm = kUniLaunchPerSM;
   } else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<false>, kPersistentThreads, 0);
   if (per_sm < 1) per_sm = 1;
