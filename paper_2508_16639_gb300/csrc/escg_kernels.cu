@@ -171,7 +171,7 @@ constexpr int kPersistentThreads = 256;
 // registers) but launched with kUniLaunchPerSM.  Measured at L = 3200: 4 per
 // SM beat 2, 3, 5 and 6 -- fewer co-resident visits finish each hop of the
 // colour-phase dependency chain sooner, and 4 still hide most of the memory
-// latency; the 40-register build was also faster than a 64-register one.
+// latency.
 constexpr int kUniMinBlocks = 6;
 constexpr int kUniLaunchPerSM = 4;
 
