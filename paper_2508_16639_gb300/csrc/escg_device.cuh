@@ -78,14 +78,22 @@ struct VisitSmem {
 // (0 exchange, 1 interaction, 2 reproduction); new a in the low nibble, new b
 // in the high nibble.  Thresholds of 2^32 are stored as 0xFFFFFFFF, which is
 // exact because u is always a multiple of 4.
+// Exchange (u < T_X) is a plain swap and needs no table: with epsilon = 2MN
+// it is the action of almost every attempt on large lattices, so it takes a
+// short path of its own (identical result: the table entry is the swap).
 __device__ __forceinline__ void apply_rule(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
                                            int ti, int tj, uint32_t u, uint32_t tx, uint32_t txi,
                                            uint32_t s1) {
   const uint32_t a = tile[ti], b = tile[tj];
-  const uint32_t act = (u >= tx ? 1u : 0u) + (u >= txi ? 1u : 0u);
-  const uint32_t nn = trans[(a * s1 + b) * 4u + act];
-  tile[ti] = (uint8_t)(nn & 15u);
-  tile[tj] = (uint8_t)(nn >> 4);
+  if (u < tx) {
+    tile[ti] = (uint8_t)b;
+    tile[tj] = (uint8_t)a;
+  } else {
+    const uint32_t act = 1u + (u >= txi ? 1u : 0u);
+    const uint32_t nn = trans[(a * s1 + b) * 4u + act];
+    tile[ti] = (uint8_t)(nn & 15u);
+    tile[tj] = (uint8_t)(nn >> 4);
+  }
 }
 
 // One elementary step (Alg. 3) of a generic sub-block.  w: the attempt's
