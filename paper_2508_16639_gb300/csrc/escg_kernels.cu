@@ -189,17 +189,32 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
     const int P = d.P, half = P >> 1;
     const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
     const uint64_t total = (uint64_t)a.n_mcs * nb;
-    // Tickets are taken one at a time, after the previous visit: taking the
-    // next one early was measured slower at L = 3200 (an item that becomes
-    // ready then waits behind a whole visit of its CTA).
+    // Tickets are taken in schedule order from a shared dispenser, one at a
+    // time, as the CTA releases the epoch of its previous visit (taking the
+    // next one at the start of a visit was measured slower at L = 3200: an
+    // item that becomes ready then waits behind a whole visit of its CTA).
+    // The ticket thread is in warp 1, not in the warp that releases the
+    // epoch, and reads the abort flag together with the ticket, so neither
+    // round trip delays the release or each other.
+    constexpr int kTicketThread = 32;
+    uint32_t c_m = 0xFFFFFFFFu, c_ord = 0;   // ticket thread: coarse order of MCS c_m
+    uint32_t t_next = 0, ab_next = 0;        // ticket thread: next ticket, abort flag seen with it
+    if (tid == kTicketThread) {
+      t_next = atomicAdd(&st->ticket, 1u);
+      ab_next = ld_volatile(&st->abort);
+    }
     for (;;) {
-      if (tid == 0) {
-        const uint32_t t = atomicAdd(&st->ticket, 1u);
+      if (tid == kTicketThread) {
+        const uint32_t t = t_next;
         s_item = t;
-        uint32_t quit = ((uint64_t)t >= total) || ld_volatile(&st->abort);
+        uint32_t quit = ((uint64_t)t >= total) || ab_next;
         if (!quit) {
           const uint32_t m = a.m_begin + t / nb;
-          s_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
+          if (m != c_m) {
+            c_m = m;
+            c_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
+          }
+          s_ord = c_ord;
         }
         s_quit = quit;
         s_abort = 0;
@@ -252,6 +267,17 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
           count_visit_generic(d, bx, by, sm, k, sV, sH, sD);
       }
       __syncthreads();
+      if (tid == 0 && by * P + bx != a.stall_block) {
+        // st.release orders the CTA's tile stores (made before the barrier
+        // above) before the new epoch; no separate fence is needed.  The
+        // counts of a log point live in shared memory and are published
+        // after the release, off the neighbours' critical path.
+        st_release(a.done + by * P + bx, m + 1u);
+      }
+      if (tid == kTicketThread) {
+        t_next = atomicAdd(&st->ticket, 1u);
+        ab_next = ld_volatile(&st->abort);
+      }
       if (log_point) {
         const uint32_t ring = ((m + 1u) / a.log_every) % (uint32_t)kPendRing;
         if (tid <= d.S && sm.hist[tid]) atomicAdd(&st->acc[ring][tid], (unsigned long long)sm.hist[tid]);
@@ -267,11 +293,6 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
             write_log_entry(st, a.lb, d.S, m + 1u, a.log_every, c, a.stop_at_extinction);
           }
         }
-      }
-      if (tid == 0 && by * P + bx != a.stall_block) {
-        // st.release orders the CTA's tile stores (made before the barrier
-        // above) before the new epoch; no separate fence is needed
-        st_release(a.done + by * P + bx, m + 1u);
       }
     }
   }
