@@ -217,14 +217,20 @@ __device__ __forceinline__ void load_trans(const LatticeDesc& d, uint32_t* trans
 // Visit of coarse block (bx, by) in MCS m, uniform geometry.  Must be called
 // by all 256 threads; the tile is free for reuse after the caller's next
 // __syncthreads().
+// Fine colour order of block (bx, by) in MCS m.
+__device__ __forceinline__ uint32_t fine_order(const LatticeDesc& d, int bx, int by, uint32_t m) {
+  const uint4 x = philox10_rk(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.rk);
+  return colour_order(x.x, d.perm24);
+}
+
+// OWN_FORDER = false: the caller has stored fine_order(d, bx, by, m) in
+// sm.forder before a barrier that precedes the call.
+template <bool OWN_FORDER = true>
 __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int by, uint32_t m,
                                               VisitSmem& sm) {
   const int x0 = bx * kUniB, y0 = by * kUniB;
   const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
-  if (t == 0) {
-    const uint4 x = philox10_rk(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.rk);
-    sm.forder = colour_order(x.x, d.perm24);
-  }
+  if (OWN_FORDER && t == 0) sm.forder = fine_order(d, bx, by, m);
   load_tile_uni(d, x0, y0, sm.tile);
   __syncthreads();
   const uint32_t ord = sm.forder, s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
@@ -247,6 +253,7 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
 }
 
 // Visit of coarse block (bx, by) in MCS m, any geometry of the partition.
+template <bool OWN_FORDER = true>
 __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int by, uint32_t m,
                                               VisitSmem& sm) {
   const int x0 = d.cs[bx], bw = d.cs[bx + 1] - x0;
@@ -257,10 +264,7 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int k = tid; k <= Qx; k += nthr) sm.fsx[k] = (int16_t)(d.fs[fx0 + k] - x0);
   for (int k = tid; k <= Qy; k += nthr) sm.fsy[k] = (int16_t)(d.fs[fy0 + k] - y0);
-  if (tid == 0) {
-    const uint4 x = philox10_rk(make_uint4(0u, (uint32_t)(by * d.P + bx), m, kTagFineOrder), d.rk);
-    sm.forder = colour_order(x.x, d.perm24);
-  }
+  if (OWN_FORDER && tid == 0) sm.forder = fine_order(d, bx, by, m);
   load_tile_generic(d, x0, y0, bw, bh, sm.tile, sp);
   __syncthreads();
   const uint32_t s1 = (uint32_t)d.S + 1u;

@@ -229,7 +229,9 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
       const int colour = order_at(ord, k);
       const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
       // Wait until the 8 neighbours (and the block itself) have completed
-      // every visit that precedes this one in schedule order.
+      // every visit that precedes this one in schedule order; meanwhile
+      // warp 1 draws the block's fine colour order.
+      if (tid == kTicketThread) sm.forder = fine_order(d, bx, by, m);
       if (tid < 9) {
         const int dx = tid % 3 - 1, dy = tid / 3 - 1;
         const int nx = (bx + dx + P) % P, ny = (by + dy + P) % P;
@@ -254,9 +256,9 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
       __syncthreads();
       if (s_abort) break;  // uniform across the CTA
       if (UNI)
-        visit_uniform(d, bx, by, m, sm);
+        visit_uniform<false>(d, bx, by, m, sm);
       else
-        visit_generic(d, bx, by, m, sm);
+        visit_generic<false>(d, bx, by, m, sm);
       const bool log_point = ((m + 1u) % a.log_every) == 0u;
       if (log_point) {
         const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1),
