@@ -124,20 +124,22 @@ constexpr int kUniB = 64;
 constexpr int kUniSP = 80;   // tile_pitch(64)
 constexpr int kUniThreads = 256;
 
-// One elementary step on a 2x2 sub-block of a tile with row pitch SP (a
-// value < 128 whose bits the sign mask can select): 4*n_k = 16, so the high
-// 4 bits of w are (row, col, dir) and u = w << 4.
+// One elementary step on a 2x2 sub-block of a tile with row pitch SP: 4*n_k
+// = 16, so the high 4 bits of w are the cell (bit 31 row, bit 30 column) and
+// the direction (bits 29..28: 0 up, 1 down, 2 left, 3 right), and u = w << 4.
+// The two offsets come from byte tables indexed by those bit pairs: a
+// __byte_perm selector below 4 picks that byte into the low byte, and its
+// three zero nibbles pick byte 0, which is 0 in both tables.  kTj holds the
+// neighbour's offset from the cell plus SP, so that every entry is a byte.
 template <int SP>
 __device__ __forceinline__ void attempt_uni(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
                                             uint32_t w, int base, uint32_t tx, uint32_t txi, uint32_t s1) {
-  static_assert(SP < 128, "row offset is selected with a sign mask");
-  const uint32_t u = w << 4;
-  const int rowoff = ((int32_t)w >> 31) & SP;
-  const int col = (int)((w >> 30) & 1u);
-  const int ti = base + rowoff + col;
-  const int mag = (w & (1u << 29)) ? 1 : SP;
-  const int tj = ti + ((w & (1u << 28)) ? mag : -mag);
-  apply_rule(tile, trans, ti, tj, u, tx, txi, s1);
+  static_assert(SP < 128, "offsets must fit the byte tables");
+  constexpr uint32_t kTi = 0u | (1u << 8) | ((uint32_t)SP << 16) | ((uint32_t)(SP + 1) << 24);
+  constexpr uint32_t kTj = 0u | ((uint32_t)(2 * SP) << 8) | ((uint32_t)(SP - 1) << 16) | ((uint32_t)(SP + 1) << 24);
+  const int ti = base + (int)__byte_perm(kTi, 0u, w >> 30);
+  const int tj = ti - SP + (int)__byte_perm(kTj, 0u, (w >> 28) & 3u);
+  apply_rule(tile, trans, ti, tj, w << 4, tx, txi, s1);
 }
 
 template <int SP, int COFF>
@@ -235,13 +237,16 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
   __syncthreads();
   const uint32_t ord = sm.forder, s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
   const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
-  const uint32_t gx0 = (uint32_t)(bx * (kUniB / 2) + 2 * qx), gy0 = (uint32_t)(by * (kUniB / 2) + 2 * qy);
-#pragma unroll 1
+  // sub-block (2 qx + cx, 2 qy + cy) of the quad: global index g00 + cy*GQ + cx,
+  // first cell at tile index base00 + 2 cy SP + 2 cx
+  const uint32_t GQ = (uint32_t)d.GQ;
+  const uint32_t g00 = (uint32_t)(by * (kUniB / 2) + 2 * qy) * GQ + (uint32_t)(bx * (kUniB / 2) + 2 * qx);
+  const int base00 = tidx(4 * qy, 4 * qx, kUniSP);
+#pragma unroll
   for (int fi = 0; fi < 4; ++fi) {
-    const int fcol = order_at(ord, fi);
-    const int cx = fcol & 1, cy = fcol >> 1;
-    const uint32_t g = (gy0 + (uint32_t)cy) * (uint32_t)d.GQ + gx0 + (uint32_t)cx;
-    const int base = tidx(4 * qy + 2 * cy, 4 * qx + 2 * cx, kUniSP);
+    const uint32_t fcol = (ord >> (2 * fi)) & 3u, cx = fcol & 1u, cy = fcol >> 1;
+    const uint32_t g = g00 + cy * GQ + cx;
+    const int base = base00 + (int)(cy * (2 * kUniSP) + 2 * cx);
     const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
     attempt_uni<kUniSP>(sm.tile, trans, x.x, base, tx, txi, s1);
     attempt_uni<kUniSP>(sm.tile, trans, x.y, base, tx, txi, s1);

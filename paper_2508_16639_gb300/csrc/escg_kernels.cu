@@ -167,12 +167,12 @@ __global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st,
 
 // ---------------------------------------------------------------------------
 constexpr int kPersistentThreads = 256;
-// The uniform persistent kernel is compiled for 6 resident CTAs per SM (40
-// registers) but launched with kUniLaunchPerSM.  Measured at L = 3200: 4 per
-// SM beat 2, 3, 5 and 6 -- fewer co-resident visits finish each hop of the
-// colour-phase dependency chain sooner, and 4 still hide most of the memory
-// latency.
-constexpr int kUniMinBlocks = 6;
+// The uniform persistent kernel is compiled for 4 resident CTAs per SM (up
+// to 64 registers, no spills) and launched with kUniLaunchPerSM.  Measured at
+// L = 3200: 4 per SM beat 2, 3, 5 and 6 -- fewer co-resident visits finish
+// each hop of the colour-phase dependency chain sooner, and 4 still hide most
+// of the memory latency.
+constexpr int kUniMinBlocks = 4;
 constexpr int kUniLaunchPerSM = 4;
 
 template <bool UNI>
@@ -554,14 +554,14 @@ __device__ void tma_consumer(const TmaArgs& a, TmaSmem& sm) {
     if (it.quit) break;
     uint8_t* tile = sm.tile[b];
     if (t < kMaxStates) sm.hist[t] = 0;
-    const uint32_t gx0 = (uint32_t)(it.bx * (kUniB / 2) + 2 * qx);
-    const uint32_t gy0 = (uint32_t)(it.by * (kUniB / 2) + 2 * qy);
-#pragma unroll 1
+    const uint32_t GQ = (uint32_t)d.GQ;
+    const uint32_t g00 = (uint32_t)(it.by * (kUniB / 2) + 2 * qy) * GQ + (uint32_t)(it.bx * (kUniB / 2) + 2 * qx);
+    const int base00 = tix(4 * qy, 4 * qx);
+#pragma unroll
     for (int fi = 0; fi < 4; ++fi) {
-      const int fcol = order_at(it.forder, fi);
-      const int cx = fcol & 1, cy = fcol >> 1;
-      const uint32_t g = (gy0 + (uint32_t)cy) * (uint32_t)d.GQ + gx0 + (uint32_t)cx;
-      const int base = tix(4 * qy + 2 * cy, 4 * qx + 2 * cx);
+      const uint32_t fcol = (it.forder >> (2 * fi)) & 3u, cx = fcol & 1u, cy = fcol >> 1;
+      const uint32_t g = g00 + cy * GQ + cx;
+      const int base = base00 + (int)(cy * (2 * kTmaSP) + 2 * cx);
       const uint4 x = philox10_rk(make_uint4(0u, g, it.m, kTagStep), d.rk);
       attempt_uni<kTmaSP>(tile, trans, x.x, base, tx, txi, s1);
       attempt_uni<kTmaSP>(tile, trans, x.y, base, tx, txi, s1);
