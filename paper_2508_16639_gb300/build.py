@@ -47,7 +47,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
     common = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-              "-I", INCLUDE, "-I", CSRC]
+              "-I", INCLUDE, "-I", CSRC] + os.environ.get("ESCG_NVCC_FLAGS", "").split()
     if ptxas_verbose:
         common += ["-Xptxas", "-v"]
     procs, objs = [], []

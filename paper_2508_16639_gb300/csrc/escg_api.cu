@@ -183,6 +183,8 @@ struct escg {
   unsigned long long* d_log = nullptr;
   uint32_t* d_log_mcs = nullptr;
   uint32_t* d_done = nullptr;    // P*P absolute epochs of the persistent kernel
+  unsigned long long* d_ob = nullptr;  // boundary records of the mailbox kernel
+  bool use_ll = false;           // uniform geometry, plain persistent path
   uint64_t mcs_enq = 0;          // MCS number after all enqueued work
   uint64_t launches = 0;
   uint64_t T_empty = 0;
@@ -263,6 +265,7 @@ void free_handle(escg* h) {
   cudaFree(h->d_log);
   cudaFree(h->d_log_mcs);
   cudaFree(h->d_done);
+  cudaFree(h->d_ob);
   cudaFree(h->d_scratch);
   for (auto& e : h->ev_used) {
     cudaEventDestroy(e.first);
@@ -480,6 +483,15 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     h->use_tma = true;
     h->grid = persistent_tma_grid(h->device);
   }
+  if (d.uniform64 && o.persistent == 1) {
+    const size_t words = (size_t)p.P * p.P * kRecordWords;
+    if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
+      set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
+      return fail(ESCG_ENOMEM);
+    }
+    h->use_ll = true;
+    h->grid = persistent_ll_grid(h->device);
+  }
   if (o.ctas_per_sm > 0) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -514,6 +526,11 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
     return ESCG_EINVAL;
   }
   const uint32_t k = h->opt.log_every;
+  if (h->use_ll && h->mcs_enq < target) {
+    // the lattice array may have been written since the last run
+    CUDA_TRY(launch_ll_seed(h->desc, h->d_ob, (uint32_t)h->mcs_enq, h->stream));
+    h->launches++;
+  }
   while (h->mcs_enq < target) {
     uint64_t end;
     if (h->opt.persistent && !h->opt.stop_at_extinction) {
@@ -544,17 +561,24 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
       a.stop_at_extinction = h->opt.stop_at_extinction;
       a.spin_limit = h->spin_limit;
       a.stall_block = h->stall_block;
+      a.ob = h->d_ob;
       CUDA_TRY(timing_begin(h));
       if (h->use_tma) {
         TmaArgs ta{};
         ta.map = h->tmap;
         ta.p = a;
         CUDA_TRY(launch_persistent_tma(ta, grid, h->stream));
+      } else if (h->use_ll) {
+        CUDA_TRY(launch_persistent_ll(a, grid, h->stream));
       } else {
         CUDA_TRY(launch_persistent(a, grid, h->stream));
       }
       CUDA_TRY(timing_end(h));
       h->launches++;
+      if (h->use_ll) {
+        CUDA_TRY(launch_ll_merge(h->desc, h->d_ob, h->d_state, h->stream));
+        h->launches++;
+      }
       h->mcs_enq = end;
       continue;  // counts of log points and the MCS number are written in-kernel
     } else {

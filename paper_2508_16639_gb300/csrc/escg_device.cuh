@@ -225,16 +225,12 @@ __device__ __forceinline__ uint32_t fine_order(const LatticeDesc& d, int bx, int
   return colour_order(x.x, d.perm24);
 }
 
-// OWN_FORDER = false: the caller has stored fine_order(d, bx, by, m) in
-// sm.forder before a barrier that precedes the call.
-template <bool OWN_FORDER = true>
-__device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int by, uint32_t m,
-                                              VisitSmem& sm) {
-  const int x0 = bx * kUniB, y0 = by * kUniB;
+// The four fine colour phases of a uniform visit on the staged tile (block
+// (bx, by), MCS m, fine order in sm.forder); all 256 threads; ends with a
+// barrier.
+__device__ __forceinline__ void fine_phases_uni(const LatticeDesc& d, int bx, int by, uint32_t m,
+                                                VisitSmem& sm) {
   const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
-  if (OWN_FORDER && t == 0) sm.forder = fine_order(d, bx, by, m);
-  load_tile_uni(d, x0, y0, sm.tile);
-  __syncthreads();
   const uint32_t ord = sm.forder, s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
   const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
   // sub-block (2 qx + cx, 2 qy + cy) of the quad: global index g00 + cy*GQ + cx,
@@ -254,6 +250,18 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
     attempt_uni<kUniSP>(sm.tile, trans, x.w, base, tx, txi, s1);
     __syncthreads();
   }
+}
+
+// OWN_FORDER = false: the caller has stored fine_order(d, bx, by, m) in
+// sm.forder before a barrier that precedes the call.
+template <bool OWN_FORDER = true>
+__device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int by, uint32_t m,
+                                              VisitSmem& sm) {
+  const int x0 = bx * kUniB, y0 = by * kUniB;
+  if (OWN_FORDER && threadIdx.x == 0) sm.forder = fine_order(d, bx, by, m);
+  load_tile_uni(d, x0, y0, sm.tile);
+  __syncthreads();
+  fine_phases_uni(d, bx, by, m, sm);
   store_tile_uni(d, x0, y0, sm.tile);
 }
 

@@ -64,12 +64,30 @@ struct PersistentArgs {
   int32_t stop_at_extinction;
   uint32_t spin_limit;
   int32_t stall_block;   // test hook: never publish this block's epoch (-1: off)
+  unsigned long long* ob;  // boundary records of the mailbox kernel ([P*P][4][32]), else null
 };
 // MCS [m_begin, m_begin + n_mcs) in one persistent dataflow launch, counts
 // of log points fused in.
 cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream);
 // Occupancy-derived grid size of the persistent kernel for a lattice.
 int persistent_grid(int device, bool uniform);
+
+// Uniform geometry, boundary-mailbox variant (the default persistent path):
+// a visit publishes its four boundary records (edge line + rim line per
+// side, 4 lattice bytes and the epoch per 8-byte word) and only its interior
+// to the lattice; neighbours read the records instead of waiting on epoch
+// flags.  a.ob must hold kRecordWords words per block.
+constexpr int kRecordWords = 128;
+cudaError_t launch_persistent_ll(const PersistentArgs& a, int grid, cudaStream_t stream);
+int persistent_ll_grid(int device);
+// Writes every block's boundary records from the lattice array, tagged with
+// epoch `tag` (the lattice's current MCS number).
+cudaError_t launch_ll_seed(const LatticeDesc& d, unsigned long long* ob, uint32_t tag, cudaStream_t stream);
+// Completes the lattice array after a mailbox launch: every edge cell of a
+// block that a neighbour's visit wrote last (in MCS st->mcs - 1) takes the
+// value from that neighbour's record.
+cudaError_t launch_ll_merge(const LatticeDesc& d, const unsigned long long* ob, const RunState* st,
+                            cudaStream_t stream);
 
 // Uniform geometry (64x64 blocks): TMA-staged, warp-specialised variant.
 // map: 2-D uint8 tensor map of the lattice (dims L x L, row stride pitch,

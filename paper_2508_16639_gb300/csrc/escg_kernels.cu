@@ -311,6 +311,368 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
 }
 
 // ---------------------------------------------------------------------------
+// Boundary-mailbox persistent kernel (uniform geometry; the default
+// persistent path).  Same work items, schedule order and results as
+// persistent_kernel; what differs is how a visit learns that its neighbours
+// are done and gets their data.
+//
+// A visit publishes its block's four boundary records -- per side, the
+// block's edge line and the rim line beyond it (the strip it wrote into the
+// neighbour), after the visit -- as 8-byte words holding 4 lattice bytes in
+// the low half and the epoch of the visit (m + 1) in the high half, each
+// written with one single-copy-atomic 64-bit store.  A neighbour polls those
+// words directly: a word with the expected epoch is also the data, so flag
+// and data arrive in one round trip and the writer needs no fence before
+// publishing.  The lattice array receives only the block's own interior,
+// released by the block's epoch flag, which only the block's next visit
+// reads (one MCS later, off the neighbours' critical path).  Rim strips
+// reach the lattice array at the end of the launch (ll_merge_kernel); the
+// records are seeded from the lattice array before a run (ll_seed_kernel).
+//
+// Record layout: ob[(block * 4 + side) * 32 + part * 16 + w]; side 0 top,
+// 1 bottom, 2 left, 3 right; part 0 the block's edge line, 1 the rim line;
+// word w holds positions 4w..4w+3 along the side, byte j = position 4w + j.
+//
+// Which visit wrote a cell last: the coarse order is drawn afresh every MCS,
+// so a neighbour of colour c was last visited (before the visit at slot k of
+// MCS m) at (m, slot_m(c)) if slot_m(c) < k, else at (m - 1, slot_m-1(c)),
+// and the block itself at (m - 1, slot_m-1(own colour)).  key = 4 + slot_m
+// for the former, slot_m-1 for the latter orders all of them.  Every staged
+// cell takes the value of its latest writer among the block's own previous
+// visit (the interior from the lattice array, the rim lines from the block's
+// own records), the edge neighbour across that side and, at the 12 cells
+// that two neighbours touch (interior corners: the vertical and the
+// horizontal neighbour; rim ends: an edge neighbour and a diagonal one), the
+// other neighbour.
+constexpr int kLLThreads = 256;
+// Compiled for and launched with 5 resident CTAs per SM (48 registers):
+// measured at L = 3200 against 4 (64 registers) and 6 (40, with spills).
+constexpr int kLLMinBlocks = 5;
+
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_word(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void bar_named(uint32_t id, uint32_t n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Tile index of position pos (0..63) of line (side, part) of a uniform block.
+__device__ __forceinline__ int line_tidx(int side, int part, int pos) {
+  const int fixed = (side & 1) ? (part ? kUniB : kUniB - 1) : (part ? -1 : 0);
+  return (side < 2) ? tidx(fixed, pos, kUniSP) : tidx(pos, fixed, kUniSP);
+}
+
+// Lattice coordinates of position pos of line (side, part) of block (x0, y0).
+__device__ __forceinline__ void line_cell(int side, int part, int pos, int x0, int y0, int L, int& y, int& x) {
+  const int fixed = (side & 1) ? (part ? kUniB : kUniB - 1) : (part ? -1 : 0);
+  y = wrap(y0 + ((side < 2) ? fixed : pos), L);
+  x = wrap(x0 + ((side < 2) ? pos : fixed), L);
+}
+
+__global__ void __launch_bounds__(kLLThreads, kLLMinBlocks) persistent_ll_kernel(PersistentArgs a) {
+  __shared__ VisitSmem sm;
+  __shared__ uint32_t s_item, s_ord, s_ordp, s_quit, s_abort;
+  const LatticeDesc& d = a.d;
+  RunState* st = a.st;
+  unsigned long long* ob = a.ob;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // roles: warps 0..3 poll / publish the records of sides 0..3; warp 4 lanes
+  // 0..7 poll the diagonal neighbours' rim ends, lane 8 the block's own epoch
+  // flag, lane 9 draws the fine order; warps 4..7 stage the interior.
+  constexpr int kTicketThread = 32;    // takes the next ticket as a visit starts
+  constexpr int kReleaseThread = 160;  // releases the previous visit's interior
+  const bool run = !ld_volatile(&st->stopped);
+  if (run) {
+    load_trans(d, sm.trans);
+    const int P = d.P, half = P >> 1, pitch = d.pitch;
+    const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
+    const uint64_t total = (uint64_t)a.n_mcs * nb;
+    uint32_t c_m = 0, c_ord = 0, c_ordp = 0;  // ticket thread: orders of MCS c_m, c_m - 1
+    bool c_valid = false;
+    uint32_t t_next = 0, ab_next = 0;        // ticket thread: next ticket, abort flag seen with it
+    int rel_blk = -1;                        // release thread: block whose epoch is pending
+    uint32_t rel_epoch = 0;
+    if (tid == kTicketThread) {
+      t_next = atomicAdd(&st->ticket, 1u);
+      ab_next = ld_volatile(&st->abort);
+    }
+    for (;;) {
+      if (tid == kTicketThread) {
+        const uint32_t t = t_next;
+        s_item = t;
+        const uint32_t quit = ((uint64_t)t >= total) || ab_next;
+        if (!quit) {
+          const uint32_t m = a.m_begin + t / nb;
+          if (m != c_m || !c_valid) {
+            c_ordp = (c_valid && m == c_m + 1u)
+                         ? c_ord
+                         : colour_order(philox10(make_uint4(0u, 0u, m - 1u, kTagOrder), d.key0, d.key1).x,
+                                        d.perm24);
+            c_m = m;
+            c_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
+            c_valid = true;
+          }
+          s_ord = c_ord;
+          s_ordp = c_ordp;
+        }
+        s_quit = quit;
+        s_abort = 0;
+      }
+      if (tid < kMaxStates) sm.hist[tid] = 0;
+      __syncthreads();
+      if (tid == kReleaseThread && rel_blk >= 0) {
+        // the previous visit's interior stores all precede the barrier above
+        st_release(a.done + rel_blk, rel_epoch);
+        rel_blk = -1;
+      }
+      if (s_quit) break;
+      const uint32_t t = s_item, ord = s_ord, ordp = s_ordp;
+      const uint32_t mi = t / nb, rem = t - mi * nb;
+      const uint32_t m = a.m_begin + mi;
+      const int k = (int)(rem / per), j = (int)(rem - (uint32_t)k * per);
+      const int colour = order_at(ord, k);
+      const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
+      const int X = by * P + bx, x0 = bx * kUniB, y0 = by * kUniB;
+      const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1), sD = slot_of(ord, colour ^ 3);
+      const int kV = sV < k ? sV + 4 : slot_of(ordp, colour ^ 2);
+      const int kH = sH < k ? sH + 4 : slot_of(ordp, colour ^ 1);
+      const int kD = sD < k ? sD + 4 : slot_of(ordp, colour ^ 3);
+      const int kXp = slot_of(ordp, colour);
+      const uint32_t eV = sV < k ? m + 1u : m, eH = sH < k ? m + 1u : m, eD = sD < k ? m + 1u : m;
+      unsigned long long word = 0, own = 0;
+      if (warp < 4) {
+        // edge neighbour on side `warp`; its record of the opposite side
+        const int s = warp;
+        const int nx = (s == 2) ? (bx + P - 1) % P : (s == 3) ? (bx + 1) % P : bx;
+        const int ny = (s == 0) ? (by + P - 1) % P : (s == 1) ? (by + 1) % P : by;
+        const uint32_t e = (s < 2) ? eV : eH;
+        const unsigned long long* p = ob + ((size_t)(ny * P + nx) * 4 + (s ^ 1)) * 32 + lane;
+        // lanes 0..15 also read the block's own rim line of that side, as its
+        // previous visit left it
+        const unsigned long long* q = ob + ((size_t)X * 4 + s) * 32 + 16 + (lane & 15);
+        uint32_t spins = 0;
+        bool got = false, got_own = lane >= 16;
+        while (!got || !got_own) {
+          if (!got) got = (uint32_t)((word = ld_word(p)) >> 32) == e;
+          if (!got_own) got_own = (uint32_t)((own = ld_word(q)) >> 32) == m;
+          if (got && got_own) break;
+          if (ld_volatile(&st->abort)) {
+            s_abort = 1;
+            break;
+          }
+          if (++spins > a.spin_limit) {
+            atomicOr(&st->error, kErrTimeout);
+            atomicExch(&st->abort, 1u);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+      } else if (warp == 4) {
+        if (lane < 8) {
+          // rim end of a diagonal neighbour: lanes 0..3 the ends of the top
+          // and bottom rim rows, 4..7 those of the left and right rim columns
+          const int dx = (lane == 0 || lane == 2 || lane == 4 || lane == 5) ? -1 : 1;
+          const int dy = (lane == 0 || lane == 1 || lane == 4 || lane == 6) ? -1 : 1;
+          const int rec = (lane < 4) ? (dx < 0 ? 3 : 2) : (dy < 0 ? 1 : 0);
+          const int pos = (lane < 4) ? (dy < 0 ? 63 : 0) : (dx < 0 ? 63 : 0);
+          const int nx = (bx + P + dx) % P, ny = (by + P + dy) % P;
+          const unsigned long long* p = ob + ((size_t)(ny * P + nx) * 4 + rec) * 32 + 16 + (pos >> 2);
+          uint32_t spins = 0;
+          while ((uint32_t)((word = ld_word(p)) >> 32) != eD) {
+            if (ld_volatile(&st->abort)) {
+              s_abort = 1;
+              break;
+            }
+            if (++spins > a.spin_limit) {
+              atomicOr(&st->error, kErrTimeout);
+              atomicExch(&st->abort, 1u);
+              s_abort = 1;
+              break;
+            }
+            __nanosleep(64);
+          }
+        } else if (lane == 8) {
+          // the block's own previous visit: its interior in the lattice array
+          uint32_t spins = 0;
+          while (ld_acquire(a.done + X) < m) {
+            if (ld_volatile(&st->abort)) {
+              s_abort = 1;
+              break;
+            }
+            if (++spins > a.spin_limit) {
+              atomicOr(&st->error, kErrTimeout);
+              atomicExch(&st->abort, 1u);
+              s_abort = 1;
+              break;
+            }
+            __nanosleep(64);
+          }
+        } else if (lane == 9) {
+          sm.forder = fine_order(d, bx, by, m);
+        }
+        __syncwarp();
+      }
+      if (warp >= 4) {
+        // interior from the lattice array, after the block's own flag
+        bar_named(1, 128);
+        const int i = tid - 128;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int idx = i + 128 * h, r = idx >> 2, q = idx & 3;
+          const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q);
+          uint2* dst = reinterpret_cast<uint2*>(sm.tile + tidx(r, 16 * q, kUniSP));
+          dst[0] = make_uint2(v.x, v.y);
+          dst[1] = make_uint2(v.z, v.w);
+        }
+      }
+      __syncthreads();
+      if (s_abort) break;  // uniform across the CTA
+      // the records supersede the interior's edge lines; of the two writers
+      // of a shared cell only the later one's value is placed
+      if (warp < 4) {
+        const int s = warp, xp = 1 - (lane >> 4), w = lane & 15;
+        const int kS = (s < 2) ? kV : kH, kO = (s < 2) ? kH : kV;
+        const uint32_t data = (uint32_t)word, mine = (uint32_t)own;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int pos = 4 * w + jj;
+          const bool end = (pos == 0) || (pos == kUniB - 1);
+          uint8_t* cell = sm.tile + line_tidx(s, xp, pos);
+          if (xp == 0) {
+            // edge line: the interior already holds the block's own value
+            if (kS > (end ? max(kO, kXp) : kXp)) *cell = (uint8_t)(data >> (8 * jj));
+          } else if (kS > (end ? max(kD, kXp) : kXp)) {
+            *cell = (uint8_t)(data >> (8 * jj));
+          } else if (kXp > (end ? max(kS, kD) : kS)) {
+            *cell = (uint8_t)(mine >> (8 * jj));
+          }
+        }
+      } else if (warp == 4 && lane < 8) {
+        const int xs = (lane < 4) ? (lane >> 1) : 2 + ((lane - 4) >> 1);
+        const int xpos = (lane & 1) ? kUniB - 1 : 0;
+        const int dpos = (lane < 4) ? ((lane < 2) ? 63 : 0) : ((lane < 6) ? 63 : 0);
+        if (kD > max((xs < 2) ? kV : kH, kXp))
+          sm.tile[line_tidx(xs, 1, xpos)] = (uint8_t)((uint32_t)word >> (8 * (dpos & 3)));
+      }
+      __syncthreads();
+      if (tid == kTicketThread) {   // the round trip overlaps the arithmetic
+        t_next = atomicAdd(&st->ticket, 1u);
+        ab_next = ld_volatile(&st->abort);
+      }
+      fine_phases_uni(d, bx, by, m, sm);
+      // publish the records first: they are the neighbours' critical path
+      if (warp < 4 && X != a.stall_block) {
+        const int s = warp, part = lane >> 4, w = lane & 15;
+        uint32_t bytes = 0;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) bytes |= (uint32_t)sm.tile[line_tidx(s, part, 4 * w + jj)] << (8 * jj);
+        st_word(ob + ((size_t)X * 4 + s) * 32 + lane, ((unsigned long long)(m + 1u) << 32) | bytes);
+      }
+      {  // the interior to the lattice array
+        const int r = tid >> 2, q = tid & 3;
+        const uint2* src = reinterpret_cast<const uint2*>(sm.tile + tidx(r, 16 * q, kUniSP));
+        const uint2 u0 = src[0], u1 = src[1];
+        reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(u0.x, u0.y, u1.x, u1.y);
+      }
+      if (tid == kReleaseThread && X != a.stall_block) {
+        rel_blk = X;
+        rel_epoch = m + 1u;
+      }
+      const bool log_point = ((m + 1u) % a.log_every) == 0u;
+      if (log_point) {
+        count_visit_uni<kUniSP, kColOff>(sm.tile, sm.hist, d.S, k, sV, sH, sD);
+        __syncthreads();
+        const uint32_t ring = ((m + 1u) / a.log_every) % (uint32_t)kPendRing;
+        if (tid <= d.S && sm.hist[tid]) atomicAdd(&st->acc[ring][tid], (unsigned long long)sm.hist[tid]);
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          if (atomicAdd(&st->pend[ring], 1u) == nb - 1u) {
+            // last block of this log point: every contribution is in acc
+            __threadfence();
+            unsigned long long c[kMaxStates];
+            for (int v = 0; v < kMaxStates; ++v) c[v] = atomicExch(&st->acc[ring][v], 0ull);
+            st->pend[ring] = 0;
+            write_log_entry(st, a.lb, d.S, m + 1u, a.log_every, c, a.stop_at_extinction);
+          }
+        }
+      }
+    }
+    if (tid == kReleaseThread && rel_blk >= 0) st_release(a.done + rel_blk, rel_epoch);
+  }
+  // The last CTA to leave publishes the MCS number and resets the
+  // dispensers for the next launch on this stream.
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&st->exited, 1u) == gridDim.x - 1u) {
+      st->exited = 0;
+      st->ticket = 0;
+      if (!st->stopped && !st->abort) st->mcs = a.m_begin + a.n_mcs;
+    }
+  }
+}
+
+// One CTA of 128 threads per block: thread (side, part, w) writes word w of
+// that record from the lattice array.
+__global__ void __launch_bounds__(128) ll_seed_kernel(LatticeDesc d, unsigned long long* ob, uint32_t tag) {
+  const int X = blockIdx.x, P = d.P, bx = X % P, by = X / P;
+  const int t = threadIdx.x, s = t >> 5, part = (t >> 4) & 1, w = t & 15;
+  uint32_t bytes = 0;
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    int y, x;
+    line_cell(s, part, 4 * w + jj, bx * kUniB, by * kUniB, d.L, y, x);
+    bytes |= (uint32_t)d.lat[(size_t)y * d.pitch + x] << (8 * jj);
+  }
+  ob[((size_t)X * 4 + s) * 32 + part * 16 + w] = ((unsigned long long)tag << 32) | bytes;
+}
+
+// One CTA of 256 threads per block: thread (side, pos) settles edge cell pos
+// of the block's side `side` (the interior corners by the row threads only).
+// Every block was last visited in MCS st->mcs - 1; the cell's last writer is
+// the block itself or the neighbour across that side or, at a corner, the
+// neighbour across the other side -- whichever has the latest slot.
+__global__ void __launch_bounds__(256) ll_merge_kernel(LatticeDesc d, const unsigned long long* ob,
+                                                       const RunState* st) {
+  const uint32_t mcs = st->mcs;
+  if (mcs == 0u) return;
+  const int X = blockIdx.x, P = d.P, bx = X % P, by = X / P;
+  const int t = threadIdx.x, s = t >> 6, pos = t & 63;
+  const bool end = (pos == 0) || (pos == kUniB - 1);
+  if (s >= 2 && end) return;
+  const uint32_t ord = colour_order(philox10(make_uint4(0u, 0u, mcs - 1u, kTagOrder), d.key0, d.key1).x, d.perm24);
+  const int colour = 2 * (by & 1) + (bx & 1);
+  const int kX = slot_of(ord, colour), sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1);
+  // neighbour across side s: its record of the opposite side, rim line
+  int best = kX, nbr = -1, rec = 0, npos = pos;
+  const int kS = (s < 2) ? sV : sH;
+  if (kS > best) {
+    best = kS;
+    nbr = (s == 0) ? ((by + P - 1) % P) * P + bx : (s == 1) ? ((by + 1) % P) * P + bx
+        : (s == 2) ? by * P + (bx + P - 1) % P : by * P + (bx + 1) % P;
+    rec = s ^ 1;
+  }
+  if (end && sH > best) {   // row threads: the horizontal neighbour at the corner
+    best = sH;
+    nbr = (pos == 0) ? by * P + (bx + P - 1) % P : by * P + (bx + 1) % P;
+    rec = (pos == 0) ? 3 : 2;
+    npos = (s == 0) ? 0 : kUniB - 1;
+  }
+  if (nbr < 0) return;  // the block's own value is already in the lattice array
+  const unsigned long long wv = ob[((size_t)nbr * 4 + rec) * 32 + 16 + (npos >> 2)];
+  int y, x;
+  line_cell(s, 0, pos, bx * kUniB, by * kUniB, d.L, y, x);
+  d.lat[(size_t)y * d.pitch + x] = (uint8_t)((uint32_t)wv >> (8 * (npos & 3)));
+}
+
+// ---------------------------------------------------------------------------
 // Warp-specialised persistent kernel for the uniform geometry (64x64 blocks,
 // 2x2 sub-blocks).  Warp 8 is the producer: it takes the next work item from
 // the ticket counter, waits for the block's 8 neighbours, and stages the
@@ -710,6 +1072,31 @@ cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t st
     persistent_kernel<true><<<grid, kPersistentThreads, 0, stream>>>(a);
   else
     persistent_kernel<false><<<grid, kPersistentThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_persistent_ll(const PersistentArgs& a, int grid, cudaStream_t stream) {
+  persistent_ll_kernel<<<grid, kLLThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+int persistent_ll_grid(int device) {
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_ll_kernel, kLLThreads, 0);
+  if (per_sm > kLLMinBlocks) per_sm = kLLMinBlocks;
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+cudaError_t launch_ll_seed(const LatticeDesc& d, unsigned long long* ob, uint32_t tag, cudaStream_t stream) {
+  ll_seed_kernel<<<d.P * d.P, 128, 0, stream>>>(d, ob, tag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ll_merge(const LatticeDesc& d, const unsigned long long* ob, const RunState* st,
+                            cudaStream_t stream) {
+  ll_merge_kernel<<<d.P * d.P, 256, 0, stream>>>(d, ob, st);
   return cudaGetLastError();
 }
 
