@@ -70,9 +70,13 @@ typedef struct {
     int32_t stop_at_extinction;  /* stop at the first logged MCS with <= 1
                                     non-empty species alive (stasis())        */
     uint32_t schedule_version;   /* 0 or 1 (only version 1 exists)            */
-    int32_t persistent;          /* 1: persistent dataflow launches (default);
-                                    2: same, uniform 64x64 partitions staged by
-                                    a TMA producer warp (warp-specialised);
+    int32_t persistent;          /* 1: persistent dataflow launches (default;
+                                    uniform 64x64 partitions use the boundary-
+                                    mailbox kernel where it is faster);
+                                    2: same, uniform partitions staged by a
+                                    TMA producer warp (warp-specialised);
+                                    3: persistent, epoch flags only (no
+                                    mailbox kernel);
                                     0: one launch per coarse phase            */
     void* cuda_stream;           /* cudaStream_t to enqueue on, or NULL for a
                                     stream owned by the handle                */

@@ -59,10 +59,14 @@ class Lattice:
 
     rates: (interact, reproduce, exchange).  device_buffer: optional torch
     uint8 CUDA tensor of at least lattice_bytes(L) bytes used as the lattice
-    storage; stream: optional torch.cuda.Stream (or raw cudaStream_t int)."""
+    storage; stream: optional torch.cuda.Stream (or raw cudaStream_t int).
+    persistent: 1 persistent dataflow launches (default; uniform 64x64
+    partitions use the boundary-mailbox kernel where it is faster), 3 the
+    same with epoch flags only, 2 with a TMA producer warp, 0 one launch per
+    coarse phase -- all bit-identical."""
 
     def __init__(self, L: int, S: int, digraph, rates, seed: int, p_empty: float = 0.0,
-                 log_every: int = 10, stop_at_extinction: bool = False, persistent: bool = True,
+                 log_every: int = 10, stop_at_extinction: bool = False, persistent: int = 1,
                  stream=None, device_buffer=None, time_kernels: bool = False, ctas_per_sm: int = 0):
         lib = load()
         self.L, self.S = int(L), int(S)

@@ -3,6 +3,8 @@
 One nvcc invocation per translation unit, run in parallel, then one link:
 ``nvcc -gencode arch=compute_103a,code=sm_103a -lineinfo -O3``.  The result
 lands in ``paper_2508_16639_gb300/_build/libescg.so`` (git-ignored).
+Extra nvcc flags may be given in the environment variable ESCG_NVCC_FLAGS
+(not tracked by the up-to-date check: force a rebuild after changing it).
 """
 from __future__ import annotations
 

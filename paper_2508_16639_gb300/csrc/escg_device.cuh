@@ -23,7 +23,8 @@ namespace escg_impl {
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64-bit multiplies; the high halves are mixed with the other two
 // counter words and the round key.  One wide multiply gives both halves.
-__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+// Also compiled for the host (launchers that need a draw of the schedule).
+__host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
@@ -225,14 +226,15 @@ __device__ __forceinline__ uint32_t fine_order(const LatticeDesc& d, int bx, int
   return colour_order(x.x, d.perm24);
 }
 
-// The four fine colour phases of a uniform visit on the staged tile (block
-// (bx, by), MCS m, fine order in sm.forder); all 256 threads; ends with a
-// barrier.
-__device__ __forceinline__ void fine_phases_uni(const LatticeDesc& d, int bx, int by, uint32_t m,
-                                                VisitSmem& sm) {
+// The four fine colour phases of a uniform visit on a staged tile (block
+// (bx, by), MCS m, fine order ord), run by threads 0..255; each phase ends
+// with a barrier: __syncthreads() when BAR_N == 0, else named barrier
+// BAR_ID over BAR_N threads (the threads of the visit).
+template <int BAR_ID = 0, int BAR_N = 0>
+__device__ __forceinline__ void fine_phases_tile(const LatticeDesc& d, int bx, int by, uint32_t m, uint8_t* tile,
+                                                 uint32_t ord, const uint8_t* trans) {
   const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
-  const uint32_t ord = sm.forder, s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
-  const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
+  const uint32_t s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
   // sub-block (2 qx + cx, 2 qy + cy) of the quad: global index g00 + cy*GQ + cx,
   // first cell at tile index base00 + 2 cy SP + 2 cx
   const uint32_t GQ = (uint32_t)d.GQ;
@@ -244,12 +246,21 @@ __device__ __forceinline__ void fine_phases_uni(const LatticeDesc& d, int bx, in
     const uint32_t g = g00 + cy * GQ + cx;
     const int base = base00 + (int)(cy * (2 * kUniSP) + 2 * cx);
     const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
-    attempt_uni<kUniSP>(sm.tile, trans, x.x, base, tx, txi, s1);
-    attempt_uni<kUniSP>(sm.tile, trans, x.y, base, tx, txi, s1);
-    attempt_uni<kUniSP>(sm.tile, trans, x.z, base, tx, txi, s1);
-    attempt_uni<kUniSP>(sm.tile, trans, x.w, base, tx, txi, s1);
-    __syncthreads();
+    attempt_uni<kUniSP>(tile, trans, x.x, base, tx, txi, s1);
+    attempt_uni<kUniSP>(tile, trans, x.y, base, tx, txi, s1);
+    attempt_uni<kUniSP>(tile, trans, x.z, base, tx, txi, s1);
+    attempt_uni<kUniSP>(tile, trans, x.w, base, tx, txi, s1);
+    if (BAR_N)
+      asm volatile("bar.sync %0, %1;" ::"n"(BAR_ID), "n"(BAR_N) : "memory");
+    else
+      __syncthreads();
   }
+}
+
+// Same on sm.tile with the fine order in sm.forder, all 256 threads.
+__device__ __forceinline__ void fine_phases_uni(const LatticeDesc& d, int bx, int by, uint32_t m,
+                                                VisitSmem& sm) {
+  fine_phases_tile(d, bx, by, m, sm.tile, sm.forder, reinterpret_cast<const uint8_t*>(sm.trans));
 }
 
 // OWN_FORDER = false: the caller has stored fine_order(d, bx, by, m) in

@@ -80,14 +80,12 @@ int persistent_grid(int device, bool uniform);
 constexpr int kRecordWords = 128;
 cudaError_t launch_persistent_ll(const PersistentArgs& a, int grid, cudaStream_t stream);
 int persistent_ll_grid(int device);
-// Writes every block's boundary records from the lattice array, tagged with
-// epoch `tag` (the lattice's current MCS number).
-cudaError_t launch_ll_seed(const LatticeDesc& d, unsigned long long* ob, uint32_t tag, cudaStream_t stream);
-// Completes the lattice array after a mailbox launch: every edge cell of a
-// block that a neighbour's visit wrote last (in MCS st->mcs - 1) takes the
-// value from that neighbour's record.
+// Completes the lattice array after a mailbox launch that ended at MCS
+// m_end: every edge cell of a block that a neighbour's visit wrote last (in
+// MCS m_end - 1) takes the value from that neighbour's record.  Does nothing
+// unless the lattice reached m_end (st->mcs).
 cudaError_t launch_ll_merge(const LatticeDesc& d, const unsigned long long* ob, const RunState* st,
-                            cudaStream_t stream);
+                            uint32_t m_end, cudaStream_t stream);
 
 // Uniform geometry (64x64 blocks): TMA-staged, warp-specialised variant.
 // map: 2-D uint8 tensor map of the lattice (dims L x L, row stride pitch,

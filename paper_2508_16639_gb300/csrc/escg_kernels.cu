@@ -326,8 +326,9 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
 // publishing.  The lattice array receives only the block's own interior,
 // released by the block's epoch flag, which only the block's next visit
 // reads (one MCS later, off the neighbours' critical path).  Rim strips
-// reach the lattice array at the end of the launch (ll_merge_kernel); the
-// records are seeded from the lattice array before a run (ll_seed_kernel).
+// reach the lattice array at the end of the launch (ll_merge_kernel), so a
+// launch starts from a complete lattice array and needs no record from an
+// earlier launch.
 //
 // Record layout: ob[(block * 4 + side) * 32 + part * 16 + w]; side 0 top,
 // 1 bottom, 2 left, 3 right; part 0 the block's edge line, 1 the rim line;
@@ -344,10 +345,10 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
 // that two neighbours touch (interior corners: the vertical and the
 // horizontal neighbour; rim ends: an edge neighbour and a diagonal one), the
 // other neighbour.
-constexpr int kLLThreads = 256;
-// Compiled for and launched with 5 resident CTAs per SM (48 registers):
-// measured at L = 3200 against 4 (64 registers) and 6 (40, with spills).
-constexpr int kLLMinBlocks = 5;
+constexpr int kLLConsumers = 256, kLLThreads = kLLConsumers + 32;
+// 4 CTAs of 9 warps per SM (56 registers); 5 (40 registers, with spills)
+// was measured slower at L = 3200.
+constexpr int kLLMinBlocks = 4;
 
 __device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
   unsigned long long v;
@@ -374,107 +375,192 @@ __device__ __forceinline__ void line_cell(int side, int part, int pos, int x0, i
   x = wrap(x0 + ((side < 2) ? pos : fixed), L);
 }
 
+// Shared state of the mailbox kernel: two tiles -- the consumers (warps
+// 0..7) visit one while the producer (warp 8) stages the next work item in
+// the other -- and the two items' decoded fields.
+constexpr int kUniTileBytes = (kUniB + 2) * kUniSP;
+struct LLItem {
+  uint32_t m, ord, ordp, forder, quit, staged;
+  int32_t k, bx, by;
+};
+struct LLSmem {
+  alignas(16) uint8_t tile[2][kUniTileBytes];
+  uint32_t trans[kMaxStates * kMaxStates];
+  uint32_t hist[kMaxStates];
+  LLItem item[2];
+  uint32_t abort;
+};
+
+__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void cons_hi_sync() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void tile_row16(uint8_t* tile, int r, int c, uint4 v) {
+  uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, c, kUniSP));
+  dst[0] = make_uint2(v.x, v.y);
+  dst[1] = make_uint2(v.z, v.w);
+}
+
+// Producer (one warp): takes the next ticket, decodes it into sm.item[b]
+// and, when it can do so without waiting, stages the block's interior in
+// sm.tile[b] (and, on the first visit of the launch, its rim lines from the
+// lattice array).  Never blocks on another CTA.
+struct LLOrders {
+  uint32_t m, ord, ordp;
+  bool valid;
+};
+__device__ void ll_produce(const PersistentArgs& a, LLSmem& sm, int b, LLOrders& o) {
+  const LatticeDesc& d = a.d;
+  RunState* st = a.st;
+  const int lane = threadIdx.x & 31;
+  const int P = d.P, half = P >> 1, pitch = d.pitch;
+  const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
+  const uint64_t total = (uint64_t)a.n_mcs * nb;
+  uint32_t t = 0, ab = 0;
+  if (lane == 0) {
+    t = atomicAdd(&st->ticket, 1u);
+    ab = ld_volatile(&st->abort);
+  }
+  t = __shfl_sync(0xFFFFFFFFu, t, 0);
+  ab = __shfl_sync(0xFFFFFFFFu, ab, 0);
+  LLItem it{};
+  it.quit = ((uint64_t)t >= total) || ab;
+  if (!it.quit) {
+    const uint32_t mi = t / nb, rem = t - mi * nb, m = a.m_begin + mi;
+    if (m != o.m || !o.valid) {
+      o.ordp = (o.valid && m == o.m + 1u)
+                   ? o.ord
+                   : colour_order(philox10(make_uint4(0u, 0u, m - 1u, kTagOrder), d.key0, d.key1).x, d.perm24);
+      o.ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
+      o.m = m;
+      o.valid = true;
+    }
+    it.m = m;
+    it.ord = o.ord;
+    it.ordp = o.ordp;
+    it.k = (int)(rem / per);
+    const int j = (int)(rem - (uint32_t)it.k * per);
+    const int colour = order_at(o.ord, it.k);
+    it.bx = 2 * (j % half) + (colour & 1);
+    it.by = 2 * (j / half) + (colour >> 1);
+    it.forder = fine_order(d, it.bx, it.by, m);
+    const int X = it.by * P + it.bx, x0 = it.bx * kUniB, y0 = it.by * kUniB;
+    const bool first = (m == a.m_begin);
+    uint32_t ready = first ? 1u : 0u;
+    if (!first && lane == 0) ready = ld_acquire(a.done + X) >= m ? 1u : 0u;
+    ready = __shfl_sync(0xFFFFFFFFu, ready, 0);   // orders the loads below after the acquire
+    it.staged = ready;
+    uint8_t* tile = sm.tile[b];
+    if (ready) {
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const int idx = lane + 32 * h, r = idx >> 2, q = idx & 3;
+        tile_row16(tile, r, 16 * q,
+                   __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q));
+      }
+    }
+    if (first) {   // rim lines, as the lattice array holds them at launch start
+      const int L = d.L;
+      if (lane < 8) {
+        const int r = (lane < 4) ? -1 : kUniB, q = lane & 3;
+        tile_row16(tile, r, 16 * q,
+                   __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, L) * pitch + x0) + q));
+      }
+      const int xl = wrap(x0 - 1, L), xr = wrap(x0 + kUniB, L);
+      for (int r = lane; r < kUniB; r += 32) {
+        tile[tidx(r, -1, kUniSP)] = __ldcg(d.lat + (size_t)(y0 + r) * pitch + xl);
+        tile[tidx(r, kUniB, kUniSP)] = __ldcg(d.lat + (size_t)(y0 + r) * pitch + xr);
+      }
+    }
+  }
+  if (lane == 0) sm.item[b] = it;
+}
+
 __global__ void __launch_bounds__(kLLThreads, kLLMinBlocks) persistent_ll_kernel(PersistentArgs a) {
-  __shared__ VisitSmem sm;
-  __shared__ uint32_t s_item, s_ord, s_ordp, s_quit, s_abort;
+  __shared__ LLSmem sm;
   const LatticeDesc& d = a.d;
   RunState* st = a.st;
   unsigned long long* ob = a.ob;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // roles: warps 0..3 poll / publish the records of sides 0..3; warp 4 lanes
-  // 0..7 poll the diagonal neighbours' rim ends, lane 8 the block's own epoch
-  // flag, lane 9 draws the fine order; warps 4..7 stage the interior.
-  constexpr int kTicketThread = 32;    // takes the next ticket as a visit starts
-  constexpr int kReleaseThread = 160;  // releases the previous visit's interior
+  const bool producer = (warp == kLLConsumers / 32);
+  // consumer roles besides the visit: warps 0..3 poll and publish the
+  // records of sides 0..3; warp 4 lanes 0..7 poll the diagonal neighbours'
+  // rim ends, lane 8 waits for the block's own epoch when the producer could
+  // not stage the interior; tid 255 releases the epochs.
+  constexpr int kReleaseThread = kLLConsumers - 1;
   const bool run = !ld_volatile(&st->stopped);
+  int rel_blk = -1;
+  uint32_t rel_epoch = 0;
   if (run) {
     load_trans(d, sm.trans);
-    const int P = d.P, half = P >> 1, pitch = d.pitch;
-    const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
-    const uint64_t total = (uint64_t)a.n_mcs * nb;
-    uint32_t c_m = 0, c_ord = 0, c_ordp = 0;  // ticket thread: orders of MCS c_m, c_m - 1
-    bool c_valid = false;
-    uint32_t t_next = 0, ab_next = 0;        // ticket thread: next ticket, abort flag seen with it
-    int rel_blk = -1;                        // release thread: block whose epoch is pending
-    uint32_t rel_epoch = 0;
-    if (tid == kTicketThread) {
-      t_next = atomicAdd(&st->ticket, 1u);
-      ab_next = ld_volatile(&st->abort);
-    }
-    for (;;) {
-      if (tid == kTicketThread) {
-        const uint32_t t = t_next;
-        s_item = t;
-        const uint32_t quit = ((uint64_t)t >= total) || ab_next;
-        if (!quit) {
-          const uint32_t m = a.m_begin + t / nb;
-          if (m != c_m || !c_valid) {
-            c_ordp = (c_valid && m == c_m + 1u)
-                         ? c_ord
-                         : colour_order(philox10(make_uint4(0u, 0u, m - 1u, kTagOrder), d.key0, d.key1).x,
-                                        d.perm24);
-            c_m = m;
-            c_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
-            c_valid = true;
-          }
-          s_ord = c_ord;
-          s_ordp = c_ordp;
+    if (tid == 0) sm.abort = 0;
+    const int P = d.P, pitch = d.pitch;
+    const uint32_t nb = (uint32_t)(P * P);
+    LLOrders ords{0u, 0u, 0u, false};
+    if (producer) ll_produce(a, sm, 0, ords);
+    __syncthreads();
+    const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
+    for (uint32_t n = 0;; ++n) {
+      const int b = (int)(n & 1u);
+      const LLItem it = sm.item[b];
+      if (it.quit || sm.abort) break;   // uniform: read after a barrier
+      if (producer) {
+        ll_produce(a, sm, b ^ 1, ords);
+      } else {
+        if (tid == kReleaseThread && rel_blk >= 0) {
+          // the previous visit's interior stores all precede the barrier
+          st_release(a.done + rel_blk, rel_epoch);
+          rel_blk = -1;
         }
-        s_quit = quit;
-        s_abort = 0;
-      }
-      if (tid < kMaxStates) sm.hist[tid] = 0;
-      __syncthreads();
-      if (tid == kReleaseThread && rel_blk >= 0) {
-        // the previous visit's interior stores all precede the barrier above
-        st_release(a.done + rel_blk, rel_epoch);
-        rel_blk = -1;
-      }
-      if (s_quit) break;
-      const uint32_t t = s_item, ord = s_ord, ordp = s_ordp;
-      const uint32_t mi = t / nb, rem = t - mi * nb;
-      const uint32_t m = a.m_begin + mi;
-      const int k = (int)(rem / per), j = (int)(rem - (uint32_t)k * per);
-      const int colour = order_at(ord, k);
-      const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
-      const int X = by * P + bx, x0 = bx * kUniB, y0 = by * kUniB;
-      const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1), sD = slot_of(ord, colour ^ 3);
-      const int kV = sV < k ? sV + 4 : slot_of(ordp, colour ^ 2);
-      const int kH = sH < k ? sH + 4 : slot_of(ordp, colour ^ 1);
-      const int kD = sD < k ? sD + 4 : slot_of(ordp, colour ^ 3);
-      const int kXp = slot_of(ordp, colour);
-      const uint32_t eV = sV < k ? m + 1u : m, eH = sH < k ? m + 1u : m, eD = sD < k ? m + 1u : m;
-      unsigned long long word = 0, own = 0;
-      if (warp < 4) {
-        // edge neighbour on side `warp`; its record of the opposite side
-        const int s = warp;
-        const int nx = (s == 2) ? (bx + P - 1) % P : (s == 3) ? (bx + 1) % P : bx;
-        const int ny = (s == 0) ? (by + P - 1) % P : (s == 1) ? (by + 1) % P : by;
-        const uint32_t e = (s < 2) ? eV : eH;
-        const unsigned long long* p = ob + ((size_t)(ny * P + nx) * 4 + (s ^ 1)) * 32 + lane;
-        // lanes 0..15 also read the block's own rim line of that side, as its
-        // previous visit left it
-        const unsigned long long* q = ob + ((size_t)X * 4 + s) * 32 + 16 + (lane & 15);
-        uint32_t spins = 0;
-        bool got = false, got_own = lane >= 16;
-        while (!got || !got_own) {
-          if (!got) got = (uint32_t)((word = ld_word(p)) >> 32) == e;
-          if (!got_own) got_own = (uint32_t)((own = ld_word(q)) >> 32) == m;
-          if (got && got_own) break;
-          if (ld_volatile(&st->abort)) {
-            s_abort = 1;
-            break;
+        if (tid < kMaxStates) sm.hist[tid] = 0;
+        const uint32_t m = it.m, ord = it.ord, ordp = it.ordp;
+        const int k = it.k, bx = it.bx, by = it.by, colour = order_at(ord, k);
+        const int X = by * P + bx, x0 = bx * kUniB, y0 = by * kUniB;
+        uint8_t* tile = sm.tile[b];
+        const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1), sD = slot_of(ord, colour ^ 3);
+        const int kV0 = sV < k ? sV + 4 : slot_of(ordp, colour ^ 2);
+        const int kH0 = sH < k ? sH + 4 : slot_of(ordp, colour ^ 1);
+        const int kD0 = sD < k ? sD + 4 : slot_of(ordp, colour ^ 3);
+        const uint32_t eV = sV < k ? m + 1u : m, eH = sH < k ? m + 1u : m, eD = sD < k ? m + 1u : m;
+        // The first visit of a launch stages its tile from the lattice array
+        // (complete at launch start; a neighbour that has not visited yet in
+        // this launch cannot write it before this visit publishes) and takes
+        // only the neighbours that visited earlier in this launch from their
+        // records: their keys (>= 4) beat the lattice's (3), the others' (-1)
+        // lose to it.
+        const bool first = (m == a.m_begin);
+        const int kV = first && sV > k ? -1 : kV0, kH = first && sH > k ? -1 : kH0;
+        const int kD = first && sD > k ? -1 : kD0, kXp = first ? 3 : slot_of(ordp, colour);
+        unsigned long long word = 0, own = 0;
+        bool failed = false;
+        if (warp < 4) {
+          // edge neighbour on side `warp`: its record of the opposite side;
+          // lanes 0..15 also the block's own rim line of that side as its
+          // previous visit left it (first visit: already staged)
+          const int s = warp;
+          const int nx = (s == 2) ? (bx + P - 1) % P : (s == 3) ? (bx + 1) % P : bx;
+          const int ny = (s == 0) ? (by + P - 1) % P : (s == 1) ? (by + 1) % P : by;
+          const uint32_t e = (s < 2) ? eV : eH;
+          const unsigned long long* p = ob + ((size_t)(ny * P + nx) * 4 + (s ^ 1)) * 32 + lane;
+          const unsigned long long* q = ob + ((size_t)X * 4 + s) * 32 + 16 + (lane & 15);
+          bool got = first && ((s < 2) ? sV : sH) > k, got_own = first || lane >= 16;
+          uint32_t spins = 0;
+          while (!got || !got_own) {
+            if (!got) got = (uint32_t)((word = ld_word(p)) >> 32) == e;
+            if (!got_own) got_own = (uint32_t)((own = ld_word(q)) >> 32) == m;
+            if (got && got_own) break;
+            if (ld_volatile(&st->abort)) {
+              failed = true;
+              break;
+            }
+            if (++spins > a.spin_limit) {
+              atomicOr(&st->error, kErrTimeout);
+              atomicExch(&st->abort, 1u);
+              failed = true;
+              break;
+            }
+            __nanosleep(64);
           }
-          if (++spins > a.spin_limit) {
-            atomicOr(&st->error, kErrTimeout);
-            atomicExch(&st->abort, 1u);
-            s_abort = 1;
-            break;
-          }
-          __nanosleep(64);
-        }
-      } else if (warp == 4) {
-        if (lane < 8) {
+        } else if (warp == 4 && lane < 8) {
           // rim end of a diagonal neighbour: lanes 0..3 the ends of the top
           // and bottom rim rows, 4..7 those of the left and right rim columns
           const int dx = (lane == 0 || lane == 2 || lane == 4 || lane == 5) ? -1 : 1;
@@ -484,125 +570,128 @@ __global__ void __launch_bounds__(kLLThreads, kLLMinBlocks) persistent_ll_kernel
           const int nx = (bx + P + dx) % P, ny = (by + P + dy) % P;
           const unsigned long long* p = ob + ((size_t)(ny * P + nx) * 4 + rec) * 32 + 16 + (pos >> 2);
           uint32_t spins = 0;
-          while ((uint32_t)((word = ld_word(p)) >> 32) != eD) {
+          while (!(first && sD > k) && (uint32_t)((word = ld_word(p)) >> 32) != eD) {
             if (ld_volatile(&st->abort)) {
-              s_abort = 1;
+              failed = true;
               break;
             }
             if (++spins > a.spin_limit) {
               atomicOr(&st->error, kErrTimeout);
               atomicExch(&st->abort, 1u);
-              s_abort = 1;
+              failed = true;
               break;
             }
             __nanosleep(64);
           }
-        } else if (lane == 8) {
-          // the block's own previous visit: its interior in the lattice array
-          uint32_t spins = 0;
-          while (ld_acquire(a.done + X) < m) {
-            if (ld_volatile(&st->abort)) {
-              s_abort = 1;
-              break;
-            }
-            if (++spins > a.spin_limit) {
-              atomicOr(&st->error, kErrTimeout);
-              atomicExch(&st->abort, 1u);
-              s_abort = 1;
-              break;
-            }
-            __nanosleep(64);
-          }
-        } else if (lane == 9) {
-          sm.forder = fine_order(d, bx, by, m);
         }
-        __syncwarp();
-      }
-      if (warp >= 4) {
-        // interior from the lattice array, after the block's own flag
-        bar_named(1, 128);
-        const int i = tid - 128;
+        if (!it.staged && warp >= 4) {
+          // the producer found the block's previous visit unfinished: wait
+          // for its epoch here, then stage the interior
+          if (tid == 4 * 32 + 8) {
+            uint32_t spins = 0;
+            while (ld_acquire(a.done + X) < m) {
+              if (ld_volatile(&st->abort)) {
+                failed = true;
+                break;
+              }
+              if (++spins > a.spin_limit) {
+                atomicOr(&st->error, kErrTimeout);
+                atomicExch(&st->abort, 1u);
+                failed = true;
+                break;
+              }
+              __nanosleep(64);
+            }
+          }
+          cons_hi_sync();
+          const int i = tid - 128;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int idx = i + 128 * h, r = idx >> 2, q = idx & 3;
-          const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q);
-          uint2* dst = reinterpret_cast<uint2*>(sm.tile + tidx(r, 16 * q, kUniSP));
-          dst[0] = make_uint2(v.x, v.y);
-          dst[1] = make_uint2(v.z, v.w);
+          for (int h = 0; h < 2; ++h) {
+            const int idx = i + 128 * h, r = idx >> 2, q = idx & 3;
+            tile_row16(tile, r, 16 * q,
+                       __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q));
+          }
+        }
+        if (failed) sm.abort = 1u;
+        // each staged boundary cell takes the value of its latest writer (the
+        // choice depends only on the schedule, so every writer decides alone)
+        auto place = [&]() {
+          if (warp < 4) {
+            const int s = warp, xp = 1 - (lane >> 4), w = lane & 15;
+            const int kS = (s < 2) ? kV : kH, kO = (s < 2) ? kH : kV;
+            const uint32_t data = (uint32_t)word, mine = (uint32_t)own;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int pos = 4 * w + jj;
+              const bool end = (pos == 0) || (pos == kUniB - 1);
+              uint8_t* cell = tile + line_tidx(s, xp, pos);
+              if (xp == 0) {
+                // edge line: the interior already holds the block's own value
+                if (kS > (end ? max(kO, kXp) : kXp)) *cell = (uint8_t)(data >> (8 * jj));
+              } else if (kS > (end ? max(kD, kXp) : kXp)) {
+                *cell = (uint8_t)(data >> (8 * jj));
+              } else if (!first && kXp > (end ? max(kS, kD) : kS)) {
+                *cell = (uint8_t)(mine >> (8 * jj));
+              }
+            }
+          } else if (warp == 4 && lane < 8) {
+            const int xs = (lane < 4) ? (lane >> 1) : 2 + ((lane - 4) >> 1);
+            const int xpos = (lane & 1) ? kUniB - 1 : 0;
+            const int dpos = (lane < 4) ? ((lane < 2) ? 63 : 0) : ((lane < 6) ? 63 : 0);
+            if (kD > max((xs < 2) ? kV : kH, kXp))
+              tile[line_tidx(xs, 1, xpos)] = (uint8_t)((uint32_t)word >> (8 * (dpos & 3)));
+          }
+        };
+        // staged interior: place at once; otherwise after the interior lands
+        if (it.staged && !failed) place();
+        cons_sync();
+        if (!sm.abort) {
+          if (!it.staged) {
+            place();
+            cons_sync();
+          }
+          fine_phases_tile<1, kLLConsumers>(d, bx, by, m, tile, it.forder, trans);
+          if (X != a.stall_block) {
+            // publish the records first: they are the neighbours' critical path
+            if (warp < 4) {
+              const int s = warp, part = lane >> 4, w = lane & 15;
+              uint32_t bytes = 0;
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) bytes |= (uint32_t)tile[line_tidx(s, part, 4 * w + jj)] << (8 * jj);
+              st_word(ob + ((size_t)X * 4 + s) * 32 + lane, ((unsigned long long)(m + 1u) << 32) | bytes);
+            }
+            {  // the interior to the lattice array
+              const int r = tid >> 2, q = tid & 3;
+              const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+              const uint2 u0 = src[0], u1 = src[1];
+              reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(u0.x, u0.y, u1.x, u1.y);
+            }
+            if (tid == kReleaseThread) {
+              rel_blk = X;
+              rel_epoch = m + 1u;
+            }
+          }
+          if (((m + 1u) % a.log_every) == 0u) {
+            count_visit_uni<kUniSP, kColOff>(tile, sm.hist, d.S, k, sV, sH, sD);
+            cons_sync();
+            const uint32_t ring = ((m + 1u) / a.log_every) % (uint32_t)kPendRing;
+            if (tid <= d.S && sm.hist[tid]) atomicAdd(&st->acc[ring][tid], (unsigned long long)sm.hist[tid]);
+            cons_sync();
+            if (tid == 0) {
+              __threadfence();
+              if (atomicAdd(&st->pend[ring], 1u) == nb - 1u) {
+                // last block of this log point: every contribution is in acc
+                __threadfence();
+                unsigned long long c[kMaxStates];
+                for (int v = 0; v < kMaxStates; ++v) c[v] = atomicExch(&st->acc[ring][v], 0ull);
+                st->pend[ring] = 0;
+                write_log_entry(st, a.lb, d.S, m + 1u, a.log_every, c, a.stop_at_extinction);
+              }
+            }
+          }
         }
       }
       __syncthreads();
-      if (s_abort) break;  // uniform across the CTA
-      // the records supersede the interior's edge lines; of the two writers
-      // of a shared cell only the later one's value is placed
-      if (warp < 4) {
-        const int s = warp, xp = 1 - (lane >> 4), w = lane & 15;
-        const int kS = (s < 2) ? kV : kH, kO = (s < 2) ? kH : kV;
-        const uint32_t data = (uint32_t)word, mine = (uint32_t)own;
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int pos = 4 * w + jj;
-          const bool end = (pos == 0) || (pos == kUniB - 1);
-          uint8_t* cell = sm.tile + line_tidx(s, xp, pos);
-          if (xp == 0) {
-            // edge line: the interior already holds the block's own value
-            if (kS > (end ? max(kO, kXp) : kXp)) *cell = (uint8_t)(data >> (8 * jj));
-          } else if (kS > (end ? max(kD, kXp) : kXp)) {
-            *cell = (uint8_t)(data >> (8 * jj));
-          } else if (kXp > (end ? max(kS, kD) : kS)) {
-            *cell = (uint8_t)(mine >> (8 * jj));
-          }
-        }
-      } else if (warp == 4 && lane < 8) {
-        const int xs = (lane < 4) ? (lane >> 1) : 2 + ((lane - 4) >> 1);
-        const int xpos = (lane & 1) ? kUniB - 1 : 0;
-        const int dpos = (lane < 4) ? ((lane < 2) ? 63 : 0) : ((lane < 6) ? 63 : 0);
-        if (kD > max((xs < 2) ? kV : kH, kXp))
-          sm.tile[line_tidx(xs, 1, xpos)] = (uint8_t)((uint32_t)word >> (8 * (dpos & 3)));
-      }
-      __syncthreads();
-      if (tid == kTicketThread) {   // the round trip overlaps the arithmetic
-        t_next = atomicAdd(&st->ticket, 1u);
-        ab_next = ld_volatile(&st->abort);
-      }
-      fine_phases_uni(d, bx, by, m, sm);
-      // publish the records first: they are the neighbours' critical path
-      if (warp < 4 && X != a.stall_block) {
-        const int s = warp, part = lane >> 4, w = lane & 15;
-        uint32_t bytes = 0;
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) bytes |= (uint32_t)sm.tile[line_tidx(s, part, 4 * w + jj)] << (8 * jj);
-        st_word(ob + ((size_t)X * 4 + s) * 32 + lane, ((unsigned long long)(m + 1u) << 32) | bytes);
-      }
-      {  // the interior to the lattice array
-        const int r = tid >> 2, q = tid & 3;
-        const uint2* src = reinterpret_cast<const uint2*>(sm.tile + tidx(r, 16 * q, kUniSP));
-        const uint2 u0 = src[0], u1 = src[1];
-        reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(u0.x, u0.y, u1.x, u1.y);
-      }
-      if (tid == kReleaseThread && X != a.stall_block) {
-        rel_blk = X;
-        rel_epoch = m + 1u;
-      }
-      const bool log_point = ((m + 1u) % a.log_every) == 0u;
-      if (log_point) {
-        count_visit_uni<kUniSP, kColOff>(sm.tile, sm.hist, d.S, k, sV, sH, sD);
-        __syncthreads();
-        const uint32_t ring = ((m + 1u) / a.log_every) % (uint32_t)kPendRing;
-        if (tid <= d.S && sm.hist[tid]) atomicAdd(&st->acc[ring][tid], (unsigned long long)sm.hist[tid]);
-        __syncthreads();
-        if (tid == 0) {
-          __threadfence();
-          if (atomicAdd(&st->pend[ring], 1u) == nb - 1u) {
-            // last block of this log point: every contribution is in acc
-            __threadfence();
-            unsigned long long c[kMaxStates];
-            for (int v = 0; v < kMaxStates; ++v) c[v] = atomicExch(&st->acc[ring][v], 0ull);
-            st->pend[ring] = 0;
-            write_log_entry(st, a.lb, d.S, m + 1u, a.log_every, c, a.stop_at_extinction);
-          }
-        }
-      }
     }
     if (tid == kReleaseThread && rel_blk >= 0) st_release(a.done + rel_blk, rel_epoch);
   }
@@ -619,35 +708,21 @@ __global__ void __launch_bounds__(kLLThreads, kLLMinBlocks) persistent_ll_kernel
   }
 }
 
-// One CTA of 128 threads per block: thread (side, part, w) writes word w of
-// that record from the lattice array.
-__global__ void __launch_bounds__(128) ll_seed_kernel(LatticeDesc d, unsigned long long* ob, uint32_t tag) {
-  const int X = blockIdx.x, P = d.P, bx = X % P, by = X / P;
-  const int t = threadIdx.x, s = t >> 5, part = (t >> 4) & 1, w = t & 15;
-  uint32_t bytes = 0;
-#pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
-    int y, x;
-    line_cell(s, part, 4 * w + jj, bx * kUniB, by * kUniB, d.L, y, x);
-    bytes |= (uint32_t)d.lat[(size_t)y * d.pitch + x] << (8 * jj);
-  }
-  ob[((size_t)X * 4 + s) * 32 + part * 16 + w] = ((unsigned long long)tag << 32) | bytes;
-}
-
 // One CTA of 256 threads per block: thread (side, pos) settles edge cell pos
 // of the block's side `side` (the interior corners by the row threads only).
-// Every block was last visited in MCS st->mcs - 1; the cell's last writer is
-// the block itself or the neighbour across that side or, at a corner, the
-// neighbour across the other side -- whichever has the latest slot.
+// Every block was last visited in MCS m_end - 1 (coarse order `ord`); the
+// cell's last writer is the block itself or the neighbour across that side
+// or, at a corner, the neighbour across the other side -- whichever has the
+// latest slot.
 __global__ void __launch_bounds__(256) ll_merge_kernel(LatticeDesc d, const unsigned long long* ob,
-                                                       const RunState* st) {
-  const uint32_t mcs = st->mcs;
-  if (mcs == 0u) return;
+                                                       const RunState* st, uint32_t m_end, uint32_t ord) {
+  // a launch that did not run (the lattice had stopped earlier) left nothing
+  // to merge
+  if (st->mcs != m_end || st->abort) return;
   const int X = blockIdx.x, P = d.P, bx = X % P, by = X / P;
   const int t = threadIdx.x, s = t >> 6, pos = t & 63;
   const bool end = (pos == 0) || (pos == kUniB - 1);
   if (s >= 2 && end) return;
-  const uint32_t ord = colour_order(philox10(make_uint4(0u, 0u, mcs - 1u, kTagOrder), d.key0, d.key1).x, d.perm24);
   const int colour = 2 * (by & 1) + (bx & 1);
   const int kX = slot_of(ord, colour), sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1);
   // neighbour across side s: its record of the opposite side, rim line
@@ -1089,14 +1164,12 @@ int persistent_ll_grid(int device) {
   return sms * per_sm;
 }
 
-cudaError_t launch_ll_seed(const LatticeDesc& d, unsigned long long* ob, uint32_t tag, cudaStream_t stream) {
-  ll_seed_kernel<<<d.P * d.P, 128, 0, stream>>>(d, ob, tag);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_ll_merge(const LatticeDesc& d, const unsigned long long* ob, const RunState* st,
-                            cudaStream_t stream) {
-  ll_merge_kernel<<<d.P * d.P, 256, 0, stream>>>(d, ob, st);
+                            uint32_t m_end, cudaStream_t stream) {
+  // coarse order of MCS m_end - 1, as the device draws it
+  const uint32_t x = philox10(make_uint4(0u, 0u, m_end - 1u, kTagOrder), d.key0, d.key1).x;
+  const uint32_t ord = d.perm24[(uint32_t)(((uint64_t)x * 24u) >> 32)];
+  ll_merge_kernel<<<d.P * d.P, 256, 0, stream>>>(d, ob, st, m_end, ord);
   return cudaGetLastError();
 }
 

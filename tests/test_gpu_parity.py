@@ -66,7 +66,7 @@ SMALL = [  # (L, S, K, p_empty, I, P, X, n_mcs)
 ]
 
 
-@pytest.mark.parametrize("persistent", [1, 2, 0], ids=["persistent", "persistent-tma", "phase"])
+@pytest.mark.parametrize("persistent", [1, 3, 2, 0], ids=["persistent", "persistent-flags", "persistent-tma", "phase"])
 @pytest.mark.parametrize("case", SMALL, ids=[f"L{c[0]}" for c in SMALL])
 def test_replay_parity_every_mcs(case, persistent):
     L, S, K, p_empty, I, P, X, n = case
@@ -81,6 +81,28 @@ def test_replay_parity_every_mcs(case, persistent):
                                        f"{int((got != o).sum())} sites differ"
     c, mcs = g.counts()
     assert mcs == n and np.array_equal(c, O.counts(o, S))
+
+
+@pytest.mark.parametrize("persistent", [1, 3], ids=["persistent", "persistent-flags"])
+@pytest.mark.parametrize("L,S,X,n,log_every", [(128, 3, 3.3, 7, 10), (256, 5, 13.1, 5, 2), (384, 3, 29.5, 4, 3),
+                                               (640, 4, 50.0, 3, 10)])
+def test_many_mcs_per_launch(L, S, X, n, log_every, persistent):
+    """Several MCS in one launch (and several launches per run when log
+    points end them): the coarse colour order changes every MCS, so a
+    block's neighbours may have visited before or after its own previous
+    visit -- exactly what the boundary records must get right."""
+    seed = 4242 + L
+    K = (1,) if S == 3 else (1, 2)
+    g, o, D = _pair(L, S, K, 0.2, 1.0, 1.0, X, seed, persistent=persistent, log_every=log_every)
+    g.run(n)
+    o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, n)
+    got = g.snapshot()
+    assert np.array_equal(got, o), f"{int((got != o).sum())} sites differ"
+    g.run(2).run(1)
+    o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 3, mcs_begin=n)
+    assert np.array_equal(g.snapshot(), o)
+    c, mcs = g.counts()
+    assert mcs == n + 3 and np.array_equal(c, O.counts(o, S))
 
 
 def test_cfg1_competition_only_L64():
