@@ -52,16 +52,21 @@ UNIT = "site-updates/s"
 ALG_INT_INSTR_PER_ATTEMPT = 24
 
 # DRAM traffic of persistent_kernel from one ncu capture (bytes per launch of
-# a 10-MCS chunk at L = 3200), valid only for the kernel sources it was taken
-# from (hash of csrc/*); None when not measured for the current sources.
-NCU_TRAFFIC = {"sources_sha1": "a7ad03384fdb7bac40021e12c9889504b570a300", "bytes_per_launch": 10293248 + 2765312,
+# a 10-MCS chunk at L = 3200), valid only for that kernel and workload and the
+# kernel sources it was taken from (hash below); None otherwise.
+NCU_TRAFFIC = {"sources_sha1": "b23e32e22183e951cfe01d02ba084c38fd50b17b", "bytes_per_launch": 10300160 + 2254848,
+               "kernel": "persistent_kernel", "L": 3200, "mcs_per_launch": 10,
                "profile": "profiles/persistent_kernel_L3200_M1e-4.md"}
 
 
+KERNEL_SOURCES = ("escg_kernels.cu", "escg_device.cuh", "escg_types.h", "escg_internal.h", "escg_tma.cuh")
+
+
 def _sources_sha1() -> str:
+    """Hash of the translation unit that defines the single-lattice kernels."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2508_16639_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in KERNEL_SOURCES:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode() + f.read())
     return h.hexdigest()
@@ -311,8 +316,10 @@ def main():
     per_launch_attempts = mps * N  # one persistent launch = one 10-MCS chunk
     avg_launch_s = (kernel_ms * 1e-3) / max(1, kernel_n)
     achieved = per_launch_attempts * ALG_INT_INSTR_PER_ATTEMPT / avg_launch_s
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sources_sha1"] == _sources_sha1() else None
-    roofline = {"bound": "alu", "kernel": "persistent_kernel" if args.persistent else "phase_kernel",
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if (NCU_TRAFFIC["sources_sha1"] == _sources_sha1() and g.update_kernel == NCU_TRAFFIC["kernel"]
+                   and w.L == NCU_TRAFFIC["L"] and mps == NCU_TRAFFIC["mcs_per_launch"]) else None)
+    roofline = {"bound": "alu", "kernel": g.update_kernel,
                 "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tinstr/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "alg_int_instr_per_attempt": ALG_INT_INSTR_PER_ATTEMPT,

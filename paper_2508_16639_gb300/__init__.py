@@ -172,6 +172,11 @@ class Lattice:
         return int(load().escg_coarse_blocks(self._h))
 
     @property
+    def update_kernel(self) -> str:
+        """Name of the kernel that advances this lattice (fixed at creation)."""
+        return load().escg_update_kernel(self._h).decode()
+
+    @property
     def mcs(self) -> int:
         return int(load().escg_current_mcs(self._h))
 

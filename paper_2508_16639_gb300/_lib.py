@@ -99,6 +99,7 @@ SIGNATURES = {
     "escg_diag_int_throughput": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "escg_debug_stall_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint32]),
     "escg_coarse_blocks": (C.c_int32, [C.c_void_p]),
+    "escg_update_kernel": (C.c_char_p, [C.c_void_p]),
 }
 
 _lib = None

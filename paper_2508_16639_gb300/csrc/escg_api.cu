@@ -774,6 +774,13 @@ int escg_debug_stall_block(escg_t* h, int32_t block, uint32_t spin_limit) {
 
 int32_t escg_coarse_blocks(escg_t* h) { return h ? h->part.P : 0; }
 
+const char* escg_update_kernel(escg_t* h) {
+  if (!h) return "";
+  if (!h->opt.persistent) return "phase_kernel";
+  if (h->use_tma) return "persistent_tma_kernel";
+  return h->use_ll ? "persistent_ll_kernel" : "persistent_kernel";
+}
+
 void escg_destroy(escg_t* h) { free_handle(h); }
 
 }  // extern "C"
