@@ -205,6 +205,19 @@ namespace {
 
 LogBuffers log_buffers(escg* h) { return LogBuffers{h->d_log, h->d_log_mcs}; }
 
+// Host <-> device copy of the L x L lattice (host rows packed, device rows of
+// the handle's pitch); one linear copy when the two layouts coincide.
+cudaError_t copy_to_device(escg* h, const uint8_t* host) {
+  if (h->pitch == h->L)
+    return cudaMemcpyAsync(h->lattice, host, (size_t)h->L * h->L, cudaMemcpyHostToDevice, h->stream);
+  return cudaMemcpy2DAsync(h->lattice, h->pitch, host, h->L, h->L, h->L, cudaMemcpyHostToDevice, h->stream);
+}
+cudaError_t copy_to_host(escg* h, uint8_t* host) {
+  if (h->pitch == h->L)
+    return cudaMemcpyAsync(host, h->lattice, (size_t)h->L * h->L, cudaMemcpyDeviceToHost, h->stream);
+  return cudaMemcpy2DAsync(host, h->L, h->lattice, h->pitch, h->L, h->L, cudaMemcpyDeviceToHost, h->stream);
+}
+
 int enqueue_log(escg* h, uint32_t m_end, bool log) {
   if (log) {
     CUDA_TRY(launch_count(h->desc, h->d_state, h->stream));
@@ -237,18 +250,16 @@ cudaError_t timing_end(escg* h) {
   return cudaEventRecord(h->ev_used.back().second, h->stream);
 }
 
+// Device-side reset of the run state to MCS `mcs` (no host memory is read
+// asynchronously, so nothing waits here).
 int reset_state(escg* h, uint64_t mcs) {
-  CUDA_TRY(cudaMemsetAsync(h->d_state, 0, sizeof(RunState), h->stream));
-  uint32_t head[2] = {(uint32_t)mcs, 0u};
   const uint32_t le = h->opt.log_every;
   const uint32_t num0 = (uint32_t)((mcs + le - 1) / le);
-  CUDA_TRY(cudaMemcpyAsync(&h->d_state->mcs, &head[0], sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream));
-  h->log_num0_host = num0;
-  CUDA_TRY(cudaMemcpyAsync(&h->d_state->log_num0, &h->log_num0_host, sizeof(uint32_t),
-                           cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(launch_state_reset(h->d_state, (uint32_t)mcs, num0, h->stream));
+  h->launches++;
   CUDA_TRY(launch_fill_u32(h->d_done, h->part.P * h->part.P, (uint32_t)mcs, h->stream));
   h->launches++;
-  CUDA_TRY(cudaStreamSynchronize(h->stream));  // the host values above are stack/handle-owned
+  h->log_num0_host = num0;
   h->mcs_enq = mcs;
   h->failed = false;
   if (mcs % h->opt.log_every == 0) return enqueue_log(h, (uint32_t)mcs, true);
@@ -675,8 +686,7 @@ int escg_snapshot(escg_t* h, uint8_t* host_out) {
   }
   int rc = escg_sync(h);
   if (rc != ESCG_OK) return rc;
-  CUDA_TRY(cudaMemcpy2DAsync(host_out, h->L, h->lattice, h->pitch, h->L, h->L, cudaMemcpyDeviceToHost,
-                             h->stream));
+  CUDA_TRY(copy_to_host(h, host_out));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   return ESCG_OK;
 }
@@ -690,19 +700,17 @@ int escg_restore(escg_t* h, const uint8_t* host_lattice, uint64_t mcs) {
     set_err("mcs exceeds 2^32-1");
     return ESCG_EINVAL;
   }
-  CUDA_TRY(cudaStreamSynchronize(h->stream));
-  CUDA_TRY(cudaMemcpy2DAsync(h->lattice, h->pitch, host_lattice, h->L, h->L, h->L, cudaMemcpyHostToDevice,
-                             h->stream));
-  // values are checked on the device (reset_state synchronises)
-  uint32_t* bad = &h->d_scratch->error;
-  CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(uint32_t), h->stream));
-  CUDA_TRY(launch_validate(h->desc, bad, h->stream));
-  h->launches++;
+  CUDA_TRY(copy_to_device(h, host_lattice));
   const int rc = reset_state(h, mcs);
   if (rc != ESCG_OK) return rc;
-  uint32_t flag = 0;
-  CUDA_TRY(cudaMemcpy(&flag, bad, sizeof flag, cudaMemcpyDeviceToHost));
-  if (flag) {
+  // values are checked on the device; an invalid lattice also stops the
+  // run state, so that nothing enqueued later touches it
+  CUDA_TRY(launch_validate(h->desc, &h->d_state->error, kErrBadValue, &h->d_state->stopped, h->stream));
+  h->launches++;
+  uint32_t err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, &h->d_state->error, sizeof err, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (err & kErrBadValue) {
     h->failed = true;
     set_err("restored lattice holds a value outside 0..S=%d; restore a valid lattice", h->S);
     return ESCG_EINVAL;
@@ -716,11 +724,42 @@ int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_m
     set_err("NULL argument");
     return ESCG_EINVAL;
   }
-  int rc = escg_restore(h, host_in, mcs);
-  if (rc == ESCG_OK) rc = escg_run(h, n_mcs);
-  if (rc == ESCG_OK) rc = escg_snapshot(h, host_out);
-  if (rc == ESCG_OK && counts_out) rc = escg_counts(h, counts_out, nullptr);
-  return rc;
+  if (mcs > 0xFFFFFFFFull) {
+    set_err("mcs exceeds 2^32-1");
+    return ESCG_EINVAL;
+  }
+  // One synchronisation for the whole call: copy in, reset, check (an
+  // invalid lattice stops the run state on the device), run, copy out,
+  // count, then read the error word.
+  CUDA_TRY(copy_to_device(h, host_in));
+  int rc = reset_state(h, mcs);
+  if (rc != ESCG_OK) return rc;
+  CUDA_TRY(launch_validate(h->desc, &h->d_state->error, kErrBadValue, &h->d_state->stopped, h->stream));
+  h->launches++;
+  rc = escg_run(h, n_mcs);
+  if (rc != ESCG_OK) return rc;
+  CUDA_TRY(copy_to_host(h, host_out));
+  if (counts_out) {
+    CUDA_TRY(cudaMemsetAsync(h->d_scratch, 0, sizeof(RunState), h->stream));
+    CUDA_TRY(launch_count(h->desc, h->d_scratch, h->stream));
+    h->launches++;
+    CUDA_TRY(cudaMemcpyAsync(counts_out, h->d_scratch->cur, sizeof(uint64_t) * (h->S + 1),
+                             cudaMemcpyDeviceToHost, h->stream));
+  }
+  uint32_t err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, &h->d_state->error, sizeof err, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (err & kErrBadValue) {
+    h->failed = true;
+    set_err("input lattice holds a value outside 0..S=%d", h->S);
+    return ESCG_EINVAL;
+  }
+  if (err & kErrTimeout) {
+    h->failed = true;
+    set_err("a bounded device-side wait timed out; the lattice is inconsistent until restored");
+    return ESCG_ETIMEOUT;
+  }
+  return ESCG_OK;
 }
 
 void* escg_device_lattice(escg_t* h) { return h ? (void*)h->lattice : nullptr; }

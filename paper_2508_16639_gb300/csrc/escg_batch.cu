@@ -95,11 +95,7 @@ __global__ void batch_count_kernel(const SlotDesc* slots, SlotState* states, con
   __shared__ uint32_t hist[kMaxStates];
   if (threadIdx.x < kMaxStates) hist[threadIdx.x] = 0;
   __syncthreads();
-  const int L = d.L, pitch = d.pitch;
-  for (int k = threadIdx.x; k < L * L; k += blockDim.x) {
-    const int r = k / L, c = k - r * L;
-    atomicAdd(&hist[d.lat[(size_t)r * pitch + c]], 1u);
-  }
+  count_vectors(d, threadIdx.x, blockDim.x, hist);
   __syncthreads();
   if (threadIdx.x == 0) {
     SlotState& st = states[s];

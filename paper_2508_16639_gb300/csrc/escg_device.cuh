@@ -342,6 +342,49 @@ __device__ __forceinline__ uint32_t bytes_equal(uint32_t w, uint32_t v) {
   return __popc(z);
 }
 
+// Adds the species counts of the 16-byte vectors k = start, start + stride,
+// ... of a lattice (rows of d.pitch bytes; bytes past column L masked as
+// 0xFF, never a state) to a shared histogram part[0..S]: SWAR zero-byte
+// counts in registers, one warp reduction and one shared atomic per warp and
+// state.  Every lane of the calling warps must call.
+__device__ __forceinline__ void count_vectors(const LatticeDesc& d, uint32_t start, uint32_t stride,
+                                              uint32_t* part) {
+  const int L = d.L, pitch = d.pitch, S = d.S;
+  const uint32_t vec_per_row = (uint32_t)pitch / 16u;
+  const uint32_t total = (uint32_t)L * vec_per_row;   // < 2^32 for L <= 16384
+  uint32_t c[kMaxStates];
+#pragma unroll
+  for (int v = 0; v < kMaxStates; ++v) c[v] = 0;
+  for (uint32_t k = start; k < total; k += stride) {
+    const uint32_t row = k / vec_per_row, q = k - row * vec_per_row;
+    uint4 w = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)row * pitch) + q);
+    const int col = 16 * (int)q;
+    if (col + 16 > L) {
+      uint32_t* p = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int valid = L - (col + 4 * e);
+        if (valid <= 0)
+          p[e] = 0xFFFFFFFFu;
+        else if (valid < 4)
+          p[e] |= 0xFFFFFFFFu << (8 * valid);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kMaxStates; ++v)
+      if (v <= S) c[v] += bytes_equal(w.x, v) + bytes_equal(w.y, v) + bytes_equal(w.z, v) +
+                         bytes_equal(w.w, v);
+  }
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int v = 0; v < kMaxStates; ++v) {
+    if (v <= S) {
+      const uint32_t sum = __reduce_add_sync(0xFFFFFFFFu, c[v]);
+      if (lane == 0 && sum) atomicAdd(&part[v], sum);
+    }
+  }
+}
+
 __device__ __forceinline__ void hist_add_words(uint32_t* hist, int S, uint32_t w0, uint32_t w1, uint32_t w2,
                                                uint32_t w3) {
   const int lane = threadIdx.x & 31;

@@ -29,6 +29,7 @@ struct RunState {
 };
 
 constexpr uint32_t kErrTimeout = 1u;
+constexpr uint32_t kErrBadValue = 2u;   // a restored lattice held a value outside 0..S
 
 struct LogBuffers {
   unsigned long long* counts;  // [kLogCap][kMaxStates]
@@ -41,8 +42,12 @@ void set_last_error(const char* fmt, ...);
 // Host-side launchers (all asynchronous on `stream`).
 cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream);
 cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t stream);
-// Sets *bad = 1 if any lattice byte is outside 0..S.
-cudaError_t launch_validate(const LatticeDesc& d, uint32_t* bad, cudaStream_t stream);
+// Sets *bad |= flag if any lattice byte is outside 0..S, and then *stop = 1
+// unless stop is null.
+cudaError_t launch_validate(const LatticeDesc& d, uint32_t* bad, uint32_t flag, uint32_t* stop,
+                            cudaStream_t stream);
+// Zeroes *st and sets its MCS number and first log number.
+cudaError_t launch_state_reset(RunState* st, uint32_t mcs, uint32_t log_num0, cudaStream_t stream);
 // Accumulates the lattice histogram into st->cur (which must be zero).
 cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream);
 // After work ending at MCS m_end: st->mcs = m_end (unless stopped); if `log`

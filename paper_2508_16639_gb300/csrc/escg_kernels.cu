@@ -51,7 +51,10 @@ __global__ void init_kernel(LatticeDesc d, uint64_t T_empty) {
 }
 
 // Flags (*bad = 1) any lattice byte outside 0..S (padding bytes excluded).
-__global__ void validate_kernel(LatticeDesc d, uint32_t* bad) {
+// Sets *bad |= flag if any lattice byte is outside 0..S; with stop != null
+// also *stop = 1, so that the kernels that follow on the stream leave the
+// lattice alone.
+__global__ void validate_kernel(LatticeDesc d, uint32_t* bad, uint32_t flag, uint32_t* stop) {
   const int L = d.L, pitch = d.pitch, vec_per_row = pitch / 16;
   const uint32_t lim = 0x7Fu - (uint32_t)d.S;  // byte + lim has bit 7 set iff byte > S (byte < 128)
   const size_t total = (size_t)L * vec_per_row;
@@ -72,50 +75,40 @@ __global__ void validate_kernel(LatticeDesc d, uint32_t* bad) {
       any |= (x | ((x & 0x7F7F7F7Fu) + lim * 0x01010101u)) & 0x80808080u;
     }
   }
-  if (__any_sync(0xFFFFFFFFu, any != 0) && (threadIdx.x & 31) == 0) atomicExch(bad, 1u);
+  if (__any_sync(0xFFFFFFFFu, any != 0) && (threadIdx.x & 31) == 0) {
+    atomicOr(bad, flag);
+    if (stop) atomicExch(stop, 1u);
+  }
+}
+
+// Zeroes a RunState and sets its MCS number and first log number.
+__global__ void state_reset_kernel(RunState* st, uint32_t mcs, uint32_t log_num0) {
+  uint32_t* w = reinterpret_cast<uint32_t*>(st);
+  constexpr int n = (int)(sizeof(RunState) / sizeof(uint32_t));
+  for (int k = threadIdx.x; k < n; k += blockDim.x) w[k] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->mcs = mcs;
+    st->log_num0 = log_num0;
+  }
 }
 
 __global__ void fill_u32_kernel(uint32_t* p, int n, uint32_t value) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) p[k] = value;
 }
 
-__global__ void count_kernel(LatticeDesc d, RunState* st) {
+// Species histogram (count_vectors per thread, per-CTA sums in shared
+// memory, one global atomic per CTA and state: per-warp global atomics on the
+// S+1 counters serialised and dominated the kernel).
+__global__ void __launch_bounds__(256) count_kernel(LatticeDesc d, RunState* st) {
   if (ld_volatile(&st->stopped)) return;
-  const int L = d.L, pitch = d.pitch, S = d.S;
-  const int vec_per_row = pitch / 16;
-  const size_t total = (size_t)L * vec_per_row;
-  uint32_t c[kMaxStates];
-#pragma unroll
-  for (int v = 0; v < kMaxStates; ++v) c[v] = 0;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
-       k += (size_t)gridDim.x * blockDim.x) {
-    const int row = (int)(k / vec_per_row), q = (int)(k % vec_per_row);
-    uint4 w = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)row * pitch) + q);
-    const int col = 16 * q;
-    if (col + 16 > L) {  // mask padding bytes with 0xFF (never a state)
-      uint32_t* p = reinterpret_cast<uint32_t*>(&w);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int valid = L - (col + 4 * e);
-        if (valid <= 0)
-          p[e] = 0xFFFFFFFFu;
-        else if (valid < 4)
-          p[e] |= 0xFFFFFFFFu << (8 * valid);
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < kMaxStates; ++v)
-      if (v <= S) c[v] += bytes_equal(w.x, v) + bytes_equal(w.y, v) + bytes_equal(w.z, v) +
-                         bytes_equal(w.w, v);
-  }
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int v = 0; v < kMaxStates; ++v) {
-    if (v <= S) {
-      const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, c[v]);
-      if (lane == 0 && s) atomicAdd(&st->cur[v], (unsigned long long)s);
-    }
-  }
+  __shared__ uint32_t part[kMaxStates];
+  if (threadIdx.x < kMaxStates) part[threadIdx.x] = 0u;
+  __syncthreads();
+  count_vectors(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, part);
+  __syncthreads();
+  if ((int)threadIdx.x <= d.S && part[threadIdx.x])
+    atomicAdd(&st->cur[threadIdx.x], (unsigned long long)part[threadIdx.x]);
 }
 
 // Writes the log entry of MCS m_end from counts c[0..S]; stasis check.
@@ -1105,15 +1098,21 @@ cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t str
   return cudaGetLastError();
 }
 
-cudaError_t launch_validate(const LatticeDesc& d, uint32_t* bad, cudaStream_t stream) {
+cudaError_t launch_validate(const LatticeDesc& d, uint32_t* bad, uint32_t flag, uint32_t* stop,
+                            cudaStream_t stream) {
   const size_t n = (size_t)d.L * (d.pitch / 16);
-  validate_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, bad);
+  validate_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, bad, flag, stop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_reset(RunState* st, uint32_t mcs, uint32_t log_num0, cudaStream_t stream) {
+  state_reset_kernel<<<1, 256, 0, stream>>>(st, mcs, log_num0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream) {
   const size_t n = (size_t)d.L * (d.pitch / 16);
-  count_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, st);
+  count_kernel<<<blocks_for(n, 256 * 4, 152 * 4), 256, 0, stream>>>(d, st);
   return cudaGetLastError();
 }
 
