@@ -26,7 +26,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-EXCHANGE, INTERACT, REPRODUCE = 0, 1, 2
+EXCHANGE, INTERACT, REPRODUCE, INTERACT_FAIL = 0, 1, 2, 3
 SHUFFLE_BLOCKS, SHUFFLE_SUBS = 1, 2
 
 
@@ -64,6 +64,7 @@ def _load():
             u8p, u32p, u64p, i32p, i64p = (P(C.c_uint8), P(C.c_uint32), P(C.c_uint64),
                                            P(C.c_int32), P(C.c_int64))
             d = C.c_double
+            dp = P(C.c_double)
             sig = {
                 "orc_philox_many": (None, [C.c_int64, u32p, u32p, u32p]),
                 "orc_circulant": (C.c_int, [C.c_int32, i32p, C.c_int32, u8p]),
@@ -85,6 +86,18 @@ def _load():
                 "orc_run_observed": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, u8p, d, d, d,
                                                C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                                C.c_int32, u8p, u64p, C.c_int64, i64p, u32p]),
+                "orc_pair_prob": (d, [C.c_int32, C.c_int32, C.c_int32, u8p, dp]),
+                "orc_interaction_threshold": (C.c_uint64, [C.c_uint64, C.c_uint64, d]),
+                "orc_rs_attempts_p": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, u8p, dp, d, d, d,
+                                                C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, u8p]),
+                "orc_rs_run_p": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, u8p, dp, d, d, d,
+                                           C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, u8p]),
+                "orc_replay_run_p": (C.c_int, [C.c_int32, C.c_int32, u8p, dp, d, d, d, C.c_uint64,
+                                               C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, u8p,
+                                               C.c_uint32, C.c_uint64, P(TraceRec), C.c_int64, i64p]),
+                "orc_run_observed_p": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, u8p, dp, d, d, d,
+                                                 C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                                 C.c_int32, u8p, u64p, C.c_int64, i64p, u32p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -154,23 +167,49 @@ def counts(lattice: np.ndarray, S: int) -> np.ndarray:
     return c
 
 
-def rs_attempts(lattice, D, I, P, X, seed, n_attempts, stream=0, mcs=0):
-    """n_attempts random-sequential elementary steps (Alg. 3) in place."""
+def _prob(prob, S):
+    """Edge probabilities as a contiguous S x S float64 array, or None."""
+    if prob is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(prob, dtype=np.float64).reshape(S, S))
+    return a
+
+
+def _pp(a):
+    return None if a is None else _ptr(a, C.c_double)
+
+
+def pair_prob(a: int, b: int, D: np.ndarray, prob=None) -> float:
+    """Probability of the interaction of the pair (selected a, neighbour b)."""
+    D = np.ascontiguousarray(D, dtype=np.uint8)
+    pr = _prob(prob, D.shape[0])
+    return float(_load().orc_pair_prob(a, b, D.shape[0], _ptr(D, C.c_uint8), _pp(pr)))
+
+
+def interaction_threshold(TX: int, TXI: int, p: float) -> int:
+    return int(_load().orc_interaction_threshold(TX, TXI, p))
+
+
+def rs_attempts(lattice, D, I, P, X, seed, n_attempts, stream=0, mcs=0, prob=None):
+    """n_attempts random-sequential elementary steps (Alg. 3) in place;
+    prob: optional S x S edge probabilities (Park, Chen, Szolnoki)."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8)
     H, L = lat.shape
     D = np.ascontiguousarray(D, dtype=np.uint8)
-    _check(_load().orc_rs_attempts(L, H, D.shape[0], _ptr(D, C.c_uint8), I, P, X, seed, stream,
-                                   mcs, n_attempts, _ptr(lat, C.c_uint8)), "rs_attempts")
+    pr = _prob(prob, D.shape[0])
+    _check(_load().orc_rs_attempts_p(L, H, D.shape[0], _ptr(D, C.c_uint8), _pp(pr), I, P, X, seed, stream,
+                                     mcs, n_attempts, _ptr(lat, C.c_uint8)), "rs_attempts")
     return lat
 
 
-def rs_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, stream=0):
+def rs_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, stream=0, prob=None):
     """n_mcs random-sequential MCS (Alg. 4: N elementary steps each)."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8).copy()
     H, L = lat.shape
     D = np.ascontiguousarray(D, dtype=np.uint8)
-    _check(_load().orc_rs_run(L, H, D.shape[0], _ptr(D, C.c_uint8), I, P, X, seed, stream,
-                              mcs_begin, n_mcs, _ptr(lat, C.c_uint8)), "rs_run")
+    pr = _prob(prob, D.shape[0])
+    _check(_load().orc_rs_run_p(L, H, D.shape[0], _ptr(D, C.c_uint8), _pp(pr), I, P, X, seed, stream,
+                                mcs_begin, n_mcs, _ptr(lat, C.c_uint8)), "rs_run")
     return lat
 
 
@@ -199,7 +238,7 @@ def init(L: int, S: int, p_empty: float, seed: int) -> np.ndarray:
 
 
 def replay_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, G=None, F=None, flags=0,
-               shuffle_seed=0, trace_cap=0):
+               shuffle_seed=0, trace_cap=0, prob=None):
     """Schedule-v1 replay.  Returns (lattice, attempts[, trace])."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8).copy()
     L = lat.shape[0]
@@ -211,9 +250,10 @@ def replay_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, G=None, F=None, fl
     D = np.ascontiguousarray(D, dtype=np.uint8)
     att = C.c_int64()
     tr = (TraceRec * trace_cap)() if trace_cap else None
-    _check(_load().orc_replay_run(L, D.shape[0], _ptr(D, C.c_uint8), I, P, X, seed, G, F,
-                                  mcs_begin, n_mcs, _ptr(lat, C.c_uint8), flags, shuffle_seed,
-                                  tr, trace_cap, C.byref(att)), "replay_run")
+    pr = _prob(prob, D.shape[0])
+    _check(_load().orc_replay_run_p(L, D.shape[0], _ptr(D, C.c_uint8), _pp(pr), I, P, X, seed, G, F,
+                                    mcs_begin, n_mcs, _ptr(lat, C.c_uint8), flags, shuffle_seed,
+                                    tr, trace_cap, C.byref(att)), "replay_run")
     if trace_cap:
         n = min(att.value, trace_cap)
         arr = np.frombuffer(tr, dtype=TRACE_DTYPE, count=n).copy()
@@ -222,7 +262,7 @@ def replay_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, G=None, F=None, fl
 
 
 def run_observed(lattice, D, I, P, X, seed, n_mcs, log_every=1, stop_at_extinction=False,
-                 mcs_begin=0, use_rs=False):
+                 mcs_begin=0, use_rs=False, prob=None):
     """Run with counts logged every log_every MCS; returns (lattice, log, mcs_end)."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8).copy()
     L = lat.shape[0]
@@ -231,8 +271,9 @@ def run_observed(lattice, D, I, P, X, seed, n_mcs, log_every=1, stop_at_extincti
     cap = n_mcs // log_every + 2
     log = np.zeros((cap, S + 1), dtype=np.uint64)
     nl, mend = C.c_int64(), C.c_uint32()
-    _check(_load().orc_run_observed(int(use_rs), L, S, _ptr(D, C.c_uint8), I, P, X, seed,
-                                    mcs_begin, n_mcs, log_every, int(stop_at_extinction),
+    pr = _prob(prob, S)
+    _check(_load().orc_run_observed_p(int(use_rs), L, S, _ptr(D, C.c_uint8), _pp(pr), I, P, X, seed,
+                                      mcs_begin, n_mcs, log_every, int(stop_at_extinction),
                                     _ptr(lat, C.c_uint8), _ptr(log, C.c_uint64), cap,
                                     C.byref(nl), C.byref(mend)), "run_observed")
     return lat, log[:min(nl.value, cap)], mend.value

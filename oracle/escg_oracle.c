@@ -98,7 +98,7 @@ int orc_dominates(int32_t a, int32_t b, int32_t S, const uint8_t* D)
 void orc_rule(int32_t action, int32_t S, const uint8_t* D, uint8_t* a, uint8_t* b)
 {
     uint8_t species = *a, neighbour = *b;
-    if (species == neighbour) return;
+    if (species == neighbour || action == ORC_INTERACT_FAIL) return;
     if (action == ORC_EXCHANGE) {
         *a = neighbour;
         *b = species;
@@ -127,6 +127,29 @@ int orc_thresholds(double I, double P, double X, uint64_t* TX, uint64_t* TXI)
     *TX = (uint64_t)floor(ldexp(X / R, 32) + 0.5);
     *TXI = (uint64_t)floor(ldexp((X + I) / R, 32) + 0.5);
     return 0;
+}
+
+/* Park, Chen and Szolnoki's probabilistic dominance (Section "Park, Chen,
+ * Szolnoki"): the edge between the two species of a pair carries the
+ * probability that an interaction across it takes place.  Pairs without an
+ * edge, with an empty site, or of equal species: 1 (Alg. 2 already makes
+ * their interaction a no-op). */
+double orc_pair_prob(int32_t a, int32_t b, int32_t S, const uint8_t* D, const double* Pd)
+{
+    if (!Pd || a == 0 || b == 0 || a == b) return 1.0;
+    if (orc_dominates(a, b, S, D)) return Pd[(a - 1) * S + (b - 1)];
+    if (orc_dominates(b, a, S, D)) return Pd[(b - 1) * S + (a - 1)];
+    return 1.0;
+}
+
+uint64_t orc_interaction_threshold(uint64_t TX, uint64_t TXI, double p)
+{
+    if (!(p > 0.0)) return TX;
+    if (p >= 1.0) return TXI;
+    /* q = p in 0.32 fixed point, rounded; the product is exact in 128 bits */
+    uint64_t q = (uint64_t)floor(ldexp(p, 32) + 0.5);
+    unsigned __int128 w = (unsigned __int128)(TXI - TX) * q + ((unsigned __int128)1 << 31);
+    return TX + (uint64_t)(w >> 32);
 }
 
 int orc_counts(int64_t n, const uint8_t* lattice, int32_t S, uint64_t* counts)
@@ -160,6 +183,14 @@ static int check_common(int32_t S, const uint8_t* D)
     for (int32_t i = 0; i < S; ++i)
         for (int32_t j = 0; j < S; ++j)
             if (D[i * S + j] > 1) return -1;
+    return 0;
+}
+
+static int check_prob(int32_t S, const double* Pd)
+{
+    if (!Pd) return 0;
+    for (int32_t i = 0; i < S * S; ++i)
+        if (!(Pd[i] >= 0.0 && Pd[i] <= 1.0)) return -1;
     return 0;
 }
 
@@ -210,7 +241,14 @@ int orc_rs_attempts(int32_t L, int32_t H, int32_t S, const uint8_t* D,
                     double I, double P, double X, uint64_t seed, uint32_t stream,
                     uint32_t mcs, int64_t n_attempts, uint8_t* lattice)
 {
-    if (L < 3 || H < 3 || check_common(S, D) || !lattice || n_attempts < 0) return -1;
+    return orc_rs_attempts_p(L, H, S, D, NULL, I, P, X, seed, stream, mcs, n_attempts, lattice);
+}
+
+int orc_rs_attempts_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const double* Pd,
+                      double I, double P, double X, uint64_t seed, uint32_t stream,
+                      uint32_t mcs, int64_t n_attempts, uint8_t* lattice)
+{
+    if (L < 3 || H < 3 || check_common(S, D) || check_prob(S, Pd) || !lattice || n_attempts < 0) return -1;
     if (!(I >= 0.0) || !(P >= 0.0) || !(X >= 0.0)) return -1;
     double R = X + I + P;          /* mu + sigma + epsilon, normalised below */
     if (!(R > 0.0)) return -1;
@@ -227,7 +265,10 @@ int orc_rs_attempts(int32_t L, int32_t H, int32_t S, const uint8_t* D,
         if (r < X)
             action = ORC_EXCHANGE;
         else if (r < X + I)
-            action = ORC_INTERACT;
+            /* the draw's position inside the interaction band is a fresh
+               uniform: the interaction happens with the edge's probability */
+            action = (r < X + orc_pair_prob(lattice[i], lattice[ni], S, D, Pd) * I) ? ORC_INTERACT
+                                                                                  : ORC_INTERACT_FAIL;
         else
             action = ORC_REPRODUCE;
         orc_rule(action, S, D, &lattice[i], &lattice[ni]);
@@ -239,9 +280,16 @@ int orc_rs_run(int32_t L, int32_t H, int32_t S, const uint8_t* D,
                double I, double P, double X, uint64_t seed, uint32_t stream,
                uint32_t mcs_begin, uint32_t n_mcs, uint8_t* lattice)
 {
+    return orc_rs_run_p(L, H, S, D, NULL, I, P, X, seed, stream, mcs_begin, n_mcs, lattice);
+}
+
+int orc_rs_run_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const double* Pd,
+                 double I, double P, double X, uint64_t seed, uint32_t stream,
+                 uint32_t mcs_begin, uint32_t n_mcs, uint8_t* lattice)
+{
     int64_t N = (int64_t)L * H;
     for (uint32_t k = 0; k < n_mcs; ++k) {
-        int rc = orc_rs_attempts(L, H, S, D, I, P, X, seed, stream, mcs_begin + k, N, lattice);
+        int rc = orc_rs_attempts_p(L, H, S, D, Pd, I, P, X, seed, stream, mcs_begin + k, N, lattice);
         if (rc) return rc;
     }
     return 0;
@@ -357,10 +405,27 @@ int orc_replay_run(int32_t L, int32_t S, const uint8_t* D,
                    uint8_t* lattice, uint32_t flags, uint64_t shuffle_seed,
                    orc_trace_rec* trace, int64_t trace_cap, int64_t* attempts_out)
 {
-    if (L < 8 || L > 65535 || check_common(S, D) || !lattice || G < 1 || F < 1) return -1;
+    return orc_replay_run_p(L, S, D, NULL, I, P, X, seed, G, F, mcs_begin, n_mcs, lattice, flags,
+                            shuffle_seed, trace, trace_cap, attempts_out);
+}
+
+int orc_replay_run_p(int32_t L, int32_t S, const uint8_t* D, const double* Pd,
+                     double I, double P, double X, uint64_t seed,
+                     int32_t G, int32_t F, uint32_t mcs_begin, uint32_t n_mcs,
+                     uint8_t* lattice, uint32_t flags, uint64_t shuffle_seed,
+                     orc_trace_rec* trace, int64_t trace_cap, int64_t* attempts_out)
+{
+    if (L < 8 || L > 65535 || check_common(S, D) || check_prob(S, Pd) || !lattice || G < 1 || F < 1)
+        return -1;
     if ((uint64_t)mcs_begin + n_mcs > 0xFFFFFFFFull) return -1;
     uint64_t TX, TXI;
     if (orc_thresholds(I, P, X, &TX, &TXI)) return -1;
+    /* interaction happens iff u < TP[a][b] (TX <= TP <= TXI) */
+    const int32_t s1 = S + 1;
+    uint64_t* TP = (uint64_t*)malloc(sizeof(uint64_t) * s1 * s1);
+    for (int32_t a = 0; a < s1; ++a)
+        for (int32_t b = 0; b < s1; ++b)
+            TP[a * s1 + b] = orc_interaction_threshold(TX, TXI, orc_pair_prob(a, b, S, D, Pd));
 
     int32_t Pc, GQ;
     orc_v1_partition(L, &Pc, &GQ, NULL, NULL, NULL);
@@ -423,6 +488,8 @@ int orc_replay_run(int32_t L, int32_t S, const uint8_t* D,
                                     int32_t action = ((uint64_t)u < TX)    ? ORC_EXCHANGE
                                                      : ((uint64_t)u < TXI) ? ORC_INTERACT
                                                                            : ORC_REPRODUCE;
+                                    if (action == ORC_INTERACT && (uint64_t)u >= TP[lattice[i] * s1 + lattice[j]])
+                                        action = ORC_INTERACT_FAIL;
                                     orc_rule(action, S, D, &lattice[i], &lattice[j]);
                                     if (trace && nrec < trace_cap) {
                                         orc_trace_rec* r = &trace[nrec++];
@@ -442,7 +509,7 @@ int orc_replay_run(int32_t L, int32_t S, const uint8_t* D,
             }
         }
     }
-    free(cs); free(fs); free(fc); free(blocks); free(subs);
+    free(cs); free(fs); free(fc); free(blocks); free(subs); free(TP);
     if (attempts_out) *attempts_out = attempts;
     return 0;
 }
@@ -462,6 +529,17 @@ int orc_run_observed(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D,
                      uint64_t* counts_log, int64_t log_cap, int64_t* n_logged,
                      uint32_t* mcs_end)
 {
+    return orc_run_observed_p(use_rs, L, S, D, NULL, I, P, X, seed, mcs_begin, n_mcs, log_every,
+                              stop_at_extinction, lattice, counts_log, log_cap, n_logged, mcs_end);
+}
+
+int orc_run_observed_p(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, const double* Pd,
+                       double I, double P, double X, uint64_t seed,
+                       uint32_t mcs_begin, uint32_t n_mcs, uint32_t log_every,
+                       int32_t stop_at_extinction, uint8_t* lattice,
+                       uint64_t* counts_log, int64_t log_cap, int64_t* n_logged,
+                       uint32_t* mcs_end)
+{
     if (log_every == 0 || !lattice) return -1;
     int32_t G, F;
     if (orc_v1_cycles(L, &G, &F)) return -1;
@@ -477,8 +555,8 @@ int orc_run_observed(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D,
             if (stop_at_extinction && alive_species(c, S) <= 1) break;
         }
         if (m == mcs_begin + n_mcs) break;
-        rc = use_rs ? orc_rs_run(L, L, S, D, I, P, X, seed, 0, m, 1, lattice)
-                    : orc_replay_run(L, S, D, I, P, X, seed, G, F, m, 1, lattice, 0, 0, NULL, 0, NULL);
+        rc = use_rs ? orc_rs_run_p(L, L, S, D, Pd, I, P, X, seed, 0, m, 1, lattice)
+                    : orc_replay_run_p(L, S, D, Pd, I, P, X, seed, G, F, m, 1, lattice, 0, 0, NULL, 0, NULL);
         if (rc) break;
         ++m;
     }

@@ -44,8 +44,9 @@ int orc_circulant(int32_t S, const int32_t* K, int32_t nK, uint8_t* D);
 /* Alg. 2: false if either site is empty, else D[(a-1)*S + (b-1)] == 1. */
 int orc_dominates(int32_t a, int32_t b, int32_t S, const uint8_t* D);
 
-/* Action codes, in the order Alg. 3 tests them. */
-enum { ORC_EXCHANGE = 0, ORC_INTERACT = 1, ORC_REPRODUCE = 2 };
+/* Action codes, in the order Alg. 3 tests them; ORC_INTERACT_FAIL is an
+ * interaction across a probabilistic edge that did not take place. */
+enum { ORC_EXCHANGE = 0, ORC_INTERACT = 1, ORC_REPRODUCE = 2, ORC_INTERACT_FAIL = 3 };
 /* Alg. 3 applied to the pair (selected site a, neighbour b) for a given
  * action; a and b are updated in place. */
 void orc_rule(int32_t action, int32_t S, const uint8_t* D, uint8_t* a, uint8_t* b);
@@ -57,6 +58,19 @@ double orc_exchange_from_mobility(double M, int64_t N);
  * u < TX, interaction iff TX <= u < TXI, reproduction otherwise, with
  * R = (X + I) + P, TX = floor(2^32 X/R + 1/2), TXI = floor(2^32 (X+I)/R + 1/2). */
 int orc_thresholds(double I, double P, double X, uint64_t* TX, uint64_t* TXI);
+
+/* Probabilistic dominance (Park, Chen and Szolnoki's model, Section "Park,
+ * Chen, Szolnoki"): Pd is S*S row-major, Pd[(a-1)*S + (b-1)] = probability
+ * that an interaction across the edge a -> b (D[(a-1)*S + (b-1)] = 1) takes
+ * place; NULL means every edge is certain.  orc_pair_prob returns the
+ * probability that applies to the pair (selected a, neighbour b): that of
+ * the edge between them, whichever its direction, else 1.
+ * Random-sequential oracle: an interaction draw r in [X, X+I) takes place iff
+ * r < X + p*I.  Schedule v1: iff u < orc_interaction_threshold(TX, TXI, p)
+ * = TX + floor((TXI - TX) * q / 2^32 + 1/2), q = floor(p * 2^32 + 1/2), in
+ * exact integer arithmetic (p = 0 gives TX, p = 1 gives TXI). */
+double orc_pair_prob(int32_t a, int32_t b, int32_t S, const uint8_t* D, const double* Pd);
+uint64_t orc_interaction_threshold(uint64_t TX, uint64_t TXI, double p);
 
 /* Histogram of lattice values 0..S (Alg. 4 densities(), as counts). */
 int orc_counts(int64_t n, const uint8_t* lattice, int32_t S, uint64_t* counts);
@@ -76,6 +90,13 @@ int orc_rs_attempts(int32_t L, int32_t H, int32_t S, const uint8_t* D,
 int orc_rs_run(int32_t L, int32_t H, int32_t S, const uint8_t* D,
                double I, double P, double X, uint64_t seed, uint32_t stream,
                uint32_t mcs_begin, uint32_t n_mcs, uint8_t* lattice);
+/* The same with edge probabilities Pd (may be NULL). */
+int orc_rs_attempts_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const double* Pd,
+                      double I, double P, double X, uint64_t seed, uint32_t stream,
+                      uint32_t mcs, int64_t n_attempts, uint8_t* lattice);
+int orc_rs_run_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const double* Pd,
+                 double I, double P, double X, uint64_t seed, uint32_t stream,
+                 uint32_t mcs_begin, uint32_t n_mcs, uint8_t* lattice);
 
 /* ---- Schedule v1 (coloured two-level sublattice), replay oracle ---- */
 /* Coarse partition of one axis: P segments (P even); fine partition: GQ
@@ -112,6 +133,12 @@ int orc_replay_run(int32_t L, int32_t S, const uint8_t* D,
                    int32_t G, int32_t F, uint32_t mcs_begin, uint32_t n_mcs,
                    uint8_t* lattice, uint32_t flags, uint64_t shuffle_seed,
                    orc_trace_rec* trace, int64_t trace_cap, int64_t* attempts_out);
+/* The same with edge probabilities Pd (may be NULL). */
+int orc_replay_run_p(int32_t L, int32_t S, const uint8_t* D, const double* Pd,
+                     double I, double P, double X, uint64_t seed,
+                     int32_t G, int32_t F, uint32_t mcs_begin, uint32_t n_mcs,
+                     uint8_t* lattice, uint32_t flags, uint64_t shuffle_seed,
+                     orc_trace_rec* trace, int64_t trace_cap, int64_t* attempts_out);
 
 /* Run with observation: counts after every log_every-th MCS (absolute MCS
  * number a multiple of log_every) are appended to counts_log
@@ -125,6 +152,12 @@ int orc_run_observed(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D,
                      int32_t stop_at_extinction, uint8_t* lattice,
                      uint64_t* counts_log, int64_t log_cap, int64_t* n_logged,
                      uint32_t* mcs_end);
+int orc_run_observed_p(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, const double* Pd,
+                       double I, double P, double X, uint64_t seed,
+                       uint32_t mcs_begin, uint32_t n_mcs, uint32_t log_every,
+                       int32_t stop_at_extinction, uint8_t* lattice,
+                       uint64_t* counts_log, int64_t log_cap, int64_t* n_logged,
+                       uint32_t* mcs_end);
 
 #ifdef __cplusplus
 }
