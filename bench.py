@@ -14,10 +14,13 @@ exchange = 2 M N with M = 1e-4), counts logged every 10 MCS.  One step =
   e2e       the same metric through the C ABI with host buffers
             (escg_step_host: pinned host lattice in, K x 10 MCS, lattice and
             counts out, copies inside the timed region);
-  roofline  the dominant kernel (persistent_kernel): algorithmic integer
+  roofline  the dominant kernel (the lattice-update kernel the library
+            picks, persistent_kernel at L = 3200): algorithmic integer
             instructions per launch / its event-timed launch duration
             against the GPU's integer-issue peak;
-  cpu_baseline  the CPU replay oracle (single thread) on a bounded sample.
+  cpu_baseline  the CPU replay oracle (single thread) on a bounded sample;
+  ensemble, serving, park  batched runs (A7), a request stream (A8) and the
+            probabilistic-dominance ensemble, each with its own metric.
 
 `--impl reference` times the CPU oracle itself (the reference arm of this
 tier) on the same metric and workload.  Multi-GPU (torchrun): replicas only,
@@ -90,6 +93,8 @@ def _parse():
     ap.add_argument("--ensemble-replicas", type=int, default=1024)
     ap.add_argument("--ensemble-baseline-sample", type=int, default=16)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-park", action="store_true")
+    ap.add_argument("--park-per-point", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=200.0,
                     help="mean Poisson arrival rate (requests/s); ~ the measured capacity")
@@ -232,6 +237,42 @@ def _ensemble(args, rank):
     return out
 
 
+def _park(args, rank):
+    """Probabilistic-dominance ensemble (the Park, Chen and Szolnoki model the
+    paper replicates): L = 100, 8 species, edge probabilities (alpha, beta,
+    gamma = 1), no mobility, L^2 MCS or until one species is left; reports
+    runs/s and the distribution of surviving species per (alpha, beta)."""
+    import time
+    import numpy as np
+    from paper_2508_16639_gb300 import workloads as W
+    from paper_2508_16639_gb300 import Batch
+    specs = W.park_ensemble(per_point=args.park_per_point)
+    for sp in specs:
+        sp["seed"] += 1000003 * rank
+    t0 = time.perf_counter()
+    b = Batch([{k: v for k, v in sp.items() if k != "point"} for sp in specs], log_every=10)
+    t1 = time.perf_counter()
+    b.run()
+    mcs, ext, cnt = b.status()
+    t2 = time.perf_counter()
+    surv = {}
+    for sp, c in zip(specs, cnt):
+        key = "a%.1f_b%.1f" % sp["point"]
+        n = int((c[1:9] > 0).sum())
+        surv.setdefault(key, np.zeros(9, dtype=int))[n] += 1
+    site_updates = float(sum(int(m) * sp["L"] ** 2 for m, sp in zip(mcs, specs)))
+    out = {"metric": "probabilistic-dominance ensemble runs/s", "runs": len(specs),
+           "seconds": t2 - t1, "setup_seconds": t1 - t0, "runs_per_s": len(specs) / (t2 - t1),
+           "site_updates_per_s": site_updates / (t2 - t1), "threads": b.threads, "launches": b.launches,
+           "mean_mcs": float(np.mean(mcs)),
+           "surviving_species_histogram": {k: v.tolist() for k, v in sorted(surv.items())},
+           "config": {"workload": f"{len(specs)} replicas: L=100, 8 species beating the next 3 with "
+                                  "probabilities (alpha, beta, 1), alpha, beta in {0.2,0.5,0.8}, "
+                                  "I=P=1, no mobility, to one species or L^2 MCS"}}
+    b.close()
+    return out
+
+
 def _serving(args, rank):
     """Serving: Poisson arrivals of run requests (L log-uniform [50,1600],
     S in {3,5}, budgets log-uniform 10^2-10^4 MCS, half stop at extinction),
@@ -352,6 +393,9 @@ def main():
     serving = None
     if not args.no_serving:
         serving = _serving(args, rank)
+    park = None
+    if not args.no_park:
+        park = _park(args, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -366,7 +410,7 @@ def main():
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": _config(w, mps), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks,
-                "ensemble": ensemble, "serving": serving,
+                "ensemble": ensemble, "serving": serving, "park": park,
                 "context": {"paper_cuda_ms_L3200_site_updates_per_s": 2.45e8,
                             "paper_hardware": "RTX A2000 (not a target)"}}
         print(json.dumps(line), flush=True)

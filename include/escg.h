@@ -88,6 +88,16 @@ typedef struct {
                                     back with escg_kernel_time)               */
     int32_t ctas_per_sm;         /* persistent CTAs per SM (0: as many as fit);
                                     physical mapping only, results unchanged  */
+    const double* dominance_prob;/* optional S*S row-major edge probabilities
+                                    (Park, Chen and Szolnoki's probabilistic
+                                    dominance, the paper's section "Park,
+                                    Chen, Szolnoki"): entry (a-1)*S+(b-1) in
+                                    [0,1] is the probability that an
+                                    interaction across the edge a -> b takes
+                                    place; read during creation; NULL: every
+                                    edge certain.  An interaction draw u in
+                                    [T_X, T_XI) takes place iff u < T_X +
+                                    round((T_XI - T_X) round(p 2^32) / 2^32)  */
 } escg_options;
 
 typedef struct escg escg_t;
@@ -182,6 +192,8 @@ typedef struct {
     double p_empty;
     uint64_t max_mcs;             /* budget (absolute MCS number to stop at)     */
     int32_t stop_at_extinction;
+    const double* dominance_prob; /* optional S*S edge probabilities, as in
+                                     escg_options (copied on submission)       */
 } escg_replica_spec;
 
 typedef struct {

@@ -63,11 +63,13 @@ class Lattice:
     persistent: 1 persistent dataflow launches (default; uniform 64x64
     partitions use the boundary-mailbox kernel where it is faster), 3 the
     same with epoch flags only, 2 with a TMA producer warp, 0 one launch per
-    coarse phase -- all bit-identical."""
+    coarse phase -- all bit-identical.  dominance_prob: optional S x S edge
+    probabilities (Park, Chen and Szolnoki's probabilistic dominance)."""
 
     def __init__(self, L: int, S: int, digraph, rates, seed: int, p_empty: float = 0.0,
                  log_every: int = 10, stop_at_extinction: bool = False, persistent: int = 1,
-                 stream=None, device_buffer=None, time_kernels: bool = False, ctas_per_sm: int = 0):
+                 stream=None, device_buffer=None, time_kernels: bool = False, ctas_per_sm: int = 0,
+                 dominance_prob=None):
         lib = load()
         self.L, self.S = int(L), int(S)
         D = np.ascontiguousarray(np.asarray(digraph, dtype=np.uint8).reshape(S, S))
@@ -80,6 +82,9 @@ class Lattice:
         opt.persistent = int(persistent)
         opt.time_kernels = int(bool(time_kernels))
         opt.ctas_per_sm = int(ctas_per_sm)
+        if dominance_prob is not None:
+            Pd = np.ascontiguousarray(np.asarray(dominance_prob, dtype=np.float64).reshape(S, S))
+            opt.dominance_prob = Pd.ctypes.data_as(C.POINTER(C.c_double))   # read during creation
         if stream is not None:
             opt.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         self._buffer = device_buffer  # keep the torch tensor alive
@@ -212,6 +217,10 @@ def _replica_spec(sp, keep):
     r.p_empty = float(sp.get("p_empty", 0.0))
     r.max_mcs = int(sp["max_mcs"])
     r.stop_at_extinction = int(bool(sp.get("stop_at_extinction", False)))
+    if sp.get("dominance_prob") is not None:
+        Pd = np.ascontiguousarray(np.asarray(sp["dominance_prob"], dtype=np.float64).reshape(r.S, r.S))
+        keep.append(Pd)
+        r.dominance_prob = Pd.ctypes.data_as(C.POINTER(C.c_double))
     return r
 
 

@@ -24,13 +24,14 @@ class Options(C.Structure):
                 ("stop_at_extinction", C.c_int32), ("schedule_version", C.c_uint32),
                 ("persistent", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("device_lattice", C.c_void_p), ("time_kernels", C.c_int32),
-                ("ctas_per_sm", C.c_int32)]
+                ("ctas_per_sm", C.c_int32), ("dominance_prob", C.POINTER(C.c_double))]
 
 
 class ReplicaSpec(C.Structure):
     _fields_ = [("L", C.c_int32), ("S", C.c_int32), ("digraph", C.POINTER(C.c_uint8)),
                 ("rates", Rates), ("seed", C.c_uint64), ("p_empty", C.c_double),
-                ("max_mcs", C.c_uint64), ("stop_at_extinction", C.c_int32)]
+                ("max_mcs", C.c_uint64), ("stop_at_extinction", C.c_int32),
+                ("dominance_prob", C.POINTER(C.c_double))]
 
 
 class BatchOptions(C.Structure):

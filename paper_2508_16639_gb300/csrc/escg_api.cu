@@ -133,15 +133,27 @@ bool thresholds(const escg_rates* r, uint64_t* tx, uint64_t* txi) {
   return true;
 }
 
-// Transition table of Alg. 3 for every (action, selected a, neighbour b):
-// exchange swaps distinct values; interaction empties the dominated one
-// (selected site tested first; empty sites never dominate, Alg. 2);
-// reproduction fills an empty site of the pair with the other's species.
-void build_trans(int S, const uint8_t* D, std::vector<uint8_t>& t) {
+}  // namespace
+
+namespace escg_impl {
+
+// Transition table (LatticeDesc::trans) of Alg. 3 for every (action,
+// selected a, neighbour b): exchange swaps distinct values; interaction
+// empties the dominated one (selected site tested first; empty sites never
+// dominate, Alg. 2); reproduction copies the selected species into an empty
+// neighbour or the neighbour's species into an empty selected site; action 3
+// changes nothing.  Interaction thresholds: an edge with probability p
+// (Park, Chen and Szolnoki) takes place iff u < T_X + round((T_XI - T_X) q /
+// 2^32), q = round(p 2^32) -- exact integer arithmetic, so the value does not
+// depend on the compiler's floating-point contraction; prob == nullptr
+// means every edge is certain (T_XI).
+void build_transitions(int S, const uint8_t* D, const double* prob, uint64_t tx, uint64_t txi,
+                       uint32_t* out) {
   const int s1 = S + 1;
-  t.assign(4 * s1 * s1, 0);
-  auto dom = [&](int a, int b) { return a != 0 && b != 0 && D[(a - 1) * S + (b - 1)] == 1; };
-  for (int act = 0; act < 3; ++act)
+  std::memset(out, 0, sizeof(uint32_t) * kTransWords);
+  uint8_t* t = reinterpret_cast<uint8_t*>(out);
+  auto dom = [&](int x, int y) { return x != 0 && y != 0 && D[(x - 1) * S + (y - 1)] == 1; };
+  for (int act = 0; act < 4; ++act)
     for (int a = 0; a < s1; ++a)
       for (int b = 0; b < s1; ++b) {
         int na = a, nb = b;
@@ -154,7 +166,7 @@ void build_trans(int S, const uint8_t* D, std::vector<uint8_t>& t) {
               nb = 0;
             else if (dom(b, a))
               na = 0;
-          } else {
+          } else if (act == 2) {
             if (b == 0)
               nb = a;
             else if (a == 0)
@@ -163,9 +175,28 @@ void build_trans(int S, const uint8_t* D, std::vector<uint8_t>& t) {
         }
         t[(a * s1 + b) * 4 + act] = (uint8_t)(na | (nb << 4));
       }
+  for (int a = 0; a < s1; ++a)
+    for (int b = 0; b < s1; ++b) {
+      double p = 1.0;
+      if (prob && a != 0 && b != 0 && a != b) {
+        if (dom(a, b))
+          p = prob[(a - 1) * S + (b - 1)];
+        else if (dom(b, a))
+          p = prob[(b - 1) * S + (a - 1)];
+      }
+      uint64_t tp = txi;
+      if (!(p > 0.0)) {
+        tp = tx;
+      } else if (p < 1.0) {
+        const uint64_t q = (uint64_t)std::floor(std::ldexp(p, 32) + 0.5);
+        const unsigned __int128 w = (unsigned __int128)(txi - tx) * q + ((unsigned __int128)1 << 31);
+        tp = tx + (uint64_t)(w >> 32);
+      }
+      out[kTransPairs + a * s1 + b] = (tp >> 32) ? 0xFFFFFFFFu : (uint32_t)tp;
+    }
 }
 
-}  // namespace
+}  // namespace escg_impl
 
 struct escg {
   int device = 0;
@@ -373,6 +404,13 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   escg_default_options(&o);
   if (opt) o = *opt;
   if (o.log_every == 0) o.log_every = 10;
+  if (o.dominance_prob) {
+    for (int k = 0; k < S * S; ++k)
+      if (!(o.dominance_prob[k] >= 0.0 && o.dominance_prob[k] <= 1.0)) {
+        set_err("dominance_prob[%d] is not in [0,1]", k);
+        return nullptr;
+      }
+  }
   if (o.persistent < 0 || o.persistent > 3) {
     set_err("persistent must be 0..3 (got %d)", o.persistent);
     return nullptr;
@@ -437,7 +475,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   const Partition& p = h->part;
   const size_t ntab = p.cs.size() + p.fs.size() + p.fc.size();
   if (e == cudaSuccess) e = cudaMalloc(&h->d_tables, ntab * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_trans, 4 * kMaxStates * kMaxStates);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_trans, sizeof(uint32_t) * kTransWords);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_state, sizeof(RunState));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_log, sizeof(unsigned long long) * kLogCap * kMaxStates);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_log_mcs, sizeof(uint32_t) * kLogCap);
@@ -451,13 +489,13 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   tab.insert(tab.end(), p.cs.begin(), p.cs.end());
   tab.insert(tab.end(), p.fs.begin(), p.fs.end());
   tab.insert(tab.end(), p.fc.begin(), p.fc.end());
-  std::vector<uint8_t> trans;
-  build_trans(S, digraph, trans);
   uint64_t tx = 0, txi = 0;
   thresholds(rates, &tx, &txi);
+  std::vector<uint32_t> trans(kTransWords);
+  build_transitions(S, digraph, o.dominance_prob, tx, txi, trans.data());
   if (cudaMemcpyAsync(h->d_tables, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess ||
-      cudaMemcpyAsync(h->d_trans, trans.data(), trans.size(), cudaMemcpyHostToDevice, h->stream) !=
+      cudaMemcpyAsync(h->d_trans, trans.data(), trans.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess) {
     set_err("upload of lattice tables failed");

@@ -335,7 +335,7 @@ struct BItem {
 
 struct BatchTmaSmem {
   alignas(128) uint8_t tile[2][kBTileStride];
-  uint32_t trans[2][kMaxStates * kMaxStates];
+  uint32_t trans[2][kTransWords];
   SlotDesc sd[2];
   BItem item[2];
   alignas(8) uint64_t full[2], empty[2], tma[2];
@@ -419,7 +419,10 @@ __device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t
     {
       const int nt = (d.S + 1) * (d.S + 1);
       const uint32_t* tr = reinterpret_cast<const uint32_t*>(d.trans);
-      for (int w = lane; w < nt; w += 32) sm.trans[b][w] = tr[w];
+      for (int w = lane; w < nt; w += 32) {
+        sm.trans[b][w] = tr[w];
+        sm.trans[b][kTransPairs + w] = tr[kTransPairs + w];
+      }
     }
     // wait until the 8 neighbours (and the block itself) have completed
     // every visit that precedes this one in schedule order
@@ -722,6 +725,12 @@ int plan_slot(const escg_replica_spec& sp, SlotPlan* pl, int idx) {
       set_last_error("replica %d: digraph must be 0/1 with a zero diagonal", idx);
       return ESCG_EINVAL;
     }
+  if (sp.dominance_prob)
+    for (int a = 0; a < sp.S * sp.S; ++a)
+      if (!(sp.dominance_prob[a] >= 0.0 && sp.dominance_prob[a] <= 1.0)) {
+        set_last_error("replica %d: dominance_prob must be in [0,1]", idx);
+        return ESCG_EINVAL;
+      }
   const double I = sp.rates.interact, Pr = sp.rates.reproduce, X = sp.rates.exchange;
   if (!(I >= 0 && Pr >= 0 && X >= 0) || !((X + I) + Pr > 0) || std::isinf((X + I) + Pr) ||
       !(sp.p_empty >= 0.0 && sp.p_empty <= 1.0) || sp.max_mcs > 0xFFFFFFFFull) {
@@ -741,7 +750,7 @@ int plan_slot(const escg_replica_spec& sp, SlotPlan* pl, int idx) {
   pl->tab = off;
   off = align_up(off + 4 * (p.cs.size() + p.fs.size() + p.fc.size()), 256);
   pl->trans = off;
-  off = align_up(off + 4 * (size_t)(sp.S + 1) * (sp.S + 1), 256);
+  off = align_up(off + sizeof(uint32_t) * kTransWords, 256);
   pl->done = off;
   off = align_up(off + 4 * (size_t)p.P * p.P, 256);
   pl->bytes = off;
@@ -907,31 +916,12 @@ int engine_add(Engine* e, const escg_replica_spec& sp, const SlotPlan& pl, int s
   for (int32_t v : p.cs) tab[w++] = v;
   for (int32_t v : p.fs) tab[w++] = v;
   for (int32_t v : p.fc) tab[w++] = v;
-  const int s1 = sp.S + 1;
-  uint8_t* tr = img.data() + (pl.trans - pl.tab);
-  auto dom = [&](int x, int y) { return x != 0 && y != 0 && sp.digraph[(x - 1) * sp.S + (y - 1)] == 1; };
-  for (int act = 0; act < 3; ++act)
-    for (int x = 0; x < s1; ++x)
-      for (int y = 0; y < s1; ++y) {
-        int nx = x, ny = y;
-        if (x != y) {
-          if (act == 0) {
-            nx = y;
-            ny = x;
-          } else if (act == 1) {
-            if (dom(x, y))
-              ny = 0;
-            else if (dom(y, x))
-              nx = 0;
-          } else {
-            if (y == 0)
-              ny = x;
-            else if (x == 0)
-              nx = y;
-          }
-        }
-        tr[(x * s1 + y) * 4 + act] = (uint8_t)(nx | (ny << 4));
-      }
+  const double I = sp.rates.interact, Pr = sp.rates.reproduce, X = sp.rates.exchange;
+  const double R = (X + I) + Pr;
+  const uint64_t tx = (uint64_t)std::floor(std::ldexp(X / R, 32) + 0.5);
+  const uint64_t txi = (uint64_t)std::floor(std::ldexp((X + I) / R, 32) + 0.5);
+  build_transitions(sp.S, sp.digraph, sp.dominance_prob, tx, txi,
+                    reinterpret_cast<uint32_t*>(img.data() + (pl.trans - pl.tab)));
   SlotDesc sd;
   std::memset(&sd, 0, sizeof sd);
   LatticeDesc& d = sd.d;
@@ -950,10 +940,6 @@ int engine_add(Engine* e, const escg_replica_spec& sp, const SlotPlan& pl, int s
     d.rk[2 * r] = d.key0 + (uint32_t)r * 0x9E3779B9u;
     d.rk[2 * r + 1] = d.key1 + (uint32_t)r * 0xBB67AE85u;
   }
-  const double I = sp.rates.interact, Pr = sp.rates.reproduce, X = sp.rates.exchange;
-  const double R = (X + I) + Pr;
-  const uint64_t tx = (uint64_t)std::floor(std::ldexp(X / R, 32) + 0.5);
-  const uint64_t txi = (uint64_t)std::floor(std::ldexp((X + I) / R, 32) + 0.5);
   d.tx = tx >> 32 ? 0xFFFFFFFFu : (uint32_t)tx;
   d.txi = txi >> 32 ? 0xFFFFFFFFu : (uint32_t)txi;
   d.S = sp.S;
@@ -1268,7 +1254,8 @@ namespace {
 struct Request {
   int64_t id = 0;
   escg_replica_spec spec{};
-  std::vector<uint8_t> digraph;   // owned copy
+  std::vector<uint8_t> digraph;   // owned copies
+  std::vector<double> prob;
   SlotPlan plan;
 };
 
@@ -1345,9 +1332,11 @@ int64_t escg_server_submit(escg_server_t* s, const escg_replica_spec* spec) {
   }
   r.spec = *spec;
   r.digraph.assign(spec->digraph, spec->digraph + spec->S * spec->S);
-  r.spec.digraph = r.digraph.data();
+  if (spec->dominance_prob) r.prob.assign(spec->dominance_prob, spec->dominance_prob + spec->S * spec->S);
   s->queue.push_back(std::move(r));
-  s->queue.back().spec.digraph = s->queue.back().digraph.data();
+  Request& q = s->queue.back();
+  q.spec.digraph = q.digraph.data();
+  q.spec.dominance_prob = q.prob.empty() ? nullptr : q.prob.data();
   return s->next_id++;
 }
 

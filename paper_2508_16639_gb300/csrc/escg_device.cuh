@@ -68,17 +68,19 @@ __device__ __forceinline__ int slot_of(uint32_t ord, int colour) {
 // Per-CTA shared state of a block visit.
 struct VisitSmem {
   uint8_t tile[kMaxTileRows * kMaxTilePitch];
-  uint32_t trans[kMaxStates * kMaxStates];   // word (a*(S+1)+b), byte = action
+  uint32_t trans[kTransWords];   // LatticeDesc::trans
   int16_t fsx[kMaxFine + 1], fsy[kMaxFine + 1];   // block-local fine starts
   uint32_t forder;
   uint32_t hist[kMaxStates];
 };
 
 // Transition of the pair (a, b) under the action drawn by u: byte
-// (a*(S+1)+b)*4 + action of the table, action = [u >= T_X] + [u >= T_XI]
-// (0 exchange, 1 interaction, 2 reproduction); new a in the low nibble, new b
-// in the high nibble.  Thresholds of 2^32 are stored as 0xFFFFFFFF, which is
-// exact because u is always a multiple of 4.
+// (a*(S+1)+b)*4 + action of the table, action = exchange if u < T_X,
+// interaction if u < T_XI and u is below the pair's interaction threshold
+// (an edge that wins with a probability: Park, Chen and Szolnoki's model),
+// no change if only the latter fails, reproduction otherwise.  New a in the
+// low nibble, new b in the high nibble.  Thresholds of 2^32 are stored as
+// 0xFFFFFFFF, which is exact because u is always a multiple of 4.
 // Exchange (u < T_X) is a plain swap and needs no table: with epsilon = 2MN
 // it is the action of almost every attempt on large lattices, so it takes a
 // short path of its own (identical result: the table entry is the swap).
@@ -90,8 +92,10 @@ __device__ __forceinline__ void apply_rule(uint8_t* __restrict__ tile, const uin
     tile[ti] = (uint8_t)b;
     tile[tj] = (uint8_t)a;
   } else {
-    const uint32_t act = 1u + (u >= txi ? 1u : 0u);
-    const uint32_t nn = trans[(a * s1 + b) * 4u + act];
+    const uint32_t pair = a * s1 + b;
+    const uint32_t tp = reinterpret_cast<const uint32_t*>(trans)[kTransPairs + pair];
+    const uint32_t act = (u >= txi) ? 2u : (u < tp ? 1u : 3u);
+    const uint32_t nn = trans[pair * 4u + act];
     tile[ti] = (uint8_t)(nn & 15u);
     tile[tj] = (uint8_t)(nn >> 4);
   }
@@ -214,7 +218,11 @@ __device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int
 // Loads the transition table (built on the host) and the fine order.
 __device__ __forceinline__ void load_trans(const LatticeDesc& d, uint32_t* trans) {
   const int n = (d.S + 1) * (d.S + 1);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) trans[k] = reinterpret_cast<const uint32_t*>(d.trans)[k];
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(d.trans);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    trans[k] = src[k];
+    trans[kTransPairs + k] = src[kTransPairs + k];
+  }
 }
 
 // Visit of coarse block (bx, by) in MCS m, uniform geometry.  Must be called

@@ -39,6 +39,12 @@ struct LogBuffers {
 // Sets the thread-local message returned by escg_last_error().
 void set_last_error(const char* fmt, ...);
 
+// Fills out[kTransWords] with the transition table of LatticeDesc::trans for
+// S species, dominance digraph D (S*S), optional edge probabilities prob
+// (S*S, nullptr: every edge certain) and the 64-bit rate thresholds.
+void build_transitions(int S, const uint8_t* D, const double* prob, uint64_t tx, uint64_t txi,
+                       uint32_t* out);
+
 // Host-side launchers (all asynchronous on `stream`).
 cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream);
 cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t stream);

@@ -378,7 +378,7 @@ struct LLItem {
 };
 struct LLSmem {
   alignas(16) uint8_t tile[2][kUniTileBytes];
-  uint32_t trans[kMaxStates * kMaxStates];
+  uint32_t trans[kTransWords];
   uint32_t hist[kMaxStates];
   LLItem item[2];
   uint32_t abort;
@@ -768,7 +768,7 @@ struct TmaItem {
 
 struct TmaSmem {
   alignas(128) uint8_t tile[2][kTmaTileStride];
-  uint32_t trans[kMaxStates * kMaxStates];
+  uint32_t trans[kTransWords];
   alignas(8) uint64_t full[2], empty[2], tma[2];
   TmaItem item[2];
   uint32_t hist[kMaxStates];

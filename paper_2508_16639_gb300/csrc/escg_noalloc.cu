@@ -28,7 +28,7 @@ constexpr size_t kNoallocDoneOff = kNoallocStateBytes;
 constexpr size_t kNoallocTabOff = kNoallocDoneOff + 4 * (size_t)kNoallocMaxP * kNoallocMaxP;
 constexpr size_t kNoallocTransOff =
     kNoallocTabOff + 4 * (size_t)((kNoallocMaxP + 1) * 2 + kNoallocMaxGQ + 1 + 63) / 64 * 64;
-static_assert(kNoallocTransOff + 4 * kMaxStates * kMaxStates <= kNoallocScratchBytes, "scratch too small");
+static_assert(kNoallocTransOff + 4 * kTransWords <= kNoallocScratchBytes, "scratch too small");
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocScratchBytes];
 
@@ -78,7 +78,10 @@ __global__ void noalloc_setup_kernel(uint8_t* scratch, NoallocSetup a) {
     fc[P] = GQ;
     const int S = a.S, s1 = S + 1;
     uint8_t* tr = scratch + kNoallocTransOff;
-    for (int act = 0; act < 3; ++act)
+    // every edge certain: interaction thresholds 2^32 (stored as 0xFFFFFFFF)
+    uint32_t* thr = reinterpret_cast<uint32_t*>(tr) + kTransPairs;
+    for (int k = 0; k < s1 * s1; ++k) thr[k] = 0xFFFFFFFFu;
+    for (int act = 0; act < 4; ++act)
       for (int x = 0; x < s1; ++x)
         for (int y = 0; y < s1; ++y) {
           const bool xy = x && y && a.digraph[(x - 1) * S + (y - 1)];
@@ -93,7 +96,7 @@ __global__ void noalloc_setup_kernel(uint8_t* scratch, NoallocSetup a) {
                 ny = 0;
               else if (yx)
                 nx = 0;
-            } else {
+            } else if (act == 2) {
               if (y == 0)
                 ny = x;
               else if (x == 0)

@@ -18,6 +18,10 @@ constexpr int kMaxTilePitch = 112;   // round_up(kColOff + kMaxBlock + 1, 16)
 constexpr int kMaxTileRows = kMaxBlock + 2;
 constexpr int kMaxFine = kMaxBlock / 2;  // fine segments per block axis
 constexpr int kMaxStates = 16;           // S <= 15
+// Transition table: kMaxStates^2 words of action bytes, then kMaxStates^2
+// words of interaction thresholds (see LatticeDesc::trans).
+constexpr int kTransPairs = kMaxStates * kMaxStates;
+constexpr int kTransWords = 2 * kTransPairs;
 
 // Everything a kernel needs to know about one lattice.
 struct LatticeDesc {
@@ -27,8 +31,12 @@ struct LatticeDesc {
   const int32_t* cs;    // [P+1] coarse segment starts
   const int32_t* fs;    // [GQ+1] fine segment starts (global coordinates)
   const int32_t* fc;    // [P+1] first global fine index of each coarse segment
-  const uint8_t* trans; // [(S+1)*(S+1)][4]: byte (a*(S+1)+b)*4 + action holds
-                        // the new pair (a' | b' << 4)
+  const uint8_t* trans; // kTransWords words: byte (a*(S+1)+b)*4 + action of
+                        // the first half holds the new pair (a' | b' << 4),
+                        // actions 0 exchange, 1 interaction, 2 reproduction,
+                        // 3 no change; word kTransPairs + a*(S+1)+b holds the
+                        // pair's interaction threshold (an interaction draw
+                        // u >= it does not take place; 0xFFFFFFFF: always)
   uint32_t key0, key1;  // Philox key (seed)
   uint32_t rk[20];      // Philox round keys: rk[2r] = key0 + r*0x9E3779B9,
                         // rk[2r+1] = key1 + r*0xBB67AE85

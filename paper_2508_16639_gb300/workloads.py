@@ -75,3 +75,36 @@ def request_stream(n: int = 10000, seed: int = 2, rate_per_s: float = 1000.0, L_
                                                             np.log10(budget_range[1])))),
                         stop_at_extinction=bool(rng.random() < p_stop)))
     return out
+
+
+def park_network(alpha: float, beta: float, gamma: float, S: int = 8):
+    """(digraph, edge probabilities) of an S-species cyclic network in which
+    species a beats a+1, a+2 and a+3 (mod S) with probabilities alpha, beta
+    and gamma: the probability structure of Park, Chen and Szolnoki's
+    eight-species model.  The paper's figure of their network is missing
+    from the text, so this edge set is a stand-in of the same shape."""
+    D = np.zeros((S, S), dtype=np.uint8)
+    P = np.zeros((S, S))
+    for a in range(S):
+        for d, p in zip((1, 2, 3), (alpha, beta, gamma)):
+            D[a, (a + d) % S] = 1
+            P[a, (a + d) % S] = p
+    return D, P
+
+
+def park_ensemble(per_point: int = 64, alphas=(0.2, 0.5, 0.8), betas=(0.2, 0.5, 0.8), gamma: float = 1.0,
+                  L: int = 100, seed0: int = SEED0 + 500000):
+    """Replica specs of the probabilistic-dominance experiment the paper
+    replicates: no mobility, L = 100, 8 species, runs of L^2 MCS (or until
+    at most one species is left), per_point seeds at every (alpha, beta)."""
+    out = []
+    k = 0
+    for a in alphas:
+        for b in betas:
+            D, P = park_network(a, b, gamma)
+            for _ in range(per_point):
+                out.append(dict(L=L, S=8, digraph=D, dominance_prob=P, rates=(1.0, 1.0, 0.0),
+                                seed=seed0 + k, p_empty=0.0, max_mcs=L * L, stop_at_extinction=True,
+                                point=(a, b)))
+                k += 1
+    return out
