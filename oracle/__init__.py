@@ -55,6 +55,11 @@ TRACE_DTYPE = np.dtype([("mcs", "<u4"), ("coarse_phase", "<u4"), ("fine_phase", 
                         ("nbr", "<u4"), ("dir", "u1"), ("action", "u1"), ("pad", "u1", 2)])
 
 
+class Variant(C.Structure):
+    """orc_variant: neighbourhood 4/8, reflecting boundary, edge probabilities."""
+    _fields_ = [("neighbourhood", C.c_int32), ("reflect", C.c_int32), ("prob", C.POINTER(C.c_double))]
+
+
 def _load():
     global _lib
     with _lock:
@@ -65,6 +70,7 @@ def _load():
                                            P(C.c_int32), P(C.c_int64))
             d = C.c_double
             dp = P(C.c_double)
+            vp = P(Variant)
             sig = {
                 "orc_philox_many": (None, [C.c_int64, u32p, u32p, u32p]),
                 "orc_circulant": (C.c_int, [C.c_int32, i32p, C.c_int32, u8p]),
@@ -96,6 +102,16 @@ def _load():
                                                C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, u8p,
                                                C.c_uint32, C.c_uint64, P(TraceRec), C.c_int64, i64p]),
                 "orc_run_observed_p": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, u8p, dp, d, d, d,
+                                                 C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                                 C.c_int32, u8p, u64p, C.c_int64, i64p, u32p]),
+                "orc_rs_attempts_v": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, u8p, vp, d, d, d,
+                                                C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, u8p]),
+                "orc_rs_run_v": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, u8p, vp, d, d, d,
+                                           C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, u8p]),
+                "orc_replay_run_v": (C.c_int, [C.c_int32, C.c_int32, u8p, vp, d, d, d, C.c_uint64,
+                                               C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, u8p,
+                                               C.c_uint32, C.c_uint64, P(TraceRec), C.c_int64, i64p]),
+                "orc_run_observed_v": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, u8p, vp, d, d, d,
                                                  C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                                  C.c_int32, u8p, u64p, C.c_int64, i64p, u32p]),
             }
@@ -179,6 +195,13 @@ def _pp(a):
     return None if a is None else _ptr(a, C.c_double)
 
 
+def _variant(S, neighbourhood, reflect, prob):
+    """(Variant, keep-alive array) for the _v entry points."""
+    pr = _prob(prob, S)
+    v = Variant(int(neighbourhood), int(bool(reflect)), _pp(pr))
+    return v, pr
+
+
 def pair_prob(a: int, b: int, D: np.ndarray, prob=None) -> float:
     """Probability of the interaction of the pair (selected a, neighbour b)."""
     D = np.ascontiguousarray(D, dtype=np.uint8)
@@ -190,25 +213,27 @@ def interaction_threshold(TX: int, TXI: int, p: float) -> int:
     return int(_load().orc_interaction_threshold(TX, TXI, p))
 
 
-def rs_attempts(lattice, D, I, P, X, seed, n_attempts, stream=0, mcs=0, prob=None):
+def rs_attempts(lattice, D, I, P, X, seed, n_attempts, stream=0, mcs=0, prob=None, neighbourhood=4,
+                reflect=False):
     """n_attempts random-sequential elementary steps (Alg. 3) in place;
-    prob: optional S x S edge probabilities (Park, Chen, Szolnoki)."""
+    prob: optional S x S edge probabilities (Park, Chen, Szolnoki);
+    neighbourhood 4 or 8, reflect: reflecting instead of periodic boundary."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8)
     H, L = lat.shape
     D = np.ascontiguousarray(D, dtype=np.uint8)
-    pr = _prob(prob, D.shape[0])
-    _check(_load().orc_rs_attempts_p(L, H, D.shape[0], _ptr(D, C.c_uint8), _pp(pr), I, P, X, seed, stream,
+    v, _keep = _variant(D.shape[0], neighbourhood, reflect, prob)
+    _check(_load().orc_rs_attempts_v(L, H, D.shape[0], _ptr(D, C.c_uint8), C.byref(v), I, P, X, seed, stream,
                                      mcs, n_attempts, _ptr(lat, C.c_uint8)), "rs_attempts")
     return lat
 
 
-def rs_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, stream=0, prob=None):
+def rs_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, stream=0, prob=None, neighbourhood=4, reflect=False):
     """n_mcs random-sequential MCS (Alg. 4: N elementary steps each)."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8).copy()
     H, L = lat.shape
     D = np.ascontiguousarray(D, dtype=np.uint8)
-    pr = _prob(prob, D.shape[0])
-    _check(_load().orc_rs_run_p(L, H, D.shape[0], _ptr(D, C.c_uint8), _pp(pr), I, P, X, seed, stream,
+    v, _keep = _variant(D.shape[0], neighbourhood, reflect, prob)
+    _check(_load().orc_rs_run_v(L, H, D.shape[0], _ptr(D, C.c_uint8), C.byref(v), I, P, X, seed, stream,
                                 mcs_begin, n_mcs, _ptr(lat, C.c_uint8)), "rs_run")
     return lat
 
@@ -238,7 +263,7 @@ def init(L: int, S: int, p_empty: float, seed: int) -> np.ndarray:
 
 
 def replay_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, G=None, F=None, flags=0,
-               shuffle_seed=0, trace_cap=0, prob=None):
+               shuffle_seed=0, trace_cap=0, prob=None, neighbourhood=4, reflect=False):
     """Schedule-v1 replay.  Returns (lattice, attempts[, trace])."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8).copy()
     L = lat.shape[0]
@@ -250,8 +275,8 @@ def replay_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, G=None, F=None, fl
     D = np.ascontiguousarray(D, dtype=np.uint8)
     att = C.c_int64()
     tr = (TraceRec * trace_cap)() if trace_cap else None
-    pr = _prob(prob, D.shape[0])
-    _check(_load().orc_replay_run_p(L, D.shape[0], _ptr(D, C.c_uint8), _pp(pr), I, P, X, seed, G, F,
+    v, _keep = _variant(D.shape[0], neighbourhood, reflect, prob)
+    _check(_load().orc_replay_run_v(L, D.shape[0], _ptr(D, C.c_uint8), C.byref(v), I, P, X, seed, G, F,
                                     mcs_begin, n_mcs, _ptr(lat, C.c_uint8), flags, shuffle_seed,
                                     tr, trace_cap, C.byref(att)), "replay_run")
     if trace_cap:
@@ -262,7 +287,7 @@ def replay_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, G=None, F=None, fl
 
 
 def run_observed(lattice, D, I, P, X, seed, n_mcs, log_every=1, stop_at_extinction=False,
-                 mcs_begin=0, use_rs=False, prob=None):
+                 mcs_begin=0, use_rs=False, prob=None, neighbourhood=4, reflect=False):
     """Run with counts logged every log_every MCS; returns (lattice, log, mcs_end)."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8).copy()
     L = lat.shape[0]
@@ -271,8 +296,8 @@ def run_observed(lattice, D, I, P, X, seed, n_mcs, log_every=1, stop_at_extincti
     cap = n_mcs // log_every + 2
     log = np.zeros((cap, S + 1), dtype=np.uint64)
     nl, mend = C.c_int64(), C.c_uint32()
-    pr = _prob(prob, S)
-    _check(_load().orc_run_observed_p(int(use_rs), L, S, _ptr(D, C.c_uint8), _pp(pr), I, P, X, seed,
+    v, _keep = _variant(S, neighbourhood, reflect, prob)
+    _check(_load().orc_run_observed_v(int(use_rs), L, S, _ptr(D, C.c_uint8), C.byref(v), I, P, X, seed,
                                       mcs_begin, n_mcs, log_every, int(stop_at_extinction),
                                     _ptr(lat, C.c_uint8), _ptr(log, C.c_uint64), cap,
                                     C.byref(nl), C.byref(mend)), "run_observed")

@@ -163,18 +163,32 @@ int orc_counts(int64_t n, const uint8_t* lattice, int32_t S, uint64_t* counts)
     return 0;
 }
 
-/* Periodic neighbour of (row, col) on an L-column, H-row lattice in
- * direction dir (Section 3.1: up, down, left, right with mod wrap). */
-static int64_t neighbour_index(int32_t L, int32_t H, int32_t row, int32_t col, int32_t dir)
+/* Neighbour in one of the paper's neighbourhoods (Alg. 3: a direction from
+ * [0, neighbourhood), "von-Neumann or Moore"): 0 up, 1 down, 2 left, 3 right,
+ * then the diagonals 4 up-left, 5 up-right, 6 down-left, 7 down-right.  At
+ * the lattice edge the step wraps ("flux") or, with reflect, is mirrored:
+ * a coordinate that would leave the lattice moves the other way instead. */
+static const int8_t kDirRow[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
+static const int8_t kDirCol[8] = {0, 0, -1, 1, -1, 1, -1, 1};
+static int64_t neighbour_v(int32_t L, int32_t H, int32_t row, int32_t col, int32_t dir, int32_t reflect)
 {
-    int32_t nr = row, nc = col;
-    switch (dir) {
-    case 0: nr = (row - 1 + H) % H; break;
-    case 1: nr = (row + 1) % H; break;
-    case 2: nc = (col - 1 + L) % L; break;
-    default: nc = (col + 1) % L; break;
+    int32_t nr = row + kDirRow[dir], nc = col + kDirCol[dir];
+    if (reflect) {
+        if (nr < 0 || nr >= H) nr = row - kDirRow[dir];
+        if (nc < 0 || nc >= L) nc = col - kDirCol[dir];
+    } else {
+        nr = (nr + H) % H;
+        nc = (nc + L) % L;
     }
     return (int64_t)nr * L + nc;
+}
+
+static int check_variant(const orc_variant* v)
+{
+    if (!v) return 0;
+    if (v->neighbourhood != 4 && v->neighbourhood != 8) return -1;
+    if (v->reflect != 0 && v->reflect != 1) return -1;
+    return 0;
 }
 
 static int check_common(int32_t S, const uint8_t* D)
@@ -248,7 +262,19 @@ int orc_rs_attempts_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const d
                       double I, double P, double X, uint64_t seed, uint32_t stream,
                       uint32_t mcs, int64_t n_attempts, uint8_t* lattice)
 {
-    if (L < 3 || H < 3 || check_common(S, D) || check_prob(S, Pd) || !lattice || n_attempts < 0) return -1;
+    orc_variant v = {4, 0, Pd};
+    return orc_rs_attempts_v(L, H, S, D, &v, I, P, X, seed, stream, mcs, n_attempts, lattice);
+}
+
+int orc_rs_attempts_v(int32_t L, int32_t H, int32_t S, const uint8_t* D, const orc_variant* var,
+                      double I, double P, double X, uint64_t seed, uint32_t stream,
+                      uint32_t mcs, int64_t n_attempts, uint8_t* lattice)
+{
+    const double* Pd = var ? var->prob : NULL;
+    const int32_t nb = var ? var->neighbourhood : 4, reflect = var ? var->reflect : 0;
+    if (L < 3 || H < 3 || check_common(S, D) || check_prob(S, Pd) || check_variant(var) || !lattice ||
+        n_attempts < 0)
+        return -1;
     if (!(I >= 0.0) || !(P >= 0.0) || !(X >= 0.0)) return -1;
     double R = X + I + P;          /* mu + sigma + epsilon, normalised below */
     if (!(R > 0.0)) return -1;
@@ -257,10 +283,10 @@ int orc_rs_attempts_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const d
     rs_stream s = {seed, stream, mcs, 0, {0, 0, 0, 0}, 4};
     for (int64_t n = 0; n < n_attempts; ++n) {
         uint32_t i = rs_bounded(&s, (uint32_t)N);          /* random cell */
-        uint32_t dir = rs_bounded(&s, 4);                   /* von Neumann direction */
+        uint32_t dir = rs_bounded(&s, (uint32_t)nb);        /* von Neumann or Moore direction */
         double r = rs_unit(&s) * R;                         /* action draw in [0, R) */
         int32_t row = (int32_t)(i / (uint32_t)L), col = (int32_t)(i % (uint32_t)L);
-        int64_t ni = neighbour_index(L, H, row, col, (int32_t)dir);
+        int64_t ni = neighbour_v(L, H, row, col, (int32_t)dir, reflect);
         int32_t action;
         if (r < X)
             action = ORC_EXCHANGE;
@@ -287,9 +313,17 @@ int orc_rs_run_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const double
                  double I, double P, double X, uint64_t seed, uint32_t stream,
                  uint32_t mcs_begin, uint32_t n_mcs, uint8_t* lattice)
 {
+    orc_variant v = {4, 0, Pd};
+    return orc_rs_run_v(L, H, S, D, &v, I, P, X, seed, stream, mcs_begin, n_mcs, lattice);
+}
+
+int orc_rs_run_v(int32_t L, int32_t H, int32_t S, const uint8_t* D, const orc_variant* var,
+                 double I, double P, double X, uint64_t seed, uint32_t stream,
+                 uint32_t mcs_begin, uint32_t n_mcs, uint8_t* lattice)
+{
     int64_t N = (int64_t)L * H;
     for (uint32_t k = 0; k < n_mcs; ++k) {
-        int rc = orc_rs_attempts_p(L, H, S, D, Pd, I, P, X, seed, stream, mcs_begin + k, N, lattice);
+        int rc = orc_rs_attempts_v(L, H, S, D, var, I, P, X, seed, stream, mcs_begin + k, N, lattice);
         if (rc) return rc;
     }
     return 0;
@@ -415,7 +449,22 @@ int orc_replay_run_p(int32_t L, int32_t S, const uint8_t* D, const double* Pd,
                      uint8_t* lattice, uint32_t flags, uint64_t shuffle_seed,
                      orc_trace_rec* trace, int64_t trace_cap, int64_t* attempts_out)
 {
-    if (L < 8 || L > 65535 || check_common(S, D) || check_prob(S, Pd) || !lattice || G < 1 || F < 1)
+    orc_variant v = {4, 0, Pd};
+    return orc_replay_run_v(L, S, D, &v, I, P, X, seed, G, F, mcs_begin, n_mcs, lattice, flags,
+                            shuffle_seed, trace, trace_cap, attempts_out);
+}
+
+int orc_replay_run_v(int32_t L, int32_t S, const uint8_t* D, const orc_variant* var,
+                     double I, double P, double X, uint64_t seed,
+                     int32_t G, int32_t F, uint32_t mcs_begin, uint32_t n_mcs,
+                     uint8_t* lattice, uint32_t flags, uint64_t shuffle_seed,
+                     orc_trace_rec* trace, int64_t trace_cap, int64_t* attempts_out)
+{
+    const double* Pd = var ? var->prob : NULL;
+    const uint32_t nbh = var ? (uint32_t)var->neighbourhood : 4u;   /* directions */
+    const int32_t reflect = var ? var->reflect : 0;
+    if (L < 8 || L > 65535 || check_common(S, D) || check_prob(S, Pd) || check_variant(var) || !lattice ||
+        G < 1 || F < 1)
         return -1;
     if ((uint64_t)mcs_begin + n_mcs > 0xFFFFFFFFull) return -1;
     uint64_t TX, TXI;
@@ -478,13 +527,15 @@ int orc_replay_run_p(int32_t L, int32_t S, const uint8_t* D, const double* Pd,
                                     uint32_t w4[4];
                                     philox_at(seed, t >> 2, (uint32_t)g, m, TAG_STEP, w4);
                                     uint32_t w = w4[t & 3];
-                                    uint64_t prod = (uint64_t)w * (4u * nk);
+                                    /* p = w * (nb * n_g): the high word picks the cell and
+                                       the direction, the low word is the action draw */
+                                    uint64_t prod = (uint64_t)w * (nbh * nk);
                                     uint32_t hi = (uint32_t)(prod >> 32), u = (uint32_t)prod;
-                                    uint32_t site = hi >> 2, dir = hi & 3u;
+                                    uint32_t site = hi / nbh, dir = hi % nbh;
                                     int32_t row = y0 + (int32_t)(site / (uint32_t)wx);
                                     int32_t col = x0 + (int32_t)(site % (uint32_t)wx);
                                     int64_t i = (int64_t)row * L + col;
-                                    int64_t j = neighbour_index(L, L, row, col, (int32_t)dir);
+                                    int64_t j = neighbour_v(L, L, row, col, (int32_t)dir, reflect);
                                     int32_t action = ((uint64_t)u < TX)    ? ORC_EXCHANGE
                                                      : ((uint64_t)u < TXI) ? ORC_INTERACT
                                                                            : ORC_REPRODUCE;
@@ -540,6 +591,18 @@ int orc_run_observed_p(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, c
                        uint64_t* counts_log, int64_t log_cap, int64_t* n_logged,
                        uint32_t* mcs_end)
 {
+    orc_variant v = {4, 0, Pd};
+    return orc_run_observed_v(use_rs, L, S, D, &v, I, P, X, seed, mcs_begin, n_mcs, log_every,
+                              stop_at_extinction, lattice, counts_log, log_cap, n_logged, mcs_end);
+}
+
+int orc_run_observed_v(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, const orc_variant* var,
+                       double I, double P, double X, uint64_t seed,
+                       uint32_t mcs_begin, uint32_t n_mcs, uint32_t log_every,
+                       int32_t stop_at_extinction, uint8_t* lattice,
+                       uint64_t* counts_log, int64_t log_cap, int64_t* n_logged,
+                       uint32_t* mcs_end)
+{
     if (log_every == 0 || !lattice) return -1;
     int32_t G, F;
     if (orc_v1_cycles(L, &G, &F)) return -1;
@@ -555,8 +618,8 @@ int orc_run_observed_p(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, c
             if (stop_at_extinction && alive_species(c, S) <= 1) break;
         }
         if (m == mcs_begin + n_mcs) break;
-        rc = use_rs ? orc_rs_run_p(L, L, S, D, Pd, I, P, X, seed, 0, m, 1, lattice)
-                    : orc_replay_run_p(L, S, D, Pd, I, P, X, seed, G, F, m, 1, lattice, 0, 0, NULL, 0, NULL);
+        rc = use_rs ? orc_rs_run_v(L, L, S, D, var, I, P, X, seed, 0, m, 1, lattice)
+                    : orc_replay_run_v(L, S, D, var, I, P, X, seed, G, F, m, 1, lattice, 0, 0, NULL, 0, NULL);
         if (rc) break;
         ++m;
     }

@@ -72,6 +72,19 @@ int orc_thresholds(double I, double P, double X, uint64_t* TX, uint64_t* TXI);
 double orc_pair_prob(int32_t a, int32_t b, int32_t S, const uint8_t* D, const double* Pd);
 uint64_t orc_interaction_threshold(uint64_t TX, uint64_t TXI, double p);
 
+/* Rule variant (the paper's --neighbourhood and --flux options): a
+ * neighbourhood of 4 (von Neumann) or 8 (Moore) directions -- 0 up, 1 down,
+ * 2 left, 3 right, 4 up-left, 5 up-right, 6 down-left, 7 down-right -- and
+ * a periodic ("flux") or reflecting boundary (a step that would leave the
+ * lattice is mirrored back), with optional edge probabilities.  In the
+ * schedule an attempt's word w gives p = w * (neighbourhood * n_g): cell =
+ * floor(hi / neighbourhood), direction = hi mod neighbourhood. */
+typedef struct {
+    int32_t neighbourhood;   /* 4 or 8 */
+    int32_t reflect;         /* 0 periodic, 1 reflecting */
+    const double* prob;      /* S*S edge probabilities or NULL */
+} orc_variant;
+
 /* Histogram of lattice values 0..S (Alg. 4 densities(), as counts). */
 int orc_counts(int64_t n, const uint8_t* lattice, int32_t S, uint64_t* counts);
 
@@ -95,6 +108,13 @@ int orc_rs_attempts_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const d
                       double I, double P, double X, uint64_t seed, uint32_t stream,
                       uint32_t mcs, int64_t n_attempts, uint8_t* lattice);
 int orc_rs_run_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const double* Pd,
+                 double I, double P, double X, uint64_t seed, uint32_t stream,
+                 uint32_t mcs_begin, uint32_t n_mcs, uint8_t* lattice);
+/* The same for a rule variant (NULL: von Neumann, periodic, certain edges). */
+int orc_rs_attempts_v(int32_t L, int32_t H, int32_t S, const uint8_t* D, const orc_variant* var,
+                      double I, double P, double X, uint64_t seed, uint32_t stream,
+                      uint32_t mcs, int64_t n_attempts, uint8_t* lattice);
+int orc_rs_run_v(int32_t L, int32_t H, int32_t S, const uint8_t* D, const orc_variant* var,
                  double I, double P, double X, uint64_t seed, uint32_t stream,
                  uint32_t mcs_begin, uint32_t n_mcs, uint8_t* lattice);
 
@@ -133,7 +153,12 @@ int orc_replay_run(int32_t L, int32_t S, const uint8_t* D,
                    int32_t G, int32_t F, uint32_t mcs_begin, uint32_t n_mcs,
                    uint8_t* lattice, uint32_t flags, uint64_t shuffle_seed,
                    orc_trace_rec* trace, int64_t trace_cap, int64_t* attempts_out);
-/* The same with edge probabilities Pd (may be NULL). */
+/* The same with edge probabilities Pd (may be NULL), or a rule variant. */
+int orc_replay_run_v(int32_t L, int32_t S, const uint8_t* D, const orc_variant* var,
+                     double I, double P, double X, uint64_t seed,
+                     int32_t G, int32_t F, uint32_t mcs_begin, uint32_t n_mcs,
+                     uint8_t* lattice, uint32_t flags, uint64_t shuffle_seed,
+                     orc_trace_rec* trace, int64_t trace_cap, int64_t* attempts_out);
 int orc_replay_run_p(int32_t L, int32_t S, const uint8_t* D, const double* Pd,
                      double I, double P, double X, uint64_t seed,
                      int32_t G, int32_t F, uint32_t mcs_begin, uint32_t n_mcs,
@@ -152,6 +177,12 @@ int orc_run_observed(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D,
                      int32_t stop_at_extinction, uint8_t* lattice,
                      uint64_t* counts_log, int64_t log_cap, int64_t* n_logged,
                      uint32_t* mcs_end);
+int orc_run_observed_v(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, const orc_variant* var,
+                       double I, double P, double X, uint64_t seed,
+                       uint32_t mcs_begin, uint32_t n_mcs, uint32_t log_every,
+                       int32_t stop_at_extinction, uint8_t* lattice,
+                       uint64_t* counts_log, int64_t log_cap, int64_t* n_logged,
+                       uint32_t* mcs_end);
 int orc_run_observed_p(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, const double* Pd,
                        double I, double P, double X, uint64_t seed,
                        uint32_t mcs_begin, uint32_t n_mcs, uint32_t log_every,
