@@ -98,6 +98,17 @@ typedef struct {
                                     edge certain.  An interaction draw u in
                                     [T_X, T_XI) takes place iff u < T_X +
                                     round((T_XI - T_X) round(p 2^32) / 2^32)  */
+    int32_t neighbourhood;       /* 4 (von Neumann, default; 0 means 4) or 8
+                                    (Moore): Alg. 3 draws the direction from
+                                    [0, neighbourhood); the attempt's word w
+                                    gives p = w * (neighbourhood * n_g), cell
+                                    floor(hi / neighbourhood), direction hi mod
+                                    neighbourhood (0 up, 1 down, 2 left,
+                                    3 right, 4 up-left, 5 up-right, 6 down-
+                                    left, 7 down-right)                       */
+    int32_t reflecting_boundary; /* 1: a step that would leave the lattice is
+                                    mirrored back (the paper's "reflect");
+                                    0: periodic ("flux", default)             */
 } escg_options;
 
 typedef struct escg escg_t;

@@ -64,12 +64,14 @@ class Lattice:
     partitions use the boundary-mailbox kernel where it is faster), 3 the
     same with epoch flags only, 2 with a TMA producer warp, 0 one launch per
     coarse phase -- all bit-identical.  dominance_prob: optional S x S edge
-    probabilities (Park, Chen and Szolnoki's probabilistic dominance)."""
+    probabilities (Park, Chen and Szolnoki's probabilistic dominance);
+    neighbourhood 4 or 8 (Moore) and reflecting_boundary: the paper's rule
+    variants."""
 
     def __init__(self, L: int, S: int, digraph, rates, seed: int, p_empty: float = 0.0,
                  log_every: int = 10, stop_at_extinction: bool = False, persistent: int = 1,
                  stream=None, device_buffer=None, time_kernels: bool = False, ctas_per_sm: int = 0,
-                 dominance_prob=None):
+                 dominance_prob=None, neighbourhood: int = 4, reflecting_boundary: bool = False):
         lib = load()
         self.L, self.S = int(L), int(S)
         D = np.ascontiguousarray(np.asarray(digraph, dtype=np.uint8).reshape(S, S))
@@ -82,6 +84,8 @@ class Lattice:
         opt.persistent = int(persistent)
         opt.time_kernels = int(bool(time_kernels))
         opt.ctas_per_sm = int(ctas_per_sm)
+        opt.neighbourhood = int(neighbourhood)
+        opt.reflecting_boundary = int(bool(reflecting_boundary))
         if dominance_prob is not None:
             Pd = np.ascontiguousarray(np.asarray(dominance_prob, dtype=np.float64).reshape(S, S))
             opt.dominance_prob = Pd.ctypes.data_as(C.POINTER(C.c_double))   # read during creation

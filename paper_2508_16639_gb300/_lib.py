@@ -24,7 +24,8 @@ class Options(C.Structure):
                 ("stop_at_extinction", C.c_int32), ("schedule_version", C.c_uint32),
                 ("persistent", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("device_lattice", C.c_void_p), ("time_kernels", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("dominance_prob", C.POINTER(C.c_double))]
+                ("ctas_per_sm", C.c_int32), ("dominance_prob", C.POINTER(C.c_double)),
+                ("neighbourhood", C.c_int32), ("reflecting_boundary", C.c_int32)]
 
 
 class ReplicaSpec(C.Structure):

@@ -411,6 +411,11 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
         return nullptr;
       }
   }
+  if (o.neighbourhood == 0) o.neighbourhood = 4;
+  if ((o.neighbourhood != 4 && o.neighbourhood != 8) || (o.reflecting_boundary != 0 && o.reflecting_boundary != 1)) {
+    set_err("neighbourhood must be 4 or 8 and reflecting_boundary 0 or 1");
+    return nullptr;
+  }
   if (o.persistent < 0 || o.persistent > 3) {
     set_err("persistent must be 0..3 (got %d)", o.persistent);
     return nullptr;
@@ -526,7 +531,10 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   bool uni = true;
   for (int k = 0; k < p.P; ++k) uni = uni && (p.cs[k + 1] - p.cs[k] == 64);
   for (int k = 0; k < p.GQ; ++k) uni = uni && (p.fs[k + 1] - p.fs[k] == 2);
-  d.uniform64 = (uni && h->pitch % 16 == 0) ? 1 : 0;
+  d.nbh = o.neighbourhood;
+  d.reflect = o.reflecting_boundary;
+  // the uniform kernels implement the von Neumann, periodic rule only
+  d.uniform64 = (uni && h->pitch % 16 == 0 && d.nbh == 4 && !d.reflect) ? 1 : 0;
   h->grid = persistent_grid(h->device, d.uniform64 != 0);
   if (d.uniform64 && o.persistent == 2) {
     if (!make_tensor_map(&h->tmap, h->lattice, L, h->pitch)) {
@@ -585,9 +593,11 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
     return ESCG_EINVAL;
   }
   const uint32_t k = h->opt.log_every;
+  // rule variants count log points with the count kernel between launches
+  const bool fused = h->desc.nbh == 4 && !h->desc.reflect;
   while (h->mcs_enq < target) {
     uint64_t end;
-    if (h->opt.persistent && !h->opt.stop_at_extinction) {
+    if (h->opt.persistent && !h->opt.stop_at_extinction && fused) {
       // one launch may leave up to kPendRing log points open
       const uint64_t lim = (h->mcs_enq / k + kPendRing) * k;
       end = lim < target ? lim : target;
@@ -616,6 +626,7 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
       a.spin_limit = h->spin_limit;
       a.stall_block = h->stall_block;
       a.ob = h->d_ob;
+      a.fuse_counts = fused ? 1 : 0;
       CUDA_TRY(timing_begin(h));
       if (h->use_tma) {
         TmaArgs ta{};
@@ -633,8 +644,10 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
         CUDA_TRY(launch_ll_merge(h->desc, h->d_ob, h->d_state, (uint32_t)end, h->stream));
         h->launches++;
       }
-      h->mcs_enq = end;
-      continue;  // counts of log points and the MCS number are written in-kernel
+      if (fused) {
+        h->mcs_enq = end;
+        continue;  // counts of log points and the MCS number are written in-kernel
+      }
     } else {
       for (uint32_t m = m0; m < m0 + n; ++m)
         for (int slot = 0; slot < 4; ++slot) {

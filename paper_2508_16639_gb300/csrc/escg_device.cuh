@@ -118,6 +118,34 @@ __device__ __forceinline__ void attempt(uint8_t* __restrict__ tile, const uint8_
   apply_rule(tile, trans, ti, tj, u, tx, txi, s1);
 }
 
+// One elementary step of a generic sub-block under a rule variant (the
+// paper's --neighbourhood 4/8 and --flux options): p = w * (nbh * n_k), cell
+// = hi >> lg(nbh), direction = hi & (nbh - 1) (0 up, 1 down, 2 left,
+// 3 right, 4 up-left, 5 up-right, 6 down-left, 7 down-right); with reflect,
+// a step that would leave the lattice is mirrored.  (gy, gx): lattice
+// coordinates of the sub-block's first cell.
+__device__ __forceinline__ void attempt_variant(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
+                                                uint32_t w, uint32_t nn, int lg, int base, int wx,
+                                                uint32_t inv_wx, int sp, uint32_t tx, uint32_t txi,
+                                                uint32_t s1, bool reflect, int gy, int gx, int L) {
+  const uint32_t hi = __umulhi(w, nn);
+  const uint32_t u = w * nn;
+  const uint32_t site = hi >> lg, dir = hi & ((1u << lg) - 1u);
+  const uint32_t r = (site * inv_wx) >> 16;
+  const uint32_t c = site - r * (uint32_t)wx;
+  // row and column steps of the eight directions, two bits each
+  int dr = (int)((0xA058u >> (2 * dir)) & 3u) - 1;   // -1, 1, 0, 0, -1, -1, 1, 1
+  int dc = (int)((0x8885u >> (2 * dir)) & 3u) - 1;   //  0, 0, -1, 1, -1, 1, -1, 1
+  if (reflect) {
+    const int row = gy + (int)r, col = gx + (int)c;
+    if (row + dr < 0 || row + dr >= L) dr = -dr;
+    if (col + dc < 0 || col + dc >= L) dc = -dc;
+  }
+  const int ti = base + (int)r * sp + (int)c;
+  const int tj = ti + dr * sp + dc;
+  apply_rule(tile, trans, ti, tj, u, tx, txi, s1);
+}
+
 // Tile index of block-local (row r, col c), r, c in [-1, B].
 __device__ __forceinline__ int tidx(int r, int c, int sp) { return (r + 1) * sp + c + kColOff; }
 __device__ __forceinline__ int tile_pitch(int bw) { return ((kColOff + bw + 1) + 15) & ~15; }
@@ -153,12 +181,22 @@ __device__ __forceinline__ int tidx_u(int r, int c) { return (r + 1) * SP + c + 
 // Loads block interior + the four 1-site rim strips (no corners) into the
 // tile through L2 (ld.global.cg: data written by other CTAs of the same
 // launch must not be served from a stale L1 line).
+// Whether tile cell (r, c) of the block at (x0, y0) takes part in a visit:
+// the interior and the rim strips; the corners too in the Moore
+// neighbourhood; nothing beyond the lattice edge with a reflecting boundary.
+__device__ __forceinline__ bool tile_cell_used(const LatticeDesc& d, int x0, int y0, int bw, int bh, int r,
+                                               int c) {
+  if ((r < 0 || r >= bh) && (c < 0 || c >= bw) && d.nbh != 8) return false;
+  if (d.reflect && (y0 + r < 0 || y0 + r >= d.L || x0 + c < 0 || x0 + c >= d.L)) return false;
+  return true;
+}
+
 __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
                                                   uint8_t* tile, int sp) {
   const int L = d.L, pitch = d.pitch, W = bw + 2, H = bh + 2;
   for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
     const int r = k / W - 1, c = k % W - 1;
-    if ((r < 0 || r >= bh) && (c < 0 || c >= bw)) continue;   // corners
+    if (!tile_cell_used(d, x0, y0, bw, bh, r, c)) continue;
     tile[tidx(r, c, sp)] = __ldcg(d.lat + (size_t)wrap(y0 + r, L) * pitch + wrap(x0 + c, L));
   }
 }
@@ -170,7 +208,7 @@ __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0,
   const int L = d.L, pitch = d.pitch, W = bw + 2, H = bh + 2;
   for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
     const int r = k / W - 1, c = k % W - 1;
-    if ((r < 0 || r >= bh) && (c < 0 || c >= bw)) continue;
+    if (!tile_cell_used(d, x0, y0, bw, bh, r, c)) continue;
     d.lat[(size_t)wrap(y0 + r, L) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, sp)];
   }
 }
@@ -315,13 +353,20 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
       const uint32_t g = (uint32_t)(fy0 + fy) * (uint32_t)d.GQ + (uint32_t)(fx0 + fx);
       const uint32_t inv_wx = (65536u + (uint32_t)wx - 1u) / (uint32_t)wx;
       const int base = tidx(sy, sx, sp);
+      const bool variant = d.nbh == 8 || d.reflect;
+      const int lg = d.nbh == 8 ? 3 : 2;
       for (uint32_t j = 0; 4u * j < nk; ++j) {
         const uint4 x = philox10_rk(make_uint4(j, g, m, kTagStep), d.rk);
         const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          if (4u * j + (uint32_t)e < nk)
-            attempt(sm.tile, trans, wv[e], n4, base, wx, inv_wx, sp, d.tx, d.txi, s1);
+          if (4u * j + (uint32_t)e < nk) {
+            if (variant)
+              attempt_variant(sm.tile, trans, wv[e], nk << lg, lg, base, wx, inv_wx, sp, d.tx, d.txi, s1,
+                              d.reflect != 0, y0 + sy, x0 + sx, d.L);
+            else
+              attempt(sm.tile, trans, wv[e], n4, base, wx, inv_wx, sp, d.tx, d.txi, s1);
+          }
       }
     }
     __syncthreads();

@@ -76,6 +76,7 @@ struct PersistentArgs {
   uint32_t spin_limit;
   int32_t stall_block;   // test hook: never publish this block's epoch (-1: off)
   unsigned long long* ob;  // boundary records of the mailbox kernel ([P*P][4][32]), else null
+  int32_t fuse_counts;     // 1: counts of log points fused into the visits; 0: the host counts
 };
 // MCS [m_begin, m_begin + n_mcs) in one persistent dataflow launch, counts
 // of log points fused in.

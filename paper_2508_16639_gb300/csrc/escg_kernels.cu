@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
         visit_uniform<false>(d, bx, by, m, sm);
       else
         visit_generic<false>(d, bx, by, m, sm);
-      const bool log_point = ((m + 1u) % a.log_every) == 0u;
+      const bool log_point = a.fuse_counts && ((m + 1u) % a.log_every) == 0u;
       if (log_point) {
         const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1),
                   sD = slot_of(ord, colour ^ 3);

@@ -44,6 +44,8 @@ struct LatticeDesc {
                         // action draw u is always a multiple of 4)
   int32_t S;
   int32_t uniform64;    // all blocks 64x64 and all sub-blocks 2x2
+  int32_t nbh;          // neighbourhood: 4 (von Neumann) or 8 (Moore)
+  int32_t reflect;      // 1: reflecting boundary, 0: periodic
   uint8_t perm24[24];   // the 24 colour orders, lexicographic (4 x 2 bits)
 };
 
