@@ -19,8 +19,10 @@ exchange = 2 M N with M = 1e-4), counts logged every 10 MCS.  One step =
             instructions per launch / its event-timed launch duration
             against the GPU's integer-issue peak;
   cpu_baseline  the CPU replay oracle (single thread) on a bounded sample;
-  ensemble, serving, park  batched runs (A7), a request stream (A8) and the
-            probabilistic-dominance ensemble, each with its own metric.
+  ensemble, serving, park, variants  batched runs (A7), a request stream
+            (A8), the probabilistic-dominance ensemble and the benchmark
+            lattice under the Moore / reflecting rule variants, each with its
+            own metric.
 
 `--impl reference` times the CPU oracle itself (the reference arm of this
 tier) on the same metric and workload.  Multi-GPU (torchrun): replicas only,
@@ -94,6 +96,8 @@ def _parse():
     ap.add_argument("--ensemble-baseline-sample", type=int, default=16)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-park", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant-steps", type=int, default=100)
     ap.add_argument("--park-per-point", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=200.0,
@@ -273,6 +277,43 @@ def _park(args, rank):
     return out
 
 
+def _variants(args, rank, w):
+    """The benchmark lattice under the paper's rule variants (Moore
+    neighbourhood, reflecting boundary): device time per 10-MCS step, L2
+    flushed before each step, as the main measurement."""
+    import torch
+    import paper_2508_16639_gb300 as E
+    from paper_2508_16639_gb300 import replicas as R
+    N = w.L * w.L
+    X = E.exchange_from_mobility(w.mobility, N)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, nbh, refl in [("moore", 8, False), ("reflect", 4, True), ("moore_reflect", 8, True)]:
+        stream = torch.cuda.Stream()
+        g = E.Lattice(w.L, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X),
+                      R.replica_seed(w.seed, rank), p_empty=w.p_empty, log_every=w.log_every, stream=stream,
+                      neighbourhood=nbh, reflecting_boundary=refl)
+        for _ in range(3):
+            g.run(10)
+        g.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.variant_steps)]
+        for a, b in ev:
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            a.record(stream)
+            g.run(10)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        out[name] = {"site_updates_per_s": 10 * N / (ms * 1e-3), "ms_per_10_mcs": ms,
+                     "kernel": g.update_kernel}
+        g.close()
+    out["config"] = {"workload": f"{w.name} with the Moore neighbourhood and/or a reflecting boundary",
+                     "steps": args.variant_steps}
+    return out
+
+
 def _serving(args, rank):
     """Serving: Poisson arrivals of run requests (L log-uniform [50,1600],
     S in {3,5}, budgets log-uniform 10^2-10^4 MCS, half stop at extinction),
@@ -396,6 +437,9 @@ def main():
     park = None
     if not args.no_park:
         park = _park(args, rank)
+    variants = None
+    if not args.no_variants:
+        variants = _variants(args, rank, w)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -410,7 +454,7 @@ def main():
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": _config(w, mps), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks,
-                "ensemble": ensemble, "serving": serving, "park": park,
+                "ensemble": ensemble, "serving": serving, "park": park, "variants": variants,
                 "context": {"paper_cuda_ms_L3200_site_updates_per_s": 2.45e8,
                             "paper_hardware": "RTX A2000 (not a target)"}}
         print(json.dumps(line), flush=True)
