@@ -56,8 +56,10 @@ TRACE_DTYPE = np.dtype([("mcs", "<u4"), ("coarse_phase", "<u4"), ("fine_phase", 
 
 
 class Variant(C.Structure):
-    """orc_variant: neighbourhood 4/8, reflecting boundary, edge probabilities."""
-    _fields_ = [("neighbourhood", C.c_int32), ("reflect", C.c_int32), ("prob", C.POINTER(C.c_double))]
+    """orc_variant: neighbourhood 4/8, reflecting boundary, edge probabilities,
+    rows of an L x H lattice (0: square)."""
+    _fields_ = [("neighbourhood", C.c_int32), ("reflect", C.c_int32), ("prob", C.POINTER(C.c_double)),
+                ("height", C.c_int32)]
 
 
 def _load():
@@ -86,6 +88,7 @@ def _load():
                 "orc_v1_partition": (C.c_int, [C.c_int32, i32p, i32p, i32p, i32p, i32p]),
                 "orc_v1_cycles": (C.c_int, [C.c_int32, i32p, i32p]),
                 "orc_init": (C.c_int, [C.c_int32, C.c_int32, d, C.c_uint64, u8p]),
+                "orc_init_rect": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, d, C.c_uint64, u8p]),
                 "orc_replay_run": (C.c_int, [C.c_int32, C.c_int32, u8p, d, d, d, C.c_uint64,
                                              C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, u8p,
                                              C.c_uint32, C.c_uint64, P(TraceRec), C.c_int64, i64p]),
@@ -195,10 +198,10 @@ def _pp(a):
     return None if a is None else _ptr(a, C.c_double)
 
 
-def _variant(S, neighbourhood, reflect, prob):
+def _variant(S, neighbourhood, reflect, prob, height=0):
     """(Variant, keep-alive array) for the _v entry points."""
     pr = _prob(prob, S)
-    v = Variant(int(neighbourhood), int(bool(reflect)), _pp(pr))
+    v = Variant(int(neighbourhood), int(bool(reflect)), _pp(pr), int(height))
     return v, pr
 
 
@@ -256,18 +259,19 @@ def v1_cycles(L: int):
     return G.value, F.value
 
 
-def init(L: int, S: int, p_empty: float, seed: int) -> np.ndarray:
-    lat = np.zeros((L, L), dtype=np.uint8)
-    _check(_load().orc_init(L, S, p_empty, seed, _ptr(lat, C.c_uint8)), "init")
+def init(L: int, S: int, p_empty: float, seed: int, H: int = None) -> np.ndarray:
+    """Initial lattice of H rows (default L) and L columns, shape (H, L)."""
+    H = L if H is None else H
+    lat = np.zeros((H, L), dtype=np.uint8)
+    _check(_load().orc_init_rect(L, H, S, p_empty, seed, _ptr(lat, C.c_uint8)), "init")
     return lat
 
 
 def replay_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, G=None, F=None, flags=0,
                shuffle_seed=0, trace_cap=0, prob=None, neighbourhood=4, reflect=False):
-    """Schedule-v1 replay.  Returns (lattice, attempts[, trace])."""
+    """Schedule-v1 replay of an (H, L) lattice.  Returns (lattice, attempts[, trace])."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8).copy()
-    L = lat.shape[0]
-    assert lat.shape == (L, L)
+    H, L = lat.shape
     if G is None or F is None:
         G0, F0 = v1_cycles(L)
         G = G0 if G is None else G
@@ -275,7 +279,7 @@ def replay_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, G=None, F=None, fl
     D = np.ascontiguousarray(D, dtype=np.uint8)
     att = C.c_int64()
     tr = (TraceRec * trace_cap)() if trace_cap else None
-    v, _keep = _variant(D.shape[0], neighbourhood, reflect, prob)
+    v, _keep = _variant(D.shape[0], neighbourhood, reflect, prob, H)
     _check(_load().orc_replay_run_v(L, D.shape[0], _ptr(D, C.c_uint8), C.byref(v), I, P, X, seed, G, F,
                                     mcs_begin, n_mcs, _ptr(lat, C.c_uint8), flags, shuffle_seed,
                                     tr, trace_cap, C.byref(att)), "replay_run")
@@ -288,15 +292,16 @@ def replay_run(lattice, D, I, P, X, seed, n_mcs, mcs_begin=0, G=None, F=None, fl
 
 def run_observed(lattice, D, I, P, X, seed, n_mcs, log_every=1, stop_at_extinction=False,
                  mcs_begin=0, use_rs=False, prob=None, neighbourhood=4, reflect=False):
-    """Run with counts logged every log_every MCS; returns (lattice, log, mcs_end)."""
+    """Run an (H, L) lattice with counts logged every log_every MCS; returns
+    (lattice, log, mcs_end)."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8).copy()
-    L = lat.shape[0]
+    H, L = lat.shape
     S = D.shape[0]
     D = np.ascontiguousarray(D, dtype=np.uint8)
     cap = n_mcs // log_every + 2
     log = np.zeros((cap, S + 1), dtype=np.uint64)
     nl, mend = C.c_int64(), C.c_uint32()
-    v, _keep = _variant(S, neighbourhood, reflect, prob)
+    v, _keep = _variant(S, neighbourhood, reflect, prob, H)
     _check(_load().orc_run_observed_v(int(use_rs), L, S, _ptr(D, C.c_uint8), C.byref(v), I, P, X, seed,
                                       mcs_begin, n_mcs, log_every, int(stop_at_extinction),
                                     _ptr(lat, C.c_uint8), _ptr(log, C.c_uint64), cap,

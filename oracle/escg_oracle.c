@@ -188,6 +188,7 @@ static int check_variant(const orc_variant* v)
     if (!v) return 0;
     if (v->neighbourhood != 4 && v->neighbourhood != 8) return -1;
     if (v->reflect != 0 && v->reflect != 1) return -1;
+    if (v->height < 0) return -1;
     return 0;
 }
 
@@ -262,7 +263,7 @@ int orc_rs_attempts_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const d
                       double I, double P, double X, uint64_t seed, uint32_t stream,
                       uint32_t mcs, int64_t n_attempts, uint8_t* lattice)
 {
-    orc_variant v = {4, 0, Pd};
+    orc_variant v = {4, 0, Pd, 0};
     return orc_rs_attempts_v(L, H, S, D, &v, I, P, X, seed, stream, mcs, n_attempts, lattice);
 }
 
@@ -313,7 +314,7 @@ int orc_rs_run_p(int32_t L, int32_t H, int32_t S, const uint8_t* D, const double
                  double I, double P, double X, uint64_t seed, uint32_t stream,
                  uint32_t mcs_begin, uint32_t n_mcs, uint8_t* lattice)
 {
-    orc_variant v = {4, 0, Pd};
+    orc_variant v = {4, 0, Pd, 0};
     return orc_rs_run_v(L, H, S, D, &v, I, P, X, seed, stream, mcs_begin, n_mcs, lattice);
 }
 
@@ -404,9 +405,15 @@ static void colour_orders(uint8_t perms[24][4])
 
 int orc_init(int32_t L, int32_t S, double p_empty, uint64_t seed, uint8_t* lattice)
 {
-    if (L < 1 || S < 1 || S > 255 || !lattice || !(p_empty >= 0.0) || p_empty > 1.0) return -1;
+    return orc_init_rect(L, L, S, p_empty, seed, lattice);
+}
+
+int orc_init_rect(int32_t L, int32_t H, int32_t S, double p_empty, uint64_t seed, uint8_t* lattice)
+{
+    if (L < 1 || H < 1 || S < 1 || S > 255 || !lattice || !(p_empty >= 0.0) || p_empty > 1.0) return -1;
     uint64_t TE = (uint64_t)floor(ldexp(p_empty, 32) + 0.5);
-    int64_t N = (int64_t)L * L;
+    int64_t N = (int64_t)L * H;
+    if (N > 0xFFFFFFFFll) return -1;
     for (int64_t i = 0; i < N; ++i) {
         uint32_t x[4];
         philox_at(seed, (uint32_t)i, 0, 0, TAG_INIT, x);
@@ -449,7 +456,7 @@ int orc_replay_run_p(int32_t L, int32_t S, const uint8_t* D, const double* Pd,
                      uint8_t* lattice, uint32_t flags, uint64_t shuffle_seed,
                      orc_trace_rec* trace, int64_t trace_cap, int64_t* attempts_out)
 {
-    orc_variant v = {4, 0, Pd};
+    orc_variant v = {4, 0, Pd, 0};
     return orc_replay_run_v(L, S, D, &v, I, P, X, seed, G, F, mcs_begin, n_mcs, lattice, flags,
                             shuffle_seed, trace, trace_cap, attempts_out);
 }
@@ -463,8 +470,9 @@ int orc_replay_run_v(int32_t L, int32_t S, const uint8_t* D, const orc_variant* 
     const double* Pd = var ? var->prob : NULL;
     const uint32_t nbh = var ? (uint32_t)var->neighbourhood : 4u;   /* directions */
     const int32_t reflect = var ? var->reflect : 0;
-    if (L < 8 || L > 65535 || check_common(S, D) || check_prob(S, Pd) || check_variant(var) || !lattice ||
-        G < 1 || F < 1)
+    const int32_t H = (var && var->height) ? var->height : L;         /* rows */
+    if (L < 8 || L > 65535 || H < 8 || H > 65535 || check_common(S, D) || check_prob(S, Pd) ||
+        check_variant(var) || !lattice || G < 1 || F < 1)
         return -1;
     if ((uint64_t)mcs_begin + n_mcs > 0xFFFFFFFFull) return -1;
     uint64_t TX, TXI;
@@ -476,18 +484,24 @@ int orc_replay_run_v(int32_t L, int32_t S, const uint8_t* D, const orc_variant* 
         for (int32_t b = 0; b < s1; ++b)
             TP[a * s1 + b] = orc_interaction_threshold(TX, TXI, orc_pair_prob(a, b, S, D, Pd));
 
-    int32_t Pc, GQ;
+    /* each axis partitioned on its own: columns (L) and rows (H) */
+    int32_t Pc, GQ, Pr, GQr;
     orc_v1_partition(L, &Pc, &GQ, NULL, NULL, NULL);
+    orc_v1_partition(H, &Pr, &GQr, NULL, NULL, NULL);
     int32_t* cs = (int32_t*)malloc(sizeof(int32_t) * (Pc + 1));
     int32_t* fs = (int32_t*)malloc(sizeof(int32_t) * (GQ + 1));
     int32_t* fc = (int32_t*)malloc(sizeof(int32_t) * (Pc + 1));
     orc_v1_partition(L, NULL, NULL, cs, fs, fc);
+    int32_t* rcs = (int32_t*)malloc(sizeof(int32_t) * (Pr + 1));
+    int32_t* rfs = (int32_t*)malloc(sizeof(int32_t) * (GQr + 1));
+    int32_t* rfc = (int32_t*)malloc(sizeof(int32_t) * (Pr + 1));
+    orc_v1_partition(H, NULL, NULL, rcs, rfs, rfc);
 
     uint8_t perms[24][4];
     colour_orders(perms);
     const int32_t V = G * F;
-    int32_t* blocks = (int32_t*)malloc(sizeof(int32_t) * Pc * Pc);
-    int32_t* subs = (int32_t*)malloc(sizeof(int32_t) * GQ * GQ);
+    int32_t* blocks = (int32_t*)malloc(sizeof(int32_t) * Pc * Pr);
+    int32_t* subs = (int32_t*)malloc(sizeof(int32_t) * GQ * GQr);
     uint64_t shuf = shuffle_seed;
     int64_t attempts = 0, nrec = 0;
     uint32_t coarse_phase = 0, fine_phase = 0;
@@ -500,7 +514,7 @@ int orc_replay_run_v(int32_t L, int32_t S, const uint8_t* D, const orc_variant* 
             const uint8_t* order = perms[umulhi32(x[0], 24)];
             for (int ci = 0; ci < 4; ++ci, ++coarse_phase) {
                 int32_t colour = order[ci], nb = 0;
-                for (int32_t by = 0; by < Pc; ++by)
+                for (int32_t by = 0; by < Pr; ++by)
                     for (int32_t bx = 0; bx < Pc; ++bx)
                         if (2 * (by & 1) + (bx & 1) == colour) blocks[nb++] = by * Pc + bx;
                 if (flags & ORC_SHUFFLE_BLOCKS) shuffle_ints(blocks, nb, &shuf);
@@ -512,14 +526,14 @@ int orc_replay_run_v(int32_t L, int32_t S, const uint8_t* D, const orc_variant* 
                         const uint8_t* forder = perms[umulhi32(x[0], 24)];
                         for (int fi = 0; fi < 4; ++fi, ++fine_phase) {
                             int32_t fcol = forder[fi], ns = 0;
-                            for (int32_t gy = fc[by]; gy < fc[by + 1]; ++gy)
+                            for (int32_t gy = rfc[by]; gy < rfc[by + 1]; ++gy)
                                 for (int32_t gx = fc[bx]; gx < fc[bx + 1]; ++gx)
                                     if (2 * (gy & 1) + (gx & 1) == fcol) subs[ns++] = gy * GQ + gx;
                             if (flags & ORC_SHUFFLE_SUBS) shuffle_ints(subs, ns, &shuf);
                             for (int32_t si = 0; si < ns; ++si) {
                                 int32_t g = subs[si], gy = g / GQ, gx = g % GQ;
                                 int32_t x0 = fs[gx], wx = fs[gx + 1] - fs[gx];
-                                int32_t y0 = fs[gy], wy = fs[gy + 1] - fs[gy];
+                                int32_t y0 = rfs[gy], wy = rfs[gy + 1] - rfs[gy];
                                 uint32_t nk = (uint32_t)(wx * wy);
                                 uint32_t t0 = (uint32_t)(((uint64_t)v * nk) / V);
                                 uint32_t t1 = (uint32_t)(((uint64_t)(v + 1) * nk) / V);
@@ -535,7 +549,7 @@ int orc_replay_run_v(int32_t L, int32_t S, const uint8_t* D, const orc_variant* 
                                     int32_t row = y0 + (int32_t)(site / (uint32_t)wx);
                                     int32_t col = x0 + (int32_t)(site % (uint32_t)wx);
                                     int64_t i = (int64_t)row * L + col;
-                                    int64_t j = neighbour_v(L, L, row, col, (int32_t)dir, reflect);
+                                    int64_t j = neighbour_v(L, H, row, col, (int32_t)dir, reflect);
                                     int32_t action = ((uint64_t)u < TX)    ? ORC_EXCHANGE
                                                      : ((uint64_t)u < TXI) ? ORC_INTERACT
                                                                            : ORC_REPRODUCE;
@@ -560,7 +574,7 @@ int orc_replay_run_v(int32_t L, int32_t S, const uint8_t* D, const orc_variant* 
             }
         }
     }
-    free(cs); free(fs); free(fc); free(blocks); free(subs); free(TP);
+    free(cs); free(fs); free(fc); free(rcs); free(rfs); free(rfc); free(blocks); free(subs); free(TP);
     if (attempts_out) *attempts_out = attempts;
     return 0;
 }
@@ -591,7 +605,7 @@ int orc_run_observed_p(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, c
                        uint64_t* counts_log, int64_t log_cap, int64_t* n_logged,
                        uint32_t* mcs_end)
 {
-    orc_variant v = {4, 0, Pd};
+    orc_variant v = {4, 0, Pd, 0};
     return orc_run_observed_v(use_rs, L, S, D, &v, I, P, X, seed, mcs_begin, n_mcs, log_every,
                               stop_at_extinction, lattice, counts_log, log_cap, n_logged, mcs_end);
 }
@@ -606,7 +620,8 @@ int orc_run_observed_v(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, c
     if (log_every == 0 || !lattice) return -1;
     int32_t G, F;
     if (orc_v1_cycles(L, &G, &F)) return -1;
-    int64_t N = (int64_t)L * L, nl = 0;
+    const int32_t H = (var && var->height) ? var->height : L;
+    int64_t N = (int64_t)L * H, nl = 0;
     uint64_t* c = (uint64_t*)malloc(sizeof(uint64_t) * (S + 1));
     uint32_t m = mcs_begin;
     int rc = 0;
@@ -618,7 +633,7 @@ int orc_run_observed_v(int32_t use_rs, int32_t L, int32_t S, const uint8_t* D, c
             if (stop_at_extinction && alive_species(c, S) <= 1) break;
         }
         if (m == mcs_begin + n_mcs) break;
-        rc = use_rs ? orc_rs_run_v(L, L, S, D, var, I, P, X, seed, 0, m, 1, lattice)
+        rc = use_rs ? orc_rs_run_v(L, H, S, D, var, I, P, X, seed, 0, m, 1, lattice)
                     : orc_replay_run_v(L, S, D, var, I, P, X, seed, G, F, m, 1, lattice, 0, 0, NULL, 0, NULL);
         if (rc) break;
         ++m;

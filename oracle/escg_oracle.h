@@ -83,6 +83,11 @@ typedef struct {
     int32_t neighbourhood;   /* 4 or 8 */
     int32_t reflect;         /* 0 periodic, 1 reflecting */
     const double* prob;      /* S*S edge probabilities or NULL */
+    int32_t height;          /* rows H of an L x H lattice (the paper's --length
+                                and --height); 0: H = L.  The schedule
+                                partitions columns and rows independently
+                                (Pc x Pr blocks, block id by*Pc + bx, sub-block
+                                id gy*GQ + gx with GQ the column count). */
 } orc_variant;
 
 /* Histogram of lattice values 0..S (Alg. 4 densities(), as counts). */
@@ -130,6 +135,8 @@ int orc_v1_cycles(int32_t L, int32_t* G_out, int32_t* F_out);
 /* Initialisation (schedule v1): site i gets x = Philox(seed, (i, 0, 0, 1));
  * empty iff x0 < floor(2^32 p_empty + 1/2), else 1 + floor(x1 * S / 2^32). */
 int orc_init(int32_t L, int32_t S, double p_empty, uint64_t seed, uint8_t* lattice);
+/* The same for L columns and H rows (site i = row*L + col). */
+int orc_init_rect(int32_t L, int32_t H, int32_t S, double p_empty, uint64_t seed, uint8_t* lattice);
 
 /* Trace record of one attempt (for structural tests on small lattices). */
 typedef struct {
