@@ -81,7 +81,7 @@ typedef struct {
     void* cuda_stream;           /* cudaStream_t to enqueue on, or NULL for a
                                     stream owned by the handle                */
     void* device_lattice;        /* optional caller-owned device buffer of
-                                    escg_lattice_bytes(L) bytes (e.g. a torch
+                                    escg_lattice_bytes_rect(L, H) bytes (e.g. a torch
                                     tensor); NULL: the library allocates      */
     int32_t time_kernels;        /* 1: bracket every lattice-update launch with
                                     CUDA events on the handle's stream (read
@@ -109,6 +109,15 @@ typedef struct {
     int32_t reflecting_boundary; /* 1: a step that would leave the lattice is
                                     mirrored back (the paper's "reflect");
                                     0: periodic ("flux", default)             */
+    int32_t height;              /* rows H of an L x H lattice (the paper's
+                                    --length and --height; 8 <= H <= 16384;
+                                    0: H = L).  N = L*H; each axis is
+                                    partitioned on its own (P x Py coarse
+                                    blocks, block id by*P + bx; sub-block id
+                                    gy*GQ + gx, GQ fine segments along the
+                                    columns); site i = row*L + col.  The
+                                    lattice buffers of the calls below hold H
+                                    rows of L (host) or pitch (device) bytes. */
 } escg_options;
 
 typedef struct escg escg_t;
@@ -118,8 +127,10 @@ typedef struct escg escg_t;
 void escg_default_options(escg_options* opt);
 
 /* Bytes of device memory a lattice of side L occupies: L rows of pitch
- * escg_lattice_pitch(L) (L rounded up to 16) bytes. */
+ * escg_lattice_pitch(L) (L rounded up to 16) bytes; an L x H lattice: H
+ * rows of that pitch. */
 size_t escg_lattice_bytes(int32_t L);
+size_t escg_lattice_bytes_rect(int32_t L, int32_t H);
 int32_t escg_lattice_pitch(int32_t L);
 
 /* Creates a lattice of side L (8 <= L <= 16384) with S species
@@ -150,11 +161,11 @@ int escg_counts(escg_t* h, uint64_t* out, uint64_t* mcs_out);
  * the number of entries copied.  Synchronises. */
 int escg_counts_log(escg_t* h, uint64_t* out, uint64_t* mcs_out, int64_t cap, int64_t* n_out);
 
-/* Copies the lattice (L*L bytes, row-major, no padding) to host memory.
+/* Copies the lattice (L*H bytes, row-major, no padding) to host memory.
  * Synchronises. */
 int escg_snapshot(escg_t* h, uint8_t* host_out);
 
-/* Replaces the lattice with host_lattice (L*L bytes, values 0..S) at
+/* Replaces the lattice with host_lattice (L*H bytes, values 0..S) at
  * absolute MCS number mcs; running on from there is bit-exact with a run
  * that reached this state itself.  Clears the counts log. */
 int escg_restore(escg_t* h, const uint8_t* host_lattice, uint64_t mcs);

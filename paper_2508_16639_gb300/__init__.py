@@ -50,12 +50,14 @@ def lattice_pitch(L: int) -> int:
     return int(load().escg_lattice_pitch(L))
 
 
-def lattice_bytes(L: int) -> int:
-    return int(load().escg_lattice_bytes(L))
+def lattice_bytes(L: int, H: int = None) -> int:
+    """Device bytes of an L x H lattice (H rows of lattice_pitch(L) bytes)."""
+    return int(load().escg_lattice_bytes_rect(L, L if H is None else H))
 
 
 class Lattice:
-    """One L x L lattice resident on the GPU (a handle of the C ABI).
+    """One lattice of L columns and H rows (default H = L) resident on the
+    GPU (a handle of the C ABI); host-side arrays have shape (H, L).
 
     rates: (interact, reproduce, exchange).  device_buffer: optional torch
     uint8 CUDA tensor of at least lattice_bytes(L) bytes used as the lattice
@@ -71,9 +73,11 @@ class Lattice:
     def __init__(self, L: int, S: int, digraph, rates, seed: int, p_empty: float = 0.0,
                  log_every: int = 10, stop_at_extinction: bool = False, persistent: int = 1,
                  stream=None, device_buffer=None, time_kernels: bool = False, ctas_per_sm: int = 0,
-                 dominance_prob=None, neighbourhood: int = 4, reflecting_boundary: bool = False):
+                 dominance_prob=None, neighbourhood: int = 4, reflecting_boundary: bool = False,
+                 H: int = None):
         lib = load()
         self.L, self.S = int(L), int(S)
+        self.H = self.L if H is None else int(H)
         D = np.ascontiguousarray(np.asarray(digraph, dtype=np.uint8).reshape(S, S))
         r = Rates(*[float(x) for x in rates])
         opt = Options()
@@ -86,6 +90,7 @@ class Lattice:
         opt.ctas_per_sm = int(ctas_per_sm)
         opt.neighbourhood = int(neighbourhood)
         opt.reflecting_boundary = int(bool(reflecting_boundary))
+        opt.height = self.H
         if dominance_prob is not None:
             Pd = np.ascontiguousarray(np.asarray(dominance_prob, dtype=np.float64).reshape(S, S))
             opt.dominance_prob = Pd.ctypes.data_as(C.POINTER(C.c_double))   # read during creation
@@ -93,8 +98,8 @@ class Lattice:
             opt.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         self._buffer = device_buffer  # keep the torch tensor alive
         if device_buffer is not None:
-            if device_buffer.numel() * device_buffer.element_size() < lattice_bytes(L):
-                raise ValueError("device_buffer is smaller than lattice_bytes(L)")
+            if device_buffer.numel() * device_buffer.element_size() < lattice_bytes(L, self.H):
+                raise ValueError("device_buffer is smaller than lattice_bytes(L, H)")
             opt.device_lattice = int(device_buffer.data_ptr())
         h = lib.escg_create_ex(self.L, self.S, _u8(D), C.byref(r), C.c_uint64(seed & (2**64 - 1)),
                                C.byref(opt))
@@ -144,13 +149,13 @@ class Lattice:
         return ms[:n.value].astype(np.int64), out[:n.value]
 
     def snapshot(self) -> np.ndarray:
-        out = np.empty((self.L, self.L), dtype=np.uint8)
+        out = np.empty((self.H, self.L), dtype=np.uint8)
         check(load().escg_snapshot(self._h, _u8(out)))
         return out
 
     def restore(self, lattice: np.ndarray, mcs: int):
         lat = np.ascontiguousarray(lattice, dtype=np.uint8)
-        if lat.shape != (self.L, self.L):
+        if lat.shape != (self.H, self.L):
             raise ValueError("lattice shape mismatch")
         check(load().escg_restore(self._h, _u8(lat), int(mcs)))
 
@@ -158,7 +163,11 @@ class Lattice:
         """End-to-end host call: lattice in, n_mcs on the GPU, lattice and
         counts out (host buffers, copies included)."""
         lat = np.ascontiguousarray(lattice_in, dtype=np.uint8)
+        if lat.shape != (self.H, self.L):
+            raise ValueError("lattice shape mismatch")
         out = np.empty_like(lat) if out is None else out
+        if out.shape != lat.shape or out.dtype != np.uint8 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous uint8 array of the lattice's shape")
         counts = np.zeros(self.S + 1, dtype=np.uint64)
         check(load().escg_step_host(self._h, _u8(lat), int(mcs), int(n_mcs), _u8(out),
                                     counts.ctypes.data_as(C.POINTER(C.c_uint64))))
@@ -202,11 +211,11 @@ class Lattice:
         return int(load().escg_stream(self._h) or 0)
 
     def as_tensor(self):
-        """torch view of the device lattice (L x pitch uint8), when the
+        """torch view of the device lattice (H x pitch uint8), when the
         lattice lives in a torch-allocated buffer."""
         if self._buffer is None:
             raise RuntimeError("lattice storage is library-owned; pass device_buffer= to get a view")
-        return self._buffer.view(-1)[: self.L * self.pitch].view(self.L, self.pitch)
+        return self._buffer.view(-1)[: self.H * self.pitch].view(self.H, self.pitch)
 
 
 def _replica_spec(sp, keep):

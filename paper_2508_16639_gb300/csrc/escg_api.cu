@@ -200,20 +200,20 @@ void build_transitions(int S, const uint8_t* D, const double* prob, uint64_t tx,
 
 struct escg {
   int device = 0;
-  int L = 0, S = 0, pitch = 0;
+  int L = 0, H = 0, S = 0, pitch = 0;   // columns, rows, species, row stride
   uint64_t seed = 0;
   escg_options opt{};
-  Partition part;
+  Partition part, part_y;               // column and row partitions
   LatticeDesc desc{};
   cudaStream_t stream = nullptr;
   bool own_stream = false, own_lattice = false;
   uint8_t* lattice = nullptr;
-  int32_t* d_tables = nullptr;   // cs | fs | fc
+  int32_t* d_tables = nullptr;   // cs | fs | fc, then the row axis's (if H != L)
   uint8_t* d_trans = nullptr;
   RunState* d_state = nullptr;
   unsigned long long* d_log = nullptr;
   uint32_t* d_log_mcs = nullptr;
-  uint32_t* d_done = nullptr;    // P*P absolute epochs of the persistent kernel
+  uint32_t* d_done = nullptr;    // P*Py absolute epochs of the persistent kernel
   unsigned long long* d_ob = nullptr;  // boundary records of the mailbox kernel
   bool use_ll = false;           // uniform geometry, plain persistent path
   uint64_t mcs_enq = 0;          // MCS number after all enqueued work
@@ -236,17 +236,17 @@ namespace {
 
 LogBuffers log_buffers(escg* h) { return LogBuffers{h->d_log, h->d_log_mcs}; }
 
-// Host <-> device copy of the L x L lattice (host rows packed, device rows of
+// Host <-> device copy of the H x L lattice (host rows packed, device rows of
 // the handle's pitch); one linear copy when the two layouts coincide.
 cudaError_t copy_to_device(escg* h, const uint8_t* host) {
   if (h->pitch == h->L)
-    return cudaMemcpyAsync(h->lattice, host, (size_t)h->L * h->L, cudaMemcpyHostToDevice, h->stream);
-  return cudaMemcpy2DAsync(h->lattice, h->pitch, host, h->L, h->L, h->L, cudaMemcpyHostToDevice, h->stream);
+    return cudaMemcpyAsync(h->lattice, host, (size_t)h->L * h->H, cudaMemcpyHostToDevice, h->stream);
+  return cudaMemcpy2DAsync(h->lattice, h->pitch, host, h->L, h->L, h->H, cudaMemcpyHostToDevice, h->stream);
 }
 cudaError_t copy_to_host(escg* h, uint8_t* host) {
   if (h->pitch == h->L)
-    return cudaMemcpyAsync(host, h->lattice, (size_t)h->L * h->L, cudaMemcpyDeviceToHost, h->stream);
-  return cudaMemcpy2DAsync(host, h->L, h->lattice, h->pitch, h->L, h->L, cudaMemcpyDeviceToHost, h->stream);
+    return cudaMemcpyAsync(host, h->lattice, (size_t)h->L * h->H, cudaMemcpyDeviceToHost, h->stream);
+  return cudaMemcpy2DAsync(host, h->L, h->lattice, h->pitch, h->L, h->H, cudaMemcpyDeviceToHost, h->stream);
 }
 
 int enqueue_log(escg* h, uint32_t m_end, bool log) {
@@ -288,7 +288,7 @@ int reset_state(escg* h, uint64_t mcs) {
   const uint32_t num0 = (uint32_t)((mcs + le - 1) / le);
   CUDA_TRY(launch_state_reset(h->d_state, (uint32_t)mcs, num0, h->stream));
   h->launches++;
-  CUDA_TRY(launch_fill_u32(h->d_done, h->part.P * h->part.P, (uint32_t)mcs, h->stream));
+  CUDA_TRY(launch_fill_u32(h->d_done, h->part.P * h->part_y.P, (uint32_t)mcs, h->stream));
   h->launches++;
   h->log_num0_host = num0;
   h->mcs_enq = mcs;
@@ -371,6 +371,10 @@ int32_t escg_lattice_pitch(int32_t L) { return L <= 0 ? 0 : ((L + 15) / 16) * 16
 
 size_t escg_lattice_bytes(int32_t L) { return L <= 0 ? 0 : (size_t)L * escg_lattice_pitch(L); }
 
+size_t escg_lattice_bytes_rect(int32_t L, int32_t H) {
+  return (L <= 0 || H <= 0) ? 0 : (size_t)H * escg_lattice_pitch(L);
+}
+
 const char* escg_last_error(void) { return g_err; }
 
 double escg_exchange_from_mobility(double M, int64_t N) { return 2.0 * M * (double)N; }
@@ -416,6 +420,11 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     set_err("neighbourhood must be 4 or 8 and reflecting_boundary 0 or 1");
     return nullptr;
   }
+  if (o.height == 0) o.height = L;
+  if (o.height < 8 || o.height > 16384) {
+    set_err("height=%d out of range [8, 16384]", o.height);
+    return nullptr;
+  }
   if (o.persistent < 0 || o.persistent > 3) {
     set_err("persistent must be 0..3 (got %d)", o.persistent);
     return nullptr;
@@ -433,14 +442,17 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     set_err("host allocation failed");
     return nullptr;
   }
+  const int H = o.height;
   h->L = L;
+  h->H = H;
   h->S = S;
   h->seed = seed;
   h->opt = o;
   h->pitch = escg_lattice_pitch(L);
   h->part = make_partition(L);
-  if (!partition_fits(h->part)) {
-    set_err("internal: partition of L=%d exceeds the kernel's block limits", L);
+  h->part_y = make_partition(H);
+  if (!partition_fits(h->part) || !partition_fits(h->part_y)) {
+    set_err("internal: partition of %d x %d exceeds the kernel's block limits", L, H);
     delete h;
     return nullptr;
   }
@@ -468,7 +480,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     h->own_stream = true;
   }
-  const size_t nbytes = escg_lattice_bytes(L);
+  const size_t nbytes = escg_lattice_bytes_rect(L, H);
   if (e == cudaSuccess) {
     if (o.device_lattice) {
       h->lattice = (uint8_t*)o.device_lattice;
@@ -478,13 +490,15 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     }
   }
   const Partition& p = h->part;
-  const size_t ntab = p.cs.size() + p.fs.size() + p.fc.size();
+  const Partition& py = h->part_y;
+  const size_t ntab_x = p.cs.size() + p.fs.size() + p.fc.size();
+  const size_t ntab = ntab_x + (H != L ? py.cs.size() + py.fs.size() + py.fc.size() : 0);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_tables, ntab * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_trans, sizeof(uint32_t) * kTransWords);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_state, sizeof(RunState));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_log, sizeof(unsigned long long) * kLogCap * kMaxStates);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_log_mcs, sizeof(uint32_t) * kLogCap);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_done, sizeof(uint32_t) * p.P * p.P);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_done, sizeof(uint32_t) * p.P * py.P);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, sizeof(RunState));
   if (e != cudaSuccess) {
     set_err("device allocation failed: %s", cudaGetErrorString(e));
@@ -494,6 +508,11 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   tab.insert(tab.end(), p.cs.begin(), p.cs.end());
   tab.insert(tab.end(), p.fs.begin(), p.fs.end());
   tab.insert(tab.end(), p.fc.begin(), p.fc.end());
+  if (H != L) {
+    tab.insert(tab.end(), py.cs.begin(), py.cs.end());
+    tab.insert(tab.end(), py.fs.begin(), py.fs.end());
+    tab.insert(tab.end(), py.fc.begin(), py.fc.end());
+  }
   uint64_t tx = 0, txi = 0;
   thresholds(rates, &tx, &txi);
   std::vector<uint32_t> trans(kTransWords);
@@ -515,6 +534,11 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   d.cs = h->d_tables;
   d.fs = h->d_tables + p.cs.size();
   d.fc = h->d_tables + p.cs.size() + p.fs.size();
+  d.H = H;
+  d.Py = py.P;
+  d.csy = H != L ? h->d_tables + ntab_x : d.cs;
+  d.fsy = H != L ? d.csy + py.cs.size() : d.fs;
+  d.fcy = H != L ? d.fsy + py.fs.size() : d.fc;
   d.trans = h->d_trans;
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);
@@ -531,12 +555,17 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   bool uni = true;
   for (int k = 0; k < p.P; ++k) uni = uni && (p.cs[k + 1] - p.cs[k] == 64);
   for (int k = 0; k < p.GQ; ++k) uni = uni && (p.fs[k + 1] - p.fs[k] == 2);
+  for (int k = 0; k < py.P; ++k) uni = uni && (py.cs[k + 1] - py.cs[k] == 64);
+  for (int k = 0; k < py.GQ; ++k) uni = uni && (py.fs[k + 1] - py.fs[k] == 2);
   d.nbh = o.neighbourhood;
   d.reflect = o.reflecting_boundary;
   // the uniform kernels implement the von Neumann, periodic rule only
   d.uniform64 = (uni && h->pitch % 16 == 0 && d.nbh == 4 && !d.reflect) ? 1 : 0;
   h->grid = persistent_grid(h->device, d.uniform64 != 0);
-  if (d.uniform64 && o.persistent == 2) {
+  // the TMA and mailbox kernels are written for square lattices; the flag
+  // kernel takes rectangular ones in both geometries
+  const bool square = (H == L);
+  if (d.uniform64 && square && o.persistent == 2) {
     if (!make_tensor_map(&h->tmap, h->lattice, L, h->pitch)) {
       set_err("cuTensorMapEncodeTiled failed for L=%d", L);
       return fail(ESCG_ECUDA);
@@ -550,7 +579,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   // are CTAs (L <= 2048: 10-25 %), slower with 576 or 625 blocks per phase
   // (L = 3072, 3200: 3-5 %), where the flag kernel keeps items unbound
   // until a CTA is free.
-  if (d.uniform64 && o.persistent == 1 && 2 * (p.P * p.P / 4) <= persistent_ll_grid(h->device)) {
+  if (d.uniform64 && square && o.persistent == 1 && 2 * (p.P * p.P / 4) <= persistent_ll_grid(h->device)) {
     const size_t words = (size_t)p.P * p.P * kRecordWords;
     if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
       set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
@@ -607,7 +636,7 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
       end = next_log < target ? next_log : target;
     }
     // the persistent kernel numbers work items with 32-bit tickets
-    const uint64_t per_mcs = (uint64_t)h->part.P * h->part.P;
+    const uint64_t per_mcs = (uint64_t)h->part.P * h->part_y.P;
     const uint64_t max_chunk = ((1ull << 31) - (uint64_t)h->grid) / per_mcs;
     if (end - h->mcs_enq > max_chunk) end = h->mcs_enq + max_chunk;
     const uint32_t m0 = (uint32_t)h->mcs_enq, n = (uint32_t)(end - h->mcs_enq);
@@ -853,7 +882,7 @@ int escg_debug_stall_block(escg_t* h, int32_t block, uint32_t spin_limit) {
     set_err("NULL handle");
     return ESCG_EINVAL;
   }
-  if (block >= h->part.P * h->part.P) {
+  if (block >= h->part.P * h->part_y.P) {
     set_err("block %d out of range", block);
     return ESCG_EINVAL;
   }

@@ -933,6 +933,11 @@ int engine_add(Engine* e, const escg_replica_spec& sp, const SlotPlan& pl, int s
   d.cs = reinterpret_cast<int32_t*>(base + pl.tab);
   d.fs = d.cs + p.cs.size();
   d.fc = d.fs + p.fs.size();
+  d.H = sp.L;   // replicas are square
+  d.Py = p.P;
+  d.csy = d.cs;
+  d.fsy = d.fs;
+  d.fcy = d.fc;
   d.trans = base + pl.trans;
   d.key0 = (uint32_t)sp.seed;
   d.key1 = (uint32_t)(sp.seed >> 32);

@@ -127,7 +127,7 @@ __device__ __forceinline__ void attempt(uint8_t* __restrict__ tile, const uint8_
 __device__ __forceinline__ void attempt_variant(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
                                                 uint32_t w, uint32_t nn, int lg, int base, int wx,
                                                 uint32_t inv_wx, int sp, uint32_t tx, uint32_t txi,
-                                                uint32_t s1, bool reflect, int gy, int gx, int L) {
+                                                uint32_t s1, bool reflect, int gy, int gx, int H, int L) {
   const uint32_t hi = __umulhi(w, nn);
   const uint32_t u = w * nn;
   const uint32_t site = hi >> lg, dir = hi & ((1u << lg) - 1u);
@@ -138,7 +138,7 @@ __device__ __forceinline__ void attempt_variant(uint8_t* __restrict__ tile, cons
   int dc = (int)((0x8885u >> (2 * dir)) & 3u) - 1;   //  0, 0, -1, 1, -1, 1, -1, 1
   if (reflect) {
     const int row = gy + (int)r, col = gx + (int)c;
-    if (row + dr < 0 || row + dr >= L) dr = -dr;
+    if (row + dr < 0 || row + dr >= H) dr = -dr;
     if (col + dc < 0 || col + dc >= L) dc = -dc;
   }
   const int ti = base + (int)r * sp + (int)c;
@@ -187,17 +187,17 @@ __device__ __forceinline__ int tidx_u(int r, int c) { return (r + 1) * SP + c + 
 __device__ __forceinline__ bool tile_cell_used(const LatticeDesc& d, int x0, int y0, int bw, int bh, int r,
                                                int c) {
   if ((r < 0 || r >= bh) && (c < 0 || c >= bw) && d.nbh != 8) return false;
-  if (d.reflect && (y0 + r < 0 || y0 + r >= d.L || x0 + c < 0 || x0 + c >= d.L)) return false;
+  if (d.reflect && (y0 + r < 0 || y0 + r >= d.H || x0 + c < 0 || x0 + c >= d.L)) return false;
   return true;
 }
 
 __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
                                                   uint8_t* tile, int sp) {
-  const int L = d.L, pitch = d.pitch, W = bw + 2, H = bh + 2;
+  const int L = d.L, LH = d.H, pitch = d.pitch, W = bw + 2, H = bh + 2;
   for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
     const int r = k / W - 1, c = k % W - 1;
     if (!tile_cell_used(d, x0, y0, bw, bh, r, c)) continue;
-    tile[tidx(r, c, sp)] = __ldcg(d.lat + (size_t)wrap(y0 + r, L) * pitch + wrap(x0 + c, L));
+    tile[tidx(r, c, sp)] = __ldcg(d.lat + (size_t)wrap(y0 + r, LH) * pitch + wrap(x0 + c, L));
   }
 }
 
@@ -205,11 +205,11 @@ __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, 
 // corners, which belong to diagonal blocks that may be updated meanwhile).
 __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
                                                    const uint8_t* tile, int sp) {
-  const int L = d.L, pitch = d.pitch, W = bw + 2, H = bh + 2;
+  const int L = d.L, LH = d.H, pitch = d.pitch, W = bw + 2, H = bh + 2;
   for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
     const int r = k / W - 1, c = k % W - 1;
     if (!tile_cell_used(d, x0, y0, bw, bh, r, c)) continue;
-    d.lat[(size_t)wrap(y0 + r, L) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, sp)];
+    d.lat[(size_t)wrap(y0 + r, LH) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, sp)];
   }
 }
 
@@ -224,7 +224,7 @@ __device__ __forceinline__ void load_tile_uni(const LatticeDesc& d, int x0, int 
   }
   if (t < 8) {  // top / bottom rim rows
     const int r = (t < 4) ? -1 : kUniB, q = t & 3;
-    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, L) * pitch + x0) + q);
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0) + q);
     uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
     dst[0] = make_uint2(v.x, v.y);
     dst[1] = make_uint2(v.z, v.w);
@@ -246,7 +246,7 @@ __device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int
     const int r = (t < 4) ? -1 : kUniB, q = t & 3;
     const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
     const uint2 a = src[0], b = src[1];
-    reinterpret_cast<uint4*>(d.lat + (size_t)wrap(y0 + r, L) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
+    reinterpret_cast<uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
   } else if (t >= 128) {
     const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
     d.lat[(size_t)(y0 + r) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, kUniSP)];
@@ -327,13 +327,13 @@ template <bool OWN_FORDER = true>
 __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int by, uint32_t m,
                                               VisitSmem& sm) {
   const int x0 = d.cs[bx], bw = d.cs[bx + 1] - x0;
-  const int y0 = d.cs[by], bh = d.cs[by + 1] - y0;
+  const int y0 = d.csy[by], bh = d.csy[by + 1] - y0;
   const int fx0 = d.fc[bx], Qx = d.fc[bx + 1] - fx0;
-  const int fy0 = d.fc[by], Qy = d.fc[by + 1] - fy0;
+  const int fy0 = d.fcy[by], Qy = d.fcy[by + 1] - fy0;
   const int sp = tile_pitch(bw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int k = tid; k <= Qx; k += nthr) sm.fsx[k] = (int16_t)(d.fs[fx0 + k] - x0);
-  for (int k = tid; k <= Qy; k += nthr) sm.fsy[k] = (int16_t)(d.fs[fy0 + k] - y0);
+  for (int k = tid; k <= Qy; k += nthr) sm.fsy[k] = (int16_t)(d.fsy[fy0 + k] - y0);
   if (OWN_FORDER && tid == 0) sm.forder = fine_order(d, bx, by, m);
   load_tile_generic(d, x0, y0, bw, bh, sm.tile, sp);
   __syncthreads();
@@ -363,7 +363,7 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
           if (4u * j + (uint32_t)e < nk) {
             if (variant)
               attempt_variant(sm.tile, trans, wv[e], nk << lg, lg, base, wx, inv_wx, sp, d.tx, d.txi, s1,
-                              d.reflect != 0, y0 + sy, x0 + sx, d.L);
+                              d.reflect != 0, y0 + sy, x0 + sx, d.H, d.L);
             else
               attempt(sm.tile, trans, wv[e], n4, base, wx, inv_wx, sp, d.tx, d.txi, s1);
           }
@@ -404,7 +404,7 @@ __device__ __forceinline__ void count_vectors(const LatticeDesc& d, uint32_t sta
                                               uint32_t* part) {
   const int L = d.L, pitch = d.pitch, S = d.S;
   const uint32_t vec_per_row = (uint32_t)pitch / 16u;
-  const uint32_t total = (uint32_t)L * vec_per_row;   // < 2^32 for L <= 16384
+  const uint32_t total = (uint32_t)d.H * vec_per_row;   // < 2^32 for L, H <= 16384
   uint32_t c[kMaxStates];
 #pragma unroll
   for (int v = 0; v < kMaxStates; ++v) c[v] = 0;
@@ -498,7 +498,7 @@ __device__ __forceinline__ void count_visit_uni(const uint8_t* tile, uint32_t* h
 // Any geometry: one site per thread iteration, shared-memory atomics.
 __device__ __forceinline__ void count_visit_generic(const LatticeDesc& d, int bx, int by, VisitSmem& sm,
                                                     int k, int sV, int sH, int sD) {
-  const int bw = d.cs[bx + 1] - d.cs[bx], bh = d.cs[by + 1] - d.cs[by];
+  const int bw = d.cs[bx + 1] - d.cs[bx], bh = d.csy[by + 1] - d.csy[by];
   const int sp = tile_pitch(bw), W = bw + 2, H = bh + 2;
   for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
     const int r = e / W - 1, c = e % W - 1;

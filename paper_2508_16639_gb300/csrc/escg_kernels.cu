@@ -36,7 +36,7 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
 // ---------------------------------------------------------------------------
 __global__ void init_kernel(LatticeDesc d, uint64_t T_empty) {
   const int L = d.L, pitch = d.pitch;
-  const size_t total = (size_t)L * pitch;
+  const size_t total = (size_t)d.H * pitch;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
        k += (size_t)gridDim.x * blockDim.x) {
     const int row = (int)(k / pitch), col = (int)(k % pitch);
@@ -57,7 +57,7 @@ __global__ void init_kernel(LatticeDesc d, uint64_t T_empty) {
 __global__ void validate_kernel(LatticeDesc d, uint32_t* bad, uint32_t flag, uint32_t* stop) {
   const int L = d.L, pitch = d.pitch, vec_per_row = pitch / 16;
   const uint32_t lim = 0x7Fu - (uint32_t)d.S;  // byte + lim has bit 7 set iff byte > S (byte < 128)
-  const size_t total = (size_t)L * vec_per_row;
+  const size_t total = (size_t)d.H * vec_per_row;
   uint32_t any = 0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
        k += (size_t)gridDim.x * blockDim.x) {
@@ -179,8 +179,8 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
   const bool run = !ld_volatile(&st->stopped);
   if (run) {
     load_trans(d, sm.trans);
-    const int P = d.P, half = P >> 1;
-    const uint32_t nb = (uint32_t)(P * P), per = nb >> 2;
+    const int P = d.P, half = P >> 1, Py = d.Py;
+    const uint32_t nb = (uint32_t)(P * Py), per = nb >> 2;
     const uint64_t total = (uint64_t)a.n_mcs * nb;
     // Tickets are taken in schedule order from a shared dispenser, one at a
     // time, as the CTA releases the epoch of its previous visit (taking the
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
       if (tid == kTicketThread) sm.forder = fine_order(d, bx, by, m);
       if (tid < 9) {
         const int dx = tid % 3 - 1, dy = tid / 3 - 1;
-        const int nx = (bx + dx + P) % P, ny = (by + dy + P) % P;
+        const int nx = (bx + dx + P) % P, ny = (by + dy + Py) % Py;
         const int ncol = colour ^ ((dx & 1) | ((dy & 1) << 1));
         const uint32_t need = (tid == 4) ? m : (slot_of(ord, ncol) < k ? m + 1u : m);
         const uint32_t* flag = a.done + ny * P + nx;
@@ -1088,7 +1088,7 @@ static inline int blocks_for(size_t n, int threads, int cap) {
 }
 
 cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream) {
-  const size_t n = (size_t)d.L * d.pitch;
+  const size_t n = (size_t)d.H * d.pitch;
   init_kernel<<<blocks_for(n, 256, 152 * 32), 256, 0, stream>>>(d, T_empty);
   return cudaGetLastError();
 }
@@ -1100,7 +1100,7 @@ cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t str
 
 cudaError_t launch_validate(const LatticeDesc& d, uint32_t* bad, uint32_t flag, uint32_t* stop,
                             cudaStream_t stream) {
-  const size_t n = (size_t)d.L * (d.pitch / 16);
+  const size_t n = (size_t)d.H * (d.pitch / 16);
   validate_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, bad, flag, stop);
   return cudaGetLastError();
 }
@@ -1111,7 +1111,7 @@ cudaError_t launch_state_reset(RunState* st, uint32_t mcs, uint32_t log_num0, cu
 }
 
 cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream) {
-  const size_t n = (size_t)d.L * (d.pitch / 16);
+  const size_t n = (size_t)d.H * (d.pitch / 16);
   count_kernel<<<blocks_for(n, 256 * 4, 152 * 4), 256, 0, stream>>>(d, st);
   return cudaGetLastError();
 }
@@ -1123,7 +1123,7 @@ cudaError_t launch_finalize(const LatticeDesc& d, RunState* st, LogBuffers lb, u
 }
 
 cudaError_t launch_phase(const LatticeDesc& d, RunState* st, uint32_t m, int slot, cudaStream_t stream) {
-  const int nblocks = (d.P * d.P) / 4;
+  const int nblocks = (d.P * d.Py) / 4;
   phase_kernel<<<nblocks, 256, 0, stream>>>(d, st, m, slot);
   return cudaGetLastError();
 }

@@ -198,6 +198,11 @@ extern "C" int escg_run_noalloc(uint8_t* d_lattice, int32_t L, int32_t S, const 
   d.cs = reinterpret_cast<const int32_t*>(scratch + kNoallocTabOff);
   d.fs = d.cs + (P + 1);
   d.fc = d.fs + (GQ + 1);
+  d.H = L;   // square
+  d.Py = P;
+  d.csy = d.cs;
+  d.fsy = d.fs;
+  d.fcy = d.fc;
   d.trans = scratch + kNoallocTransOff;
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);

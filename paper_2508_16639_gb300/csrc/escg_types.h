@@ -25,12 +25,18 @@ constexpr int kTransWords = 2 * kTransPairs;
 
 // Everything a kernel needs to know about one lattice.
 struct LatticeDesc {
-  uint8_t* lat;         // L rows of `pitch` bytes, values 0..S
-  int32_t L, pitch;
-  int32_t P, GQ;        // coarse segments per axis, fine segments per axis
-  const int32_t* cs;    // [P+1] coarse segment starts
-  const int32_t* fs;    // [GQ+1] fine segment starts (global coordinates)
+  uint8_t* lat;         // H rows of `pitch` bytes, values 0..S
+  int32_t L, pitch;     // columns, row stride in bytes
+  int32_t H;            // rows (L for a square lattice)
+  int32_t P, GQ;        // coarse and fine segments along the columns
+  const int32_t* cs;    // [P+1] coarse segment starts (columns)
+  const int32_t* fs;    // [GQ+1] fine segment starts (global column coordinates)
   const int32_t* fc;    // [P+1] first global fine index of each coarse segment
+  int32_t Py;           // coarse segments along the rows; block id = by * P + bx,
+                        // sub-block id = gy * GQ + gx
+  const int32_t* csy;   // the row axis's tables, as cs, fs, fc (the same
+  const int32_t* fsy;   // arrays when H = L)
+  const int32_t* fcy;
   const uint8_t* trans; // kTransWords words: byte (a*(S+1)+b)*4 + action of
                         // the first half holds the new pair (a' | b' << 4),
                         // actions 0 exchange, 1 interaction, 2 reproduction,
