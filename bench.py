@@ -21,8 +21,9 @@ exchange = 2 M N with M = 1e-4), counts logged every 10 MCS.  One step =
   cpu_baseline  the CPU replay oracle (single thread) on a bounded sample;
   ensemble, serving, park, variants  batched runs (A7), a request stream
             (A8), the probabilistic-dominance ensemble and the benchmark
-            lattice under the Moore / reflecting rule variants, each with its
-            own metric.
+            lattice under the Moore / reflecting rule variants, as
+            rectangles of the same N, and the RPSLS L = 800 workload, each
+            with its own metric.
 
 `--impl reference` times the CPU oracle itself (the reference arm of this
 tier) on the same metric and workload.  Multi-GPU (torchrun): replicas only,
@@ -279,20 +280,29 @@ def _park(args, rank):
 
 def _variants(args, rank, w):
     """The benchmark lattice under the paper's rule variants (Moore
-    neighbourhood, reflecting boundary): device time per 10-MCS step, L2
-    flushed before each step, as the main measurement."""
+    neighbourhood, reflecting boundary), as rectangles of the same N
+    (2L x L/2 and L/2 x 2L), and the RPSLS L = 800 workload (generic
+    partition: 12 blocks of 66-67 sites per axis): device time per 10-MCS
+    step, L2 flushed before each step, as the main measurement."""
     import torch
     import paper_2508_16639_gb300 as E
     from paper_2508_16639_gb300 import replicas as R
-    N = w.L * w.L
-    X = E.exchange_from_mobility(w.mobility, N)
+    from paper_2508_16639_gb300 import workloads as W
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     out = {}
-    for name, nbh, refl in [("moore", 8, False), ("reflect", 4, True), ("moore_reflect", 8, True)]:
+    c2 = W.CFG2
+    cases = [("moore", w, w.L, w.L, 8, False), ("reflect", w, w.L, w.L, 4, True),
+             ("moore_reflect", w, w.L, w.L, 8, True),
+             (f"rect_{2 * w.L}x{w.L // 2}", w, 2 * w.L, w.L // 2, 4, False),
+             (f"rect_{w.L // 2}x{2 * w.L}", w, w.L // 2, 2 * w.L, 4, False),
+             (c2.name, c2, c2.L, c2.L, 4, False)]
+    for name, wl, Lc, Hr, nbh, refl in cases:
+        N = Lc * Hr
+        X = E.exchange_from_mobility(wl.mobility, N)
         stream = torch.cuda.Stream()
-        g = E.Lattice(w.L, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X),
-                      R.replica_seed(w.seed, rank), p_empty=w.p_empty, log_every=w.log_every, stream=stream,
-                      neighbourhood=nbh, reflecting_boundary=refl)
+        g = E.Lattice(Lc, wl.S, E.circulant(wl.S, wl.K), (wl.interact, wl.reproduce, X),
+                      R.replica_seed(wl.seed, rank), p_empty=wl.p_empty, log_every=wl.log_every, stream=stream,
+                      neighbourhood=nbh, reflecting_boundary=refl, H=Hr)
         for _ in range(3):
             g.run(10)
         g.sync()
@@ -309,7 +319,9 @@ def _variants(args, rank, w):
         out[name] = {"site_updates_per_s": 10 * N / (ms * 1e-3), "ms_per_10_mcs": ms,
                      "kernel": g.update_kernel}
         g.close()
-    out["config"] = {"workload": f"{w.name} with the Moore neighbourhood and/or a reflecting boundary",
+    out["config"] = {"workload": f"{w.name} with the Moore neighbourhood and/or a reflecting boundary; "
+                                 "rect_<columns>x<rows>: the same N = L*L as a rectangle; "
+                                 f"{c2.name}: S=5 C(5,{{1,2}}), p_empty {c2.p_empty}, M {c2.mobility:g}",
                      "steps": args.variant_steps}
     return out
 

@@ -82,7 +82,8 @@ typedef struct {
                                     stream owned by the handle                */
     void* device_lattice;        /* optional caller-owned device buffer of
                                     escg_lattice_bytes_rect(L, H) bytes (e.g. a torch
-                                    tensor); NULL: the library allocates      */
+                                    tensor), 16-byte aligned (ESCG_EINVAL
+                                    otherwise); NULL: the library allocates   */
     int32_t time_kernels;        /* 1: bracket every lattice-update launch with
                                     CUDA events on the handle's stream (read
                                     back with escg_kernel_time)               */

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -423,6 +424,10 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   if (o.height == 0) o.height = L;
   if (o.height < 8 || o.height > 16384) {
     set_err("height=%d out of range [8, 16384]", o.height);
+    return nullptr;
+  }
+  if (reinterpret_cast<uintptr_t>(o.device_lattice) % 16 != 0) {
+    set_err("device_lattice must be 16-byte aligned (rows are read as 16-byte vectors)");
     return nullptr;
   }
   if (o.persistent < 0 || o.persistent > 3) {

@@ -178,38 +178,107 @@ __device__ __forceinline__ void attempt_uni(uint8_t* __restrict__ tile, const ui
 template <int SP, int COFF>
 __device__ __forceinline__ int tidx_u(int r, int c) { return (r + 1) * SP + c + COFF; }
 
-// Loads block interior + the four 1-site rim strips (no corners) into the
-// tile through L2 (ld.global.cg: data written by other CTAs of the same
-// launch must not be served from a stale L1 line).
-// Whether tile cell (r, c) of the block at (x0, y0) takes part in a visit:
-// the interior and the rim strips; the corners too in the Moore
-// neighbourhood; nothing beyond the lattice edge with a reflecting boundary.
-__device__ __forceinline__ bool tile_cell_used(const LatticeDesc& d, int x0, int y0, int bw, int bh, int r,
-                                               int c) {
-  if ((r < 0 || r >= bh) && (c < 0 || c >= bw) && d.nbh != 8) return false;
-  if (d.reflect && (y0 + r < 0 || y0 + r >= d.H || x0 + c < 0 || x0 + c >= d.L)) return false;
-  return true;
+// Generic staging of a block's tile.  A visit uses the block interior and
+// the four 1-site rim strips, the corners too in the Moore neighbourhood, and
+// nothing beyond the lattice edge with a reflecting boundary.  Tile row r
+// (r in [-1, bh]) is loaded by warp (r + 1) mod (warps): the columns that do
+// not wrap around the lattice edge as aligned 4-byte words (lane k loads
+// word k; rows are 16-byte aligned and at most 26 words wide), the one
+// column that wraps (a block at the left or right edge of a periodic
+// lattice) as a byte by lane 31 or 30.  Each warp issues the loads of up
+// to 8 rows before it writes any of them to shared memory, so a tile costs
+// two L2 round trips instead of one per row.  Loads go through L2
+// (ld.global.cg: data written by other CTAs of the same launch must not be
+// served from a stale L1 line).
+struct GenericRow {
+  int gy;          // lattice row, or -1 when the row lies beyond a reflecting edge
+  int g_lo, g_hi;  // lattice columns loaded as words (no wrap), g_lo <= g_hi
+  int wa;          // first word's column (g_lo rounded down to 4)
+  bool wrap_l, wrap_r;  // tile column -1 from lattice column L-1 / bw from 0
+};
+
+__device__ __forceinline__ GenericRow generic_row(const LatticeDesc& d, int x0, int y0, int bw, int bh, int r) {
+  GenericRow g;
+  const int L = d.L, LH = d.H;
+  const bool reflect = d.reflect != 0;
+  int gy = y0 + r;
+  if (gy < 0 || gy >= LH) gy = reflect ? -1 : (gy < 0 ? gy + LH : gy - LH);
+  g.gy = gy;
+  const bool rim_r = (r < 0 || r >= bh);
+  const int c_lo = (rim_r && d.nbh != 8) ? 0 : -1, c_hi = (rim_r && d.nbh != 8) ? bw - 1 : bw;
+  g.g_lo = max(x0 + c_lo, 0);
+  g.g_hi = min(x0 + c_hi, L - 1);
+  g.wa = g.g_lo & ~3;
+  g.wrap_l = !reflect && x0 + c_lo < 0;
+  g.wrap_r = !reflect && x0 + c_hi >= L;
+  return g;
 }
 
 __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
                                                   uint8_t* tile, int sp) {
-  const int L = d.L, LH = d.H, pitch = d.pitch, W = bw + 2, H = bh + 2;
-  for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
-    const int r = k / W - 1, c = k % W - 1;
-    if (!tile_cell_used(d, x0, y0, bw, bh, r, c)) continue;
-    tile[tidx(r, c, sp)] = __ldcg(d.lat + (size_t)wrap(y0 + r, LH) * pitch + wrap(x0 + c, L));
+  constexpr int kRows = 8;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int L = d.L, pitch = d.pitch;
+  for (int r0 = (int)(threadIdx.x >> 5) - 1; r0 <= bh; r0 += kRows * nw) {
+    uint32_t v[kRows];
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+      const int r = r0 + i * nw;
+      v[i] = 0;
+      if (r > bh) continue;
+      const GenericRow g = generic_row(d, x0, y0, bw, bh, r);
+      if (g.gy < 0) continue;
+      const uint8_t* row = d.lat + (size_t)g.gy * pitch;
+      if (g.wa + 4 * lane <= g.g_hi)
+        v[i] = __ldcg(reinterpret_cast<const uint32_t*>(row + g.wa) + lane);
+      else if (lane == 31 && g.wrap_l)
+        v[i] = __ldcg(row + (L - 1));
+      else if (lane == 30 && g.wrap_r)
+        v[i] = __ldcg(row);
+    }
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+      const int r = r0 + i * nw;
+      if (r > bh) continue;
+      const GenericRow g = generic_row(d, x0, y0, bw, bh, r);
+      if (g.gy < 0) continue;
+      uint8_t* trow = tile + (r + 1) * sp + kColOff;
+      const int gc0 = g.wa + 4 * lane;
+      if (gc0 <= g.g_hi) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int gc = gc0 + e;
+          if (gc >= g.g_lo && gc <= g.g_hi) trow[gc - x0] = (uint8_t)(v[i] >> (8 * e));
+        }
+      } else if (lane == 31 && g.wrap_l) {
+        trow[-1] = (uint8_t)v[i];
+      } else if (lane == 30 && g.wrap_r) {
+        trow[bw] = (uint8_t)v[i];
+      }
+    }
   }
 }
 
-// Writes back the block interior and its four rim strips (never the
-// corners, which belong to diagonal blocks that may be updated meanwhile).
+// Writes back exactly the cells load_tile_generic loaded (the rims and
+// corners belong to blocks of other colours, which no other CTA updates
+// during this visit), byte by byte, rows by warps as above.
 __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
                                                    const uint8_t* tile, int sp) {
-  const int L = d.L, LH = d.H, pitch = d.pitch, W = bw + 2, H = bh + 2;
-  for (int k = threadIdx.x; k < W * H; k += blockDim.x) {
-    const int r = k / W - 1, c = k % W - 1;
-    if (!tile_cell_used(d, x0, y0, bw, bh, r, c)) continue;
-    d.lat[(size_t)wrap(y0 + r, LH) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, sp)];
+  const int L = d.L, LH = d.H, pitch = d.pitch;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const bool corners = d.nbh == 8, reflect = d.reflect != 0;
+  for (int r = (int)(threadIdx.x >> 5) - 1; r <= bh; r += nw) {
+    const int gy = y0 + r;
+    if (reflect && (gy < 0 || gy >= LH)) continue;
+    const bool rim_r = (r < 0 || r >= bh);
+    uint8_t* row = d.lat + (size_t)wrap(gy, LH) * pitch;
+    const uint8_t* trow = tile + (r + 1) * sp + kColOff;
+    for (int c = lane - 1; c <= bw; c += 32) {
+      if (rim_r && (c < 0 || c >= bw) && !corners) continue;
+      const int gx = x0 + c;
+      if (reflect && (gx < 0 || gx >= L)) continue;
+      row[wrap(gx, L)] = trow[c];
+    }
   }
 }
 
@@ -499,20 +568,22 @@ __device__ __forceinline__ void count_visit_uni(const uint8_t* tile, uint32_t* h
 __device__ __forceinline__ void count_visit_generic(const LatticeDesc& d, int bx, int by, VisitSmem& sm,
                                                     int k, int sV, int sH, int sD) {
   const int bw = d.cs[bx + 1] - d.cs[bx], bh = d.csy[by + 1] - d.csy[by];
-  const int sp = tile_pitch(bw), W = bw + 2, H = bh + 2;
-  for (int e = threadIdx.x; e < W * H; e += blockDim.x) {
-    const int r = e / W - 1, c = e % W - 1;
-    const bool rim_r = (r < 0 || r >= bh), rim_c = (c < 0 || c >= bw);
-    if (rim_r && rim_c) continue;
-    const bool end_r = (r == 0 || r == bh - 1), end_c = (c == 0 || c == bw - 1);
-    bool count;
-    if (rim_r)
-      count = sV < k && (!end_c || sD < k);
-    else if (rim_c)
-      count = sH < k && (!end_r || sD < k);
-    else
-      count = !(end_r && sV > k) && !(end_c && sH > k);
-    if (count) atomicAdd(&sm.hist[sm.tile[tidx(r, c, sp)]], 1u);
+  const int sp = tile_pitch(bw), lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = (int)(threadIdx.x >> 5) - 1; r <= bh; r += nw) {
+    const bool rim_r = (r < 0 || r >= bh), end_r = (r == 0 || r == bh - 1);
+    for (int c = lane - 1; c <= bw; c += 32) {
+      const bool rim_c = (c < 0 || c >= bw);
+      if (rim_r && rim_c) continue;
+      const bool end_c = (c == 0 || c == bw - 1);
+      bool count;
+      if (rim_r)
+        count = sV < k && (!end_c || sD < k);
+      else if (rim_c)
+        count = sH < k && (!end_r || sD < k);
+      else
+        count = !(end_r && sV > k) && !(end_c && sH > k);
+      if (count) atomicAdd(&sm.hist[sm.tile[tidx(r, c, sp)]], 1u);
+    }
   }
 }
 

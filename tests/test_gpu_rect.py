@@ -89,6 +89,10 @@ def test_rect_device_buffer_and_bad_height():
     assert np.array_equal(g.as_tensor()[:, :L].cpu().numpy(), O.init(L, S, 0.1, 3, H=H))
     with pytest.raises(ValueError):
         E.Lattice(L, S, D, (1.0, 1.0, 1.0), 3, device_buffer=buf[:-1], H=H)
+    # a buffer that is not 16-byte aligned is refused before any launch
+    big = torch.zeros(E.lattice_bytes(L, H) + 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(E.EscgError, match="aligned"):
+        E.Lattice(L, S, D, (1.0, 1.0, 1.0), 3, device_buffer=big[1:], H=H)
     for bad in (7, 16385):
         with pytest.raises(E.EscgError):
             E.Lattice(L, S, D, (1.0, 1.0, 1.0), 3, H=bad)
