@@ -116,6 +116,24 @@ bool escg_impl::encode_lattice_map(CUtensorMap* map, uint8_t* lattice, int L, in
 
 namespace {
 
+// The closed form (AxisGeom) reproduces the partition tables, and every fine
+// segment is 2..4 sites wide (the kernels' reciprocal table covers those).
+bool axis_geom_matches(const AxisGeom& g, const Partition& p) {
+  for (int b = 0; b < p.P; ++b) {
+    const bool wide = b < g.r;
+    const int nw = b < g.r ? b : g.r;
+    const int s0 = b * g.q + nw, w = g.q + (wide ? 1 : 0);
+    const int f0 = nw * g.Qa + (b - nw) * g.Qb, Q = wide ? g.Qa : g.Qb;
+    const int fq = wide ? g.fqa : g.fqb, fr = wide ? g.fra : g.frb;
+    if (p.cs[b] != s0 || p.cs[b + 1] - p.cs[b] != w || p.fc[b] != f0 || p.fc[b + 1] - p.fc[b] != Q) return false;
+    for (int k = 0; k < Q; ++k) {
+      const int st = k * fq + (k < fr ? k : fr), wk = fq + (k < fr ? 1 : 0);
+      if (p.fs[f0 + k] != s0 + st || wk < 2 || wk > 4) return false;
+    }
+  }
+  return true;
+}
+
 bool partition_fits(const Partition& p) {
   for (int k = 0; k < p.P; ++k) {
     if (p.cs[k + 1] - p.cs[k] > kMaxBlock) return false;
@@ -544,6 +562,12 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   d.csy = H != L ? h->d_tables + ntab_x : d.cs;
   d.fsy = H != L ? d.csy + py.cs.size() : d.fs;
   d.fcy = H != L ? d.fsy + py.fs.size() : d.fc;
+  d.ax = make_axis_geom(L, p.P);
+  d.ay = make_axis_geom(H, py.P);
+  if (!axis_geom_matches(d.ax, p) || !axis_geom_matches(d.ay, py)) {
+    set_err("internal: closed-form partition disagrees with the tables for %d x %d", L, H);
+    return fail(ESCG_EINVAL);
+  }
   d.trans = h->d_trans;
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);

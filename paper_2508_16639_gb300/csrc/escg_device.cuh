@@ -69,7 +69,6 @@ __device__ __forceinline__ int slot_of(uint32_t ord, int colour) {
 struct VisitSmem {
   uint8_t tile[kMaxTileRows * kMaxTilePitch];
   uint32_t trans[kTransWords];   // LatticeDesc::trans
-  int16_t fsx[kMaxFine + 1], fsy[kMaxFine + 1];   // block-local fine starts
   uint32_t forder;
   uint32_t hist[kMaxStates];
 };
@@ -178,106 +177,138 @@ __device__ __forceinline__ void attempt_uni(uint8_t* __restrict__ tile, const ui
 template <int SP, int COFF>
 __device__ __forceinline__ int tidx_u(int r, int c) { return (r + 1) * SP + c + COFF; }
 
-// Generic staging of a block's tile.  A visit uses the block interior and
-// the four 1-site rim strips, the corners too in the Moore neighbourhood, and
-// nothing beyond the lattice edge with a reflecting boundary.  Tile row r
-// (r in [-1, bh]) is loaded by warp (r + 1) mod (warps): the columns that do
-// not wrap around the lattice edge as aligned 4-byte words (lane k loads
-// word k; rows are 16-byte aligned and at most 26 words wide), the one
-// column that wraps (a block at the left or right edge of a periodic
-// lattice) as a byte by lane 31 or 30.  Each warp issues the loads of up
-// to 8 rows before it writes any of them to shared memory, so a tile costs
-// two L2 round trips instead of one per row.  Loads go through L2
-// (ld.global.cg: data written by other CTAs of the same launch must not be
-// served from a stale L1 line).
-struct GenericRow {
-  int gy;          // lattice row, or -1 when the row lies beyond a reflecting edge
-  int g_lo, g_hi;  // lattice columns loaded as words (no wrap), g_lo <= g_hi
-  int wa;          // first word's column (g_lo rounded down to 4)
-  bool wrap_l, wrap_r;  // tile column -1 from lattice column L-1 / bw from 0
+// A coarse block's span along one axis and its fine segments (AxisGeom).
+struct BlockSpan {
+  int s0, w;    // first site, width
+  int f0, Q;    // global index of the first fine segment, fine segments
+  int fq, fr;   // fine segment k: start k fq + min(k, fr), width fq + (k < fr)
 };
 
-__device__ __forceinline__ GenericRow generic_row(const LatticeDesc& d, int x0, int y0, int bw, int bh, int r) {
-  GenericRow g;
-  const int L = d.L, LH = d.H;
-  const bool reflect = d.reflect != 0;
-  int gy = y0 + r;
-  if (gy < 0 || gy >= LH) gy = reflect ? -1 : (gy < 0 ? gy + LH : gy - LH);
-  g.gy = gy;
-  const bool rim_r = (r < 0 || r >= bh);
-  const int c_lo = (rim_r && d.nbh != 8) ? 0 : -1, c_hi = (rim_r && d.nbh != 8) ? bw - 1 : bw;
-  g.g_lo = max(x0 + c_lo, 0);
-  g.g_hi = min(x0 + c_hi, L - 1);
-  g.wa = g.g_lo & ~3;
-  g.wrap_l = !reflect && x0 + c_lo < 0;
-  g.wrap_r = !reflect && x0 + c_hi >= L;
-  return g;
+__device__ __forceinline__ BlockSpan block_span(const AxisGeom& g, int b) {
+  BlockSpan s;
+  const bool wide = b < g.r;
+  const int nw = min(b, g.r);
+  s.s0 = b * g.q + nw;
+  s.w = g.q + (wide ? 1 : 0);
+  s.f0 = nw * g.Qa + (b - nw) * g.Qb;
+  s.Q = wide ? g.Qa : g.Qb;
+  s.fq = wide ? g.fqa : g.fqb;
+  s.fr = wide ? g.fra : g.frb;
+  return s;
+}
+__device__ __forceinline__ int seg_start(const BlockSpan& s, int k) { return k * s.fq + min(k, s.fr); }
+__device__ __forceinline__ int seg_width(const BlockSpan& s, int k) { return s.fq + (k < s.fr ? 1 : 0); }
+
+// Generic staging of a block's tile.  A visit uses the block interior and
+// the four 1-site rim strips, the corners too in the Moore neighbourhood,
+// and nothing beyond the lattice edge with a reflecting boundary.  Every
+// tile row is moved by one warp, lane k taking the k-th aligned 4-byte word
+// of the row's columns that do not wrap around the lattice edge (rows are
+// 16-byte aligned and at most 26 words wide); the one column that wraps (a
+// block at the left or right edge of a periodic lattice) is a single byte,
+// taken by lane 31 (left) or 30 (right).  The per-lane plan is the same for
+// all rows of a kind (interior rows, rim rows), so it is worked out once per
+// visit.  Loads go through L2 (ld.global.cg: data written by other CTAs of
+// the same launch must not be served from a stale L1 line).
+struct RowPlan {
+  int gcol;       // lattice column of the word (or byte)
+  int tcol;       // tile column of its first byte
+  uint32_t mask;  // bytes of the word that belong to the tile (bit e: byte e); 0: none
+  bool byte;      // a single byte (the wrapped column), not a word
+};
+
+__device__ __forceinline__ RowPlan row_plan(const LatticeDesc& d, int x0, int bw, bool rim, int lane) {
+  RowPlan p;
+  const bool reflect = d.reflect != 0, trim = rim && d.nbh != 8;
+  const int c_lo = trim ? 0 : -1, c_hi = trim ? bw - 1 : bw;
+  const int g_lo = max(x0 + c_lo, 0), g_hi = min(x0 + c_hi, d.L - 1);
+  const int gc0 = (g_lo & ~3) + 4 * lane;
+  p.byte = false;
+  p.mask = 0;
+  p.gcol = 0;
+  p.tcol = 0;
+  if (gc0 <= g_hi) {
+    p.gcol = gc0;
+    p.tcol = gc0 - x0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (gc0 + e >= g_lo && gc0 + e <= g_hi) p.mask |= 1u << e;
+  } else if (lane == 31 && !reflect && x0 + c_lo < 0) {
+    p.gcol = d.L - 1;
+    p.tcol = -1;
+    p.mask = 1;
+    p.byte = true;
+  } else if (lane == 30 && !reflect && x0 + c_hi >= d.L) {
+    p.gcol = 0;
+    p.tcol = bw;
+    p.mask = 1;
+    p.byte = true;
+  }
+  return p;
 }
 
+// Lattice row of tile row r, or -1 beyond a reflecting edge.
+__device__ __forceinline__ int tile_row_gy(const LatticeDesc& d, int y0, int r) {
+  const int gy = y0 + r;
+  if (gy >= 0 && gy < d.H) return gy;
+  if (d.reflect) return -1;
+  return gy < 0 ? gy + d.H : gy - d.H;
+}
+
+// Each warp issues the loads of up to 8 rows before it writes any of them
+// to shared memory: a tile costs two L2 round trips.
 __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
                                                   uint8_t* tile, int sp) {
   constexpr int kRows = 8;
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int L = d.L, pitch = d.pitch;
+  const RowPlan pi = row_plan(d, x0, bw, false, lane), pr = row_plan(d, x0, bw, true, lane);
   for (int r0 = (int)(threadIdx.x >> 5) - 1; r0 <= bh; r0 += kRows * nw) {
     uint32_t v[kRows];
 #pragma unroll
     for (int i = 0; i < kRows; ++i) {
       const int r = r0 + i * nw;
       v[i] = 0;
-      if (r > bh) continue;
-      const GenericRow g = generic_row(d, x0, y0, bw, bh, r);
-      if (g.gy < 0) continue;
-      const uint8_t* row = d.lat + (size_t)g.gy * pitch;
-      if (g.wa + 4 * lane <= g.g_hi)
-        v[i] = __ldcg(reinterpret_cast<const uint32_t*>(row + g.wa) + lane);
-      else if (lane == 31 && g.wrap_l)
-        v[i] = __ldcg(row + (L - 1));
-      else if (lane == 30 && g.wrap_r)
-        v[i] = __ldcg(row);
+      const RowPlan& p = (r < 0 || r >= bh) ? pr : pi;
+      const int gy = tile_row_gy(d, y0, r);
+      if (r > bh || gy < 0 || !p.mask) continue;
+      const uint8_t* src = d.lat + (size_t)gy * d.pitch + p.gcol;
+      v[i] = p.byte ? (uint32_t)__ldcg(src) : __ldcg(reinterpret_cast<const uint32_t*>(src));
     }
 #pragma unroll
     for (int i = 0; i < kRows; ++i) {
       const int r = r0 + i * nw;
-      if (r > bh) continue;
-      const GenericRow g = generic_row(d, x0, y0, bw, bh, r);
-      if (g.gy < 0) continue;
-      uint8_t* trow = tile + (r + 1) * sp + kColOff;
-      const int gc0 = g.wa + 4 * lane;
-      if (gc0 <= g.g_hi) {
+      const RowPlan& p = (r < 0 || r >= bh) ? pr : pi;
+      if (r > bh || tile_row_gy(d, y0, r) < 0) continue;
+      uint8_t* dst = tile + (r + 1) * sp + kColOff + p.tcol;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int gc = gc0 + e;
-          if (gc >= g.g_lo && gc <= g.g_hi) trow[gc - x0] = (uint8_t)(v[i] >> (8 * e));
-        }
-      } else if (lane == 31 && g.wrap_l) {
-        trow[-1] = (uint8_t)v[i];
-      } else if (lane == 30 && g.wrap_r) {
-        trow[bw] = (uint8_t)v[i];
-      }
+      for (int e = 0; e < 4; ++e)
+        if ((p.mask >> e) & 1u) dst[e] = (uint8_t)(v[i] >> (8 * e));
     }
   }
 }
 
 // Writes back exactly the cells load_tile_generic loaded (the rims and
 // corners belong to blocks of other colours, which no other CTA updates
-// during this visit), byte by byte, rows by warps as above.
+// during this visit): whole words where all four bytes are the block's,
+// single bytes at the ends of a row.
 __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
                                                    const uint8_t* tile, int sp) {
-  const int L = d.L, LH = d.H, pitch = d.pitch;
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const bool corners = d.nbh == 8, reflect = d.reflect != 0;
+  const RowPlan pi = row_plan(d, x0, bw, false, lane), pr = row_plan(d, x0, bw, true, lane);
   for (int r = (int)(threadIdx.x >> 5) - 1; r <= bh; r += nw) {
-    const int gy = y0 + r;
-    if (reflect && (gy < 0 || gy >= LH)) continue;
-    const bool rim_r = (r < 0 || r >= bh);
-    uint8_t* row = d.lat + (size_t)wrap(gy, LH) * pitch;
-    const uint8_t* trow = tile + (r + 1) * sp + kColOff;
-    for (int c = lane - 1; c <= bw; c += 32) {
-      if (rim_r && (c < 0 || c >= bw) && !corners) continue;
-      const int gx = x0 + c;
-      if (reflect && (gx < 0 || gx >= L)) continue;
-      row[wrap(gx, L)] = trow[c];
+    const RowPlan& p = (r < 0 || r >= bh) ? pr : pi;
+    const int gy = tile_row_gy(d, y0, r);
+    if (gy < 0 || !p.mask) continue;
+    const uint8_t* src = tile + (r + 1) * sp + kColOff + p.tcol;
+    uint8_t* dst = d.lat + (size_t)gy * d.pitch + p.gcol;
+    if (p.mask == 0xFu) {
+      const uint32_t w = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16) |
+                         ((uint32_t)src[3] << 24);
+      *reinterpret_cast<uint32_t*>(dst) = w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if ((p.mask >> e) & 1u) dst[e] = src[e];
     }
   }
 }
@@ -392,38 +423,40 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
 }
 
 // Visit of coarse block (bx, by) in MCS m, any geometry of the partition.
+// The block's span and fine segments come from the closed-form partition
+// (no table loads ahead of the tile load); a thread's quad (2 x 2 fine
+// sub-blocks) is found with a reciprocal multiply, exact for the at most
+// 24 x 24 quads of a block.
 template <bool OWN_FORDER = true>
 __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int by, uint32_t m,
                                               VisitSmem& sm) {
-  const int x0 = d.cs[bx], bw = d.cs[bx + 1] - x0;
-  const int y0 = d.csy[by], bh = d.csy[by + 1] - y0;
-  const int fx0 = d.fc[bx], Qx = d.fc[bx + 1] - fx0;
-  const int fy0 = d.fcy[by], Qy = d.fcy[by + 1] - fy0;
+  const BlockSpan X = block_span(d.ax, bx), Y = block_span(d.ay, by);
+  const int x0 = X.s0, bw = X.w, y0 = Y.s0, bh = Y.w;
   const int sp = tile_pitch(bw);
   const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int k = tid; k <= Qx; k += nthr) sm.fsx[k] = (int16_t)(d.fs[fx0 + k] - x0);
-  for (int k = tid; k <= Qy; k += nthr) sm.fsy[k] = (int16_t)(d.fsy[fy0 + k] - y0);
   if (OWN_FORDER && tid == 0) sm.forder = fine_order(d, bx, by, m);
   load_tile_generic(d, x0, y0, bw, bh, sm.tile, sp);
   __syncthreads();
   const uint32_t s1 = (uint32_t)d.S + 1u;
   const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
-  const int hx = Qx >> 1, nquads = hx * (Qy >> 1);
+  const int hx = X.Q >> 1, nquads = hx * (Y.Q >> 1);
+  const uint32_t inv_hx = (65536u + (uint32_t)hx - 1u) / (uint32_t)hx;
   const uint32_t ord = sm.forder;
+  const bool variant = d.nbh == 8 || d.reflect;
+  const int lg = d.nbh == 8 ? 3 : 2;
   for (int fi = 0; fi < 4; ++fi) {
     const int fcol = order_at(ord, fi);
     const int cx = fcol & 1, cy = fcol >> 1;
     for (int q = tid; q < nquads; q += nthr) {
-      const int qy = q / hx, qx = q - qy * hx;
+      const int qy = (int)(((uint32_t)q * inv_hx) >> 16), qx = q - qy * hx;
       const int fx = 2 * qx + cx, fy = 2 * qy + cy;
-      const int sx = sm.fsx[fx], wx = sm.fsx[fx + 1] - sx;
-      const int sy = sm.fsy[fy], wy = sm.fsy[fy + 1] - sy;
+      const int sx = seg_start(X, fx), wx = seg_width(X, fx);
+      const int sy = seg_start(Y, fy), wy = seg_width(Y, fy);
       const uint32_t nk = (uint32_t)(wx * wy), n4 = 4u * nk;
-      const uint32_t g = (uint32_t)(fy0 + fy) * (uint32_t)d.GQ + (uint32_t)(fx0 + fx);
-      const uint32_t inv_wx = (65536u + (uint32_t)wx - 1u) / (uint32_t)wx;
+      const uint32_t g = (uint32_t)(Y.f0 + fy) * (uint32_t)d.GQ + (uint32_t)(X.f0 + fx);
+      // ceil(65536 / wx) for the fine widths 2, 3, 4
+      const uint32_t inv_wx = wx == 2 ? 32768u : (wx == 3 ? 21846u : 16384u);
       const int base = tidx(sy, sx, sp);
-      const bool variant = d.nbh == 8 || d.reflect;
-      const int lg = d.nbh == 8 ? 3 : 2;
       for (uint32_t j = 0; 4u * j < nk; ++j) {
         const uint4 x = philox10_rk(make_uint4(j, g, m, kTagStep), d.rk);
         const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
@@ -567,7 +600,7 @@ __device__ __forceinline__ void count_visit_uni(const uint8_t* tile, uint32_t* h
 // Any geometry: one site per thread iteration, shared-memory atomics.
 __device__ __forceinline__ void count_visit_generic(const LatticeDesc& d, int bx, int by, VisitSmem& sm,
                                                     int k, int sV, int sH, int sD) {
-  const int bw = d.cs[bx + 1] - d.cs[bx], bh = d.csy[by + 1] - d.csy[by];
+  const int bw = block_span(d.ax, bx).w, bh = block_span(d.ay, by).w;
   const int sp = tile_pitch(bw), lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int r = (int)(threadIdx.x >> 5) - 1; r <= bh; r += nw) {
     const bool rim_r = (r < 0 || r >= bh), end_r = (r == 0 || r == bh - 1);

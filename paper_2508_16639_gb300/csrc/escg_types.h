@@ -23,6 +23,32 @@ constexpr int kMaxStates = 16;           // S <= 15
 constexpr int kTransPairs = kMaxStates * kMaxStates;
 constexpr int kTransWords = 2 * kTransPairs;
 
+// Closed form of one axis's schedule-v1 partition, so that a kernel finds a
+// block's span and its fine segments by arithmetic instead of table loads:
+// n sites split evenly into P coarse parts (the first r parts q + 1 sites
+// wide, the rest q), a part of width w into Q = 2 floor(w/4) fine segments
+// split evenly the same way (the first fr segments fq + 1 wide, the rest
+// fq).  Suffix a: a wide part (q + 1), b: a narrow one (q).
+struct AxisGeom {
+  int32_t q, r;
+  int32_t Qa, Qb;
+  int32_t fqa, fra, fqb, frb;
+};
+
+inline AxisGeom make_axis_geom(int n, int P) {
+  AxisGeom g;
+  g.q = n / P;
+  g.r = n % P;
+  const int wa = g.q + 1, wb = g.q;
+  g.Qa = 2 * (wa / 4);
+  g.Qb = 2 * (wb / 4);
+  g.fqa = g.Qa > 0 ? wa / g.Qa : 0;
+  g.fra = g.Qa > 0 ? wa % g.Qa : 0;
+  g.fqb = g.Qb > 0 ? wb / g.Qb : 0;
+  g.frb = g.Qb > 0 ? wb % g.Qb : 0;
+  return g;
+}
+
 // Everything a kernel needs to know about one lattice.
 struct LatticeDesc {
   uint8_t* lat;         // H rows of `pitch` bytes, values 0..S
@@ -37,6 +63,7 @@ struct LatticeDesc {
   const int32_t* csy;   // the row axis's tables, as cs, fs, fc (the same
   const int32_t* fsy;   // arrays when H = L)
   const int32_t* fcy;
+  AxisGeom ax, ay;      // the same partitions in closed form (columns, rows)
   const uint8_t* trans; // kTransWords words: byte (a*(S+1)+b)*4 + action of
                         // the first half holds the new pair (a' | b' << 4),
                         // actions 0 exchange, 1 interaction, 2 reproduction,
