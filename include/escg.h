@@ -119,6 +119,18 @@ typedef struct {
                                     columns); site i = row*L + col.  The
                                     lattice buffers of the calls below hold H
                                     rows of L (host) or pitch (device) bytes. */
+    int32_t bits_per_site;       /* device storage of a site: 8 (one byte,
+                                    default; 0 means 8), 4 or 2 (bit-packed
+                                    rows: site c at bits [c*b, (c+1)*b) of the
+                                    row, little endian; 2 needs S <= 3; packed
+                                    needs L, H >= 64).  Kernels stage packed
+                                    groups of 4 sites and work on one byte per
+                                    site in shared memory; host buffers stay
+                                    one byte per site (converted on the device
+                                    through a byte image allocated on first
+                                    use).  Results are identical for all three;
+                                    the device buffer is H rows of
+                                    escg_lattice_pitch_ex(L, b) bytes.        */
 } escg_options;
 
 typedef struct escg escg_t;
@@ -132,6 +144,11 @@ void escg_default_options(escg_options* opt);
  * rows of that pitch. */
 size_t escg_lattice_bytes(int32_t L);
 size_t escg_lattice_bytes_rect(int32_t L, int32_t H);
+/* Row pitch and bytes of an L x H lattice stored with bits_per_site bits per
+ * site (8, 4 or 2; 0 means 8): ceil(L*b/8) rounded up to 16 bytes per row;
+ * 0 for an invalid argument. */
+int32_t escg_lattice_pitch_ex(int32_t L, int32_t bits_per_site);
+size_t escg_lattice_bytes_ex(int32_t L, int32_t H, int32_t bits_per_site);
 int32_t escg_lattice_pitch(int32_t L);
 
 /* Creates a lattice of side L (8 <= L <= 16384) with S species

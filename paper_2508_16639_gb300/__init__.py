@@ -46,13 +46,13 @@ def int_throughput():
     return float(a.value), float(b.value)
 
 
-def lattice_pitch(L: int) -> int:
-    return int(load().escg_lattice_pitch(L))
+def lattice_pitch(L: int, bits_per_site: int = 8) -> int:
+    return int(load().escg_lattice_pitch_ex(L, bits_per_site))
 
 
-def lattice_bytes(L: int, H: int = None) -> int:
-    """Device bytes of an L x H lattice (H rows of lattice_pitch(L) bytes)."""
-    return int(load().escg_lattice_bytes_rect(L, L if H is None else H))
+def lattice_bytes(L: int, H: int = None, bits_per_site: int = 8) -> int:
+    """Device bytes of an L x H lattice (H rows of lattice_pitch(L, bits) bytes)."""
+    return int(load().escg_lattice_bytes_ex(L, L if H is None else H, bits_per_site))
 
 
 class Lattice:
@@ -68,13 +68,14 @@ class Lattice:
     coarse phase -- all bit-identical.  dominance_prob: optional S x S edge
     probabilities (Park, Chen and Szolnoki's probabilistic dominance);
     neighbourhood 4 or 8 (Moore) and reflecting_boundary: the paper's rule
-    variants."""
+    variants.  H: rows (default L).  bits_per_site: device storage, 8 (one
+    byte per site), 4 or 2 (bit-packed rows; 2 needs S <= 3)."""
 
     def __init__(self, L: int, S: int, digraph, rates, seed: int, p_empty: float = 0.0,
                  log_every: int = 10, stop_at_extinction: bool = False, persistent: int = 1,
                  stream=None, device_buffer=None, time_kernels: bool = False, ctas_per_sm: int = 0,
                  dominance_prob=None, neighbourhood: int = 4, reflecting_boundary: bool = False,
-                 H: int = None):
+                 H: int = None, bits_per_site: int = 8):
         lib = load()
         self.L, self.S = int(L), int(S)
         self.H = self.L if H is None else int(H)
@@ -91,6 +92,8 @@ class Lattice:
         opt.neighbourhood = int(neighbourhood)
         opt.reflecting_boundary = int(bool(reflecting_boundary))
         opt.height = self.H
+        opt.bits_per_site = int(bits_per_site)
+        self.bits_per_site = int(bits_per_site)
         if dominance_prob is not None:
             Pd = np.ascontiguousarray(np.asarray(dominance_prob, dtype=np.float64).reshape(S, S))
             opt.dominance_prob = Pd.ctypes.data_as(C.POINTER(C.c_double))   # read during creation
@@ -98,15 +101,15 @@ class Lattice:
             opt.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         self._buffer = device_buffer  # keep the torch tensor alive
         if device_buffer is not None:
-            if device_buffer.numel() * device_buffer.element_size() < lattice_bytes(L, self.H):
-                raise ValueError("device_buffer is smaller than lattice_bytes(L, H)")
+            if device_buffer.numel() * device_buffer.element_size() < lattice_bytes(L, self.H, bits_per_site):
+                raise ValueError("device_buffer is smaller than lattice_bytes(L, H, bits_per_site)")
             opt.device_lattice = int(device_buffer.data_ptr())
         h = lib.escg_create_ex(self.L, self.S, _u8(D), C.byref(r), C.c_uint64(seed & (2**64 - 1)),
                                C.byref(opt))
         if not h:
             raise EscgError(-1, lib.escg_last_error().decode(errors="replace"))
         self._h = C.c_void_p(h)
-        self.pitch = lattice_pitch(L)
+        self.pitch = lattice_pitch(L, bits_per_site)
 
     # -- life cycle ---------------------------------------------------------
     def close(self):

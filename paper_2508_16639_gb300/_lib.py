@@ -26,7 +26,7 @@ class Options(C.Structure):
                 ("device_lattice", C.c_void_p), ("time_kernels", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("dominance_prob", C.POINTER(C.c_double)),
                 ("neighbourhood", C.c_int32), ("reflecting_boundary", C.c_int32),
-                ("height", C.c_int32)]
+                ("height", C.c_int32), ("bits_per_site", C.c_int32)]
 
 
 class ReplicaSpec(C.Structure):
@@ -57,6 +57,8 @@ SIGNATURES = {
     "escg_default_options": (None, [C.POINTER(Options)]),
     "escg_lattice_bytes": (C.c_size_t, [C.c_int32]),
     "escg_lattice_bytes_rect": (C.c_size_t, [C.c_int32, C.c_int32]),
+    "escg_lattice_pitch_ex": (C.c_int32, [C.c_int32, C.c_int32]),
+    "escg_lattice_bytes_ex": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
     "escg_lattice_pitch": (C.c_int32, [C.c_int32]),
     "escg_create": (C.c_void_p, [C.c_int32, C.c_int32, _u8p, C.POINTER(Rates), C.c_uint64]),
     "escg_create_ex": (C.c_void_p, [C.c_int32, C.c_int32, _u8p, C.POINTER(Rates), C.c_uint64,

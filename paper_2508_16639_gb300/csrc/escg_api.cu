@@ -246,6 +246,9 @@ struct escg {
   uint32_t log_num0_host = 0;
   bool failed = false;
   RunState* d_scratch = nullptr;  // accumulator for on-demand counts
+  int bits = 8;                   // bits per site of the device lattice
+  uint8_t* d_stage = nullptr;     // packed lattices: byte image for host transfers
+  int stage_pitch = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
   double kernel_ms = 0.0;
   uint64_t kernel_launches = 0;
@@ -255,14 +258,50 @@ namespace {
 
 LogBuffers log_buffers(escg* h) { return LogBuffers{h->d_log, h->d_log_mcs}; }
 
+// Byte image of a packed lattice for host transfers (allocated on first use).
+cudaError_t ensure_stage(escg* h) {
+  if (h->d_stage) return cudaSuccess;
+  h->stage_pitch = escg_lattice_pitch(h->L);
+  return cudaMalloc(&h->d_stage, (size_t)h->H * h->stage_pitch);
+}
+
+// The lattice as one byte per site: the device lattice itself, or the byte
+// image of a packed one.
+LatticeDesc byte_view(escg* h) {
+  LatticeDesc d = h->desc;
+  if (h->bits != 8) {
+    d.lat = h->d_stage;
+    d.pitch = h->stage_pitch;
+    d.bits = 8;
+  }
+  return d;
+}
+
 // Host <-> device copy of the H x L lattice (host rows packed, device rows of
-// the handle's pitch); one linear copy when the two layouts coincide.
+// the handle's pitch); one linear copy when the two layouts coincide.  A
+// packed lattice goes through its byte image and the pack / unpack kernels.
 cudaError_t copy_to_device(escg* h, const uint8_t* host) {
+  if (h->bits != 8) {
+    cudaError_t e = ensure_stage(h);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(h->d_stage, h->stage_pitch, host, h->L, h->L, h->H, cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = launch_pack(h->desc, h->d_stage, h->stage_pitch, h->stream);
+    return e;
+  }
   if (h->pitch == h->L)
     return cudaMemcpyAsync(h->lattice, host, (size_t)h->L * h->H, cudaMemcpyHostToDevice, h->stream);
   return cudaMemcpy2DAsync(h->lattice, h->pitch, host, h->L, h->L, h->H, cudaMemcpyHostToDevice, h->stream);
 }
 cudaError_t copy_to_host(escg* h, uint8_t* host) {
+  if (h->bits != 8) {
+    cudaError_t e = ensure_stage(h);
+    if (e == cudaSuccess) e = launch_unpack(h->desc, h->d_stage, h->stage_pitch, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(host, h->L, h->d_stage, h->stage_pitch, h->L, h->H, cudaMemcpyDeviceToHost,
+                            h->stream);
+    return e;
+  }
   if (h->pitch == h->L)
     return cudaMemcpyAsync(host, h->lattice, (size_t)h->L * h->H, cudaMemcpyDeviceToHost, h->stream);
   return cudaMemcpy2DAsync(host, h->L, h->lattice, h->pitch, h->L, h->H, cudaMemcpyDeviceToHost, h->stream);
@@ -321,6 +360,7 @@ void free_handle(escg* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->own_lattice && h->lattice) cudaFree(h->lattice);
   cudaFree(h->d_tables);
+  cudaFree(h->d_stage);
   cudaFree(h->d_trans);
   cudaFree(h->d_state);
   cudaFree(h->d_log);
@@ -394,6 +434,17 @@ size_t escg_lattice_bytes_rect(int32_t L, int32_t H) {
   return (L <= 0 || H <= 0) ? 0 : (size_t)H * escg_lattice_pitch(L);
 }
 
+int32_t escg_lattice_pitch_ex(int32_t L, int32_t bits_per_site) {
+  if (bits_per_site == 0) bits_per_site = 8;
+  if (L <= 0 || (bits_per_site != 8 && bits_per_site != 4 && bits_per_site != 2)) return 0;
+  const int64_t bytes = ((int64_t)L * bits_per_site + 7) / 8;
+  return (int32_t)((bytes + 15) / 16 * 16);
+}
+
+size_t escg_lattice_bytes_ex(int32_t L, int32_t H, int32_t bits_per_site) {
+  return H <= 0 ? 0 : (size_t)H * escg_lattice_pitch_ex(L, bits_per_site);
+}
+
 const char* escg_last_error(void) { return g_err; }
 
 double escg_exchange_from_mobility(double M, int64_t N) { return 2.0 * M * (double)N; }
@@ -444,6 +495,19 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     set_err("height=%d out of range [8, 16384]", o.height);
     return nullptr;
   }
+  if (o.bits_per_site == 0) o.bits_per_site = 8;
+  if (o.bits_per_site != 8 && o.bits_per_site != 4 && o.bits_per_site != 2) {
+    set_err("bits_per_site must be 8, 4 or 2 (got %d)", o.bits_per_site);
+    return nullptr;
+  }
+  if (o.bits_per_site == 2 && S > 3) {
+    set_err("2 bits per site hold the values 0..3: S=%d needs 4 or 8", S);
+    return nullptr;
+  }
+  if (o.bits_per_site != 8 && (L < 64 || o.height < 64)) {
+    set_err("a packed lattice needs L, H >= 64 (blocks at least 32 sites wide), got %d x %d", L, o.height);
+    return nullptr;
+  }
   if (reinterpret_cast<uintptr_t>(o.device_lattice) % 16 != 0) {
     set_err("device_lattice must be 16-byte aligned (rows are read as 16-byte vectors)");
     return nullptr;
@@ -471,7 +535,8 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   h->S = S;
   h->seed = seed;
   h->opt = o;
-  h->pitch = escg_lattice_pitch(L);
+  h->bits = o.bits_per_site;
+  h->pitch = escg_lattice_pitch_ex(L, h->bits);
   h->part = make_partition(L);
   h->part_y = make_partition(H);
   if (!partition_fits(h->part) || !partition_fits(h->part_y)) {
@@ -503,7 +568,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     h->own_stream = true;
   }
-  const size_t nbytes = escg_lattice_bytes_rect(L, H);
+  const size_t nbytes = escg_lattice_bytes_ex(L, H, h->bits);
   if (e == cudaSuccess) {
     if (o.device_lattice) {
       h->lattice = (uint8_t*)o.device_lattice;
@@ -564,6 +629,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   d.fcy = H != L ? d.fsy + py.fs.size() : d.fc;
   d.ax = make_axis_geom(L, p.P);
   d.ay = make_axis_geom(H, py.P);
+  d.bits = h->bits;
   if (!axis_geom_matches(d.ax, p) || !axis_geom_matches(d.ay, py)) {
     set_err("internal: closed-form partition disagrees with the tables for %d x %d", L, H);
     return fail(ESCG_EINVAL);
@@ -591,9 +657,10 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   // the uniform kernels implement the von Neumann, periodic rule only
   d.uniform64 = (uni && h->pitch % 16 == 0 && d.nbh == 4 && !d.reflect) ? 1 : 0;
   h->grid = persistent_grid(h->device, d.uniform64 != 0);
-  // the TMA and mailbox kernels are written for square lattices; the flag
-  // kernel takes rectangular ones in both geometries
-  const bool square = (H == L);
+  // the TMA and mailbox kernels are written for square lattices of one byte
+  // per site; the flag kernel takes rectangular and packed ones in both
+  // geometries
+  const bool square = (H == L) && h->bits == 8;
   if (d.uniform64 && square && o.persistent == 2) {
     if (!make_tensor_map(&h->tmap, h->lattice, L, h->pitch)) {
       set_err("cuTensorMapEncodeTiled failed for L=%d", L);
@@ -814,7 +881,7 @@ int escg_restore(escg_t* h, const uint8_t* host_lattice, uint64_t mcs) {
   if (rc != ESCG_OK) return rc;
   // values are checked on the device; an invalid lattice also stops the
   // run state, so that nothing enqueued later touches it
-  CUDA_TRY(launch_validate(h->desc, &h->d_state->error, kErrBadValue, &h->d_state->stopped, h->stream));
+  CUDA_TRY(launch_validate(byte_view(h), &h->d_state->error, kErrBadValue, &h->d_state->stopped, h->stream));
   h->launches++;
   uint32_t err = 0;
   CUDA_TRY(cudaMemcpyAsync(&err, &h->d_state->error, sizeof err, cudaMemcpyDeviceToHost, h->stream));
@@ -843,7 +910,7 @@ int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_m
   CUDA_TRY(copy_to_device(h, host_in));
   int rc = reset_state(h, mcs);
   if (rc != ESCG_OK) return rc;
-  CUDA_TRY(launch_validate(h->desc, &h->d_state->error, kErrBadValue, &h->d_state->stopped, h->stream));
+  CUDA_TRY(launch_validate(byte_view(h), &h->d_state->error, kErrBadValue, &h->d_state->stopped, h->stream));
   h->launches++;
   rc = escg_run(h, n_mcs);
   if (rc != ESCG_OK) return rc;

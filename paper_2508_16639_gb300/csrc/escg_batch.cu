@@ -940,6 +940,7 @@ int engine_add(Engine* e, const escg_replica_spec& sp, const SlotPlan& pl, int s
   d.fcy = d.fc;
   d.ax = make_axis_geom(sp.L, p.P);
   d.ay = d.ax;
+  d.bits = 8;
   d.trans = base + pl.trans;
   d.key0 = (uint32_t)sp.seed;
   d.key1 = (uint32_t)(sp.seed >> 32);

@@ -150,6 +150,38 @@ __device__ __forceinline__ int tidx(int r, int c, int sp) { return (r + 1) * sp 
 __device__ __forceinline__ int tile_pitch(int bw) { return ((kColOff + bw + 1) + 15) & ~15; }
 __device__ __forceinline__ int wrap(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
+// Bit-packed lattices: site c of a row occupies bits [c b, (c + 1) b) of the
+// row's little-endian bit string, b = LatticeDesc::bits (8: one byte per
+// site; 4 or 2: packed).  A group of 4 sites that starts at a multiple of 4
+// is one 32-bit word (b = 8), one 16-bit word (4) or one byte (2); kernels
+// move groups and work on one byte per site in shared memory.
+__device__ __forceinline__ uint32_t load_group(const uint8_t* row, int c0, int bits) {
+  if (bits == 8) return __ldcg(reinterpret_cast<const uint32_t*>(row + c0));
+  if (bits == 4) return __ldcg(reinterpret_cast<const uint16_t*>(row + (c0 >> 1)));
+  return __ldcg(row + (c0 >> 2));
+}
+__device__ __forceinline__ void store_group(uint8_t* row, int c0, int bits, uint32_t raw) {
+  if (bits == 8)
+    *reinterpret_cast<uint32_t*>(row + c0) = raw;
+  else if (bits == 4)
+    *reinterpret_cast<uint16_t*>(row + (c0 >> 1)) = (uint16_t)raw;
+  else
+    row[c0 >> 2] = (uint8_t)raw;
+}
+// 4 packed sites -> 4 bytes (site e in byte e), and back.
+__device__ __forceinline__ uint32_t unpack4(uint32_t raw, int bits) {
+  if (bits == 8) return raw;
+  if (bits == 4)
+    return (raw & 0xFu) | ((raw & 0xF0u) << 4) | ((raw & 0xF00u) << 8) | ((raw & 0xF000u) << 12);
+  return (raw & 0x3u) | ((raw & 0xCu) << 6) | ((raw & 0x30u) << 12) | ((raw & 0xC0u) << 18);
+}
+__device__ __forceinline__ uint32_t pack4(uint32_t v, int bits) {
+  if (bits == 8) return v;
+  if (bits == 4)
+    return (v & 0xFu) | ((v >> 4) & 0xF0u) | ((v >> 8) & 0xF00u) | ((v >> 12) & 0xF000u);
+  return (v & 0x3u) | ((v >> 6) & 0xCu) | ((v >> 12) & 0x30u) | ((v >> 18) & 0xC0u);
+}
+
 // Uniform geometry: 64x64 blocks, 2x2 sub-blocks, one thread per 2x2 pair of
 // sub-blocks ("quad"), 256 threads.
 constexpr int kUniB = 64;
@@ -202,19 +234,18 @@ __device__ __forceinline__ int seg_width(const BlockSpan& s, int k) { return s.f
 // Generic staging of a block's tile.  A visit uses the block interior and
 // the four 1-site rim strips, the corners too in the Moore neighbourhood,
 // and nothing beyond the lattice edge with a reflecting boundary.  Every
-// tile row is moved by one warp, lane k taking the k-th aligned 4-byte word
-// of the row's columns that do not wrap around the lattice edge (rows are
-// 16-byte aligned and at most 26 words wide); the one column that wraps (a
-// block at the left or right edge of a periodic lattice) is a single byte,
-// taken by lane 31 (left) or 30 (right).  The per-lane plan is the same for
-// all rows of a kind (interior rows, rim rows), so it is worked out once per
-// visit.  Loads go through L2 (ld.global.cg: data written by other CTAs of
-// the same launch must not be served from a stale L1 line).
+// tile row is moved by one warp, lane k taking the k-th aligned group of 4
+// sites of the row's columns that do not wrap around the lattice edge (at
+// most 26 groups); the one column that wraps (a block at the left or right
+// edge of a periodic lattice) comes with its group, taken by lane 31 (left)
+// or 30 (right).  The per-lane plan is the same for all rows of a kind
+// (interior rows, rim rows), so it is worked out once per visit.  Loads go
+// through L2 (ld.global.cg: data written by other CTAs of the same launch
+// must not be served from a stale L1 line).
 struct RowPlan {
-  int gcol;       // lattice column of the word (or byte)
-  int tcol;       // tile column of its first byte
-  uint32_t mask;  // bytes of the word that belong to the tile (bit e: byte e); 0: none
-  bool byte;      // a single byte (the wrapped column), not a word
+  int gcol;       // lattice column of the group's first site (a multiple of 4)
+  int tcol;       // tile column of that site
+  uint32_t mask;  // sites of the group that belong to the tile (bit e: site e); 0: none
 };
 
 __device__ __forceinline__ RowPlan row_plan(const LatticeDesc& d, int x0, int bw, bool rim, int lane) {
@@ -223,7 +254,6 @@ __device__ __forceinline__ RowPlan row_plan(const LatticeDesc& d, int x0, int bw
   const int c_lo = trim ? 0 : -1, c_hi = trim ? bw - 1 : bw;
   const int g_lo = max(x0 + c_lo, 0), g_hi = min(x0 + c_hi, d.L - 1);
   const int gc0 = (g_lo & ~3) + 4 * lane;
-  p.byte = false;
   p.mask = 0;
   p.gcol = 0;
   p.tcol = 0;
@@ -234,15 +264,14 @@ __device__ __forceinline__ RowPlan row_plan(const LatticeDesc& d, int x0, int bw
     for (int e = 0; e < 4; ++e)
       if (gc0 + e >= g_lo && gc0 + e <= g_hi) p.mask |= 1u << e;
   } else if (lane == 31 && !reflect && x0 + c_lo < 0) {
-    p.gcol = d.L - 1;
-    p.tcol = -1;
-    p.mask = 1;
-    p.byte = true;
+    const int e = (d.L - 1) & 3;
+    p.gcol = (d.L - 1) & ~3;
+    p.tcol = -1 - e;
+    p.mask = 1u << e;
   } else if (lane == 30 && !reflect && x0 + c_hi >= d.L) {
     p.gcol = 0;
     p.tcol = bw;
     p.mask = 1;
-    p.byte = true;
   }
   return p;
 }
@@ -255,12 +284,20 @@ __device__ __forceinline__ int tile_row_gy(const LatticeDesc& d, int y0, int r) 
   return gy < 0 ? gy + d.H : gy - d.H;
 }
 
+// Stash of a packed lattice's partially used groups, one 16-bit entry per
+// tile row and lane: the write-back merges the tile's sites into the group
+// as it was loaded.  Every group a visit writes holds no site that another
+// block of the same colour reads or writes (blocks are at least 32 sites
+// wide), and no other block writes its other sites during the visit.
+constexpr int kStashLanes = 32;
+constexpr int kStashWords = kMaxTileRows * kStashLanes;
+
 // Each warp issues the loads of up to 8 rows before it writes any of them
 // to shared memory: a tile costs two L2 round trips.
 __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
-                                                  uint8_t* tile, int sp) {
+                                                  uint8_t* tile, int sp, uint16_t* stash) {
   constexpr int kRows = 8;
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, bits = d.bits;
   const RowPlan pi = row_plan(d, x0, bw, false, lane), pr = row_plan(d, x0, bw, true, lane);
   for (int r0 = (int)(threadIdx.x >> 5) - 1; r0 <= bh; r0 += kRows * nw) {
     uint32_t v[kRows];
@@ -271,85 +308,160 @@ __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, 
       const RowPlan& p = (r < 0 || r >= bh) ? pr : pi;
       const int gy = tile_row_gy(d, y0, r);
       if (r > bh || gy < 0 || !p.mask) continue;
-      const uint8_t* src = d.lat + (size_t)gy * d.pitch + p.gcol;
-      v[i] = p.byte ? (uint32_t)__ldcg(src) : __ldcg(reinterpret_cast<const uint32_t*>(src));
+      v[i] = load_group(d.lat + (size_t)gy * d.pitch, p.gcol, bits);
     }
 #pragma unroll
     for (int i = 0; i < kRows; ++i) {
       const int r = r0 + i * nw;
       const RowPlan& p = (r < 0 || r >= bh) ? pr : pi;
       if (r > bh || tile_row_gy(d, y0, r) < 0) continue;
+      if (bits != 8 && p.mask && p.mask != 0xFu) stash[(r + 1) * kStashLanes + lane] = (uint16_t)v[i];
+      const uint32_t u = unpack4(v[i], bits);
       uint8_t* dst = tile + (r + 1) * sp + kColOff + p.tcol;
 #pragma unroll
       for (int e = 0; e < 4; ++e)
-        if ((p.mask >> e) & 1u) dst[e] = (uint8_t)(v[i] >> (8 * e));
+        if ((p.mask >> e) & 1u) dst[e] = (uint8_t)(u >> (8 * e));
     }
   }
 }
 
-// Writes back exactly the cells load_tile_generic loaded (the rims and
+// Writes back exactly the sites load_tile_generic loaded (the rims and
 // corners belong to blocks of other colours, which no other CTA updates
-// during this visit): whole words where all four bytes are the block's,
-// single bytes at the ends of a row.
+// during this visit): whole groups where all four sites are the tile's;
+// at the ends of a row single bytes (one byte per site) or the loaded group
+// with the tile's sites merged in (packed).
 __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
-                                                   const uint8_t* tile, int sp) {
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+                                                   const uint8_t* tile, int sp, const uint16_t* stash) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, bits = d.bits;
   const RowPlan pi = row_plan(d, x0, bw, false, lane), pr = row_plan(d, x0, bw, true, lane);
   for (int r = (int)(threadIdx.x >> 5) - 1; r <= bh; r += nw) {
     const RowPlan& p = (r < 0 || r >= bh) ? pr : pi;
     const int gy = tile_row_gy(d, y0, r);
     if (gy < 0 || !p.mask) continue;
     const uint8_t* src = tile + (r + 1) * sp + kColOff + p.tcol;
-    uint8_t* dst = d.lat + (size_t)gy * d.pitch + p.gcol;
+    uint8_t* row = d.lat + (size_t)gy * d.pitch;
     if (p.mask == 0xFu) {
       const uint32_t w = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16) |
                          ((uint32_t)src[3] << 24);
-      *reinterpret_cast<uint32_t*>(dst) = w;
-    } else {
+      store_group(row, p.gcol, bits, pack4(w, bits));
+    } else if (bits == 8) {
 #pragma unroll
       for (int e = 0; e < 4; ++e)
-        if ((p.mask >> e) & 1u) dst[e] = src[e];
+        if ((p.mask >> e) & 1u) row[p.gcol + e] = src[e];
+    } else {
+      uint32_t u = unpack4(stash[(r + 1) * kStashLanes + lane], bits);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if ((p.mask >> e) & 1u) u = (u & ~(0xFFu << (8 * e))) | ((uint32_t)src[e] << (8 * e));
+      store_group(row, p.gcol, bits, pack4(u, bits));
     }
   }
 }
 
-__device__ __forceinline__ void load_tile_uni(const LatticeDesc& d, int x0, int y0, uint8_t* tile) {
-  const int L = d.L, pitch = d.pitch, t = threadIdx.x;
-  {  // interior: 64 rows x 4 x 16 bytes, one 16-byte load per thread
-    const int r = t >> 2, q = t & 3;
-    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q);
+// Uniform staging: 64 x 64 interior (64 rows of 16 + 16 + 16 + 16 sites,
+// one quarter row per thread), the top and bottom rim rows, and the left and
+// right rim columns (threads 128..255, one site each).  Packed lattices: a
+// quarter row is one 32-bit (2 bits per site) or 64-bit (4 bits) load, and
+// a rim-column site comes with its group of 4, which the thread keeps
+// (returned, then passed to store_tile_uni) to write the group back whole.
+__device__ __forceinline__ uint32_t load_tile_uni(const LatticeDesc& d, int x0, int y0, uint8_t* tile) {
+  const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = d.bits;
+  uint32_t rim_raw = 0;
+  if (bits == 8) {
+    {  // interior: 64 rows x 4 x 16 bytes, one 16-byte load per thread
+      const int r = t >> 2, q = t & 3;
+      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q);
+      uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
+      dst[0] = make_uint2(v.x, v.y);
+      dst[1] = make_uint2(v.z, v.w);
+    }
+    if (t < 8) {  // top / bottom rim rows
+      const int r = (t < 4) ? -1 : kUniB, q = t & 3;
+      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0) + q);
+      uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
+      dst[0] = make_uint2(v.x, v.y);
+      dst[1] = make_uint2(v.z, v.w);
+    } else if (t >= 128) {  // left / right rim columns
+      const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
+      tile[tidx(r, c, kUniSP)] = __ldcg(d.lat + (size_t)(y0 + r) * pitch + wrap(x0 + c, L));
+    }
+    return rim_raw;
+  }
+  // packed: 16 sites = 32 bits (2 bits per site) or 64 bits (4 bits)
+  auto quarter = [&](int r, int gy, int q) {
+    const uint8_t* row = d.lat + (size_t)gy * pitch;
+    uint32_t lo, hi;
+    if (bits == 2) {
+      const uint32_t w = __ldcg(reinterpret_cast<const uint32_t*>(row + ((x0 + 16 * q) >> 2)));
+      lo = w & 0xFFFFu;
+      hi = w >> 16;
+    } else {
+      const uint2 w = __ldcg(reinterpret_cast<const uint2*>(row + ((x0 + 16 * q) >> 1)));
+      lo = w.x;
+      hi = w.y;
+    }
+    // lo/hi hold sites 0..7 / 8..15 of the quarter (16 or 32 bits each)
+    const int sh = bits == 2 ? 8 : 16;
     uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
-    dst[0] = make_uint2(v.x, v.y);
-    dst[1] = make_uint2(v.z, v.w);
-  }
-  if (t < 8) {  // top / bottom rim rows
-    const int r = (t < 4) ? -1 : kUniB, q = t & 3;
-    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0) + q);
-    uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
-    dst[0] = make_uint2(v.x, v.y);
-    dst[1] = make_uint2(v.z, v.w);
-  } else if (t >= 128) {  // left / right rim columns
-    const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
-    tile[tidx(r, c, kUniSP)] = __ldcg(d.lat + (size_t)(y0 + r) * pitch + wrap(x0 + c, L));
-  }
-}
-
-__device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int y0, const uint8_t* tile) {
-  const int L = d.L, pitch = d.pitch, t = threadIdx.x;
-  {
-    const int r = t >> 2, q = t & 3;
-    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
-    const uint2 a = src[0], b = src[1];
-    reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
-  }
+    dst[0] = make_uint2(unpack4(lo, bits), unpack4(lo >> sh, bits));
+    dst[1] = make_uint2(unpack4(hi, bits), unpack4(hi >> sh, bits));
+  };
+  quarter(t >> 2, y0 + (t >> 2), t & 3);
   if (t < 8) {
-    const int r = (t < 4) ? -1 : kUniB, q = t & 3;
-    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
-    const uint2 a = src[0], b = src[1];
-    reinterpret_cast<uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
+    const int r = (t < 4) ? -1 : kUniB;
+    quarter(r, wrap(y0 + r, d.H), t & 3);
   } else if (t >= 128) {
     const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
-    d.lat[(size_t)(y0 + r) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, kUniSP)];
+    const int gx = wrap(x0 + c, L);
+    rim_raw = load_group(d.lat + (size_t)(y0 + r) * pitch, gx & ~3, bits);
+    tile[tidx(r, c, kUniSP)] = (uint8_t)(unpack4(rim_raw, bits) >> (8 * (gx & 3)));
+  }
+  return rim_raw;
+}
+
+__device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int y0, const uint8_t* tile,
+                                               uint32_t rim_raw) {
+  const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = d.bits;
+  if (bits == 8) {
+    {
+      const int r = t >> 2, q = t & 3;
+      const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+      const uint2 a = src[0], b = src[1];
+      reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
+    }
+    if (t < 8) {
+      const int r = (t < 4) ? -1 : kUniB, q = t & 3;
+      const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+      const uint2 a = src[0], b = src[1];
+      reinterpret_cast<uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
+    } else if (t >= 128) {
+      const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
+      d.lat[(size_t)(y0 + r) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, kUniSP)];
+    }
+    return;
+  }
+  auto quarter = [&](int r, int gy, int q) {
+    uint8_t* row = d.lat + (size_t)gy * pitch;
+    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    const uint2 a = src[0], b = src[1];
+    const int sh = bits == 2 ? 8 : 16;
+    const uint32_t lo = pack4(a.x, bits) | (pack4(a.y, bits) << sh);
+    const uint32_t hi = pack4(b.x, bits) | (pack4(b.y, bits) << sh);
+    if (bits == 2)
+      *reinterpret_cast<uint32_t*>(row + ((x0 + 16 * q) >> 2)) = lo | (hi << 16);
+    else
+      *reinterpret_cast<uint2*>(row + ((x0 + 16 * q) >> 1)) = make_uint2(lo, hi);
+  };
+  quarter(t >> 2, y0 + (t >> 2), t & 3);
+  if (t < 8) {
+    const int r = (t < 4) ? -1 : kUniB;
+    quarter(r, wrap(y0 + r, d.H), t & 3);
+  } else if (t >= 128) {
+    const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
+    const int gx = wrap(x0 + c, L), e = gx & 3;
+    const uint32_t u = (unpack4(rim_raw, bits) & ~(0xFFu << (8 * e))) |
+                       ((uint32_t)tile[tidx(r, c, kUniSP)] << (8 * e));
+    store_group(d.lat + (size_t)(y0 + r) * pitch, gx & ~3, bits, pack4(u, bits));
   }
 }
 
@@ -416,10 +528,10 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
                                               VisitSmem& sm) {
   const int x0 = bx * kUniB, y0 = by * kUniB;
   if (OWN_FORDER && threadIdx.x == 0) sm.forder = fine_order(d, bx, by, m);
-  load_tile_uni(d, x0, y0, sm.tile);
+  const uint32_t rim_raw = load_tile_uni(d, x0, y0, sm.tile);
   __syncthreads();
   fine_phases_uni(d, bx, by, m, sm);
-  store_tile_uni(d, x0, y0, sm.tile);
+  store_tile_uni(d, x0, y0, sm.tile, rim_raw);
 }
 
 // Visit of coarse block (bx, by) in MCS m, any geometry of the partition.
@@ -427,15 +539,17 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
 // (no table loads ahead of the tile load); a thread's quad (2 x 2 fine
 // sub-blocks) is found with a reciprocal multiply, exact for the at most
 // 24 x 24 quads of a block.
+// stash: kStashWords entries of shared memory for a packed lattice (may be
+// null when d.bits == 8).
 template <bool OWN_FORDER = true>
 __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int by, uint32_t m,
-                                              VisitSmem& sm) {
+                                              VisitSmem& sm, uint16_t* stash = nullptr) {
   const BlockSpan X = block_span(d.ax, bx), Y = block_span(d.ay, by);
   const int x0 = X.s0, bw = X.w, y0 = Y.s0, bh = Y.w;
   const int sp = tile_pitch(bw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (OWN_FORDER && tid == 0) sm.forder = fine_order(d, bx, by, m);
-  load_tile_generic(d, x0, y0, bw, bh, sm.tile, sp);
+  load_tile_generic(d, x0, y0, bw, bh, sm.tile, sp, stash);
   __syncthreads();
   const uint32_t s1 = (uint32_t)d.S + 1u;
   const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
@@ -473,7 +587,7 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
     }
     __syncthreads();
   }
-  store_tile_generic(d, x0, y0, bw, bh, sm.tile, sp);
+  store_tile_generic(d, x0, y0, bw, bh, sm.tile, sp, stash);
 }
 
 // ---------------------------------------------------------------------------
@@ -497,6 +611,18 @@ __device__ __forceinline__ uint32_t bytes_equal(uint32_t w, uint32_t v) {
   return __popc(z);
 }
 
+// Sites 16 q .. 16 q + 15 of a row as 16 bytes (any bits per site).
+__device__ __forceinline__ uint4 load16(const LatticeDesc& d, uint32_t row, uint32_t q) {
+  const uint8_t* p = d.lat + (size_t)row * d.pitch;
+  if (d.bits == 8) return __ldcg(reinterpret_cast<const uint4*>(p) + q);
+  if (d.bits == 4) {
+    const uint2 w = __ldcg(reinterpret_cast<const uint2*>(p) + q);
+    return make_uint4(unpack4(w.x, 4), unpack4(w.x >> 16, 4), unpack4(w.y, 4), unpack4(w.y >> 16, 4));
+  }
+  const uint32_t w = __ldcg(reinterpret_cast<const uint32_t*>(p) + q);
+  return make_uint4(unpack4(w, 2), unpack4(w >> 8, 2), unpack4(w >> 16, 2), unpack4(w >> 24, 2));
+}
+
 // Adds the species counts of the 16-byte vectors k = start, start + stride,
 // ... of a lattice (rows of d.pitch bytes; bytes past column L masked as
 // 0xFF, never a state) to a shared histogram part[0..S]: SWAR zero-byte
@@ -505,14 +631,14 @@ __device__ __forceinline__ uint32_t bytes_equal(uint32_t w, uint32_t v) {
 __device__ __forceinline__ void count_vectors(const LatticeDesc& d, uint32_t start, uint32_t stride,
                                               uint32_t* part) {
   const int L = d.L, pitch = d.pitch, S = d.S;
-  const uint32_t vec_per_row = (uint32_t)pitch / 16u;
+  const uint32_t vec_per_row = (uint32_t)(L + 15) / 16u;
   const uint32_t total = (uint32_t)d.H * vec_per_row;   // < 2^32 for L, H <= 16384
   uint32_t c[kMaxStates];
 #pragma unroll
   for (int v = 0; v < kMaxStates; ++v) c[v] = 0;
   for (uint32_t k = start; k < total; k += stride) {
     const uint32_t row = k / vec_per_row, q = k - row * vec_per_row;
-    uint4 w = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)row * pitch) + q);
+    uint4 w = load16(d, row, q);
     const int col = 16 * (int)q;
     if (col + 16 > L) {
       uint32_t* p = reinterpret_cast<uint32_t*>(&w);

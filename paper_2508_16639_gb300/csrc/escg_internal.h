@@ -47,6 +47,9 @@ void build_transitions(int S, const uint8_t* D, const double* prob, uint64_t tx,
 
 // Host-side launchers (all asynchronous on `stream`).
 cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream);
+// Packed lattice (d.bits 4 or 2) from / to a byte image of byte_pitch-byte rows.
+cudaError_t launch_pack(const LatticeDesc& d, const uint8_t* bytes, int byte_pitch, cudaStream_t stream);
+cudaError_t launch_unpack(const LatticeDesc& d, uint8_t* bytes, int byte_pitch, cudaStream_t stream);
 cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t stream);
 // Sets *bad |= flag if any lattice byte is outside 0..S, and then *stop = 1
 // unless stop is null.

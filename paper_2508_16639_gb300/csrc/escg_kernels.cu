@@ -34,19 +34,58 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
 }
 
 // ---------------------------------------------------------------------------
+// One thread per group of 4 sites (a 32-bit word, 16-bit word or byte of
+// the row, by bits per site); sites past column L (row padding) are 0.
 __global__ void init_kernel(LatticeDesc d, uint64_t T_empty) {
-  const int L = d.L, pitch = d.pitch;
-  const size_t total = (size_t)d.H * pitch;
+  const int L = d.L, bits = d.bits;
+  const int groups = d.pitch * 2 / bits;   // groups of 4 sites per row of pitch bytes
+  const size_t total = (size_t)d.H * groups;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
        k += (size_t)gridDim.x * blockDim.x) {
-    const int row = (int)(k / pitch), col = (int)(k % pitch);
-    uint8_t v = 0;
-    if (col < L) {
-      const uint32_t i = (uint32_t)row * (uint32_t)L + (uint32_t)col;
-      const uint4 x = philox10(make_uint4(i, 0u, 0u, kTagInit), d.key0, d.key1);
-      v = ((uint64_t)x.x < T_empty) ? 0 : (uint8_t)(1u + __umulhi(x.y, (uint32_t)d.S));
+    const int row = (int)(k / groups), c0 = 4 * (int)(k % groups);
+    uint32_t u = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int col = c0 + e;
+      if (col < L) {
+        const uint32_t i = (uint32_t)row * (uint32_t)L + (uint32_t)col;
+        const uint4 x = philox10(make_uint4(i, 0u, 0u, kTagInit), d.key0, d.key1);
+        const uint32_t v = ((uint64_t)x.x < T_empty) ? 0u : 1u + __umulhi(x.y, (uint32_t)d.S);
+        u |= v << (8 * e);
+      }
     }
-    d.lat[k] = v;
+    store_group(d.lat + (size_t)row * d.pitch, c0, bits, pack4(u, bits));
+  }
+}
+
+// Packed lattice <-> one byte per site (host transfers of a packed lattice
+// go through a byte image with pitch round_up(L, 16)).  One thread per group.
+__global__ void pack_kernel(LatticeDesc d, const uint8_t* bytes, int byte_pitch) {
+  const int groups = (d.L + 3) / 4;
+  const size_t total = (size_t)d.H * groups;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(k / groups), c0 = 4 * (int)(k % groups);
+    const uint8_t* src = bytes + (size_t)row * byte_pitch + c0;
+    uint32_t u = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (c0 + e < d.L) u |= (uint32_t)(src[e] & ((1u << d.bits) - 1u)) << (8 * e);
+    store_group(d.lat + (size_t)row * d.pitch, c0, d.bits, pack4(u, d.bits));
+  }
+}
+
+__global__ void unpack_kernel(LatticeDesc d, uint8_t* bytes, int byte_pitch) {
+  const int groups = (d.L + 3) / 4;
+  const size_t total = (size_t)d.H * groups;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(k / groups), c0 = 4 * (int)(k % groups);
+    const uint32_t u = unpack4(load_group(d.lat + (size_t)row * d.pitch, c0, d.bits), d.bits);
+    uint8_t* dst = bytes + (size_t)row * byte_pitch + c0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (c0 + e < d.L) dst[e] = (uint8_t)(u >> (8 * e));
   }
 }
 
@@ -55,14 +94,14 @@ __global__ void init_kernel(LatticeDesc d, uint64_t T_empty) {
 // also *stop = 1, so that the kernels that follow on the stream leave the
 // lattice alone.
 __global__ void validate_kernel(LatticeDesc d, uint32_t* bad, uint32_t flag, uint32_t* stop) {
-  const int L = d.L, pitch = d.pitch, vec_per_row = pitch / 16;
+  const int L = d.L, vec_per_row = (L + 15) / 16;
   const uint32_t lim = 0x7Fu - (uint32_t)d.S;  // byte + lim has bit 7 set iff byte > S (byte < 128)
   const size_t total = (size_t)d.H * vec_per_row;
   uint32_t any = 0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
        k += (size_t)gridDim.x * blockDim.x) {
     const int row = (int)(k / vec_per_row), q = (int)(k % vec_per_row);
-    uint4 w = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)row * pitch) + q);
+    uint4 w = load16(d, (uint32_t)row, (uint32_t)q);
     uint32_t* p = reinterpret_cast<uint32_t*>(&w);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -147,6 +186,7 @@ __global__ void finalize_kernel(RunState* st, int S, LogBuffers lb, uint32_t m_e
 __global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st, uint32_t m, int slot) {
   if (ld_volatile(&st->stopped)) return;
   __shared__ VisitSmem sm;
+  __shared__ uint16_t stash[kStashWords];
   load_trans(d, sm.trans);
   const uint4 x = philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1);
   const int colour = order_at(colour_order(x.x, d.perm24), slot);
@@ -155,7 +195,7 @@ __global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st,
   if (d.uniform64)
     visit_uniform(d, bx, by, m, sm);
   else
-    visit_generic(d, bx, by, m, sm);
+    visit_generic(d, bx, by, m, sm, stash);
 }
 
 // ---------------------------------------------------------------------------
@@ -172,6 +212,7 @@ template <bool UNI>
 __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
     persistent_kernel(PersistentArgs a) {
   __shared__ VisitSmem sm;
+  __shared__ uint16_t stash[UNI ? 1 : kStashWords];
   __shared__ uint32_t s_item, s_ord, s_quit, s_abort;
   const LatticeDesc& d = a.d;
   RunState* st = a.st;
@@ -251,7 +292,7 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
       if (UNI)
         visit_uniform<false>(d, bx, by, m, sm);
       else
-        visit_generic<false>(d, bx, by, m, sm);
+        visit_generic<false>(d, bx, by, m, sm, stash);
       const bool log_point = a.fuse_counts && ((m + 1u) % a.log_every) == 0u;
       if (log_point) {
         const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1),
@@ -1088,8 +1129,20 @@ static inline int blocks_for(size_t n, int threads, int cap) {
 }
 
 cudaError_t launch_init(const LatticeDesc& d, uint64_t T_empty, cudaStream_t stream) {
-  const size_t n = (size_t)d.H * d.pitch;
+  const size_t n = (size_t)d.H * (d.pitch * 2 / d.bits);
   init_kernel<<<blocks_for(n, 256, 152 * 32), 256, 0, stream>>>(d, T_empty);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const LatticeDesc& d, const uint8_t* bytes, int byte_pitch, cudaStream_t stream) {
+  const size_t n = (size_t)d.H * ((d.L + 3) / 4);
+  pack_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, bytes, byte_pitch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const LatticeDesc& d, uint8_t* bytes, int byte_pitch, cudaStream_t stream) {
+  const size_t n = (size_t)d.H * ((d.L + 3) / 4);
+  unpack_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, bytes, byte_pitch);
   return cudaGetLastError();
 }
 
@@ -1100,7 +1153,7 @@ cudaError_t launch_fill_u32(uint32_t* p, int n, uint32_t value, cudaStream_t str
 
 cudaError_t launch_validate(const LatticeDesc& d, uint32_t* bad, uint32_t flag, uint32_t* stop,
                             cudaStream_t stream) {
-  const size_t n = (size_t)d.H * (d.pitch / 16);
+  const size_t n = (size_t)d.H * ((d.L + 15) / 16);
   validate_kernel<<<blocks_for(n, 256, 152 * 8), 256, 0, stream>>>(d, bad, flag, stop);
   return cudaGetLastError();
 }
@@ -1111,7 +1164,7 @@ cudaError_t launch_state_reset(RunState* st, uint32_t mcs, uint32_t log_num0, cu
 }
 
 cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream) {
-  const size_t n = (size_t)d.H * (d.pitch / 16);
+  const size_t n = (size_t)d.H * ((d.L + 15) / 16);
   count_kernel<<<blocks_for(n, 256 * 4, 152 * 4), 256, 0, stream>>>(d, st);
   return cudaGetLastError();
 }

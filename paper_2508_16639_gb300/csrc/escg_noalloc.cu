@@ -205,6 +205,7 @@ extern "C" int escg_run_noalloc(uint8_t* d_lattice, int32_t L, int32_t S, const 
   d.fcy = d.fc;
   d.ax = make_axis_geom(L, P);
   d.ay = d.ax;
+  d.bits = 8;
   d.trans = scratch + kNoallocTransOff;
   d.key0 = (uint32_t)seed;
   d.key1 = (uint32_t)(seed >> 32);

@@ -51,7 +51,7 @@ inline AxisGeom make_axis_geom(int n, int P) {
 
 // Everything a kernel needs to know about one lattice.
 struct LatticeDesc {
-  uint8_t* lat;         // H rows of `pitch` bytes, values 0..S
+  uint8_t* lat;         // H rows of `pitch` bytes, site values 0..S
   int32_t L, pitch;     // columns, row stride in bytes
   int32_t H;            // rows (L for a square lattice)
   int32_t P, GQ;        // coarse and fine segments along the columns
@@ -79,6 +79,8 @@ struct LatticeDesc {
   int32_t uniform64;    // all blocks 64x64 and all sub-blocks 2x2
   int32_t nbh;          // neighbourhood: 4 (von Neumann) or 8 (Moore)
   int32_t reflect;      // 1: reflecting boundary, 0: periodic
+  int32_t bits;         // bits per site in `lat`: 8 (one byte) or 4, 2 (packed
+                        // rows: site c at bits [c*bits, (c+1)*bits), little endian)
   uint8_t perm24[24];   // the 24 colour orders, lexicographic (4 x 2 bits)
 };
 
