@@ -19,11 +19,12 @@ exchange = 2 M N with M = 1e-4), counts logged every 10 MCS.  One step =
             instructions per launch / its event-timed launch duration
             against the GPU's integer-issue peak;
   cpu_baseline  the CPU replay oracle (single thread) on a bounded sample;
-  ensemble, serving, park, variants  batched runs (A7), a request stream
+  ensemble, serving, park, variants, packed  batched runs (A7), a request stream
             (A8), the probabilistic-dominance ensemble and the benchmark
             lattice under the Moore / reflecting rule variants, as
-            rectangles of the same N, and the RPSLS L = 800 workload, each
-            with its own metric.
+            rectangles of the same N, and the RPSLS L = 800 workload;
+            packed: bit-packed lattices (2 bits per site) against one byte per
+            site at L = 3200 and 12800; each with its own metric.
 
 `--impl reference` times the CPU oracle itself (the reference arm of this
 tier) on the same metric and workload.  Multi-GPU (torchrun): replicas only,
@@ -98,6 +99,8 @@ def _parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-park", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-packed", action="store_true")
+    ap.add_argument("--packed-steps", type=int, default=100)
     ap.add_argument("--variant-steps", type=int, default=100)
     ap.add_argument("--park-per-point", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -326,6 +329,45 @@ def _variants(args, rank, w):
     return out
 
 
+def _packed(args, rank, w):
+    """Bit-packed device lattices: the benchmark lattice and one 4x larger
+    (L = 12800: 164 MB with one byte per site, more than the 129 MB L2; 41 MB
+    with 2 bits per site) with 8 and 2 bits per site, device time per 10-MCS
+    step, L2 flushed before each step."""
+    import torch
+    import paper_2508_16639_gb300 as E
+    from paper_2508_16639_gb300 import replicas as R
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for L, steps in ((w.L, args.packed_steps), (4 * w.L, max(3, args.packed_steps // 8))):
+        N = L * L
+        X = E.exchange_from_mobility(w.mobility, N)
+        for bits in (8, 2):
+            stream = torch.cuda.Stream()
+            g = E.Lattice(L, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X),
+                          R.replica_seed(w.seed, rank), p_empty=w.p_empty, log_every=w.log_every, stream=stream,
+                          bits_per_site=bits)
+            for _ in range(3):
+                g.run(10)
+            g.sync()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            for a, b in ev:
+                with torch.cuda.stream(stream):
+                    flush.fill_(1)
+                a.record(stream)
+                g.run(10)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+            out[f"L{L}_bits{bits}"] = {"site_updates_per_s": 10 * N / (ms * 1e-3), "ms_per_10_mcs": ms,
+                                       "device_bytes": E.lattice_bytes(L, L, bits), "kernel": g.update_kernel,
+                                       "steps": steps}
+            g.close()
+    out["config"] = {"workload": f"{w.name} and the same rates at 4x the side, 8 and 2 bits per site"}
+    return out
+
+
 def _serving(args, rank):
     """Serving: Poisson arrivals of run requests (L log-uniform [50,1600],
     S in {3,5}, budgets log-uniform 10^2-10^4 MCS, half stop at extinction),
@@ -449,6 +491,9 @@ def main():
     park = None
     if not args.no_park:
         park = _park(args, rank)
+    packed = None
+    if not args.no_packed:
+        packed = _packed(args, rank, w)
     variants = None
     if not args.no_variants:
         variants = _variants(args, rank, w)
@@ -466,7 +511,7 @@ def main():
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": _config(w, mps), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks,
-                "ensemble": ensemble, "serving": serving, "park": park, "variants": variants,
+                "ensemble": ensemble, "serving": serving, "park": park, "variants": variants, "packed": packed,
                 "context": {"paper_cuda_ms_L3200_site_updates_per_s": 2.45e8,
                             "paper_hardware": "RTX A2000 (not a target)"}}
         print(json.dumps(line), flush=True)
