@@ -77,6 +77,12 @@ typedef struct {
                                     TMA producer warp (warp-specialised);
                                     3: persistent, epoch flags only (no
                                     mailbox kernel);
+                                    4: whole-lattice residency: one CTA keeps
+                                    the lattice in shared memory for the
+                                    whole launch (lattices with at most 8
+                                    coarse blocks per axis whose image fits
+                                    one CTA's shared memory, about 470 x 470;
+                                    larger ones run as 3);
                                     0: one launch per coarse phase            */
     void* cuda_stream;           /* cudaStream_t to enqueue on, or NULL for a
                                     stream owned by the handle                */
@@ -241,6 +247,13 @@ typedef struct {
     int32_t threads;              /* CTA size 64, 128 or 256; 0: autotune        */
     int32_t use_graph;            /* capture chunk sequences in a CUDA graph     */
     void* cuda_stream;            /* cudaStream_t or NULL (library-owned)        */
+    int32_t resident;             /* 1: replicas whose lattice fits one CTA's
+                                     shared memory (L up to about 470) run with
+                                     the whole lattice resident there for each
+                                     chunk; 0 (default, faster on GB300 for
+                                     every size measured): every replica in the
+                                     block-by-block chunk kernel.  Results are
+                                     identical.                                   */
 } escg_batch_options;
 
 typedef struct escg_batch escg_batch_t;

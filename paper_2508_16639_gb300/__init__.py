@@ -64,8 +64,9 @@ class Lattice:
     storage; stream: optional torch.cuda.Stream (or raw cudaStream_t int).
     persistent: 1 persistent dataflow launches (default; uniform 64x64
     partitions use the boundary-mailbox kernel where it is faster), 3 the
-    same with epoch flags only, 2 with a TMA producer warp, 0 one launch per
-    coarse phase -- all bit-identical.  dominance_prob: optional S x S edge
+    same with epoch flags only, 2 with a TMA producer warp, 4 the whole
+    lattice resident in one CTA's shared memory (small lattices; larger ones
+    run as 3), 0 one launch per coarse phase -- all bit-identical.  dominance_prob: optional S x S edge
     probabilities (Park, Chen and Szolnoki's probabilistic dominance);
     neighbourhood 4 or 8 (Moore) and reflecting_boundary: the paper's rule
     variants.  H: rows (default L).  bits_per_site: device storage, 8 (one
@@ -244,10 +245,13 @@ class Batch:
     """An ensemble of independent replicas run together on the GPU (a batch
     handle of the C ABI).  specs: sequence of dicts with keys L, S, digraph,
     rates (interact, reproduce, exchange), seed, p_empty, max_mcs,
-    stop_at_extinction.  threads: CTA size (64/128/256) or 0 to autotune."""
+    stop_at_extinction.  threads: CTA size (64/128/256) or 0 to autotune.
+    resident: replicas that fit one CTA's shared memory keep their whole
+    lattice there for each chunk (default False: the block-by-block chunk
+    kernel, faster for every size measured)."""
 
     def __init__(self, specs, log_every: int = 10, threads: int = 0, use_graph: bool = True,
-                 stream=None):
+                 stream=None, resident: bool = False):
         lib = load()
         self.n = len(specs)
         self._digraphs = []
@@ -263,6 +267,7 @@ class Batch:
         opt.log_every = int(log_every)
         opt.threads = int(threads)
         opt.use_graph = int(bool(use_graph))
+        opt.resident = int(bool(resident))
         if stream is not None:
             opt.cuda_stream = int(getattr(stream, "cuda_stream", stream))
         h = lib.escg_batch_create(self.n, arr, C.byref(opt))

@@ -38,7 +38,7 @@ class ReplicaSpec(C.Structure):
 
 class BatchOptions(C.Structure):
     _fields_ = [("log_every", C.c_uint32), ("threads", C.c_int32), ("use_graph", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("resident", C.c_int32)]
 
 
 class ServerOptions(C.Structure):

@@ -240,6 +240,7 @@ struct escg {
   uint64_t T_empty = 0;
   int grid = 0;
   bool use_tma = false;
+  bool use_resident = false;     // persistent = 4 and the lattice fits one CTA's shared memory
   CUtensorMap tmap{};
   uint32_t spin_limit = kDefaultSpinLimit;
   int stall_block = -1;
@@ -512,8 +513,8 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     set_err("device_lattice must be 16-byte aligned (rows are read as 16-byte vectors)");
     return nullptr;
   }
-  if (o.persistent < 0 || o.persistent > 3) {
-    set_err("persistent must be 0..3 (got %d)", o.persistent);
+  if (o.persistent < 0 || o.persistent > 4) {
+    set_err("persistent must be 0..4 (got %d)", o.persistent);
     return nullptr;
   }
   if (o.schedule_version != 0 && o.schedule_version != 1) {
@@ -684,6 +685,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     h->use_ll = true;
     h->grid = persistent_ll_grid(h->device);
   }
+  if (o.persistent == 4 && resident_fits(d, h->device)) h->use_resident = true;
   if (o.ctas_per_sm > 0) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -719,7 +721,8 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
   }
   const uint32_t k = h->opt.log_every;
   // rule variants count log points with the count kernel between launches
-  const bool fused = h->desc.nbh == 4 && !h->desc.reflect;
+  // (the resident kernel counts in-kernel for every rule)
+  const bool fused = (h->desc.nbh == 4 && !h->desc.reflect) || h->use_resident;
   while (h->mcs_enq < target) {
     uint64_t end;
     if (h->opt.persistent && !h->opt.stop_at_extinction && fused) {
@@ -753,7 +756,9 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
       a.ob = h->d_ob;
       a.fuse_counts = fused ? 1 : 0;
       CUDA_TRY(timing_begin(h));
-      if (h->use_tma) {
+      if (h->use_resident) {
+        CUDA_TRY(launch_resident(a, h->stream));
+      } else if (h->use_tma) {
         TmaArgs ta{};
         ta.map = h->tmap;
         ta.p = a;
@@ -992,6 +997,7 @@ int32_t escg_coarse_blocks(escg_t* h) { return h ? h->part.P : 0; }
 const char* escg_update_kernel(escg_t* h) {
   if (!h) return "";
   if (!h->opt.persistent) return "phase_kernel";
+  if (h->use_resident) return "resident_kernel";
   if (h->use_tma) return "persistent_tma_kernel";
   return h->use_ll ? "persistent_ll_kernel" : "persistent_kernel";
 }

@@ -34,6 +34,7 @@
 #include "escg.h"
 #include "escg_device.cuh"
 #include "escg_internal.h"
+#include "escg_resident.cuh"
 #include "escg_tma.cuh"
 
 namespace escg_impl {
@@ -43,8 +44,8 @@ struct SlotDesc {
   uint32_t* done;       // [P*P] absolute epochs
   uint32_t max_mcs;     // budget: absolute MCS number to stop at
   int32_t stop_at_extinction;
-  int32_t nb4;          // blocks per coarse phase = P*P/4
-  int32_t pad;
+  int32_t nb4;          // blocks per coarse phase = P*P/4 in the chunk kernel's table (0: resident)
+  int32_t rclass;       // 0: chunk kernel; 1..3: whole-lattice residency class
 };
 
 struct SlotState {
@@ -60,7 +61,8 @@ struct BatchCtl {
   uint32_t n_active, tot4, chunk, ticket;
   uint32_t exited, error, abort, n_admit;
   uint32_t last_chunk;  // MCS the previous batch_kernel launch covered
-  uint32_t pad[7];
+  uint32_t res_ticket[3];  // dispensers of the resident kernels (classes 1..3)
+  uint32_t pad[4];
 };
 
 struct BatchArgs {
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(kCompactThreads) batch_compact_kernel(const Sl
     ctl->ticket = 0;
     ctl->exited = 0;
     ctl->n_admit = 0;
+    ctl->res_ticket[0] = ctl->res_ticket[1] = ctl->res_ticket[2] = 0;
     ctl->last_chunk = 0;   // consumed; the next batch_kernel launch sets it
   }
 }
@@ -309,6 +312,80 @@ __global__ void __launch_bounds__(THREADS) batch_kernel(BatchArgs a) {
       ctl->exited = 0;
       ctl->last_chunk = chunk;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Whole-lattice residency for replicas that fit one CTA's shared memory
+// (escg_resident.cuh).  Classes by image size, so that small replicas share
+// an SM: 1 up to kResBytes1 (128 threads), 2 up to kResBytes2 (256), 3 up to
+// the device's per-CTA limit (1024).  CTAs take the active replicas of their
+// class from a dispenser and run each one's chunk from its lattice in
+// shared memory: no work table, no epochs, no waits; the chunk's final MCS
+// (a log point) sets the replica's counts and stasis exactly as the chunk
+// kernel's last block does.
+constexpr int kResBytes1 = 16 * 1024, kResBytes2 = 56 * 1024;
+constexpr int kResThreads[4] = {0, 128, 256, 1024};
+
+// 64 registers a thread (8, 4 and 1 CTAs per SM for the three classes).
+template <int THREADS, int CLASS>
+__global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64)) batch_resident_kernel(BatchArgs a,
+                                                                                          const uint32_t* active) {
+  extern __shared__ __align__(16) uint8_t res_dyn[];
+  __shared__ ResidentSmem rs;
+  __shared__ SlotDesc sd;
+  __shared__ uint32_t s_slot, s_quit;
+  BatchCtl* ctl = a.ctl;
+  const int tid = threadIdx.x;
+  const uint32_t n_active = ctl->n_active, chunk = ctl->chunk;
+  for (;;) {
+    if (tid == 0) {
+      uint32_t quit = 0, s = 0;
+      for (;;) {
+        const uint32_t t = atomicAdd(&ctl->res_ticket[CLASS - 1], 1u);
+        if (t >= n_active || b_ld_volatile(&ctl->abort)) {
+          quit = 1;
+          break;
+        }
+        s = active[t];
+        if (a.slots[s].rclass == CLASS) break;
+      }
+      s_slot = s;
+      s_quit = quit;
+    }
+    __syncthreads();
+    if (s_quit) break;
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(a.slots + s_slot);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&sd);
+      for (int w = tid; w < (int)(sizeof(SlotDesc) / 4); w += THREADS) dst[w] = src[w];
+    }
+    __syncthreads();
+    const LatticeDesc& d = sd.d;
+    SlotState* st = a.states + s_slot;
+    const uint32_t m0 = st->mcs;
+    const uint32_t m_end = min(m0 + chunk, sd.max_mcs);
+    if (m0 >= m_end) continue;   // uniform: every thread read the same words
+    const int sp = resident_pitch(d.L);
+    uint8_t* img = res_dyn;
+    uint8_t* snap = res_dyn + (d.H + 2) * sp;
+    load_trans(d, rs.trans);
+    resident_load(d, img, sp);
+    __syncthreads();
+    resident_run(d, img, sp, snap, rs, m0, m_end, a.log_every, [&](uint32_t mm, const uint32_t* hist) {
+      int alive = 0;
+      for (int v = 0; v < kMaxStates; ++v) {
+        const unsigned long long c = (v <= d.S) ? hist[v] : 0ull;
+        st->counts[v] = c;
+        if (v >= 1 && v <= d.S && c > 0) ++alive;
+      }
+      st->counts_mcs = mm;
+      const bool stop = sd.stop_at_extinction && alive <= 1;
+      if (stop) st->stopped = 1;
+      return stop;
+    });
+    resident_store(d, img, sp);
+    __syncthreads();
   }
 }
 
@@ -786,6 +863,9 @@ struct Engine {
   std::vector<size_t> slot_off, slot_bytes;
   std::vector<uint32_t> pending_admit;
   int grid[3] = {0, 0, 0};
+  bool resident = false;          // whole-lattice residency for replicas that fit
+  int res_bytes3 = 0;             // dynamic shared memory of class 3
+  int grid_res[4] = {0, 0, 0, 0};
   uint64_t launches = 0;
   cudaGraphExec_t graph = nullptr;
   uint32_t spin_limit = 2000000;
@@ -814,6 +894,17 @@ cudaError_t launch_batch_kernel(Engine* e, int threads) {
     batch_kernel<128><<<g, 128, 0, e->stream>>>(a);
   else
     batch_kernel<256><<<g, 256, 0, e->stream>>>(a);
+  return cudaGetLastError();
+}
+
+// The resident kernels of the three classes (CTAs of a class with no
+// replica leave at once).
+cudaError_t launch_resident_kernels(Engine* e) {
+  if (!e->resident) return cudaSuccess;
+  BatchArgs a{e->d_slots, e->d_states, e->d_ctl, e->d_table, e->log_every, e->spin_limit};
+  batch_resident_kernel<128, 1><<<e->grid_res[1], 128, kResBytes1, e->stream>>>(a, e->d_active);
+  batch_resident_kernel<256, 2><<<e->grid_res[2], 256, kResBytes2, e->stream>>>(a, e->d_active);
+  batch_resident_kernel<1024, 3><<<e->grid_res[3], 1024, e->res_bytes3, e->stream>>>(a, e->d_active);
   return cudaGetLastError();
 }
 
@@ -896,6 +987,23 @@ int engine_init(Engine* e, int max_slots, size_t arena_bytes, size_t table_cap, 
   e->grid_tma[1] = sms * (per < 1 ? 1 : per);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_tma_kernel<256>, 256 + 32, 0);
   e->grid_tma[2] = sms * (per < 1 ? 1 : per);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->device);
+  e->res_bytes3 = optin - (int)(sizeof(ResidentSmem) + sizeof(SlotDesc)) - 256;
+  cudaFuncSetAttribute(batch_resident_kernel<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kResBytes1);
+  cudaFuncSetAttribute(batch_resident_kernel<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kResBytes2);
+  if (cudaFuncSetAttribute(batch_resident_kernel<1024, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           e->res_bytes3) != cudaSuccess)
+    e->res_bytes3 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_resident_kernel<128, 1>, 128, kResBytes1);
+  e->grid_res[1] = sms * (per < 1 ? 1 : per);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_resident_kernel<256, 2>, 256, kResBytes2);
+  e->grid_res[2] = sms * (per < 1 ? 1 : per);
+  per = 0;
+  if (e->res_bytes3 > 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_resident_kernel<1024, 3>, 1024, e->res_bytes3);
+  e->grid_res[3] = sms * (per < 1 ? 1 : per);
+  cudaGetLastError();
   return ESCG_OK;
 }
 
@@ -957,6 +1065,13 @@ int engine_add(Engine* e, const escg_replica_spec& sp, const SlotPlan& pl, int s
   sd.max_mcs = (uint32_t)sp.max_mcs;
   sd.stop_at_extinction = sp.stop_at_extinction ? 1 : 0;
   sd.nb4 = p.P * p.P / 4;
+  // whole-lattice residency class by the size of the shared-memory image (when
+  // enabled)
+  if (e->resident && p.P <= 8) {
+    const int bytes = resident_dyn_bytes(sp.L, sp.L);
+    sd.rclass = bytes <= kResBytes1 ? 1 : (bytes <= kResBytes2 ? 2 : (bytes <= e->res_bytes3 ? 3 : 0));
+    if (sd.rclass) sd.nb4 = 0;   // not in the chunk kernel's table
+  }
   CUtensorMap map;
   if (!encode_lattice_map(&map, d.lat, d.L, d.pitch, kBSP, kBRows)) {
     e->arena.release(off, pl.bytes);
@@ -1019,12 +1134,15 @@ int engine_flush_admits(Engine* e) {
   return ESCG_OK;
 }
 
+// One chunk: compaction, the resident kernels, then the chunk kernel (whose
+// last CTA records how far the launch advanced the replicas).
 int engine_chunk(Engine* e, int threads) {
-  if (launch_compact(e) != cudaSuccess || launch_batch_kernel(e, threads) != cudaSuccess) {
+  if (launch_compact(e) != cudaSuccess || launch_resident_kernels(e) != cudaSuccess ||
+      launch_batch_kernel(e, threads) != cudaSuccess) {
     set_last_error("chunk launch failed");
     return ESCG_ECUDA;
   }
-  e->launches += 2;
+  e->launches += e->resident ? 5 : 2;
   return ESCG_OK;
 }
 
@@ -1066,6 +1184,7 @@ int engine_build_graph(Engine* e) {
   }
   for (int c = 0; c < Engine::kGraphChunks; ++c) {
     launch_compact(e);
+    launch_resident_kernels(e);
     launch_batch_kernel(e, e->threads);
   }
   if (cudaStreamEndCapture(e->stream, &g) != cudaSuccess || cudaGraphInstantiate(&e->graph, g, 0) != cudaSuccess) {
@@ -1108,7 +1227,7 @@ int engine_run(Engine* e, uint64_t chunks, bool until_idle) {
         set_last_error("graph launch failed");
         return ESCG_ECUDA;
       }
-      e->launches += 2 * G;
+      e->launches += (e->resident ? 5 : 2) * G;
       left = left >= G ? left - G : 0;
       group = true;
     } else {
@@ -1164,6 +1283,7 @@ void escg_batch_default_options(escg_batch_options* opt) {
   opt->log_every = 10;
   opt->threads = 0;
   opt->use_graph = 1;
+  opt->resident = 0;
 }
 
 escg_batch_t* escg_batch_create(int32_t n, const escg_replica_spec* specs, const escg_batch_options* opt) {
@@ -1189,6 +1309,7 @@ escg_batch_t* escg_batch_create(int32_t n, const escg_replica_spec* specs, const
     delete b;
     return nullptr;
   }
+  b->e.resident = o.resident != 0;
   for (int i = 0; i < n; ++i) {
     if (engine_add(&b->e, specs[i], plans[i], i) != ESCG_OK) {
       engine_free(&b->e);

@@ -630,7 +630,7 @@ __device__ __forceinline__ uint4 load16(const LatticeDesc& d, uint32_t row, uint
 // state.  Every lane of the calling warps must call.
 __device__ __forceinline__ void count_vectors(const LatticeDesc& d, uint32_t start, uint32_t stride,
                                               uint32_t* part) {
-  const int L = d.L, pitch = d.pitch, S = d.S;
+  const int L = d.L, S = d.S;
   const uint32_t vec_per_row = (uint32_t)(L + 15) / 16u;
   const uint32_t total = (uint32_t)d.H * vec_per_row;   // < 2^32 for L, H <= 16384
   uint32_t c[kMaxStates];

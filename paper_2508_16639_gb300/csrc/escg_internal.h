@@ -87,6 +87,11 @@ cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t st
 // Occupancy-derived grid size of the persistent kernel for a lattice.
 int persistent_grid(int device, bool uniform);
 
+// Whole-lattice residency: one CTA runs MCS [m_begin, m_begin + n_mcs) with
+// the lattice in shared memory (counts of log points written in-kernel).
+bool resident_fits(const LatticeDesc& d, int device);
+cudaError_t launch_resident(const PersistentArgs& a, cudaStream_t stream);
+
 // Uniform geometry, boundary-mailbox variant (the default persistent path):
 // a visit publishes its four boundary records (edge line + rim line per
 // side, 4 lattice bytes and the epoch per 8-byte word) and only its interior

@@ -15,6 +15,7 @@
 #include <cstdio>
 
 #include "escg_device.cuh"
+#include "escg_resident.cuh"
 #include "escg_internal.h"
 #include "escg_tma.cuh"
 
@@ -1119,6 +1120,53 @@ __global__ void __launch_bounds__(kTmaThreads, 4) persistent_tma_kernel(const __
       if (!st->stopped && !st->abort) st->mcs = a.p.m_begin + a.p.n_mcs;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Whole-lattice residency (escg_resident.cuh): one CTA holds the lattice in
+// shared memory for the whole launch; counts of log points and the MCS
+// number are written in-kernel.
+constexpr int kResThreads = 1024;
+__global__ void __launch_bounds__(kResThreads) resident_kernel(PersistentArgs a) {
+  extern __shared__ __align__(16) uint8_t res_dyn[];
+  __shared__ ResidentSmem rs;
+  const LatticeDesc& d = a.d;
+  RunState* st = a.st;
+  if (ld_volatile(&st->stopped)) return;
+  const int sp = resident_pitch(d.L);
+  uint8_t* img = res_dyn;
+  uint8_t* snap = res_dyn + (d.H + 2) * sp;
+  load_trans(d, rs.trans);
+  resident_load(d, img, sp);
+  __syncthreads();
+  const uint32_t m_end = a.m_begin + a.n_mcs;
+  resident_run(d, img, sp, snap, rs, a.m_begin, m_end, a.log_every, [&](uint32_t mm, const uint32_t* hist) {
+    unsigned long long c[kMaxStates];
+    for (int v = 0; v < kMaxStates; ++v) c[v] = hist[v];
+    write_log_entry(st, a.lb, d.S, mm, a.log_every, c, a.stop_at_extinction);
+    return st->stopped != 0u;
+  });
+  resident_store(d, img, sp);
+  if (threadIdx.x == 0 && !st->stopped) st->mcs = m_end;
+}
+
+// Largest dynamic shared memory a resident launch may use on this device.
+int resident_max_dyn_bytes(int device) {
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  return optin - (int)sizeof(ResidentSmem) - 256;
+}
+
+bool resident_fits(const LatticeDesc& d, int device) {
+  return d.P <= 8 && d.Py <= 8 && resident_dyn_bytes(d.L, d.H) <= resident_max_dyn_bytes(device);
+}
+
+cudaError_t launch_resident(const PersistentArgs& a, cudaStream_t stream) {
+  const int bytes = resident_dyn_bytes(a.d.L, a.d.H);
+  cudaError_t e = cudaFuncSetAttribute(resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  resident_kernel<<<1, kResThreads, bytes, stream>>>(a);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

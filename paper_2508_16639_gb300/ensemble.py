@@ -12,10 +12,10 @@ from . import Batch, Lattice, circulant
 from .serve import request_spec
 
 
-def run_batch(reps, log_every: int = 10, threads: int = 0, use_graph: bool = True) -> dict:
+def run_batch(reps, log_every: int = 10, threads: int = 0, use_graph: bool = True, resident: bool = False) -> dict:
     specs = [request_spec(r) for r in reps]
     t0 = time.perf_counter()
-    b = Batch(specs, log_every=log_every, threads=threads, use_graph=use_graph)
+    b = Batch(specs, log_every=log_every, threads=threads, use_graph=use_graph, resident=resident)
     t1 = time.perf_counter()
     b.run()
     mcs, ext, _ = b.status()

@@ -95,3 +95,32 @@ def test_batch_single_replica_and_immediate_extinction():
     b.run()
     mcs, ext, cnt = b.status()
     assert mcs[0] == 0 and ext[0] and cnt[0, 0] == 256
+
+
+def test_batch_resident_classes_match_chunk_kernel():
+    """Replicas of every whole-lattice residency class (L 8..131, 200,
+    448) next to ones that stay in the block-by-block chunk kernel (L 600):
+    the same lattices, MCS numbers, counts and extinction flags with
+    residency on and off, and the oracle for a sample."""
+    specs = _specs(n=10, seed=21)
+    rng = np.random.default_rng(5)
+    for i, L in enumerate([448, 600, 448, 600]):
+        S = 3
+        specs.append(dict(L=L, S=S, K=(1,), digraph=O.circulant(S, (1,)), rates=(1.0, 1.0, 2e-4 * L * L),
+                          seed=0x5EED7000 + i, p_empty=0.25, max_mcs=int(rng.integers(12, 40)),
+                          stop_at_extinction=False))
+    a = E.Batch(specs, log_every=10, threads=128, resident=True)
+    a.run()
+    c = E.Batch(specs, log_every=10, threads=128, resident=False)
+    c.run()
+    ma, ea, ca = a.status()
+    mc, ec, cc = c.status()
+    assert np.array_equal(ma, mc) and np.array_equal(ea, ec) and np.array_equal(ca, cc)
+    for i in range(len(specs)):
+        assert np.array_equal(a.snapshot(i), c.snapshot(i)), i
+    for i in (0, 3, len(specs) - 4):
+        sp = specs[i]
+        o = O.init(sp["L"], sp["S"], sp["p_empty"], sp["seed"])
+        lat, log, mend = O.run_observed(o, sp["digraph"], *sp["rates"], sp["seed"], sp["max_mcs"],
+                                        log_every=10, stop_at_extinction=sp["stop_at_extinction"])
+        assert ma[i] == mend and np.array_equal(a.snapshot(i), lat), i
