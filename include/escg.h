@@ -72,7 +72,9 @@ typedef struct {
     uint32_t schedule_version;   /* 0 or 1 (only version 1 exists)            */
     int32_t persistent;          /* 1: persistent dataflow launches (default;
                                     uniform 64x64 partitions use the boundary-
-                                    mailbox kernel where it is faster);
+                                    mailbox kernel where it is faster, generic
+                                    partitions of 2 x 2 coarse blocks the
+                                    whole-lattice residency of 4);
                                     2: same, uniform partitions staged by a
                                     TMA producer warp (warp-specialised);
                                     3: persistent, epoch flags only (no

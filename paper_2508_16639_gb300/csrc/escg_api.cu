@@ -685,7 +685,14 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     h->use_ll = true;
     h->grid = persistent_ll_grid(h->device);
   }
-  if (o.persistent == 4 && resident_fits(d, h->device)) h->use_resident = true;
+  // Whole-lattice residency: on request (4), and by default (1) for a generic
+  // partition with 2 x 2 coarse blocks (L, H < 192 and not 128), where it was
+  // measured 1.4-2.2x faster than the flag kernel's dependency chain of
+  // generic visits (tied at L = 200, slower beyond; the mailbox kernel is
+  // faster for the uniform L = 128).
+  if ((o.persistent == 4 || (o.persistent == 1 && !d.uniform64 && p.P == 2 && py.P == 2)) &&
+      resident_fits(d, h->device))
+    h->use_resident = true;
   if (o.ctas_per_sm > 0) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);

@@ -99,3 +99,15 @@ def test_resident_fallback_for_large_lattices():
     g.run(2)
     o, _ = O.replay_run(O.init(800, 3, 0.0, 1), D, 1.0, 1.0, 2.0, 1, 2)
     assert np.array_equal(g.snapshot(), o)
+
+
+@pytest.mark.parametrize("L,H,expect", [(100, 100, "resident_kernel"), (64, 150, "resident_kernel"),
+                                        (128, 128, "persistent_ll_kernel"), (200, 200, "persistent_kernel")])
+def test_default_kernel_choice(L, H, expect):
+    """persistent = 1 picks residency for generic 2 x 2-block partitions."""
+    D = O.circulant(3, (1,))
+    g = E.Lattice(L, 3, D, (1.0, 1.0, 2.0), 11, p_empty=0.2, H=H)
+    assert g.update_kernel == expect
+    g.run(3)
+    o, _ = O.replay_run(O.init(L, 3, 0.2, 11, H=H), D, 1.0, 1.0, 2.0, 11, 3)
+    assert np.array_equal(g.snapshot(), o)
