@@ -61,12 +61,13 @@ ALG_INT_INSTR_PER_ATTEMPT = 24
 # DRAM traffic of persistent_kernel from one ncu capture (bytes per launch of
 # a 10-MCS chunk at L = 3200), valid only for that kernel and workload and the
 # kernel sources it was taken from (hash below); None otherwise.
-NCU_TRAFFIC = {"sources_sha1": "b23e32e22183e951cfe01d02ba084c38fd50b17b", "bytes_per_launch": 10300160 + 2254848,
+NCU_TRAFFIC = {"sources_sha1": "f5d70089ad39ebd25284c6614bb5b2602a7f1d2f", "bytes_per_launch": 10308352 + 2273792,
                "kernel": "persistent_kernel", "L": 3200, "mcs_per_launch": 10,
                "profile": "profiles/persistent_kernel_L3200_M1e-4.md"}
 
 
-KERNEL_SOURCES = ("escg_kernels.cu", "escg_device.cuh", "escg_types.h", "escg_internal.h", "escg_tma.cuh")
+KERNEL_SOURCES = ("escg_kernels.cu", "escg_device.cuh", "escg_types.h", "escg_internal.h", "escg_tma.cuh",
+                  "escg_resident.cuh")
 
 
 def _sources_sha1() -> str:
