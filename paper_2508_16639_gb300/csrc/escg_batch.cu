@@ -587,18 +587,20 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
     const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans[b]);
     const uint32_t m = it.m, ord = it.ord, s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
     const int xoff = it.xoff, bw = it.bw, bh = it.bh, hx = it.Qx >> 1, nquads = hx * (it.Qy >> 1);
+    const uint32_t inv_hx = (65536u + (uint32_t)hx - 1u) / (uint32_t)hx;   // q / hx exact for q < 2^16 / hx
     if (tid < kMaxStates) sm.hist[tid] = 0;
     for (int fi = 0; fi < 4; ++fi) {
       const int fcol = order_at(it.forder, fi);
       const int cx = fcol & 1, cy = fcol >> 1;
       for (int q = tid; q < nquads; q += CONS) {
-        const int qy = q / hx, qx = q - qy * hx;
+        const int qy = (int)(((uint32_t)q * inv_hx) >> 16), qx = q - qy * hx;
         const int fx = 2 * qx + cx, fy = 2 * qy + cy;
         const int sx = it.fsx[fx], wx = it.fsx[fx + 1] - sx;
         const int sy = it.fsy[fy], wy = it.fsy[fy + 1] - sy;
         const uint32_t nk = (uint32_t)(wx * wy), n4 = 4u * nk;
         const uint32_t g = (uint32_t)(it.fy0 + fy) * (uint32_t)d.GQ + (uint32_t)(it.fx0 + fx);
-        const uint32_t inv_wx = (65536u + (uint32_t)wx - 1u) / (uint32_t)wx;
+        // ceil(65536 / wx) for the fine widths 2, 3, 4
+        const uint32_t inv_wx = wx == 2 ? 32768u : (wx == 3 ? 21846u : 16384u);
         const int base = (sy + 1) * kBSP + xoff + sx;
         for (uint32_t jj = 0; 4u * jj < nk; ++jj) {
           const uint4 x = philox10_rk(make_uint4(jj, g, m, kTagStep), d.rk);
@@ -611,33 +613,13 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
       bar_sync_consumers(CONS);
     }
     const bool log_point = ((m + 1u) % a.log_every) == 0u;
-    const int W = bw + 2, H = bh + 2;
     if (log_point) {
       const int k = it.k, colour = it.colour;
       const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1), sD = slot_of(ord, colour ^ 3);
-      for (int e = tid; e < W * H; e += CONS) {
-        const int r = e / W - 1, c = e % W - 1;
-        const bool rim_r = (r < 0 || r >= bh), rim_c = (c < 0 || c >= bw);
-        if (rim_r && rim_c) continue;
-        const bool end_r = (r == 0 || r == bh - 1), end_c = (c == 0 || c == bw - 1);
-        bool count;
-        if (rim_r)
-          count = sV < k && (!end_c || sD < k);
-        else if (rim_c)
-          count = sH < k && (!end_r || sD < k);
-        else
-          count = !(end_r && sV > k) && !(end_c && sH > k);
-        if (count) atomicAdd(&sm.hist[tile[(r + 1) * kBSP + xoff + c]], 1u);
-      }
+      count_tile_generic(tile, kBSP, xoff, bw, bh, sm.hist, CONS / 32, k, sV, sH, sD);
     }
-    {  // write back block interior and rim strips (never the corners)
-      const int L = d.L, pitch = d.pitch, x0 = it.x0, y0 = it.y0;
-      for (int e = tid; e < W * H; e += CONS) {
-        const int r = e / W - 1, c = e % W - 1;
-        if ((r < 0 || r >= bh) && (c < 0 || c >= bw)) continue;
-        d.lat[(size_t)wrap(y0 + r, L) * pitch + wrap(x0 + c, L)] = tile[(r + 1) * kBSP + xoff + c];
-      }
-    }
+    // write back block interior and rim strips (never the corners), by rows
+    store_tile_generic(d, it.x0, it.y0, bw, bh, tile, kBSP, nullptr, xoff, CONS / 32);
     bar_sync_consumers(CONS);
     const int P = d.P, slot = it.slot, bx = it.bx, by = it.by;
     if (log_point) {

@@ -330,15 +330,19 @@ __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, 
 // during this visit): whole groups where all four sites are the tile's;
 // at the ends of a row single bytes (one byte per site) or the loaded group
 // with the tile's sites merged in (packed).
+// origin: tile offset of block column 0 within a tile row (kColOff for the
+// tiles staged here); nw: warps taking part (threads 0 .. 32 nw - 1).
 __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
-                                                   const uint8_t* tile, int sp, const uint16_t* stash) {
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, bits = d.bits;
+                                                   const uint8_t* tile, int sp, const uint16_t* stash,
+                                                   int origin = kColOff, int nw = 0) {
+  const int lane = threadIdx.x & 31, bits = d.bits;
+  if (nw == 0) nw = blockDim.x >> 5;
   const RowPlan pi = row_plan(d, x0, bw, false, lane), pr = row_plan(d, x0, bw, true, lane);
   for (int r = (int)(threadIdx.x >> 5) - 1; r <= bh; r += nw) {
     const RowPlan& p = (r < 0 || r >= bh) ? pr : pi;
     const int gy = tile_row_gy(d, y0, r);
     if (gy < 0 || !p.mask) continue;
-    const uint8_t* src = tile + (r + 1) * sp + kColOff + p.tcol;
+    const uint8_t* src = tile + (r + 1) * sp + origin + p.tcol;
     uint8_t* row = d.lat + (size_t)gy * d.pitch;
     if (p.mask == 0xFu) {
       const uint32_t w = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16) |
@@ -723,11 +727,12 @@ __device__ __forceinline__ void count_visit_uni(const uint8_t* tile, uint32_t* h
   hist_add_words(hist, S, x[0], x[1], x[2], x[3]);
 }
 
-// Any geometry: one site per thread iteration, shared-memory atomics.
-__device__ __forceinline__ void count_visit_generic(const LatticeDesc& d, int bx, int by, VisitSmem& sm,
-                                                    int k, int sV, int sH, int sD) {
-  const int bw = block_span(d.ax, bx).w, bh = block_span(d.ay, by).w;
-  const int sp = tile_pitch(bw), lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+// Any geometry: rows by warps, one site per lane step, shared-memory
+// atomics.  The tile has row pitch sp and block column 0 at offset origin;
+// nw warps (threads 0 .. 32 nw - 1) take part.
+__device__ __forceinline__ void count_tile_generic(const uint8_t* tile, int sp, int origin, int bw, int bh,
+                                                   uint32_t* hist, int nw, int k, int sV, int sH, int sD) {
+  const int lane = threadIdx.x & 31;
   for (int r = (int)(threadIdx.x >> 5) - 1; r <= bh; r += nw) {
     const bool rim_r = (r < 0 || r >= bh), end_r = (r == 0 || r == bh - 1);
     for (int c = lane - 1; c <= bw; c += 32) {
@@ -741,9 +746,15 @@ __device__ __forceinline__ void count_visit_generic(const LatticeDesc& d, int bx
         count = sH < k && (!end_r || sD < k);
       else
         count = !(end_r && sV > k) && !(end_c && sH > k);
-      if (count) atomicAdd(&sm.hist[sm.tile[tidx(r, c, sp)]], 1u);
+      if (count) atomicAdd(&hist[tile[(r + 1) * sp + origin + c]], 1u);
     }
   }
+}
+
+__device__ __forceinline__ void count_visit_generic(const LatticeDesc& d, int bx, int by, VisitSmem& sm,
+                                                    int k, int sV, int sH, int sD) {
+  const int bw = block_span(d.ax, bx).w, bh = block_span(d.ay, by).w;
+  count_tile_generic(sm.tile, tile_pitch(bw), kColOff, bw, bh, sm.hist, blockDim.x >> 5, k, sV, sH, sD);
 }
 
 }  // namespace escg_impl
