@@ -488,11 +488,14 @@ __device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t
       forder = colour_order(philox10_rk(make_uint4(0u, (uint32_t)(by * P + bx), m, kTagFineOrder), d.rk).x,
                             d.perm24);
     forder = __shfl_sync(0xFFFFFFFFu, forder, 1);
-    const int x0 = d.cs[bx], bw = d.cs[bx + 1] - x0, y0 = d.cs[by], bh = d.cs[by + 1] - y0;
-    const int fx0 = d.fc[bx], Qx = d.fc[bx + 1] - fx0, fy0 = d.fc[by], Qy = d.fc[by + 1] - fy0;
+    // block span and fine segments from the closed-form partition (no
+    // dependent table loads on the producer's path)
+    const BlockSpan X = block_span(d.ax, bx), Y = block_span(d.ay, by);
+    const int x0 = X.s0, bw = X.w, y0 = Y.s0, bh = Y.w;
+    const int fx0 = X.f0, Qx = X.Q, fy0 = Y.f0, Qy = Y.Q;
     BItem& it = sm.item[b];
-    for (int q = lane; q <= Qx; q += 32) it.fsx[q] = (int16_t)(d.fs[fx0 + q] - x0);
-    for (int q = lane; q <= Qy; q += 32) it.fsy[q] = (int16_t)(d.fs[fy0 + q] - y0);
+    for (int q = lane; q <= Qx; q += 32) it.fsx[q] = (int16_t)seg_start(X, q);
+    for (int q = lane; q <= Qy; q += 32) it.fsy[q] = (int16_t)seg_start(Y, q);
     {
       const int nt = (d.S + 1) * (d.S + 1);
       const uint32_t* tr = reinterpret_cast<const uint32_t*>(d.trans);
@@ -527,6 +530,22 @@ __device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t
     }
     const int xal = (x0 - 1) & ~15;   // floor to a 16-byte boundary (x0 - 1 >= -1)
     uint32_t ok = __any_sync(0xFFFFFFFFu, fail != 0) ? 0u : 1u;
+    // wrap-around rim cells of blocks on the lattice edge (the box fills them
+    // with zeros): loaded now, beside the box, and placed once it has landed.
+    // Blocks are at most 96 sites wide: 3 cells per lane and edge.
+    const int L = d.L, pitch = d.pitch, xoff = x0 - xal;
+    const uint8_t* lat = d.lat;
+    uint8_t wrow[3] = {0, 0, 0}, wcol[3] = {0, 0, 0};
+    const bool top = by == 0, left = bx == 0;   // P >= 2: otherwise bottom / right
+    const bool wrap_row = by == 0 || by == P - 1, wrap_col = bx == 0 || bx == P - 1;
+    if (ok) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int c = lane + 32 * i;
+        if (wrap_row && c < bw) wrow[i] = __ldcg(lat + (top ? (size_t)(L - 1) * pitch : (size_t)0) + x0 + c);
+        if (wrap_col && c < bh) wcol[i] = __ldcg(lat + (size_t)(y0 + c) * pitch + (left ? L - 1 : 0));
+      }
+    }
     if (ok && lane == 0) {
       fence_proxy_async_smem();   // the consumers' accesses of this tile precede the TMA's
       mbar_arrive_expect_tx(&sm.tma[b], kBBoxBytes);
@@ -544,18 +563,13 @@ __device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t
       mbar_arrive(&sm.full[b]);
       return;
     }
-    // wrap-around rim cells (zero-filled by the box) of blocks on the edge
     uint8_t* tile = sm.tile[b];
-    const int L = d.L, pitch = d.pitch, xoff = x0 - xal;
-    const uint8_t* lat = d.lat;
-    if (by == 0)
-      for (int c = lane; c < bw; c += 32) tile[xoff + c] = __ldcg(lat + (size_t)(L - 1) * pitch + x0 + c);
-    if (by == P - 1)
-      for (int c = lane; c < bw; c += 32) tile[(bh + 1) * kBSP + xoff + c] = __ldcg(lat + x0 + c);
-    if (bx == 0)
-      for (int r = lane; r < bh; r += 32) tile[(r + 1) * kBSP + xoff - 1] = __ldcg(lat + (size_t)(y0 + r) * pitch + L - 1);
-    if (bx == P - 1)
-      for (int r = lane; r < bh; r += 32) tile[(r + 1) * kBSP + xoff + bw] = __ldcg(lat + (size_t)(y0 + r) * pitch);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int c = lane + 32 * i;
+      if (wrap_row && c < bw) tile[(top ? 0 : (bh + 1) * kBSP) + xoff + c] = wrow[i];
+      if (wrap_col && c < bh) tile[(c + 1) * kBSP + xoff + (left ? -1 : bw)] = wcol[i];
+    }
     if (lane == 0) {
       it.m = m; it.ord = ord; it.forder = forder; it.quit = 0;
       it.slot = (int32_t)slot; it.k = (int32_t)k; it.bx = bx; it.by = by; it.colour = colour;
