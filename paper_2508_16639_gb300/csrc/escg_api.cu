@@ -308,13 +308,13 @@ cudaError_t copy_to_host(escg* h, uint8_t* host) {
   return cudaMemcpy2DAsync(host, h->L, h->lattice, h->pitch, h->L, h->H, cudaMemcpyDeviceToHost, h->stream);
 }
 
-int enqueue_log(escg* h, uint32_t m_end, bool log) {
+int enqueue_log(escg* h, uint32_t m_end, bool log, uint64_t check_total = 0) {
   if (log) {
     CUDA_TRY(launch_count(h->desc, h->d_state, h->stream));
     h->launches++;
   }
   CUDA_TRY(launch_finalize(h->desc, h->d_state, log_buffers(h), m_end, h->opt.log_every, log ? 1 : 0,
-                           h->opt.stop_at_extinction, h->stream));
+                           h->opt.stop_at_extinction, h->stream, check_total));
   h->launches++;
   return ESCG_OK;
 }
@@ -341,8 +341,12 @@ cudaError_t timing_end(escg* h) {
 }
 
 // Device-side reset of the run state to MCS `mcs` (no host memory is read
-// asynchronously, so nothing waits here).
-int reset_state(escg* h, uint64_t mcs) {
+// asynchronously, so nothing waits here).  validate: the lattice was just
+// replaced; its bytes are checked (0..S, else the run state stops with
+// kErrBadValue) -- by the count of MCS mcs when that is a log point of a
+// one-byte lattice (the counts must add up to L*H), else by the validate
+// kernel.
+int reset_state(escg* h, uint64_t mcs, bool validate = false) {
   const uint32_t le = h->opt.log_every;
   const uint32_t num0 = (uint32_t)((mcs + le - 1) / le);
   CUDA_TRY(launch_state_reset(h->d_state, (uint32_t)mcs, num0, h->stream));
@@ -352,7 +356,16 @@ int reset_state(escg* h, uint64_t mcs) {
   h->log_num0_host = num0;
   h->mcs_enq = mcs;
   h->failed = false;
-  if (mcs % h->opt.log_every == 0) return enqueue_log(h, (uint32_t)mcs, true);
+  const bool log = mcs % h->opt.log_every == 0;
+  const bool by_count = validate && log && h->bits == 8;
+  if (log) {
+    const int rc = enqueue_log(h, (uint32_t)mcs, true, by_count ? (uint64_t)h->L * h->H : 0);
+    if (rc != ESCG_OK) return rc;
+  }
+  if (validate && !by_count) {
+    CUDA_TRY(launch_validate(byte_view(h), &h->d_state->error, kErrBadValue, &h->d_state->stopped, h->stream));
+    h->launches++;
+  }
   return ESCG_OK;
 }
 
@@ -889,12 +902,10 @@ int escg_restore(escg_t* h, const uint8_t* host_lattice, uint64_t mcs) {
     return ESCG_EINVAL;
   }
   CUDA_TRY(copy_to_device(h, host_lattice));
-  const int rc = reset_state(h, mcs);
-  if (rc != ESCG_OK) return rc;
   // values are checked on the device; an invalid lattice also stops the
   // run state, so that nothing enqueued later touches it
-  CUDA_TRY(launch_validate(byte_view(h), &h->d_state->error, kErrBadValue, &h->d_state->stopped, h->stream));
-  h->launches++;
+  const int rc = reset_state(h, mcs, true);
+  if (rc != ESCG_OK) return rc;
   uint32_t err = 0;
   CUDA_TRY(cudaMemcpyAsync(&err, &h->d_state->error, sizeof err, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -920,19 +931,25 @@ int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_m
   // invalid lattice stops the run state on the device), run, copy out,
   // count, then read the error word.
   CUDA_TRY(copy_to_device(h, host_in));
-  int rc = reset_state(h, mcs);
+  int rc = reset_state(h, mcs, true);
   if (rc != ESCG_OK) return rc;
-  CUDA_TRY(launch_validate(byte_view(h), &h->d_state->error, kErrBadValue, &h->d_state->stopped, h->stream));
-  h->launches++;
   rc = escg_run(h, n_mcs);
   if (rc != ESCG_OK) return rc;
   CUDA_TRY(copy_to_host(h, host_out));
   if (counts_out) {
-    CUDA_TRY(cudaMemsetAsync(h->d_scratch, 0, sizeof(RunState), h->stream));
-    CUDA_TRY(launch_count(h->desc, h->d_scratch, h->stream));
-    h->launches++;
-    CUDA_TRY(cudaMemcpyAsync(counts_out, h->d_scratch->cur, sizeof(uint64_t) * (h->S + 1),
-                             cudaMemcpyDeviceToHost, h->stream));
+    const uint64_t end = mcs + n_mcs, le = h->opt.log_every;
+    if (!h->opt.stop_at_extinction && end % le == 0 && end / le >= h->log_num0_host) {
+      // the run logged the counts of its final MCS: read that entry
+      const uint64_t slot = (end / le - h->log_num0_host) % (uint64_t)kLogCap;
+      CUDA_TRY(cudaMemcpyAsync(counts_out, h->d_log + slot * kMaxStates, sizeof(uint64_t) * (h->S + 1),
+                               cudaMemcpyDeviceToHost, h->stream));
+    } else {
+      CUDA_TRY(cudaMemsetAsync(h->d_scratch, 0, sizeof(RunState), h->stream));
+      CUDA_TRY(launch_count(h->desc, h->d_scratch, h->stream));
+      h->launches++;
+      CUDA_TRY(cudaMemcpyAsync(counts_out, h->d_scratch->cur, sizeof(uint64_t) * (h->S + 1),
+                               cudaMemcpyDeviceToHost, h->stream));
+    }
   }
   uint32_t err = 0;
   CUDA_TRY(cudaMemcpyAsync(&err, &h->d_state->error, sizeof err, cudaMemcpyDeviceToHost, h->stream));

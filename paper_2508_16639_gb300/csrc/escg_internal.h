@@ -61,9 +61,12 @@ cudaError_t launch_state_reset(RunState* st, uint32_t mcs, uint32_t log_num0, cu
 cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream);
 // After work ending at MCS m_end: st->mcs = m_end (unless stopped); if `log`
 // appends st->cur as the entry of MCS m_end and, with stop_at_extinction,
-// sets st->stopped when <= 1 species is alive.
+// sets st->stopped when <= 1 species is alive.  check_total != 0: the counts
+// must add up to it (every byte a state 0..S), else st->error |=
+// kErrBadValue and st->stopped = 1 (a restored lattice checked by its count).
 cudaError_t launch_finalize(const LatticeDesc& d, RunState* st, LogBuffers lb, uint32_t m_end,
-                            uint32_t log_every, int log, int stop_at_extinction, cudaStream_t stream);
+                            uint32_t log_every, int log, int stop_at_extinction, cudaStream_t stream,
+                            uint64_t check_total = 0);
 // One coarse phase (slot 0..3 of MCS m): one CTA per active block.
 cudaError_t launch_phase(const LatticeDesc& d, RunState* st, uint32_t m, int slot,
                          cudaStream_t stream);

@@ -171,14 +171,19 @@ __device__ void write_log_entry(RunState* st, LogBuffers lb, int S, uint32_t m_e
 }
 
 __global__ void finalize_kernel(RunState* st, int S, LogBuffers lb, uint32_t m_end, uint32_t log_every,
-                                int log, int stop_at_extinction) {
+                                int log, int stop_at_extinction, unsigned long long check_total) {
   if (st->stopped) return;
   st->mcs = m_end;
   if (!log) return;
-  unsigned long long c[kMaxStates];
+  unsigned long long c[kMaxStates], sum = 0;
   for (int v = 0; v < kMaxStates; ++v) {
     c[v] = st->cur[v];
     st->cur[v] = 0;
+    sum += (v <= S) ? c[v] : 0ull;
+  }
+  if (check_total && sum != check_total) {   // some byte is not a state
+    st->error |= kErrBadValue;
+    st->stopped = 1;
   }
   write_log_entry(st, lb, S, m_end, log_every, c, stop_at_extinction);
 }
@@ -1218,8 +1223,10 @@ cudaError_t launch_count(const LatticeDesc& d, RunState* st, cudaStream_t stream
 }
 
 cudaError_t launch_finalize(const LatticeDesc& d, RunState* st, LogBuffers lb, uint32_t m_end,
-                            uint32_t log_every, int log, int stop_at_extinction, cudaStream_t stream) {
-  finalize_kernel<<<1, 1, 0, stream>>>(st, d.S, lb, m_end, log_every, log, stop_at_extinction);
+                            uint32_t log_every, int log, int stop_at_extinction, cudaStream_t stream,
+                            uint64_t check_total) {
+  finalize_kernel<<<1, 1, 0, stream>>>(st, d.S, lb, m_end, log_every, log, stop_at_extinction,
+                                       (unsigned long long)check_total);
   return cudaGetLastError();
 }
 
