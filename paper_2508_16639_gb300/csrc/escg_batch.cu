@@ -600,17 +600,36 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
     uint8_t* tile = sm.tile[b];
     const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans[b]);
     const uint32_t m = it.m, ord = it.ord, s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
-    const int xoff = it.xoff, bw = it.bw, bh = it.bh, hx = it.Qx >> 1, nquads = hx * (it.Qy >> 1);
-    const uint32_t inv_hx = (65536u + (uint32_t)hx - 1u) / (uint32_t)hx;   // q / hx exact for q < 2^16 / hx
+    const int xoff = it.xoff, bw = it.bw, bh = it.bh, nquads = (it.Qx >> 1) * (it.Qy >> 1);
+    // regular (all 2 x 2) quads first, as in visit_generic
+    BlockSpan X, Y;
+    X.Q = it.Qx;
+    X.fq = bw / it.Qx;
+    X.fr = bw - X.fq * it.Qx;
+    Y.Q = it.Qy;
+    Y.fq = bh / it.Qy;
+    Y.fr = bh - Y.fq * it.Qy;
+    const QuadMap qm = quad_map(X, Y);
     if (tid < kMaxStates) sm.hist[tid] = 0;
     for (int fi = 0; fi < 4; ++fi) {
       const int fcol = order_at(it.forder, fi);
       const int cx = fcol & 1, cy = fcol >> 1;
       for (int q = tid; q < nquads; q += CONS) {
-        const int qy = (int)(((uint32_t)q * inv_hx) >> 16), qx = q - qy * hx;
+        int qx, qy;
+        quad_at(qm, q, qx, qy);
         const int fx = 2 * qx + cx, fy = 2 * qy + cy;
         const int sx = it.fsx[fx], wx = it.fsx[fx + 1] - sx;
         const int sy = it.fsy[fy], wy = it.fsy[fy + 1] - sy;
+        if (q < qm.n_reg) {   // a 2 x 2 sub-block: one Philox call, four attempts
+          const uint32_t g = (uint32_t)(it.fy0 + fy) * (uint32_t)d.GQ + (uint32_t)(it.fx0 + fx);
+          const int base = (sy + 1) * kBSP + xoff + sx;
+          const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
+          attempt_2x2(tile, trans, x.x, base, kBSP, tx, txi, s1);
+          attempt_2x2(tile, trans, x.y, base, kBSP, tx, txi, s1);
+          attempt_2x2(tile, trans, x.z, base, kBSP, tx, txi, s1);
+          attempt_2x2(tile, trans, x.w, base, kBSP, tx, txi, s1);
+          continue;
+        }
         const uint32_t nk = (uint32_t)(wx * wy), n4 = 4u * nk;
         const uint32_t g = (uint32_t)(it.fy0 + fy) * (uint32_t)d.GQ + (uint32_t)(it.fx0 + fx);
         // ceil(65536 / wx) for the fine widths 2, 3, 4

@@ -538,6 +538,60 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
   store_tile_uni(d, x0, y0, sm.tile, rim_raw);
 }
 
+// The step of attempt() for a 2 x 2 sub-block (n_k = 4: p = 16 w, so the
+// high 4 bits of w are the cell -- bit 31 row, bit 30 column -- and the
+// direction, and u = w << 4), on a tile of row pitch sp.
+__device__ __forceinline__ void attempt_2x2(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
+                                            uint32_t w, int base, int sp, uint32_t tx, uint32_t txi, uint32_t s1) {
+  const uint32_t dir = (w >> 28) & 3u;
+  const int ti = base + (int)(w >> 31) * sp + (int)((w >> 30) & 1u);
+  const int mag = (dir & 2u) ? 1 : sp;
+  const int tj = ti + ((dir & 1u) ? mag : -mag);
+  apply_rule(tile, trans, ti, tj, w << 4, tx, txi, s1);
+}
+
+// Order in which a visit hands out the quads (2 x 2 groups of fine
+// sub-blocks) of a block: first the rx x ry regular ones (columns qx >= irx,
+// rows qy >= iry, all four sub-blocks 2 x 2), then the rows qy < iry, then
+// the columns qx < irx of the remaining rows.  irx = ceil(fr / 2) when the
+// narrow fine width is 2, else every quad is irregular.
+struct QuadMap {
+  int hx, irx, iry, rx, n_reg, n_top;
+  uint32_t inv_hx, inv_rx, inv_irx;
+};
+
+__device__ __forceinline__ QuadMap quad_map(const BlockSpan& X, const BlockSpan& Y) {
+  QuadMap m;
+  const int hx = X.Q >> 1, hy = Y.Q >> 1;
+  m.hx = hx;
+  m.irx = X.fq == 2 ? (X.fr + 1) >> 1 : hx;
+  m.iry = Y.fq == 2 ? (Y.fr + 1) >> 1 : hy;
+  m.rx = hx - m.irx;
+  m.n_reg = m.rx * (hy - m.iry);
+  m.n_top = m.iry * hx;
+  // reciprocals: q / k exact as (q * ceil(65536 / k)) >> 16 for q < 2^16 / k
+  m.inv_hx = (65536u + (uint32_t)hx - 1u) / (uint32_t)hx;
+  m.inv_rx = m.rx > 0 ? (65536u + (uint32_t)m.rx - 1u) / (uint32_t)m.rx : 0u;
+  m.inv_irx = m.irx > 0 ? (65536u + (uint32_t)m.irx - 1u) / (uint32_t)m.irx : 0u;
+  return m;
+}
+
+__device__ __forceinline__ void quad_at(const QuadMap& m, int q, int& qx, int& qy) {
+  if (q < m.n_reg) {
+    const int r = (int)(((uint32_t)q * m.inv_rx) >> 16);
+    qy = m.iry + r;
+    qx = m.irx + (q - r * m.rx);
+  } else if (q < m.n_reg + m.n_top) {
+    const int i = q - m.n_reg, r = (int)(((uint32_t)i * m.inv_hx) >> 16);
+    qy = r;
+    qx = i - r * m.hx;
+  } else {
+    const int i = q - m.n_reg - m.n_top, r = (int)(((uint32_t)i * m.inv_irx) >> 16);
+    qy = m.iry + r;
+    qx = i - r * m.irx;
+  }
+}
+
 // Visit of coarse block (bx, by) in MCS m, any geometry of the partition.
 // The block's span and fine segments come from the closed-form partition
 // (no table loads ahead of the tile load); a thread's quad (2 x 2 fine
@@ -557,17 +611,32 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
   __syncthreads();
   const uint32_t s1 = (uint32_t)d.S + 1u;
   const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
-  const int hx = X.Q >> 1, nquads = hx * (Y.Q >> 1);
-  const uint32_t inv_hx = (65536u + (uint32_t)hx - 1u) / (uint32_t)hx;
+  const int hx = X.Q >> 1, hy = Y.Q >> 1, nquads = hx * hy;
   const uint32_t ord = sm.forder;
   const bool variant = d.nbh == 8 || d.reflect;
   const int lg = d.nbh == 8 ? 3 : 2;
+  // Quads whose four sub-blocks are all 2 x 2 ("regular": the fine segments
+  // of a block are 2 wide except the first fr, which are 3) are handed out
+  // first, so that all but the last warps run the short 2 x 2 step; the
+  // quads of the leading wide columns and rows follow.
+  const QuadMap qm = quad_map(X, Y);
   for (int fi = 0; fi < 4; ++fi) {
     const int fcol = order_at(ord, fi);
     const int cx = fcol & 1, cy = fcol >> 1;
     for (int q = tid; q < nquads; q += nthr) {
-      const int qy = (int)(((uint32_t)q * inv_hx) >> 16), qx = q - qy * hx;
+      int qx, qy;
+      quad_at(qm, q, qx, qy);
       const int fx = 2 * qx + cx, fy = 2 * qy + cy;
+      if (!variant && q < qm.n_reg) {   // a 2 x 2 sub-block: one Philox call, four attempts
+        const int base = tidx(seg_start(Y, fy), seg_start(X, fx), sp);
+        const uint32_t g = (uint32_t)(Y.f0 + fy) * (uint32_t)d.GQ + (uint32_t)(X.f0 + fx);
+        const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
+        attempt_2x2(sm.tile, trans, x.x, base, sp, d.tx, d.txi, s1);
+        attempt_2x2(sm.tile, trans, x.y, base, sp, d.tx, d.txi, s1);
+        attempt_2x2(sm.tile, trans, x.z, base, sp, d.tx, d.txi, s1);
+        attempt_2x2(sm.tile, trans, x.w, base, sp, d.tx, d.txi, s1);
+        continue;
+      }
       const int sx = seg_start(X, fx), wx = seg_width(X, fx);
       const int sy = seg_start(Y, fy), wy = seg_width(Y, fy);
       const uint32_t nk = (uint32_t)(wx * wy), n4 = 4u * nk;
