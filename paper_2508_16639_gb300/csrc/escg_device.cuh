@@ -550,6 +550,25 @@ __device__ __forceinline__ void attempt_2x2(uint8_t* __restrict__ tile, const ui
   apply_rule(tile, trans, ti, tj, w << 4, tx, txi, s1);
 }
 
+// attempt_variant for a 2 x 2 sub-block: p = w (4 nbh), so the cell is
+// bits 31..30 of w, the direction the next lg bits and u = w << (2 + lg).
+__device__ __forceinline__ void attempt_variant_2x2(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
+                                                    uint32_t w, int lg, int base, int sp, uint32_t tx,
+                                                    uint32_t txi, uint32_t s1, bool reflect, int gy, int gx,
+                                                    int H, int L) {
+  const uint32_t r = w >> 31, c = (w >> 30) & 1u;
+  const uint32_t dir = (w >> (30 - lg)) & ((1u << lg) - 1u);
+  int dr = (int)((0xA058u >> (2 * dir)) & 3u) - 1;
+  int dc = (int)((0x8885u >> (2 * dir)) & 3u) - 1;
+  if (reflect) {
+    const int row = gy + (int)r, col = gx + (int)c;
+    if (row + dr < 0 || row + dr >= H) dr = -dr;
+    if (col + dc < 0 || col + dc >= L) dc = -dc;
+  }
+  const int ti = base + (int)r * sp + (int)c;
+  apply_rule(tile, trans, ti, ti + dr * sp + dc, w << (2 + lg), tx, txi, s1);
+}
+
 // Order in which a visit hands out the quads (2 x 2 groups of fine
 // sub-blocks) of a block: first the rx x ry regular ones (columns qx >= irx,
 // rows qy >= iry, all four sub-blocks 2 x 2), then the rows qy < iry, then
@@ -627,14 +646,20 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
       int qx, qy;
       quad_at(qm, q, qx, qy);
       const int fx = 2 * qx + cx, fy = 2 * qy + cy;
-      if (!variant && q < qm.n_reg) {   // a 2 x 2 sub-block: one Philox call, four attempts
-        const int base = tidx(seg_start(Y, fy), seg_start(X, fx), sp);
+      if (q < qm.n_reg) {   // a 2 x 2 sub-block: one Philox call, four attempts
+        const int sx2 = seg_start(X, fx), sy2 = seg_start(Y, fy);
+        const int base = tidx(sy2, sx2, sp);
         const uint32_t g = (uint32_t)(Y.f0 + fy) * (uint32_t)d.GQ + (uint32_t)(X.f0 + fx);
         const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
-        attempt_2x2(sm.tile, trans, x.x, base, sp, d.tx, d.txi, s1);
-        attempt_2x2(sm.tile, trans, x.y, base, sp, d.tx, d.txi, s1);
-        attempt_2x2(sm.tile, trans, x.z, base, sp, d.tx, d.txi, s1);
-        attempt_2x2(sm.tile, trans, x.w, base, sp, d.tx, d.txi, s1);
+        const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (variant)
+            attempt_variant_2x2(sm.tile, trans, wv[e], lg, base, sp, d.tx, d.txi, s1, d.reflect != 0,
+                                y0 + sy2, x0 + sx2, d.H, d.L);
+          else
+            attempt_2x2(sm.tile, trans, wv[e], base, sp, d.tx, d.txi, s1);
+        }
         continue;
       }
       const int sx = seg_start(X, fx), wx = seg_width(X, fx);
