@@ -293,11 +293,13 @@ constexpr int kStashLanes = 32;
 constexpr int kStashWords = kMaxTileRows * kStashLanes;
 
 // Each warp issues the loads of up to 8 rows before it writes any of them
-// to shared memory: a tile costs two L2 round trips.
+// to shared memory: a tile costs two L2 round trips.  PACKED = false: one
+// byte per site (the packing code is compiled out).
+template <bool PACKED = false>
 __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
                                                   uint8_t* tile, int sp, uint16_t* stash) {
   constexpr int kRows = 8;
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, bits = d.bits;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, bits = PACKED ? d.bits : 8;
   const RowPlan pi = row_plan(d, x0, bw, false, lane), pr = row_plan(d, x0, bw, true, lane);
   for (int r0 = (int)(threadIdx.x >> 5) - 1; r0 <= bh; r0 += kRows * nw) {
     uint32_t v[kRows];
@@ -315,7 +317,7 @@ __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, 
       const int r = r0 + i * nw;
       const RowPlan& p = (r < 0 || r >= bh) ? pr : pi;
       if (r > bh || tile_row_gy(d, y0, r) < 0) continue;
-      if (bits != 8 && p.mask && p.mask != 0xFu) stash[(r + 1) * kStashLanes + lane] = (uint16_t)v[i];
+      if (PACKED && p.mask && p.mask != 0xFu) stash[(r + 1) * kStashLanes + lane] = (uint16_t)v[i];
       const uint32_t u = unpack4(v[i], bits);
       uint8_t* dst = tile + (r + 1) * sp + kColOff + p.tcol;
 #pragma unroll
@@ -332,10 +334,11 @@ __device__ __forceinline__ void load_tile_generic(const LatticeDesc& d, int x0, 
 // with the tile's sites merged in (packed).
 // origin: tile offset of block column 0 within a tile row (kColOff for the
 // tiles staged here); nw: warps taking part (threads 0 .. 32 nw - 1).
+template <bool PACKED = false>
 __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0, int y0, int bw, int bh,
                                                    const uint8_t* tile, int sp, const uint16_t* stash,
                                                    int origin = kColOff, int nw = 0) {
-  const int lane = threadIdx.x & 31, bits = d.bits;
+  const int lane = threadIdx.x & 31, bits = PACKED ? d.bits : 8;
   if (nw == 0) nw = blockDim.x >> 5;
   const RowPlan pi = row_plan(d, x0, bw, false, lane), pr = row_plan(d, x0, bw, true, lane);
   for (int r = (int)(threadIdx.x >> 5) - 1; r <= bh; r += nw) {
@@ -616,9 +619,9 @@ __device__ __forceinline__ void quad_at(const QuadMap& m, int q, int& qx, int& q
 // (no table loads ahead of the tile load); a thread's quad (2 x 2 fine
 // sub-blocks) is found with a reciprocal multiply, exact for the at most
 // 24 x 24 quads of a block.
-// stash: kStashWords entries of shared memory for a packed lattice (may be
-// null when d.bits == 8).
-template <bool OWN_FORDER = true>
+// PACKED: the lattice has 4 or 2 bits per site (d.bits); stash then points
+// to kStashWords entries of shared memory.
+template <bool OWN_FORDER = true, bool PACKED = false>
 __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int by, uint32_t m,
                                               VisitSmem& sm, uint16_t* stash = nullptr) {
   const BlockSpan X = block_span(d.ax, bx), Y = block_span(d.ay, by);
@@ -626,42 +629,27 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
   const int sp = tile_pitch(bw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (OWN_FORDER && tid == 0) sm.forder = fine_order(d, bx, by, m);
-  load_tile_generic(d, x0, y0, bw, bh, sm.tile, sp, stash);
+  load_tile_generic<PACKED>(d, x0, y0, bw, bh, sm.tile, sp, stash);
   __syncthreads();
   const uint32_t s1 = (uint32_t)d.S + 1u;
   const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
-  const int hx = X.Q >> 1, hy = Y.Q >> 1, nquads = hx * hy;
+  const int hx = X.Q >> 1, nquads = hx * (Y.Q >> 1);
+  const uint32_t inv_hx = (65536u + (uint32_t)hx - 1u) / (uint32_t)hx;
   const uint32_t ord = sm.forder;
   const bool variant = d.nbh == 8 || d.reflect;
   const int lg = d.nbh == 8 ? 3 : 2;
-  // Quads whose four sub-blocks are all 2 x 2 ("regular": the fine segments
-  // of a block are 2 wide except the first fr, which are 3) are handed out
-  // first, so that all but the last warps run the short 2 x 2 step; the
-  // quads of the leading wide columns and rows follow.
-  const QuadMap qm = quad_map(X, Y);
+  // Quads in row-major order: a fine phase lasts as long as its largest
+  // sub-block (3 x 3 at the block's leading corner), which this order shares
+  // out over all warps.  (Handing the all-2 x 2 quads out first, with a
+  // shorter 2 x 2 step, was measured 8 % slower here at L = 800 and no
+  // faster at L = 3000; the batch chunk kernel, which keeps many blocks in
+  // flight per SM, gains from it.)
   for (int fi = 0; fi < 4; ++fi) {
     const int fcol = order_at(ord, fi);
     const int cx = fcol & 1, cy = fcol >> 1;
     for (int q = tid; q < nquads; q += nthr) {
-      int qx, qy;
-      quad_at(qm, q, qx, qy);
+      const int qy = (int)(((uint32_t)q * inv_hx) >> 16), qx = q - qy * hx;
       const int fx = 2 * qx + cx, fy = 2 * qy + cy;
-      if (q < qm.n_reg) {   // a 2 x 2 sub-block: one Philox call, four attempts
-        const int sx2 = seg_start(X, fx), sy2 = seg_start(Y, fy);
-        const int base = tidx(sy2, sx2, sp);
-        const uint32_t g = (uint32_t)(Y.f0 + fy) * (uint32_t)d.GQ + (uint32_t)(X.f0 + fx);
-        const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
-        const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (variant)
-            attempt_variant_2x2(sm.tile, trans, wv[e], lg, base, sp, d.tx, d.txi, s1, d.reflect != 0,
-                                y0 + sy2, x0 + sx2, d.H, d.L);
-          else
-            attempt_2x2(sm.tile, trans, wv[e], base, sp, d.tx, d.txi, s1);
-        }
-        continue;
-      }
       const int sx = seg_start(X, fx), wx = seg_width(X, fx);
       const int sy = seg_start(Y, fy), wy = seg_width(Y, fy);
       const uint32_t nk = (uint32_t)(wx * wy), n4 = 4u * nk;
@@ -685,7 +673,7 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
     }
     __syncthreads();
   }
-  store_tile_generic(d, x0, y0, bw, bh, sm.tile, sp, stash);
+  store_tile_generic<PACKED>(d, x0, y0, bw, bh, sm.tile, sp, stash);
 }
 
 // ---------------------------------------------------------------------------

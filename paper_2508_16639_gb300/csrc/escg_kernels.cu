@@ -200,8 +200,10 @@ __global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st,
   const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
   if (d.uniform64)
     visit_uniform(d, bx, by, m, sm);
+  else if (d.bits != 8)
+    visit_generic<true, true>(d, bx, by, m, sm, stash);
   else
-    visit_generic(d, bx, by, m, sm, stash);
+    visit_generic<true, false>(d, bx, by, m, sm, stash);
 }
 
 // ---------------------------------------------------------------------------
@@ -214,11 +216,11 @@ constexpr int kPersistentThreads = 256;
 constexpr int kUniMinBlocks = 4;
 constexpr int kUniLaunchPerSM = 4;
 
-template <bool UNI>
+template <bool UNI, bool PACKED = false>
 __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
     persistent_kernel(PersistentArgs a) {
   __shared__ VisitSmem sm;
-  __shared__ uint16_t stash[UNI ? 1 : kStashWords];
+  __shared__ uint16_t stash[(UNI || !PACKED) ? 1 : kStashWords];
   __shared__ uint32_t s_item, s_ord, s_quit, s_abort;
   const LatticeDesc& d = a.d;
   RunState* st = a.st;
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
       if (UNI)
         visit_uniform<false>(d, bx, by, m, sm);
       else
-        visit_generic<false>(d, bx, by, m, sm, stash);
+        visit_generic<false, PACKED>(d, bx, by, m, sm, stash);
       const bool log_point = a.fuse_counts && ((m + 1u) % a.log_every) == 0u;
       if (log_point) {
         const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1),
@@ -1252,8 +1254,10 @@ int persistent_tma_grid(int device) {
 cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream) {
   if (a.d.uniform64)
     persistent_kernel<true><<<grid, kPersistentThreads, 0, stream>>>(a);
+  else if (a.d.bits != 8)
+    persistent_kernel<false, true><<<grid, kPersistentThreads, 0, stream>>>(a);
   else
-    persistent_kernel<false><<<grid, kPersistentThreads, 0, stream>>>(a);
+    persistent_kernel<false, false><<<grid, kPersistentThreads, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
