@@ -371,8 +371,9 @@ __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0,
 // quarter row is one 32-bit (2 bits per site) or 64-bit (4 bits) load, and
 // a rim-column site comes with its group of 4, which the thread keeps
 // (returned, then passed to store_tile_uni) to write the group back whole.
+template <bool PACKED = false>
 __device__ __forceinline__ uint32_t load_tile_uni(const LatticeDesc& d, int x0, int y0, uint8_t* tile) {
-  const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = d.bits;
+  const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = PACKED ? d.bits : 8;
   uint32_t rim_raw = 0;
   if (bits == 8) {
     {  // interior: 64 rows x 4 x 16 bytes, one 16-byte load per thread
@@ -426,9 +427,10 @@ __device__ __forceinline__ uint32_t load_tile_uni(const LatticeDesc& d, int x0, 
   return rim_raw;
 }
 
+template <bool PACKED = false>
 __device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int y0, const uint8_t* tile,
                                                uint32_t rim_raw) {
-  const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = d.bits;
+  const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = PACKED ? d.bits : 8;
   if (bits == 8) {
     {
       const int r = t >> 2, q = t & 3;
@@ -530,15 +532,15 @@ __device__ __forceinline__ void fine_phases_uni(const LatticeDesc& d, int bx, in
 
 // OWN_FORDER = false: the caller has stored fine_order(d, bx, by, m) in
 // sm.forder before a barrier that precedes the call.
-template <bool OWN_FORDER = true>
+template <bool OWN_FORDER = true, bool PACKED = false>
 __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int by, uint32_t m,
                                               VisitSmem& sm) {
   const int x0 = bx * kUniB, y0 = by * kUniB;
   if (OWN_FORDER && threadIdx.x == 0) sm.forder = fine_order(d, bx, by, m);
-  const uint32_t rim_raw = load_tile_uni(d, x0, y0, sm.tile);
+  const uint32_t rim_raw = load_tile_uni<PACKED>(d, x0, y0, sm.tile);
   __syncthreads();
   fine_phases_uni(d, bx, by, m, sm);
-  store_tile_uni(d, x0, y0, sm.tile, rim_raw);
+  store_tile_uni<PACKED>(d, x0, y0, sm.tile, rim_raw);
 }
 
 // The step of attempt() for a 2 x 2 sub-block (n_k = 4: p = 16 w, so the

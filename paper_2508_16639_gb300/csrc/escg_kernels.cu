@@ -198,8 +198,10 @@ __global__ void __launch_bounds__(256) phase_kernel(LatticeDesc d, RunState* st,
   const int colour = order_at(colour_order(x.x, d.perm24), slot);
   const int half = d.P >> 1, j = blockIdx.x;
   const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
-  if (d.uniform64)
-    visit_uniform(d, bx, by, m, sm);
+  if (d.uniform64 && d.bits != 8)
+    visit_uniform<true, true>(d, bx, by, m, sm);
+  else if (d.uniform64)
+    visit_uniform<true, false>(d, bx, by, m, sm);
   else if (d.bits != 8)
     visit_generic<true, true>(d, bx, by, m, sm, stash);
   else
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
       __syncthreads();
       if (s_abort) break;  // uniform across the CTA
       if (UNI)
-        visit_uniform<false>(d, bx, by, m, sm);
+        visit_uniform<false, PACKED>(d, bx, by, m, sm);
       else
         visit_generic<false, PACKED>(d, bx, by, m, sm, stash);
       const bool log_point = a.fuse_counts && ((m + 1u) % a.log_every) == 0u;
@@ -1252,8 +1254,10 @@ int persistent_tma_grid(int device) {
 }
 
 cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream) {
-  if (a.d.uniform64)
-    persistent_kernel<true><<<grid, kPersistentThreads, 0, stream>>>(a);
+  if (a.d.uniform64 && a.d.bits != 8)
+    persistent_kernel<true, true><<<grid, kPersistentThreads, 0, stream>>>(a);
+  else if (a.d.uniform64)
+    persistent_kernel<true, false><<<grid, kPersistentThreads, 0, stream>>>(a);
   else if (a.d.bits != 8)
     persistent_kernel<false, true><<<grid, kPersistentThreads, 0, stream>>>(a);
   else
