@@ -1,7 +1,9 @@
 /*
  * escg.h -- C ABI of libescg, a GB300 (sm_103a) implementation of the Monte
  * Carlo step (MCS) of an Evolutionary Spatial Cyclic Game (ESCG) on an L x L
- * periodic von Neumann lattice (arXiv 2508.16639).
+ * periodic von Neumann lattice (arXiv 2508.16639); options add L x H
+ * rectangles, the Moore neighbourhood, a reflecting boundary, probabilistic
+ * dominance edges and bit-packed device storage (escg_options).
  *
  * The model (Section 3.1 "Implementation" of the paper): lattice value 0 is
  * an empty site, 1..S a species; species a dominates species b iff
