@@ -61,7 +61,7 @@ ALG_INT_INSTR_PER_ATTEMPT = 24
 # DRAM traffic of persistent_kernel from one ncu capture (bytes per launch of
 # a 10-MCS chunk at L = 3200), valid only for that kernel and workload and the
 # kernel sources it was taken from (hash below); None otherwise.
-NCU_TRAFFIC = {"sources_sha1": "f5d70089ad39ebd25284c6614bb5b2602a7f1d2f", "bytes_per_launch": 10308352 + 2273792,
+NCU_TRAFFIC = {"sources_sha1": "4db1c7abf7314fe7af68bd269cbd1bdf02c5b6cc", "bytes_per_launch": 10300672 + 2286848,
                "kernel": "persistent_kernel", "L": 3200, "mcs_per_launch": 10,
                "profile": "profiles/persistent_kernel_L3200_M1e-4.md"}
 
