@@ -102,3 +102,48 @@ def test_batch_create_rejects_bad_specs(lib, bad, msg):
     spec.update(bad)
     with pytest.raises(E.EscgError, match=msg):
         E.Batch([spec, dict(spec, L=64, S=3, rates=(1, 1, 1), p_empty=0.0, max_mcs=10)])
+
+
+def test_packed_and_rectangular_size_helpers(lib):
+    """Row pitch of a lattice stored with b bits per site: ceil(L b / 8)
+    rounded up to 16 bytes; H rows of it."""
+    for L in (64, 100, 131, 3200, 12800):
+        for b in (8, 4, 2):
+            row = -(-L * b // 8)
+            assert E.lattice_pitch(L, b) == -(-row // 16) * 16
+            for H in (64, 97, L):
+                assert E.lattice_bytes(L, H, b) == H * E.lattice_pitch(L, b)
+    assert lib.escg_lattice_pitch_ex(64, 3) == 0 and lib.escg_lattice_pitch_ex(0, 8) == 0
+    assert lib.escg_lattice_pitch_ex(100, 0) == lib.escg_lattice_pitch(100)
+    assert lib.escg_lattice_bytes_rect(100, 50) == 50 * 112
+
+
+def _create_ex(lib, L, S, **fields):
+    D = np.ascontiguousarray(O.circulant(S, [1] if S == 3 else [1, 2]), dtype=np.uint8)
+    r = _lib.Rates(1.0, 1.0, 1.0)
+    opt = _lib.Options()
+    lib.escg_default_options(C.byref(opt))
+    for k, v in fields.items():
+        setattr(opt, k, v)
+    return lib.escg_create_ex(L, S, D.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(r), 1, C.byref(opt))
+
+
+@pytest.mark.parametrize("L,S,fields,msg", [
+    (64, 3, dict(height=7), "height=7"),
+    (64, 3, dict(height=16385), "height=16385"),
+    (64, 3, dict(bits_per_site=3), "bits_per_site"),
+    (64, 5, dict(bits_per_site=2), "S=5"),
+    (48, 3, dict(bits_per_site=4), ">= 64"),
+    (128, 3, dict(bits_per_site=2, height=40), ">= 64"),
+    (64, 3, dict(persistent=5), "persistent"),
+    (64, 3, dict(neighbourhood=6), "neighbourhood"),
+    (64, 3, dict(reflecting_boundary=2), "neighbourhood"),
+    (64, 3, dict(device_lattice=0x1001), "aligned"),
+    (64, 3, dict(p_empty=1.5), "p_empty"),
+])
+def test_create_rejects_bad_options(lib, L, S, fields, msg):
+    """Options are checked on the host before any device work, so an invalid
+    one (including a device buffer that is not 16-byte aligned) never
+    reaches a kernel."""
+    assert not _create_ex(lib, L, S, **fields)
+    assert msg in lib.escg_last_error().decode()
