@@ -19,8 +19,8 @@ exchange = 2 M N with M = 1e-4), counts logged every 10 MCS.  One step =
             instructions per launch / its event-timed launch duration
             against the GPU's integer-issue peak;
   cpu_baseline  the CPU replay oracle (single thread) on a bounded sample;
-  ensemble, serving, park, variants, packed  batched runs (A7), a request stream
-            (A8), the probabilistic-dominance ensemble and the benchmark
+  ensemble, serving, park, variants, packed  batched runs, a request stream
+            to the serving loop, the probabilistic-dominance ensemble and the benchmark
             lattice under the Moore / reflecting rule variants, as
             rectangles of the same N, and the RPSLS L = 800 workload;
             packed: bit-packed lattices (2 bits per site) against one byte per

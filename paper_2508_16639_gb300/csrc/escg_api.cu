@@ -1,6 +1,6 @@
 // escg_api.cu -- the C ABI of libescg (include/escg.h): handle life cycle,
-// host-side set-up (partition tables, integer thresholds, transition table;
-// SURVEY rows A1/A2) and run orchestration on the handle's stream.
+// host-side set-up (partition tables, integer rate thresholds, transition
+// table, the initial lattice) and run orchestration on the handle's stream.
 #include <cudaTypedefs.h>
 
 #include <cmath>

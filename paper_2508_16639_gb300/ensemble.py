@@ -1,4 +1,4 @@
-"""Batched-ensemble driver: runs a list of replica
+"""Batched-ensemble driver (many independent replicas): runs a list of replica
 descriptions in one batch and, for comparison, one run at a time through
 the single-lattice path; tabulates extinction per (L, mobility-decade) bin."""
 from __future__ import annotations

@@ -1,4 +1,4 @@
-"""Request loop over the continuous-batching server.
+"""Request loop over the continuous-batching server (runs arriving over time).
 
 `serve()` replays a stream of run requests in real time: each request is
 submitted to the server when its (scaled) arrival time has passed, the
