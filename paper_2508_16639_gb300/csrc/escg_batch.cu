@@ -586,6 +586,11 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
   const BatchArgs& a = ta.a;
   BatchCtl* ctl = a.ctl;
   const int tid = threadIdx.x;
+  // More blocks per coarse phase than CTAs: the chunk is throughput-bound,
+  // and the regular (all 2 x 2) quads go first through the short step.
+  // Otherwise each replica's chain of visits is the bound, and row-major
+  // order spreads a fine phase's largest sub-blocks over all warps.
+  const bool reg_first = ctl->tot4 > gridDim.x;
   for (uint32_t n = 0;; ++n) {
     const int b = (int)(n & 1u);
     const uint32_t use = n >> 1;
@@ -616,11 +621,16 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
       const int cx = fcol & 1, cy = fcol >> 1;
       for (int q = tid; q < nquads; q += CONS) {
         int qx, qy;
-        quad_at(qm, q, qx, qy);
+        if (reg_first) {
+          quad_at(qm, q, qx, qy);
+        } else {
+          qy = (int)(((uint32_t)q * qm.inv_hx) >> 16);
+          qx = q - qy * qm.hx;
+        }
         const int fx = 2 * qx + cx, fy = 2 * qy + cy;
         const int sx = it.fsx[fx], wx = it.fsx[fx + 1] - sx;
         const int sy = it.fsy[fy], wy = it.fsy[fy + 1] - sy;
-        if (q < qm.n_reg) {   // a 2 x 2 sub-block: one Philox call, four attempts
+        if (reg_first && q < qm.n_reg) {   // a 2 x 2 sub-block: one Philox call, four attempts
           const uint32_t g = (uint32_t)(it.fy0 + fy) * (uint32_t)d.GQ + (uint32_t)(it.fx0 + fx);
           const int base = (sy + 1) * kBSP + xoff + sx;
           const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
