@@ -89,6 +89,8 @@ def _parse():
     ap.add_argument("--mobility", type=float, default=1e-4)
     ap.add_argument("--mcs-per-step", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
+                    help="time budget of the reference arm's timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--persistent", type=int, default=1)
@@ -194,23 +196,32 @@ def run_reference(args):
     D = O.circulant(w.S, w.K)
     lat = O.init(w.L, w.S, w.p_empty, w.seed)
     m = 0
-    for _ in range(args.warmup):
+    for _ in range(min(args.warmup, 3)):
         lat, _ = O.replay_run(lat, D, w.interact, w.reproduce, X, w.seed, 1, mcs_begin=m)
         m += 1
+    # One step = one MCS of the benchmark lattice (about 0.35 s on one core):
+    # the timed steps stop after --ref-seconds, so that the run stays within
+    # a few minutes whatever --steps asks for; the line reports the steps
+    # actually timed.
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    done = 0
+    while done < args.steps:
         lat, _ = O.replay_run(lat, D, w.interact, w.reproduce, X, w.seed, 1, mcs_begin=m)
         m += 1
+        done += 1
+        if time.perf_counter() - t0 >= args.ref_seconds:
+            break
     el = time.perf_counter() - t0
-    value = args.steps * w.L * w.L / el
+    value = done * w.L * w.L / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": done, "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / done,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
         "config": _config(w, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"schedule-v1 replay oracle, 1 MCS of the L={w.L} lattice per step"},
+                         "sample": f"schedule-v1 replay oracle, 1 MCS of the L={w.L} lattice per step, "
+                                   f"{done} steps timed (at most {args.ref_seconds:g} s)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
