@@ -325,7 +325,6 @@ __global__ void __launch_bounds__(THREADS) batch_kernel(BatchArgs a) {
 // (a log point) sets the replica's counts and stasis exactly as the chunk
 // kernel's last block does.
 constexpr int kResBytes1 = 16 * 1024, kResBytes2 = 56 * 1024;
-constexpr int kResThreads[4] = {0, 128, 256, 1024};
 
 // 64 registers a thread (8, 4 and 1 CTAs per SM for the three classes).
 template <int THREADS, int CLASS>
