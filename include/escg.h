@@ -204,6 +204,19 @@ int escg_restore(escg_t* h, const uint8_t* host_lattice, uint64_t mcs);
 int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_mcs,
                    uint8_t* host_out, uint64_t* counts_out);
 
+/* The same step, enqueued without waiting: returns once the copies and
+ * kernels are on the handle's stream.  host_in, host_out and counts_out must
+ * stay valid (and host_out / counts_out unread) until escg_step_host_wait,
+ * which synchronises and reports the step's errors as escg_step_host does.
+ * One step at a time per handle (ESCG_ESTATE otherwise); steps on different
+ * handles (each with its own stream) overlap their copies with each other's
+ * kernels -- e.g. two handles used alternately for a stream of lattices.
+ * With pageable host buffers the copies are synchronous (CUDA semantics), so
+ * overlap needs pinned buffers. */
+int escg_step_host_async(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_mcs,
+                         uint8_t* host_out, uint64_t* counts_out);
+int escg_step_host_wait(escg_t* h);
+
 /* Device address of the lattice (row pitch escg_lattice_pitch(L)) and the
  * handle's stream, for zero-copy interop (e.g. a torch tensor view). */
 void* escg_device_lattice(escg_t* h);

@@ -177,6 +177,24 @@ class Lattice:
                                     counts.ctypes.data_as(C.POINTER(C.c_uint64))))
         return out, counts
 
+    def step_host_async(self, lattice_in: np.ndarray, mcs: int, n_mcs: int, out: np.ndarray,
+                        counts: np.ndarray):
+        """step_host without waiting: the arrays (C-contiguous; pinned, e.g.
+        from torch's pin_memory, for the copies to overlap other work) must
+        stay alive and unread until step_host_wait()."""
+        for arr, dt in ((lattice_in, np.uint8), (out, np.uint8), (counts, np.uint64)):
+            if arr.dtype != dt or not arr.flags.c_contiguous:
+                raise ValueError("arrays must be C-contiguous uint8 lattices and uint64 counts")
+        if lattice_in.shape != (self.H, self.L) or out.shape != (self.H, self.L) or counts.size < self.S + 1:
+            raise ValueError("array shapes do not match the lattice")
+        self._inflight = (lattice_in, out, counts)   # keep the buffers alive
+        check(load().escg_step_host_async(self._h, _u8(lattice_in), int(mcs), int(n_mcs), _u8(out),
+                                          counts.ctypes.data_as(C.POINTER(C.c_uint64))))
+
+    def step_host_wait(self):
+        check(load().escg_step_host_wait(self._h))
+        self._inflight = None
+
     def kernel_time(self, reset: bool = False):
         """(total ms, launches) of the lattice-update kernels, measured with
         CUDA events on the handle's stream (needs time_kernels=True)."""

@@ -70,6 +70,8 @@ SIGNATURES = {
     "escg_snapshot": (C.c_int, [C.c_void_p, _u8p]),
     "escg_restore": (C.c_int, [C.c_void_p, _u8p, C.c_uint64]),
     "escg_step_host": (C.c_int, [C.c_void_p, _u8p, C.c_uint64, C.c_uint64, _u8p, _u64p]),
+    "escg_step_host_async": (C.c_int, [C.c_void_p, _u8p, C.c_uint64, C.c_uint64, _u8p, _u64p]),
+    "escg_step_host_wait": (C.c_int, [C.c_void_p]),
     "escg_device_lattice": (C.c_void_p, [C.c_void_p]),
     "escg_stream": (C.c_void_p, [C.c_void_p]),
     "escg_current_mcs": (C.c_uint64, [C.c_void_p]),

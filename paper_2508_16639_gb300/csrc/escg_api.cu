@@ -247,6 +247,8 @@ struct escg {
   uint32_t log_num0_host = 0;
   bool failed = false;
   RunState* d_scratch = nullptr;  // accumulator for on-demand counts
+  uint32_t* h_err = nullptr;      // pinned word: error bits of an asynchronous host step
+  bool pending_step = false;      // an escg_step_host_async has not been waited for
   int bits = 8;                   // bits per site of the device lattice
   uint8_t* d_stage = nullptr;     // packed lattices: byte image for host transfers
   int stage_pitch = 0;
@@ -375,6 +377,7 @@ void free_handle(escg* h) {
   if (h->own_lattice && h->lattice) cudaFree(h->lattice);
   cudaFree(h->d_tables);
   cudaFree(h->d_stage);
+  if (h->h_err) cudaFreeHost(h->h_err);
   cudaFree(h->d_trans);
   cudaFree(h->d_state);
   cudaFree(h->d_log);
@@ -917,8 +920,10 @@ int escg_restore(escg_t* h, const uint8_t* host_lattice, uint64_t mcs) {
   return ESCG_OK;
 }
 
-int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_mcs, uint8_t* host_out,
-                   uint64_t* counts_out) {
+// Enqueues the whole host step (restore, run, snapshot, counts) and the copy
+// of the run state's error bits to the handle's pinned word; nothing waits.
+static int step_host_enqueue(escg* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_mcs, uint8_t* host_out,
+                      uint64_t* counts_out) {
   if (!h || !host_in || !host_out) {
     set_err("NULL argument");
     return ESCG_EINVAL;
@@ -927,9 +932,13 @@ int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_m
     set_err("mcs exceeds 2^32-1");
     return ESCG_EINVAL;
   }
-  // One synchronisation for the whole call: copy in, reset, check (an
-  // invalid lattice stops the run state on the device), run, copy out,
-  // count, then read the error word.
+  if (!h->h_err && cudaMallocHost(&h->h_err, sizeof(uint32_t)) != cudaSuccess) {
+    h->h_err = nullptr;
+    set_err("pinned host allocation failed");
+    return ESCG_ENOMEM;
+  }
+  // copy in, reset, check (an invalid lattice stops the run state on the
+  // device), run, copy out, counts, error bits
   CUDA_TRY(copy_to_device(h, host_in));
   int rc = reset_state(h, mcs, true);
   if (rc != ESCG_OK) return rc;
@@ -951,9 +960,20 @@ int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_m
                                cudaMemcpyDeviceToHost, h->stream));
     }
   }
-  uint32_t err = 0;
-  CUDA_TRY(cudaMemcpyAsync(&err, &h->d_state->error, sizeof err, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->h_err, &h->d_state->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+  h->pending_step = true;
+  return ESCG_OK;
+}
+
+int escg_step_host_wait(escg_t* h) {
+  if (!h) {
+    set_err("NULL handle");
+    return ESCG_EINVAL;
+  }
+  if (!h->pending_step) return ESCG_OK;
+  h->pending_step = false;
   CUDA_TRY(cudaStreamSynchronize(h->stream));
+  const uint32_t err = *h->h_err;
   if (err & kErrBadValue) {
     h->failed = true;
     set_err("input lattice holds a value outside 0..S=%d", h->S);
@@ -965,6 +985,27 @@ int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_m
     return ESCG_ETIMEOUT;
   }
   return ESCG_OK;
+}
+
+int escg_step_host_async(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_mcs, uint8_t* host_out,
+                         uint64_t* counts_out) {
+  if (h && h->pending_step) {
+    set_err("a host step is already in flight on this handle; wait for it first");
+    return ESCG_ESTATE;
+  }
+  return step_host_enqueue(h, host_in, mcs, n_mcs, host_out, counts_out);
+}
+
+int escg_step_host(escg_t* h, const uint8_t* host_in, uint64_t mcs, uint64_t n_mcs, uint8_t* host_out,
+                   uint64_t* counts_out) {
+  // one synchronisation for the whole call
+  if (h && h->pending_step) {
+    const int rc = escg_step_host_wait(h);
+    if (rc != ESCG_OK) return rc;
+  }
+  const int rc = step_host_enqueue(h, host_in, mcs, n_mcs, host_out, counts_out);
+  if (rc != ESCG_OK) return rc;
+  return escg_step_host_wait(h);
 }
 
 void* escg_device_lattice(escg_t* h) { return h ? (void*)h->lattice : nullptr; }

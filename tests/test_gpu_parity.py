@@ -297,3 +297,38 @@ def test_restore_rejects_values_outside_states():
     g.run(2)
     o, _ = O.replay_run(good, O.circulant(S, [1]), 1.0, 1.0, 1.0, 3, 2)
     assert np.array_equal(g.snapshot(), o)
+
+
+def test_async_host_steps_on_two_handles():
+    """escg_step_host_async on two handles used alternately gives what
+    escg_step_host gives; one step in flight per handle; errors surface at
+    the wait."""
+    torch = pytest.importorskip("torch")
+    L, S, seed = 128, 3, 31
+    D = E.circulant(S, [1])
+    a = E.Lattice(L, S, D, (1.0, 1.0, 2.0), seed, p_empty=0.25)
+    b = E.Lattice(L, S, D, (1.0, 1.0, 2.0), seed, p_empty=0.25, stream=torch.cuda.Stream())
+    lat = torch.from_numpy(O.init(L, S, 0.25, 77)).pin_memory().numpy()
+    ref, cref = a.step_host(lat, 10, 10)
+    outs = [torch.empty((L, L), dtype=torch.uint8).pin_memory().numpy() for _ in range(2)]
+    cnts = [torch.zeros(S + 1, dtype=torch.int64).pin_memory().numpy().view(np.uint64) for _ in range(2)]
+    hs = (a, b)
+    for k in range(6):
+        i = k & 1
+        if k >= 2:
+            hs[i].step_host_wait()
+            assert np.array_equal(outs[i], ref) and np.array_equal(cnts[i], cref)
+        hs[i].step_host_async(lat, 10, 10, outs[i], cnts[i])
+        if k == 0:
+            with pytest.raises(E.EscgError):
+                a.step_host_async(lat, 10, 10, outs[0], cnts[0])   # one in flight
+    for h in hs:
+        h.step_host_wait()
+    assert all(np.array_equal(o, ref) for o in outs)
+    o, _ = O.replay_run(O.init(L, S, 0.25, 77), O.circulant(S, [1]), 1.0, 1.0, 2.0, seed, 10, mcs_begin=10)
+    assert np.array_equal(ref, o)
+    bad = lat.copy()
+    bad[3, 4] = S + 2
+    a.step_host_async(bad, 0, 5, outs[0], cnts[0])
+    with pytest.raises(E.EscgError):
+        a.step_host_wait()
