@@ -336,6 +336,14 @@ int64_t escg_server_submit(escg_server_t* s, const escg_replica_spec* spec);
  * *finished_out (may be NULL) receives the number of runs retired. */
 int escg_server_step(escg_server_t* s, int32_t* finished_out);
 
+/* Cancels run id between steps.  A queued run is dropped (its result: MCS
+ * 0, no counts); a running one stops at the MCS it has reached (its result:
+ * that MCS, the counts of its last log point, its lattice with
+ * keep_lattice) and frees its slot and arena memory.  Either way the id is
+ * reported by the next poll.  ESCG_ESTATE if the run already finished or
+ * is unknown. */
+int escg_server_cancel(escg_server_t* s, int64_t id);
+
 /* Ids of runs finished since the previous poll (up to cap). */
 int escg_server_poll(escg_server_t* s, int64_t* ids_out, int32_t cap, int32_t* n_out);
 

@@ -391,6 +391,10 @@ class Server:
         check(load().escg_server_step(self._h, C.byref(n)))
         return int(n.value)
 
+    def cancel(self, rid: int):
+        """Cancel a queued or running run between steps (see escg_server_cancel)."""
+        check(load().escg_server_cancel(self._h, int(rid)))
+
     def poll(self, cap: int = 65536):
         ids = np.zeros(cap, dtype=np.int64)
         n = C.c_int32()

@@ -100,6 +100,7 @@ SIGNATURES = {
     "escg_server_poll": (C.c_int, [C.c_void_p, _i64p, C.c_int32, _i32p]),
     "escg_server_result": (C.c_int, [C.c_void_p, C.c_int64, _u64p, _i32p, _u64p, _u8p]),
     "escg_server_stats": (C.c_int, [C.c_void_p, _i32p, _i32p, _u64p]),
+    "escg_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
     "escg_server_threads": (C.c_int32, [C.c_void_p]),
     "escg_server_launch_count": (C.c_uint64, [C.c_void_p]),
     "escg_server_destroy": (None, [C.c_void_p]),

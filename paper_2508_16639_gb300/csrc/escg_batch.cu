@@ -1552,6 +1552,60 @@ int escg_server_step(escg_server_t* s, int32_t* finished_out) {
   return ESCG_OK;
 }
 
+int escg_server_cancel(escg_server_t* s, int64_t id) {
+  if (!s) return ESCG_EINVAL;
+  // still queued: drop it; its result is the run not started (MCS 0)
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    if (it->id != id) continue;
+    s->queue.erase(it);
+    s->results[id] = Result{};
+    s->finished.push_back(id);
+    return ESCG_OK;
+  }
+  int slot = -1;
+  for (int i = 0; i < s->opt.max_slots; ++i)
+    if (s->slot_req[i] == id) slot = i;
+  if (slot < 0) {
+    set_last_error("run %lld is neither queued nor running", (long long)id);
+    return ESCG_ESTATE;
+  }
+  // resident: between steps the device is idle and every replica's MCS is
+  // settled.  The run's budget becomes its current MCS and one compaction
+  // takes it out of the active list before its slot can be reused.
+  SlotState x;
+  cudaError_t err = cudaStreamSynchronize(s->e.stream);
+  if (err == cudaSuccess) err = cudaMemcpy(&x, s->e.d_states + slot, sizeof x, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess)
+    err = cudaMemcpy(&s->e.d_slots[slot].max_mcs, &x.mcs, sizeof(uint32_t), cudaMemcpyHostToDevice);
+  s->e.h_slots[slot].max_mcs = x.mcs;
+  if (err == cudaSuccess) err = launch_compact(&s->e);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s->e.stream);
+  if (err != cudaSuccess) {
+    set_last_error("cancelling run %lld failed: %s", (long long)id, cudaGetErrorString(err));
+    return ESCG_ECUDA;
+  }
+  s->e.launches++;
+  Result res;
+  res.mcs = x.mcs;
+  res.extinct = (int32_t)x.stopped;
+  for (int v = 0; v < kMaxStates; ++v) res.counts[v] = x.counts[v];
+  if (s->opt.keep_lattice) {
+    const LatticeDesc& d = s->e.h_slots[slot].d;
+    res.lattice.resize((size_t)d.L * d.L);
+    if (cudaMemcpy2D(res.lattice.data(), d.L, d.lat, d.pitch, d.L, d.L, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      set_last_error("copying a cancelled lattice failed");
+      return ESCG_ECUDA;
+    }
+  }
+  s->results[id] = std::move(res);
+  s->finished.push_back(id);
+  engine_release(&s->e, slot);
+  s->slot_req[slot] = -1;
+  s->free_slots.push_back(slot);
+  s->resident--;
+  return ESCG_OK;
+}
+
 int escg_server_poll(escg_server_t* s, int64_t* ids_out, int32_t cap, int32_t* n_out) {
   if (!s || (cap > 0 && !ids_out) || cap < 0) return ESCG_EINVAL;
   const int32_t n = (int32_t)std::min<size_t>((size_t)cap, s->finished.size());

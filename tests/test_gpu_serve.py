@@ -74,3 +74,43 @@ def test_submit_rejects_runs_larger_than_the_arena():
     r = _reqs(1, seed=1, L_range=(600, 601))[0]
     with pytest.raises(E.EscgError):
         srv.submit(request_spec(r))
+
+
+def test_cancel_queued_and_running_runs():
+    """A queued run cancelled before admission reports MCS 0; a running run
+    cancelled between steps stops at the MCS it reached, with the lattice a
+    run alone reaches at that MCS; the other runs are unaffected and the
+    slot and arena memory are reused."""
+    reqs = _reqs(10, seed=13, L_range=(60, 200), budget=(300, 600))
+    specs = [dict(request_spec(r), stop_at_extinction=False) for r in reqs]
+    srv = E.Server(arena_bytes=1 << 20, max_slots=4, keep_lattice=True, chunks_per_step=1)
+    ids = [srv.submit(sp) for sp in specs]
+    srv.step()                                   # a few runs resident, the rest queued
+    resident, queued, _ = srv.stats()
+    assert resident >= 1 and queued >= 1
+    running, waiting = ids[0], ids[-1]
+    srv.cancel(waiting)
+    srv.step()
+    srv.cancel(running)
+    with pytest.raises(E.EscgError):
+        srv.cancel(running)                      # already finished
+    done = set()
+    for _ in range(10000):
+        done.update(srv.poll())
+        if len(done) == len(ids):
+            break
+        srv.step()
+    assert len(done) == len(ids)
+    m, ext, cnt, lat = srv.result(waiting)
+    assert m == 0 and not ext
+    m, ext, cnt, lat = srv.result(running, lattice=True)
+    sp = specs[0]
+    assert 0 < m < sp["max_mcs"] and m % 10 == 0
+    g = E.Lattice(sp["L"], sp["S"], sp["digraph"], sp["rates"], sp["seed"], p_empty=sp["p_empty"], log_every=10)
+    g.run(m)
+    assert np.array_equal(lat, g.snapshot())
+    for rid, sp in zip(ids[1:-1], specs[1:-1]):
+        m1, lat1, _ = _alone(sp)
+        mcs, _, _, lat2 = srv.result(rid, lattice=True)
+        assert mcs == m1 and np.array_equal(lat2, lat1), rid
+    assert srv.stats() == (0, 0, 0)
