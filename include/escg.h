@@ -73,8 +73,9 @@ typedef struct {
                                     non-empty species alive (stasis())        */
     uint32_t schedule_version;   /* 0 or 1 (only version 1 exists)            */
     int32_t persistent;          /* 1: persistent dataflow launches (default;
-                                    uniform 64x64 partitions use the boundary-
-                                    mailbox kernel where it is faster, generic
+                                    uniform square partitions of one byte per
+                                    site use the block owners of 5 while they
+                                    need at most 3 CTAs per SM, generic
                                     partitions of 2 x 2 coarse blocks the
                                     whole-lattice residency of 4);
                                     2: same, uniform partitions staged by a
@@ -87,6 +88,19 @@ typedef struct {
                                     coarse blocks per axis whose image fits
                                     one CTA's shared memory, about 470 x 470;
                                     larger ones run as 3);
+                                    5: block owners: one CTA per 2 x 2 group
+                                    of 64 x 64 blocks keeps their tiles in
+                                    shared memory for the whole launch and
+                                    exchanges only boundary records (square,
+                                    one byte per site, L a multiple of 128,
+                                    (L/128)^2 CTAs resident at once, so the
+                                    launches of several handles take turns;
+                                    other lattices run as 3);
+                                    6: boundary mailbox: the work items of 3
+                                    taken from a ticket counter, neighbours'
+                                    edge and rim lines read from epoch-tagged
+                                    records (same lattices as 5, no residency
+                                    requirement; others run as 3);
                                     0: one launch per coarse phase            */
     void* cuda_stream;           /* cudaStream_t to enqueue on, or NULL for a
                                     stream owned by the handle                */

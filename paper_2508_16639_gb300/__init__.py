@@ -62,11 +62,13 @@ class Lattice:
     rates: (interact, reproduce, exchange).  device_buffer: optional torch
     uint8 CUDA tensor of at least lattice_bytes(L) bytes used as the lattice
     storage; stream: optional torch.cuda.Stream (or raw cudaStream_t int).
-    persistent: 1 persistent dataflow launches (default; uniform 64x64
-    partitions use the boundary-mailbox kernel where it is faster), 3 the
-    same with epoch flags only, 2 with a TMA producer warp, 4 the whole
+    persistent: 1 persistent dataflow launches (default; the kernel is
+    picked by lattice size), 3 with epoch flags only, 2 with a TMA producer
+    warp, 6 with boundary records (mailbox), 4 the whole
     lattice resident in one CTA's shared memory (small lattices; larger ones
-    run as 3), 0 one launch per coarse phase -- all bit-identical.  dominance_prob: optional S x S edge
+    run as 3), 5 one CTA per 2x2 group of blocks with its tiles resident
+    (uniform square lattices of one byte per site; others run as 3), 0 one
+    launch per coarse phase -- all bit-identical.  dominance_prob: optional S x S edge
     probabilities (Park, Chen and Szolnoki's probabilistic dominance);
     neighbourhood 4 or 8 (Moore) and reflecting_boundary: the paper's rule
     variants.  H: rows (default L).  bits_per_site: device storage, 8 (one

@@ -241,6 +241,9 @@ struct escg {
   int grid = 0;
   bool use_tma = false;
   bool use_resident = false;     // persistent = 4 and the lattice fits one CTA's shared memory
+  bool use_own = false;          // block-owner kernel (uniform, square, one byte per site)
+  int own_dyn = 0;               // its shared-memory padding
+  int own_threads = 0;           // and CTA size
   CUtensorMap tmap{};
   uint32_t spin_limit = kDefaultSpinLimit;
   int stall_block = -1;
@@ -355,6 +358,12 @@ int reset_state(escg* h, uint64_t mcs, bool validate = false) {
   h->launches++;
   CUDA_TRY(launch_fill_u32(h->d_done, h->part.P * h->part_y.P, (uint32_t)mcs, h->stream));
   h->launches++;
+  // Boundary records left by an earlier run carry epochs the new one may wait
+  // for (a lattice restored at an MCS the handle has run through before):
+  // epoch 0 never matches a wait, which always expects an epoch >= 1.
+  if (h->d_ob)
+    CUDA_TRY(cudaMemsetAsync(h->d_ob, 0, (size_t)h->part.P * h->part.P * kRecordWords * sizeof(unsigned long long),
+                             h->stream));
   h->log_num0_host = num0;
   h->mcs_enq = mcs;
   h->failed = false;
@@ -529,8 +538,8 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     set_err("device_lattice must be 16-byte aligned (rows are read as 16-byte vectors)");
     return nullptr;
   }
-  if (o.persistent < 0 || o.persistent > 4) {
-    set_err("persistent must be 0..4 (got %d)", o.persistent);
+  if (o.persistent < 0 || o.persistent > 6) {
+    set_err("persistent must be 0..6 (got %d)", o.persistent);
     return nullptr;
   }
   if (o.schedule_version != 0 && o.schedule_version != 1) {
@@ -688,11 +697,13 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   }
   // The mailbox kernel shortens every hop of the colour-phase chain but
   // binds each CTA's next item one visit early.  Measured (GB300, 608 CTAs):
-  // faster while a coarse phase has at most half as many blocks as there
-  // are CTAs (L <= 2048: 10-25 %), slower with 576 or 625 blocks per phase
-  // (L = 3072, 3200: 3-5 %), where the flag kernel keeps items unbound
-  // until a CTA is free.
-  if (d.uniform64 && square && o.persistent == 1 && 2 * (p.P * p.P / 4) <= persistent_ll_grid(h->device)) {
+  // faster than the flag kernel while a coarse phase has at most half as
+  // many blocks as there are CTAs (L <= 2048: 10-25 %), slower with 576 or
+  // 625 blocks per phase (L = 3072, 3200: 3-5 %), where the flag kernel keeps
+  // items unbound until a CTA is free.  It runs on request (6) and by default
+  // where the block owners below cannot.
+  if (d.uniform64 && square && (o.persistent == 1 || o.persistent == 6) &&
+      (o.persistent == 6 || 2 * (p.P * p.P / 4) <= persistent_ll_grid(h->device))) {
     const size_t words = (size_t)p.P * p.P * kRecordWords;
     if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
       set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
@@ -700,6 +711,31 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     }
     h->use_ll = true;
     h->grid = persistent_ll_grid(h->device);
+  }
+  // Block owners: on request (5), and by default (1) from 3 x 3 groups of
+  // blocks while the grid needs at most 3 CTAs per SM -- measured (GB300, µs
+  // per MCS, mailbox or flag kernel vs owners): L = 384 15.4 vs 14.1, 512
+  // 15.9 vs 14.4, 1024 18.2 vs 13.0, 1536 20.0 vs 12.4, 2048 19.7 vs 15.1,
+  // 2560 23.3 vs 19.5; tied at L = 256 and at 4 per SM (3072); slower at
+  // L = 128 (13.3 vs 14.0) and from 5 per SM (3200: 25.5 vs 29.2), where every
+  // CTA of an SM is in the same colour phase at once and the flag kernel's
+  // free binding keeps the SMs busier.  Needs the device to hold one CTA per
+  // 2x2 group of blocks at once.
+  if (d.uniform64 && square && (o.persistent == 5 || (o.persistent == 1 && p.P >= 6))) {
+    int dyn = 0, nt = 0, per_sm = 0;
+    if (persistent_own_config(d, h->device, &dyn, &nt, &per_sm) > 0 && (o.persistent == 5 || per_sm <= 3)) {
+      if (!h->d_ob) {
+        const size_t words = (size_t)p.P * p.P * kRecordWords;
+        if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
+          set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
+          return fail(ESCG_ENOMEM);
+        }
+      }
+      h->use_own = true;
+      h->own_dyn = dyn;
+      h->own_threads = nt;
+      h->use_ll = false;
+    }
   }
   // Whole-lattice residency: on request (4), and by default (1) for a generic
   // partition with 2 x 2 coarse blocks (L, H < 192 and not 128), where it was
@@ -781,6 +817,8 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
       CUDA_TRY(timing_begin(h));
       if (h->use_resident) {
         CUDA_TRY(launch_resident(a, h->stream));
+      } else if (h->use_own) {
+        CUDA_TRY(launch_persistent_own(a, h->own_dyn, h->own_threads, h->stream));
       } else if (h->use_tma) {
         TmaArgs ta{};
         ta.map = h->tmap;
@@ -793,7 +831,7 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
       }
       CUDA_TRY(timing_end(h));
       h->launches++;
-      if (h->use_ll) {
+      if (h->use_ll || h->use_own) {
         CUDA_TRY(launch_ll_merge(h->desc, h->d_ob, h->d_state, (uint32_t)end, h->stream));
         h->launches++;
       }
@@ -1063,6 +1101,7 @@ const char* escg_update_kernel(escg_t* h) {
   if (!h) return "";
   if (!h->opt.persistent) return "phase_kernel";
   if (h->use_resident) return "resident_kernel";
+  if (h->use_own) return "persistent_own_kernel";
   if (h->use_tma) return "persistent_tma_kernel";
   return h->use_ll ? "persistent_ll_kernel" : "persistent_kernel";
 }

@@ -767,13 +767,13 @@ __device__ __forceinline__ void hist_add_words(uint32_t* hist, int S, uint32_t w
   }
 }
 
-// Uniform geometry (64x64 blocks, 256 threads): every thread takes one
-// 16-byte piece of the interior and at most one rim piece; excluded bytes are
-// set to 0xFF (never a state).  hist: per-CTA histogram in shared memory.
+// Uniform geometry (64x64 blocks): piece t (0..255) is one 16-byte piece of
+// the interior and, for t < 24, one rim piece; excluded bytes are set to 0xFF
+// (never a state).  hist: per-CTA histogram in shared memory.  All lanes of a
+// warp call together.
 template <int SP, int COFF>
-__device__ __forceinline__ void count_visit_uni(const uint8_t* tile, uint32_t* hist, int S, int k, int sV,
-                                                int sH, int sD) {
-  const int t = threadIdx.x;
+__device__ __forceinline__ void count_pieces_uni(const uint8_t* tile, uint32_t* hist, int S, int k, int sV,
+                                                 int sH, int sD, int t) {
   uint32_t w[4];
   {
     const int r = t >> 2, q = t & 3;
@@ -809,6 +809,13 @@ __device__ __forceinline__ void count_visit_uni(const uint8_t* tile, uint32_t* h
     x[1] = p[1];
   }
   hist_add_words(hist, S, x[0], x[1], x[2], x[3]);
+}
+
+// 256 threads, piece t = thread t.
+template <int SP, int COFF>
+__device__ __forceinline__ void count_visit_uni(const uint8_t* tile, uint32_t* hist, int S, int k, int sV,
+                                                int sH, int sD) {
+  count_pieces_uni<SP, COFF>(tile, hist, S, k, sV, sH, sD, (int)threadIdx.x);
 }
 
 // Any geometry: rows by warps, one site per lane step, shared-memory

@@ -103,6 +103,16 @@ cudaError_t launch_resident(const PersistentArgs& a, cudaStream_t stream);
 constexpr int kRecordWords = 128;
 cudaError_t launch_persistent_ll(const PersistentArgs& a, int grid, cudaStream_t stream);
 int persistent_ll_grid(int device);
+// Block-owner variant (uniform geometry, square, one byte per site): CTA g
+// owns coarse group g (2x2 blocks) for the whole launch with their tiles in
+// shared memory and exchanges boundary records like the mailbox kernel (a.ob,
+// kRecordWords per block; ll_merge completes the lattice array afterwards).
+// All (P/2)^2 CTAs must be resident at once: persistent_own_config returns
+// the grid size, the CTA size (128 or 256 threads), the shared-memory
+// padding that spreads the grid over the SMs and the CTAs per SM that
+// leaves, or 0 when the device cannot hold the whole grid.
+int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int* threads, int* ctas_per_sm);
+cudaError_t launch_persistent_own(const PersistentArgs& a, int dyn_bytes, int threads, cudaStream_t stream);
 // Completes the lattice array after a mailbox launch that ended at MCS
 // m_end: every edge cell of a block that a neighbour's visit wrote last (in
 // MCS m_end - 1) takes the value from that neighbour's record.  Does nothing

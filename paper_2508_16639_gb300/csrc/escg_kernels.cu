@@ -12,6 +12,12 @@
 //                      required epoch (bounded spin; gives up with an error
 //                      status instead of hanging); species counts of log
 //                      points are fused into the visits
+//   persistent_ll_kernel   the same work items with boundary records (a
+//                      visit's edge and rim lines, epoch-tagged) in place of
+//                      epoch flags and rim loads
+//   persistent_own_kernel  each CTA owns one 2x2 group of blocks for the
+//                      whole launch, their tiles resident in shared memory;
+//                      visits exchange only boundary records
 #include <cstdio>
 
 #include "escg_device.cuh"
@@ -792,6 +798,292 @@ __global__ void __launch_bounds__(256) ll_merge_kernel(LatticeDesc d, const unsi
 }
 
 // ---------------------------------------------------------------------------
+// Block-owner kernel (uniform geometry, square, one byte per site).  CTA g
+// owns coarse group g -- the 2x2 blocks (2 gx + cx, 2 gy + cy), one of each
+// colour -- for the whole launch and keeps their four tiles (interior and rim
+// lines) in shared memory from visit to visit.  A visit exchanges only the
+// mailbox kernel's boundary records: it polls its 4 edge neighbours' records
+// and 8 diagonal rim-end words, places each boundary cell from its latest
+// writer (the block's own previous visit is already in the tile), runs the
+// four fine phases and publishes its 4 records.  There is no ticket, no
+// interior load or store and no epoch flag: the lattice array is read when
+// the launch starts (nothing writes it during the launch) and the interiors
+// are written when it ends; the rim strips then come from the records
+// (ll_merge_kernel), as after a mailbox launch.  Same schedule, same results.
+//
+// Every CTA waits for visits that only its neighbours' owners perform, so the
+// whole grid must be resident at once: it is a cooperative launch, made only
+// when the occupancy allows, with shared memory padded so that the CTAs
+// spread over all SMs (at most ceil(groups / SMs) per SM).
+// CTAs of 256 threads (one quad per thread) or, where the grid needs more
+// than 4 CTAs per SM, 128 (two quads per thread, stepped pairwise).
+
+struct OwnSmem {
+  alignas(16) uint8_t tile[4][kUniTileBytes];   // tile[c]: the group's block of colour c
+  uint32_t trans[kTransWords];
+  uint32_t hist[kMaxStates];
+  uint32_t forder;   // fine order of the current visit
+  uint32_t abort;
+};
+
+// The group's block (bx, by) as the lattice array holds it: interior, top and
+// bottom rim rows, left and right rim columns (the corners are not used).
+template <int NT>
+__device__ __forceinline__ void own_stage(const LatticeDesc& d, uint8_t* tile, int bx, int by) {
+  const int L = d.L, pitch = d.pitch, x0 = bx * kUniB, y0 = by * kUniB;
+  for (int i = threadIdx.x; i < (kUniB + 2) * 4; i += NT) {
+    const int r = (i >> 2) - 1, q = i & 3;
+    tile_row16(tile, r, 16 * q,
+               __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, L) * pitch + x0) + q));
+  }
+  const int xl = wrap(x0 - 1, L), xr = wrap(x0 + kUniB, L);
+  for (int i = threadIdx.x; i < 2 * kUniB; i += NT) {
+    const int r = i & (kUniB - 1), right = i >= kUniB;
+    tile[tidx(r, right ? kUniB : -1, kUniSP)] = __ldcg(d.lat + (size_t)(y0 + r) * pitch + (right ? xr : xl));
+  }
+}
+
+// New values of an attempt's pair (cell a, neighbour b) as one byte (low
+// nibble: the cell, high nibble: the neighbour), the transition of
+// apply_rule.
+__device__ __forceinline__ uint32_t rule_nn(const uint8_t* __restrict__ trans, uint32_t a, uint32_t b, uint32_t u,
+                                            uint32_t tx, uint32_t txi, uint32_t s1) {
+  if (u < tx) return b | (a << 4);
+  const uint32_t pair = a * s1 + b;
+  const uint32_t tp = reinterpret_cast<const uint32_t*>(trans)[kTransPairs + pair];
+  const uint32_t act = (u >= txi) ? 2u : (u < tp ? 1u : 3u);
+  return trans[pair * 4u + act];
+}
+
+// Two elementary steps (words wa, wb) on two sub-blocks of the same fine
+// colour (first cells at basea, baseb): their cells and neighbours are
+// disjoint, so both pairs are read before either is written and the two
+// dependency chains overlap.  Each step is attempt_uni's.
+template <int SP>
+__device__ __forceinline__ void attempt_uni_pair(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
+                                                 uint32_t wa, int basea, uint32_t wb, int baseb, uint32_t tx,
+                                                 uint32_t txi, uint32_t s1) {
+  constexpr uint32_t kTi = 0u | (1u << 8) | ((uint32_t)SP << 16) | ((uint32_t)(SP + 1) << 24);
+  constexpr uint32_t kTj = 0u | ((uint32_t)(2 * SP) << 8) | ((uint32_t)(SP - 1) << 16) | ((uint32_t)(SP + 1) << 24);
+  const int tia = basea + (int)__byte_perm(kTi, 0u, wa >> 30);
+  const int tja = tia - SP + (int)__byte_perm(kTj, 0u, (wa >> 28) & 3u);
+  const int tib = baseb + (int)__byte_perm(kTi, 0u, wb >> 30);
+  const int tjb = tib - SP + (int)__byte_perm(kTj, 0u, (wb >> 28) & 3u);
+  const uint32_t aa = tile[tia], ba = tile[tja], ab = tile[tib], bb = tile[tjb];
+  const uint32_t na = rule_nn(trans, aa, ba, wa << 4, tx, txi, s1);
+  const uint32_t nb = rule_nn(trans, ab, bb, wb << 4, tx, txi, s1);
+  tile[tia] = (uint8_t)(na & 15u);
+  tile[tja] = (uint8_t)(na >> 4);
+  tile[tib] = (uint8_t)(nb & 15u);
+  tile[tjb] = (uint8_t)(nb >> 4);
+}
+
+// The four fine colour phases of a uniform visit by 128 threads: thread t
+// takes quads t and t + 128 (rows 4 qy..4 qy+3 and 32 rows below) and runs
+// their steps pairwise.
+__device__ __forceinline__ void own_fine_phases(const LatticeDesc& d, int bx, int by, uint32_t m, uint8_t* tile,
+                                                uint32_t ord, const uint8_t* trans) {
+  const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
+  const uint32_t s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
+  const uint32_t GQ = (uint32_t)d.GQ;
+  const uint32_t g00 = (uint32_t)(by * (kUniB / 2) + 2 * qy) * GQ + (uint32_t)(bx * (kUniB / 2) + 2 * qx);
+  const int base00 = tidx(4 * qy, 4 * qx, kUniSP);
+  constexpr uint32_t kRowsB = kUniB / 4;          // quad rows 8.. are 16 sub-block rows below
+  constexpr int kBaseB = (kUniB / 2) * kUniSP;    // and 32 tile rows below
+#pragma unroll
+  for (int fi = 0; fi < 4; ++fi) {
+    const uint32_t fcol = (ord >> (2 * fi)) & 3u, cx = fcol & 1u, cy = fcol >> 1;
+    const uint32_t g = g00 + cy * GQ + cx;
+    const int base = base00 + (int)(cy * (2 * kUniSP) + 2 * cx);
+    const uint4 xa = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
+    const uint4 xb = philox10_rk(make_uint4(0u, g + kRowsB * GQ, m, kTagStep), d.rk);
+    attempt_uni_pair<kUniSP>(tile, trans, xa.x, base, xb.x, base + kBaseB, tx, txi, s1);
+    attempt_uni_pair<kUniSP>(tile, trans, xa.y, base, xb.y, base + kBaseB, tx, txi, s1);
+    attempt_uni_pair<kUniSP>(tile, trans, xa.z, base, xb.z, base + kBaseB, tx, txi, s1);
+    attempt_uni_pair<kUniSP>(tile, trans, xa.w, base, xb.w, base + kBaseB, tx, txi, s1);
+    __syncthreads();
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) persistent_own_kernel(PersistentArgs a) {
+  extern __shared__ uint8_t own_pad[];   // occupancy padding only
+  __shared__ OwnSmem sm;
+  (void)own_pad;
+  const LatticeDesc& d = a.d;
+  RunState* st = a.st;
+  unsigned long long* ob = a.ob;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool run = !ld_volatile(&st->stopped);
+  if (run) {
+    load_trans(d, sm.trans);
+    const int P = d.P, half = P >> 1, pitch = d.pitch;
+    const uint32_t nb = (uint32_t)(P * P);
+    const int gx = (int)blockIdx.x % half, gy = (int)blockIdx.x / half;
+    for (int c = 0; c < 4; ++c) own_stage<NT>(d, sm.tile[c], 2 * gx + (c & 1), 2 * gy + (c >> 1));
+    const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
+    const uint32_t m_end = a.m_begin + a.n_mcs;
+    uint32_t ordp = colour_order(philox10(make_uint4(0u, 0u, a.m_begin - 1u, kTagOrder), d.key0, d.key1).x,
+                                 d.perm24);
+    uint32_t ord = colour_order(philox10(make_uint4(0u, 0u, a.m_begin, kTagOrder), d.key0, d.key1).x, d.perm24);
+    uint32_t ord_next = ord;
+    if (tid == 0) sm.abort = 0;
+    __syncthreads();
+    bool quit = false;
+    for (uint32_t m = a.m_begin; m < m_end && !quit; ++m) {
+      if (m != a.m_begin) {
+        ordp = ord;
+        ord = ord_next;
+      }
+      for (int k = 0; k < 4; ++k) {
+        if (tid < kMaxStates) sm.hist[tid] = 0;
+        const int colour = order_at(ord, k);
+        const int bx = 2 * gx + (colour & 1), by = 2 * gy + (colour >> 1);
+        const int X = by * P + bx;
+        uint8_t* tile = sm.tile[colour];
+        const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1), sD = slot_of(ord, colour ^ 3);
+        const int kV0 = sV < k ? sV + 4 : slot_of(ordp, colour ^ 2);
+        const int kH0 = sH < k ? sH + 4 : slot_of(ordp, colour ^ 1);
+        const int kD0 = sD < k ? sD + 4 : slot_of(ordp, colour ^ 3);
+        const uint32_t eV = sV < k ? m + 1u : m, eH = sH < k ? m + 1u : m, eD = sD < k ? m + 1u : m;
+        // first visit of the launch: the tile holds the lattice array as it
+        // was at launch start; only neighbours that visited earlier in this
+        // launch come from their records (keys >= 4 beat the lattice's 3)
+        const bool first = (m == a.m_begin);
+        const int kV = first && sV > k ? -1 : kV0, kH = first && sH > k ? -1 : kH0;
+        const int kD = first && sD > k ? -1 : kD0, kXp = first ? 3 : slot_of(ordp, colour);
+        // warp s < 4: the record of the edge neighbour across side s (its
+        // record of the opposite side, one word per lane); lanes 0 and 1 also
+        // a diagonal neighbour's rim-end word, dl = 2 s + lane: dl 0..3 the
+        // ends of the top and bottom rim rows, 4..7 those of the left and
+        // right rim columns
+        const bool poller = warp < 4;
+        const int s = warp & 3;
+        const int nx = (s == 2) ? (bx + P - 1) % P : (s == 3) ? (bx + 1) % P : bx;
+        const int ny = (s == 0) ? (by + P - 1) % P : (s == 1) ? (by + 1) % P : by;
+        const uint32_t e = (s < 2) ? eV : eH;
+        const unsigned long long* p = ob + ((size_t)(ny * P + nx) * 4 + (s ^ 1)) * 32 + lane;
+        const int dl = 2 * s + (lane & 1);
+        const int ddx = (dl == 0 || dl == 2 || dl == 4 || dl == 5) ? -1 : 1;
+        const int ddy = (dl == 0 || dl == 1 || dl == 4 || dl == 6) ? -1 : 1;
+        const int drec = (dl < 4) ? (ddx < 0 ? 3 : 2) : (ddy < 0 ? 1 : 0);
+        const int dpos = (dl < 4) ? (ddy < 0 ? 63 : 0) : (ddx < 0 ? 63 : 0);
+        const unsigned long long* pd =
+            ob + ((size_t)(((by + P + ddy) % P) * P + (bx + P + ddx) % P) * 4 + drec) * 32 + 16 + (dpos >> 2);
+        bool got = !poller || (first && ((s < 2) ? sV : sH) > k);
+        bool got_d = !poller || lane >= 2 || (first && sD > k);
+        unsigned long long word = 0, dword = 0;
+        if (!got) word = ld_word(p);
+        if (!got_d) dword = ld_word(pd);
+        // while those loads are in flight: the fine order of this visit and
+        // the coarse order of the next MCS
+        if (tid == NT - 1) sm.forder = fine_order(d, bx, by, m);
+        if (k == 3) ord_next = colour_order(philox10(make_uint4(0u, 0u, m + 1u, kTagOrder), d.key0, d.key1).x,
+                                            d.perm24);
+        bool failed = false;
+        uint32_t spins = 0;
+        for (;;) {
+          if (!got) got = (uint32_t)(word >> 32) == e;
+          if (!got_d) got_d = (uint32_t)(dword >> 32) == eD;
+          if (got && got_d) break;
+          if (ld_volatile(&st->abort)) {
+            failed = true;
+            break;
+          }
+          if (++spins > a.spin_limit) {
+            atomicOr(&st->error, kErrTimeout);
+            atomicExch(&st->abort, 1u);
+            failed = true;
+            break;
+          }
+          __nanosleep(64);
+          if (!got) word = ld_word(p);
+          if (!got_d) dword = ld_word(pd);
+        }
+        if (failed) {
+          sm.abort = 1u;
+        } else if (poller) {
+          // each boundary cell takes the value of its latest writer; where
+          // that is the block itself, the tile already holds it
+          const int xp = 1 - (lane >> 4), w = lane & 15;
+          const int kS = (s < 2) ? kV : kH, kO = (s < 2) ? kH : kV;
+          const uint32_t data = (uint32_t)word;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int pos = 4 * w + jj;
+            const bool end = (pos == 0) || (pos == kUniB - 1);
+            const int beat = end ? max(xp == 0 ? kO : kD, kXp) : kXp;
+            if (kS > beat) tile[line_tidx(s, xp, pos)] = (uint8_t)(data >> (8 * jj));
+          }
+          if (lane < 2) {
+            const int xs = (dl < 4) ? (dl >> 1) : 2 + ((dl - 4) >> 1);
+            const int xpos = (dl & 1) ? kUniB - 1 : 0;
+            if (kD > max((xs < 2) ? kV : kH, kXp))
+              tile[line_tidx(xs, 1, xpos)] = (uint8_t)((uint32_t)dword >> (8 * (dpos & 3)));
+          }
+        }
+        __syncthreads();
+        if (sm.abort) {
+          quit = true;
+          break;
+        }
+        if (NT == 128)
+          own_fine_phases(d, bx, by, m, tile, sm.forder, trans);
+        else
+          fine_phases_tile(d, bx, by, m, tile, sm.forder, trans);
+        if (poller && X != a.stall_block) {
+          const int part = lane >> 4, w = lane & 15;
+          uint32_t bytes = 0;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) bytes |= (uint32_t)tile[line_tidx(s, part, 4 * w + jj)] << (8 * jj);
+          st_word(ob + ((size_t)X * 4 + s) * 32 + lane, ((unsigned long long)(m + 1u) << 32) | bytes);
+        }
+        if (((m + 1u) % a.log_every) == 0u) {
+          count_pieces_uni<kUniSP, kColOff>(tile, sm.hist, d.S, k, sV, sH, sD, tid);
+          if (NT == 128) count_pieces_uni<kUniSP, kColOff>(tile, sm.hist, d.S, k, sV, sH, sD, tid + 128);
+          __syncthreads();
+          const uint32_t ring = ((m + 1u) / a.log_every) % (uint32_t)kPendRing;
+          if (tid <= d.S && sm.hist[tid]) atomicAdd(&st->acc[ring][tid], (unsigned long long)sm.hist[tid]);
+          __syncthreads();
+          if (tid == 0) {
+            __threadfence();
+            if (atomicAdd(&st->pend[ring], 1u) == nb - 1u) {
+              // last block of this log point: every contribution is in acc
+              __threadfence();
+              unsigned long long c[kMaxStates];
+              for (int v = 0; v < kMaxStates; ++v) c[v] = atomicExch(&st->acc[ring][v], 0ull);
+              st->pend[ring] = 0;
+              write_log_entry(st, a.lb, d.S, m + 1u, a.log_every, c, a.stop_at_extinction);
+            }
+          }
+        }
+        // the next visit's placement must not overtake this visit's record
+        // reads and counts
+        __syncthreads();
+      }
+    }
+    // the interiors to the lattice array (its rim strips: ll_merge_kernel)
+    for (int i = tid; i < 4 * kUniB * 4; i += NT) {
+      const int c = i >> 8, r = (i >> 2) & (kUniB - 1), q = i & 3;
+      const int x0 = (2 * gx + (c & 1)) * kUniB, y0 = (2 * gy + (c >> 1)) * kUniB;
+      const uint2* src = reinterpret_cast<const uint2*>(sm.tile[c] + tidx(r, 16 * q, kUniSP));
+      const uint2 u0 = src[0], u1 = src[1];
+      reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(u0.x, u0.y, u1.x, u1.y);
+    }
+  }
+  // The last CTA to leave publishes the MCS number.
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&st->exited, 1u) == gridDim.x - 1u) {
+      st->exited = 0;
+      st->ticket = 0;
+      if (!st->stopped && !st->abort) st->mcs = a.m_begin + a.n_mcs;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Warp-specialised persistent kernel for the uniform geometry (64x64 blocks,
 // 2x2 sub-blocks).  Warp 8 is the producer: it takes the next work item from
 // the ticket counter, waits for the block's 8 neighbours, and stages the
@@ -1277,6 +1569,66 @@ int persistent_ll_grid(int device) {
   if (per_sm > kLLMinBlocks) per_sm = kLLMinBlocks;
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;
+}
+
+// Shared-memory padding for NT-thread owner CTAs so that an SM holds at
+// most per_sm of them (and at least per_sm fit), or -1.
+template <int NT>
+static int own_padding(int per_sm, int smem_sm, int reserved, int optin) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, persistent_own_kernel<NT>) != cudaSuccess) return -1;
+  const int stat = (int)fa.sharedSizeBytes;
+  if (optin - stat <= 0 ||
+      cudaFuncSetAttribute(persistent_own_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - stat) !=
+          cudaSuccess)
+    return -1;
+  int dyn = smem_sm / per_sm - reserved - stat - 256;
+  if (dyn > optin - stat) dyn = optin - stat;
+  for (dyn = dyn > 0 ? dyn & ~127 : 0;; dyn -= 1024) {
+    if (dyn < 0) dyn = 0;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_own_kernel<NT>, NT, (size_t)dyn) !=
+        cudaSuccess)
+      return -1;
+    if (occ >= per_sm) return dyn;
+    if (dyn == 0) return -1;   // the grid cannot be resident at once
+  }
+}
+
+int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int* threads, int* ctas_per_sm) {
+  const int groups = (d.P / 2) * (d.P / 2);
+  int sms = 0, smem_sm = 0, reserved = 0, optin = 0, coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+  if (!coop) return 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (sms <= 0) return 0;
+  // the padding spreads the grid over all SMs: at most ceil(groups / SMs)
+  // CTAs per SM
+  const int per_sm = (groups + sms - 1) / sms;
+  // 256 threads while 4 fit an SM (54 registers); beyond, 128 (a 256-thread
+  // build for 5 per SM, held to 48 registers, was measured slower)
+  const int nt = per_sm <= 4 ? 256 : 128;
+  const int dyn = nt == 256 ? own_padding<256>(per_sm, smem_sm, reserved, optin)
+                            : own_padding<128>(per_sm, smem_sm, reserved, optin);
+  if (dyn < 0) return 0;
+  *dyn_bytes = dyn;
+  *threads = nt;
+  *ctas_per_sm = per_sm;
+  return groups;
+}
+
+// A cooperative launch: the runtime starts the grid only with every CTA
+// resident, also while kernels of other streams hold part of the device.
+cudaError_t launch_persistent_own(const PersistentArgs& a, int dyn_bytes, int threads, cudaStream_t stream) {
+  const int groups = (a.d.P / 2) * (a.d.P / 2);
+  PersistentArgs arg = a;
+  void* params[] = {&arg};
+  const void* fn = threads == 256 ? reinterpret_cast<const void*>(&persistent_own_kernel<256>)
+                                  : reinterpret_cast<const void*>(&persistent_own_kernel<128>);
+  return cudaLaunchCooperativeKernel(fn, dim3(groups), dim3(threads), params, (size_t)dyn_bytes, stream);
 }
 
 cudaError_t launch_ll_merge(const LatticeDesc& d, const unsigned long long* ob, const RunState* st,

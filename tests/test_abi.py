@@ -135,7 +135,7 @@ def _create_ex(lib, L, S, **fields):
     (64, 5, dict(bits_per_site=2), "S=5"),
     (48, 3, dict(bits_per_site=4), ">= 64"),
     (128, 3, dict(bits_per_site=2, height=40), ">= 64"),
-    (64, 3, dict(persistent=5), "persistent"),
+    (64, 3, dict(persistent=7), "persistent"),
     (64, 3, dict(neighbourhood=6), "neighbourhood"),
     (64, 3, dict(reflecting_boundary=2), "neighbourhood"),
     (64, 3, dict(device_lattice=0x1001), "aligned"),

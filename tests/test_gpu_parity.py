@@ -66,7 +66,9 @@ SMALL = [  # (L, S, K, p_empty, I, P, X, n_mcs)
 ]
 
 
-@pytest.mark.parametrize("persistent", [1, 3, 2, 0], ids=["persistent", "persistent-flags", "persistent-tma", "phase"])
+@pytest.mark.parametrize("persistent", [1, 3, 2, 5, 6, 0],
+                         ids=["persistent", "persistent-flags", "persistent-tma", "persistent-owner",
+                              "persistent-mailbox", "phase"])
 @pytest.mark.parametrize("case", SMALL, ids=[f"L{c[0]}" for c in SMALL])
 def test_replay_parity_every_mcs(case, persistent):
     L, S, K, p_empty, I, P, X, n = case
@@ -83,7 +85,8 @@ def test_replay_parity_every_mcs(case, persistent):
     assert mcs == n and np.array_equal(c, O.counts(o, S))
 
 
-@pytest.mark.parametrize("persistent", [1, 3], ids=["persistent", "persistent-flags"])
+@pytest.mark.parametrize("persistent", [1, 3, 5, 6],
+                         ids=["persistent", "persistent-flags", "persistent-owner", "persistent-mailbox"])
 @pytest.mark.parametrize("L,S,X,n,log_every", [(128, 3, 3.3, 7, 10), (256, 5, 13.1, 5, 2), (384, 3, 29.5, 4, 3),
                                                (640, 4, 50.0, 3, 10)])
 def test_many_mcs_per_launch(L, S, X, n, log_every, persistent):
@@ -177,7 +180,7 @@ def test_fused_counts_log_matches_oracle(L, S, log_every):
     assert g.mcs == n
 
 
-@pytest.mark.parametrize("L,persistent", [(16, True), (16, False), (128, True)])
+@pytest.mark.parametrize("L,persistent", [(16, True), (16, False), (128, True), (128, 5), (128, 6)])
 def test_stop_at_extinction_matches_oracle(L, persistent):
     S, K, I, P = 3, (1,), 1.0, 1.0
     seed = 5 if L == 16 else 6   # both go extinct within the budget
@@ -207,6 +210,22 @@ def test_restore_resume_exact():
     assert np.array_equal(h.snapshot(), full)
     ref, _ = O.replay_run(snap7, D, I, P, X, seed, 6, mcs_begin=7)
     assert np.array_equal(full, ref)
+
+
+@pytest.mark.parametrize("L,persistent", [(128, 1), (256, 1), (128, 3), (128, 5), (384, 5), (128, 6), (256, 6)])
+def test_restore_other_lattice_at_same_mcs(L, persistent):
+    """A different lattice restored at an MCS the handle has already run
+    through: nothing left on the device by the earlier run (boundary records,
+    epochs) may reach the new one."""
+    S, D, seed = 3, E.circulant(3, [1]), 41
+    g = E.Lattice(L, S, D, (1.0, 1.0, 2.0), seed, p_empty=0.25, persistent=persistent)
+    for n in (1, 2, 3):
+        for k in range(2):
+            lat = O.init(L, S, 0.25, 1000 + 10 * n + k)
+            g.restore(lat, 0)
+            g.run(n)
+            ref, _ = O.replay_run(lat, O.circulant(S, [1]), 1.0, 1.0, 2.0, seed, n)
+            assert np.array_equal(g.snapshot(), ref), (n, k)
 
 
 def test_step_host_end_to_end():
@@ -247,13 +266,14 @@ def test_launch_modes_agree_and_chunking_is_invisible():
     assert a.launches > 0 and b.launches > a.launches
 
 
-def test_bounded_wait_times_out_with_status():
-    """A block whose epoch is never published (host-controlled hook: the
-    flag nothing sets) makes its neighbours' bounded waits run out; the
-    kernel returns, escg_sync reports ESCG_ETIMEOUT and the handle refuses
-    to run until a lattice is restored.  No hang, no fault."""
+@pytest.mark.parametrize("persistent", [3, 6], ids=["flags", "mailbox"])
+def test_bounded_wait_times_out_with_status(persistent):
+    """A block whose epoch or records are never published (host-controlled
+    hook: the flag nothing sets) makes its neighbours' bounded waits run out;
+    the kernel returns, escg_sync reports ESCG_ETIMEOUT and the handle
+    refuses to run until a lattice is restored.  No hang, no fault."""
     L, S = 256, 3
-    g = E.Lattice(L, S, E.circulant(S, [1]), (1.0, 1.0, 1.0), 3, p_empty=0.25)
+    g = E.Lattice(L, S, E.circulant(S, [1]), (1.0, 1.0, 1.0), 3, p_empty=0.25, persistent=persistent)
     ref = g.snapshot()
     g.debug_stall_block(0, spin_limit=2000)
     g.run(3)
