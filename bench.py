@@ -61,7 +61,7 @@ ALG_INT_INSTR_PER_ATTEMPT = 24
 # DRAM traffic of persistent_kernel from one ncu capture (bytes per launch of
 # a 10-MCS chunk at L = 3200), valid only for that kernel and workload and the
 # kernel sources it was taken from (hash below); None otherwise.
-NCU_TRAFFIC = {"sources_sha1": "4db1c7abf7314fe7af68bd269cbd1bdf02c5b6cc", "bytes_per_launch": 10300672 + 2286848,
+NCU_TRAFFIC = {"sources_sha1": "5d6aab8a622618b34d748ff0aad3f4711fa9ace5", "bytes_per_launch": 10300928 + 2309632,
                "kernel": "persistent_kernel", "L": 3200, "mcs_per_launch": 10,
                "profile": "profiles/persistent_kernel_L3200_M1e-4.md"}
 
