@@ -831,7 +831,7 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
       }
       CUDA_TRY(timing_end(h));
       h->launches++;
-      if (h->use_ll || h->use_own) {
+      if (h->use_ll) {
         CUDA_TRY(launch_ll_merge(h->desc, h->d_ob, h->d_state, (uint32_t)end, h->stream));
         h->launches++;
       }

@@ -106,7 +106,7 @@ int persistent_ll_grid(int device);
 // Block-owner variant (uniform geometry, square, one byte per site): CTA g
 // owns coarse group g (2x2 blocks) for the whole launch with their tiles in
 // shared memory and exchanges boundary records like the mailbox kernel (a.ob,
-// kRecordWords per block; ll_merge completes the lattice array afterwards).
+// kRecordWords per block); it leaves the lattice array complete.
 // All (P/2)^2 CTAs must be resident at once: persistent_own_config returns
 // the grid size, the CTA size (128 or 256 threads), the shared-memory
 // padding that spreads the grid over the SMs and the CTAs per SM that

@@ -807,9 +807,9 @@ __global__ void __launch_bounds__(256) ll_merge_kernel(LatticeDesc d, const unsi
 // writer (the block's own previous visit is already in the tile), runs the
 // four fine phases and publishes its 4 records.  There is no ticket, no
 // interior load or store and no epoch flag: the lattice array is read when
-// the launch starts (nothing writes it during the launch) and the interiors
-// are written when it ends; the rim strips then come from the records
-// (ll_merge_kernel), as after a mailbox launch.  Same schedule, same results.
+// the launch starts (nothing writes it during the launch) and written when
+// it ends, each block's edge cells settled first from the final records of
+// the neighbours that visited after it.  Same schedule, same results.
 //
 // Every CTA waits for visits that only its neighbours' owners perform, so the
 // whole grid must be resident at once: it is a cooperative launch, made only
@@ -1062,7 +1062,67 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) persistent_own_kernel(P
         __syncthreads();
       }
     }
-    // the interiors to the lattice array (its rim strips: ll_merge_kernel)
+    // Edge cells that a neighbour changed after the block's last visit (a
+    // vertical or horizontal neighbour visiting later in the last MCS) take
+    // the value of their latest writer from that neighbour's final record
+    // (epoch m_end).  Then the interiors, edge lines included, complete the
+    // lattice array: every rim cell is some block's edge cell.
+    if (!quit) {
+      // item i: block of colour i >> 6, side (i >> 4) & 3, record word i & 15
+      constexpr int kPer = 256 / NT;
+      unsigned long long wv[kPer];
+      const unsigned long long* wp[kPer];
+      bool need[kPer];
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int i = tid + j * NT, c = i >> 6, s = (i >> 4) & 3;
+        const int bx = 2 * gx + (c & 1), by = 2 * gy + (c >> 1);
+        const int nx = (s == 2) ? (bx + P - 1) % P : (s == 3) ? (bx + 1) % P : bx;
+        const int ny = (s == 0) ? (by + P - 1) % P : (s == 1) ? (by + 1) % P : by;
+        need[j] = slot_of(ord, (s < 2) ? c ^ 2 : c ^ 1) > slot_of(ord, c);
+        wp[j] = ob + ((size_t)(ny * P + nx) * 4 + (s ^ 1)) * 32 + 16 + (i & 15);
+        wv[j] = need[j] ? ld_word(wp[j]) : 0ull;
+      }
+      bool failed = false;
+      uint32_t spins = 0;
+      for (;;) {
+        bool all = true;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) all = all && (!need[j] || (uint32_t)(wv[j] >> 32) == m_end);
+        if (all) break;
+        if (ld_volatile(&st->abort)) {
+          failed = true;
+          break;
+        }
+        if (++spins > a.spin_limit) {
+          atomicOr(&st->error, kErrTimeout);
+          atomicExch(&st->abort, 1u);
+          failed = true;
+          break;
+        }
+        __nanosleep(64);
+#pragma unroll
+        for (int j = 0; j < kPer; ++j)
+          if (need[j] && (uint32_t)(wv[j] >> 32) != m_end) wv[j] = ld_word(wp[j]);
+      }
+      if (!failed) {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+          if (!need[j]) continue;
+          const int i = tid + j * NT, c = i >> 6, s = (i >> 4) & 3, w = i & 15;
+          const int kX = slot_of(ord, c), kS = slot_of(ord, (s < 2) ? c ^ 2 : c ^ 1);
+          const int kO = slot_of(ord, (s < 2) ? c ^ 1 : c ^ 2);
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int pos = 4 * w + jj;
+            const bool end = (pos == 0) || (pos == kUniB - 1);
+            if (kS > (end ? max(kO, kX) : kX))
+              sm.tile[c][line_tidx(s, 0, pos)] = (uint8_t)((uint32_t)wv[j] >> (8 * jj));
+          }
+        }
+      }
+      __syncthreads();
+    }
     for (int i = tid; i < 4 * kUniB * 4; i += NT) {
       const int c = i >> 8, r = (i >> 2) & (kUniB - 1), q = i & 3;
       const int x0 = (2 * gx + (c & 1)) * kUniB, y0 = (2 * gy + (c >> 1)) * kUniB;
