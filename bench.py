@@ -24,7 +24,9 @@ exchange = 2 M N with M = 1e-4), counts logged every 10 MCS.  One step =
             lattice under the Moore / reflecting rule variants, as
             rectangles of the same N, and the RPSLS L = 800 workload;
             packed: bit-packed lattices (2 bits per site) against one byte per
-            site at L = 3200 and 12800; each with its own metric.
+            site at L = 3200 and 12800; sizes: the same workload at
+            L = 128 .. 2560 with the kernel picked for each; each with its
+            own metric.
 
 `--impl reference` times the CPU oracle itself (the reference arm of this
 tier) on the same metric and workload.  Multi-GPU (torchrun): replicas only,
@@ -61,7 +63,7 @@ ALG_INT_INSTR_PER_ATTEMPT = 24
 # DRAM traffic of persistent_kernel from one ncu capture (bytes per launch of
 # a 10-MCS chunk at L = 3200), valid only for that kernel and workload and the
 # kernel sources it was taken from (hash below); None otherwise.
-NCU_TRAFFIC = {"sources_sha1": "5d6aab8a622618b34d748ff0aad3f4711fa9ace5", "bytes_per_launch": 10300928 + 2309632,
+NCU_TRAFFIC = {"sources_sha1": "9cb31bf5246b08deee6ca9b95da6413a4e89e980", "bytes_per_launch": 10301184 + 2386432,
                "kernel": "persistent_kernel", "L": 3200, "mcs_per_launch": 10,
                "profile": "profiles/persistent_kernel_L3200_M1e-4.md"}
 
@@ -102,6 +104,8 @@ def _parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-park", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-sizes", action="store_true")
+    ap.add_argument("--size-steps", type=int, default=100)
     ap.add_argument("--no-packed", action="store_true")
     ap.add_argument("--packed-steps", type=int, default=100)
     ap.add_argument("--variant-steps", type=int, default=100)
@@ -341,6 +345,44 @@ def _variants(args, rank, w):
     return out
 
 
+def _sizes(args, rank, w):
+    """Latency-bound sizes: the benchmark's workload (RPS with empty sites,
+    M = 1e-4) on smaller square lattices, each with the kernel persistent = 1
+    picks for it (the boundary mailbox at L = 128, block owners from 384 to
+    2688, the flag kernel beyond): device time per 10-MCS step, L2 flushed
+    before each step."""
+    import torch
+    import paper_2508_16639_gb300 as E
+    from paper_2508_16639_gb300 import replicas as R
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for Lc in (128, 512, 1024, 1536, 2048, 2560):
+        N = Lc * Lc
+        X = E.exchange_from_mobility(w.mobility, N)
+        stream = torch.cuda.Stream()
+        g = E.Lattice(Lc, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X), R.replica_seed(w.seed, rank),
+                      p_empty=w.p_empty, log_every=w.log_every, stream=stream)
+        for _ in range(3):
+            g.run(10)
+        g.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.size_steps)]
+        for a, b in ev:
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            a.record(stream)
+            g.run(10)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        out[f"L{Lc}"] = {"site_updates_per_s": 10 * N / (ms * 1e-3), "us_per_mcs": ms * 100.0,
+                         "kernel": g.update_kernel}
+        g.close()
+    out["config"] = {"workload": f"{w.name} workload on L x L lattices, default kernel choice",
+                     "steps": args.size_steps}
+    return out
+
+
 def _packed(args, rank, w):
     """Bit-packed device lattices: the benchmark lattice and one 4x larger
     (L = 12800: 164 MB with one byte per site, more than the 129 MB L2; 41 MB
@@ -537,6 +579,9 @@ def main():
     variants = None
     if not args.no_variants:
         variants = _variants(args, rank, w)
+    sizes = None
+    if not args.no_sizes:
+        sizes = _sizes(args, rank, w)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -552,6 +597,7 @@ def main():
                 "config": _config(w, mps), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks,
                 "ensemble": ensemble, "serving": serving, "park": park, "variants": variants, "packed": packed,
+                "sizes": sizes,
                 "context": {"paper_cuda_ms_L3200_site_updates_per_s": 2.45e8,
                             "paper_hardware": "RTX A2000 (not a target)"}}
         print(json.dumps(line), flush=True)
