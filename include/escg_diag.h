@@ -34,10 +34,11 @@ int escg_debug_stall_block(escg_t* h, int32_t block, uint32_t spin_limit);
 /* Coarse blocks per axis (P) of the handle's schedule-v1 partition. */
 int32_t escg_coarse_blocks(escg_t* h);
 
-/* Name of the kernel that advances the handle's lattice ("persistent_ll_
- * kernel", "persistent_kernel", "persistent_tma_kernel" or "phase_kernel"),
- * fixed at creation by the options and the partition; a static string, or
- * "" for a NULL handle.  The choice never changes results. */
+/* Name of the kernel that advances the handle's lattice ("persistent_own_
+ * kernel", "persistent_ll_kernel", "persistent_kernel", "persistent_tma_
+ * kernel", "resident_kernel" or "phase_kernel"), fixed at creation by the
+ * options, the partition and the device's occupancy; a static string, or ""
+ * for a NULL handle.  The choice never changes results. */
 const char* escg_update_kernel(escg_t* h);
 
 #ifdef __cplusplus
