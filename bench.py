@@ -63,7 +63,7 @@ ALG_INT_INSTR_PER_ATTEMPT = 24
 # DRAM traffic of persistent_kernel from one ncu capture (bytes per launch of
 # a 10-MCS chunk at L = 3200), valid only for that kernel and workload and the
 # kernel sources it was taken from (hash below); None otherwise.
-NCU_TRAFFIC = {"sources_sha1": "9cb31bf5246b08deee6ca9b95da6413a4e89e980", "bytes_per_launch": 10301184 + 2386432,
+NCU_TRAFFIC = {"sources_sha1": "00ea1d1572b9791b5aee5c96127acc50c2946b28", "bytes_per_launch": 10300928 + 2481408,
                "kernel": "persistent_kernel", "L": 3200, "mcs_per_launch": 10,
                "profile": "profiles/persistent_kernel_L3200_M1e-4.md"}
 

@@ -73,9 +73,10 @@ typedef struct {
                                     non-empty species alive (stasis())        */
     uint32_t schedule_version;   /* 0 or 1 (only version 1 exists)            */
     int32_t persistent;          /* 1: persistent dataflow launches (default;
-                                    uniform square partitions of one byte per
-                                    site use the block owners of 5 while they
-                                    need at most 3 CTAs per SM, generic
+                                    uniform partitions of one byte per site
+                                    use the block owners of 5 from 3 x 3
+                                    groups of blocks while they need at most
+                                    3 CTAs per SM, generic
                                     partitions of 2 x 2 coarse blocks the
                                     whole-lattice residency of 4);
                                     2: same, uniform partitions staged by a
@@ -91,11 +92,11 @@ typedef struct {
                                     5: block owners: one CTA per 2 x 2 group
                                     of 64 x 64 blocks keeps their tiles in
                                     shared memory for the whole launch and
-                                    exchanges only boundary records (square,
-                                    one byte per site, L a multiple of 128,
-                                    (L/128)^2 CTAs resident at once, so the
-                                    launches of several handles take turns;
-                                    other lattices run as 3);
+                                    exchanges only boundary records (one byte
+                                    per site, L and H multiples of 128,
+                                    (L/128)(H/128) CTAs resident at once, so
+                                    the launches of several handles take
+                                    turns; other lattices run as 3);
                                     6: boundary mailbox: the work items of 3
                                     taken from a ticket counter, neighbours'
                                     edge and rim lines read from epoch-tagged

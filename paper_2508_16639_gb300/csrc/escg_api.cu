@@ -362,7 +362,8 @@ int reset_state(escg* h, uint64_t mcs, bool validate = false) {
   // for (a lattice restored at an MCS the handle has run through before):
   // epoch 0 never matches a wait, which always expects an epoch >= 1.
   if (h->d_ob)
-    CUDA_TRY(cudaMemsetAsync(h->d_ob, 0, (size_t)h->part.P * h->part.P * kRecordWords * sizeof(unsigned long long),
+    CUDA_TRY(cudaMemsetAsync(h->d_ob, 0,
+                             (size_t)h->part.P * h->part_y.P * kRecordWords * sizeof(unsigned long long),
                              h->stream));
   h->log_num0_host = num0;
   h->mcs_enq = mcs;
@@ -721,11 +722,12 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   // CTA of an SM is in the same colour phase at once and the flag kernel's
   // free binding keeps the SMs busier.  Needs the device to hold one CTA per
   // 2x2 group of blocks at once.
-  if (d.uniform64 && square && (o.persistent == 5 || (o.persistent == 1 && p.P >= 6))) {
+  if (d.uniform64 && h->bits == 8 &&
+      (o.persistent == 5 || (o.persistent == 1 && (p.P / 2) * (py.P / 2) >= 9))) {
     int dyn = 0, nt = 0, per_sm = 0;
     if (persistent_own_config(d, h->device, &dyn, &nt, &per_sm) > 0 && (o.persistent == 5 || per_sm <= 3)) {
       if (!h->d_ob) {
-        const size_t words = (size_t)p.P * p.P * kRecordWords;
+        const size_t words = (size_t)p.P * py.P * kRecordWords;
         if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
           set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
           return fail(ESCG_ENOMEM);

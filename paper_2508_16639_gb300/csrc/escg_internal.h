@@ -103,11 +103,11 @@ cudaError_t launch_resident(const PersistentArgs& a, cudaStream_t stream);
 constexpr int kRecordWords = 128;
 cudaError_t launch_persistent_ll(const PersistentArgs& a, int grid, cudaStream_t stream);
 int persistent_ll_grid(int device);
-// Block-owner variant (uniform geometry, square, one byte per site): CTA g
-// owns coarse group g (2x2 blocks) for the whole launch with their tiles in
+// Block-owner variant (uniform geometry, one byte per site): CTA g owns
+// coarse group g (2x2 blocks) for the whole launch with their tiles in
 // shared memory and exchanges boundary records like the mailbox kernel (a.ob,
 // kRecordWords per block); it leaves the lattice array complete.
-// All (P/2)^2 CTAs must be resident at once: persistent_own_config returns
+// All (P/2)(Py/2) CTAs must be resident at once: persistent_own_config returns
 // the grid size, the CTA size (128 or 256 threads), the shared-memory
 // padding that spreads the grid over the SMs and the CTAs per SM that
 // leaves, or 0 when the device cannot hold the whole grid.

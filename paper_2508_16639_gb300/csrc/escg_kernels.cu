@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(256) ll_merge_kernel(LatticeDesc d, const unsi
 }
 
 // ---------------------------------------------------------------------------
-// Block-owner kernel (uniform geometry, square, one byte per site).  CTA g
+// Block-owner kernel (uniform geometry, one byte per site).  CTA g
 // owns coarse group g -- the 2x2 blocks (2 gx + cx, 2 gy + cy), one of each
 // colour -- for the whole launch and keeps their four tiles (interior and rim
 // lines) in shared memory from visit to visit.  A visit exchanges only the
@@ -834,7 +834,7 @@ __device__ __forceinline__ void own_stage(const LatticeDesc& d, uint8_t* tile, i
   for (int i = threadIdx.x; i < (kUniB + 2) * 4; i += NT) {
     const int r = (i >> 2) - 1, q = i & 3;
     tile_row16(tile, r, 16 * q,
-               __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, L) * pitch + x0) + q));
+               __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0) + q));
   }
   const int xl = wrap(x0 - 1, L), xr = wrap(x0 + kUniB, L);
   for (int i = threadIdx.x; i < 2 * kUniB; i += NT) {
@@ -917,8 +917,8 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) persistent_own_kernel(P
   const bool run = !ld_volatile(&st->stopped);
   if (run) {
     load_trans(d, sm.trans);
-    const int P = d.P, half = P >> 1, pitch = d.pitch;
-    const uint32_t nb = (uint32_t)(P * P);
+    const int P = d.P, Py = d.Py, half = P >> 1, pitch = d.pitch;
+    const uint32_t nb = (uint32_t)(P * Py);
     const int gx = (int)blockIdx.x % half, gy = (int)blockIdx.x / half;
     for (int c = 0; c < 4; ++c) own_stage<NT>(d, sm.tile[c], 2 * gx + (c & 1), 2 * gy + (c >> 1));
     const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) persistent_own_kernel(P
         const bool poller = warp < 4;
         const int s = warp & 3;
         const int nx = (s == 2) ? (bx + P - 1) % P : (s == 3) ? (bx + 1) % P : bx;
-        const int ny = (s == 0) ? (by + P - 1) % P : (s == 1) ? (by + 1) % P : by;
+        const int ny = (s == 0) ? (by + Py - 1) % Py : (s == 1) ? (by + 1) % Py : by;
         const uint32_t e = (s < 2) ? eV : eH;
         const unsigned long long* p = ob + ((size_t)(ny * P + nx) * 4 + (s ^ 1)) * 32 + lane;
         const int dl = 2 * s + (lane & 1);
@@ -969,7 +969,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) persistent_own_kernel(P
         const int drec = (dl < 4) ? (ddx < 0 ? 3 : 2) : (ddy < 0 ? 1 : 0);
         const int dpos = (dl < 4) ? (ddy < 0 ? 63 : 0) : (ddx < 0 ? 63 : 0);
         const unsigned long long* pd =
-            ob + ((size_t)(((by + P + ddy) % P) * P + (bx + P + ddx) % P) * 4 + drec) * 32 + 16 + (dpos >> 2);
+            ob + ((size_t)(((by + Py + ddy) % Py) * P + (bx + P + ddx) % P) * 4 + drec) * 32 + 16 + (dpos >> 2);
         bool got = !poller || (first && ((s < 2) ? sV : sH) > k);
         bool got_d = !poller || lane >= 2 || (first && sD > k);
         unsigned long long word = 0, dword = 0;
@@ -1078,7 +1078,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) persistent_own_kernel(P
         const int i = tid + j * NT, c = i >> 6, s = (i >> 4) & 3;
         const int bx = 2 * gx + (c & 1), by = 2 * gy + (c >> 1);
         const int nx = (s == 2) ? (bx + P - 1) % P : (s == 3) ? (bx + 1) % P : bx;
-        const int ny = (s == 0) ? (by + P - 1) % P : (s == 1) ? (by + 1) % P : by;
+        const int ny = (s == 0) ? (by + Py - 1) % Py : (s == 1) ? (by + 1) % Py : by;
         need[j] = slot_of(ord, (s < 2) ? c ^ 2 : c ^ 1) > slot_of(ord, c);
         wp[j] = ob + ((size_t)(ny * P + nx) * 4 + (s ^ 1)) * 32 + 16 + (i & 15);
         wv[j] = need[j] ? ld_word(wp[j]) : 0ull;
@@ -1656,7 +1656,7 @@ static int own_padding(int per_sm, int smem_sm, int reserved, int optin) {
 }
 
 int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int* threads, int* ctas_per_sm) {
-  const int groups = (d.P / 2) * (d.P / 2);
+  const int groups = (d.P / 2) * (d.Py / 2);
   int sms = 0, smem_sm = 0, reserved = 0, optin = 0, coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
   if (!coop) return 0;
@@ -1683,7 +1683,7 @@ int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int*
 // A cooperative launch: the runtime starts the grid only with every CTA
 // resident, also while kernels of other streams hold part of the device.
 cudaError_t launch_persistent_own(const PersistentArgs& a, int dyn_bytes, int threads, cudaStream_t stream) {
-  const int groups = (a.d.P / 2) * (a.d.P / 2);
+  const int groups = (a.d.P / 2) * (a.d.Py / 2);
   PersistentArgs arg = a;
   void* params[] = {&arg};
   const void* fn = threads == 256 ? reinterpret_cast<const void*>(&persistent_own_kernel<256>)

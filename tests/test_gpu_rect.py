@@ -13,8 +13,8 @@ from paper_2508_16639_gb300.build import build
 
 pytestmark = pytest.mark.gpu
 
-MODES = [1, 3, 2, 0]
-MODE_IDS = ["persistent", "persistent-flags", "persistent-tma", "phase"]
+MODES = [1, 3, 2, 5, 0]
+MODE_IDS = ["persistent", "persistent-flags", "persistent-tma", "persistent-owner", "phase"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -23,7 +23,8 @@ def _built():
 
 
 @pytest.mark.parametrize("persistent", MODES, ids=MODE_IDS)
-@pytest.mark.parametrize("L,H", [(40, 24), (24, 57), (131, 70), (256, 128), (128, 384), (64, 200)])
+@pytest.mark.parametrize("L,H", [(40, 24), (24, 57), (131, 70), (256, 128), (128, 384), (64, 200), (384, 768),
+                                 (1024, 256)])
 def test_rect_parity(L, H, persistent):
     S, K, seed = 5, (1, 2), 5000 + L + 3 * H
     D = O.circulant(S, K)
@@ -117,3 +118,16 @@ def test_rect_large_properties():
     assert np.array_equal(a.snapshot(), b.snapshot())
     _, log = a.counts_log()
     assert (log.sum(axis=1) == L * H).all()
+
+
+@pytest.mark.parametrize("L,H,expect", [(384, 768, "persistent_own_kernel"), (1024, 256, "persistent_own_kernel"),
+                                        (256, 128, "persistent_kernel"), (200, 384, "persistent_kernel")])
+def test_rect_default_kernel(L, H, expect):
+    """persistent = 1 runs block owners on uniform rectangles from 3 x 3
+    groups of 2 x 2 blocks (384 x 768: 3 x 6 groups; 1024 x 256: 8 x 2),
+    the flag kernel on smaller or generic ones."""
+    g = E.Lattice(L, 3, E.circulant(3, [1]), (1.0, 1.0, 2.0), 9, p_empty=0.25, H=H)
+    assert g.update_kernel == expect
+    g.run(4)
+    o, _ = O.replay_run(O.init(L, 3, 0.25, 9, H=H), O.circulant(3, [1]), 1.0, 1.0, 2.0, 9, 4)
+    assert np.array_equal(g.snapshot(), o)
