@@ -73,8 +73,8 @@ typedef struct {
                                     non-empty species alive (stasis())        */
     uint32_t schedule_version;   /* 0 or 1 (only version 1 exists)            */
     int32_t persistent;          /* 1: persistent dataflow launches (default;
-                                    uniform partitions of one byte per site
-                                    use the block owners of 5 from 3 x 3
+                                    uniform partitions use the block owners
+                                    of 5 from 3 x 3
                                     groups of blocks while they need at most
                                     3 CTAs per SM, generic
                                     partitions of 2 x 2 coarse blocks the
@@ -92,8 +92,8 @@ typedef struct {
                                     5: block owners: one CTA per 2 x 2 group
                                     of 64 x 64 blocks keeps their tiles in
                                     shared memory for the whole launch and
-                                    exchanges only boundary records (one byte
-                                    per site, L and H multiples of 128,
+                                    exchanges only boundary records (L and H
+                                    multiples of 128, any bits_per_site,
                                     (L/128)(H/128) CTAs resident at once, so
                                     the launches of several handles take
                                     turns; other lattices run as 3);

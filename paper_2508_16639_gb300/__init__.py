@@ -67,7 +67,7 @@ class Lattice:
     warp, 6 with boundary records (mailbox), 4 the whole
     lattice resident in one CTA's shared memory (small lattices; larger ones
     run as 3), 5 one CTA per 2x2 group of blocks with its tiles resident
-    (L and H multiples of 128, one byte per site; others run as 3), 0 one
+    (L and H multiples of 128; others run as 3), 0 one
     launch per coarse phase -- all bit-identical.  dominance_prob: optional S x S edge
     probabilities (Park, Chen and Szolnoki's probabilistic dominance);
     neighbourhood 4 or 8 (Moore) and reflecting_boundary: the paper's rule

@@ -722,8 +722,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   // CTA of an SM is in the same colour phase at once and the flag kernel's
   // free binding keeps the SMs busier.  Needs the device to hold one CTA per
   // 2x2 group of blocks at once.
-  if (d.uniform64 && h->bits == 8 &&
-      (o.persistent == 5 || (o.persistent == 1 && (p.P / 2) * (py.P / 2) >= 9))) {
+  if (d.uniform64 && (o.persistent == 5 || (o.persistent == 1 && (p.P / 2) * (py.P / 2) >= 9))) {
     int dyn = 0, nt = 0, per_sm = 0;
     if (persistent_own_config(d, h->device, &dyn, &nt, &per_sm) > 0 && (o.persistent == 5 || per_sm <= 3)) {
       if (!h->d_ob) {

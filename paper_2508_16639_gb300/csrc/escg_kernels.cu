@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(256) ll_merge_kernel(LatticeDesc d, const unsi
 }
 
 // ---------------------------------------------------------------------------
-// Block-owner kernel (uniform geometry, one byte per site).  CTA g
+// Block-owner kernel (uniform geometry; one byte per site or packed).  CTA g
 // owns coarse group g -- the 2x2 blocks (2 gx + cx, 2 gy + cy), one of each
 // colour -- for the whole launch and keeps their four tiles (interior and rim
 // lines) in shared memory from visit to visit.  A visit exchanges only the
@@ -828,18 +828,30 @@ struct OwnSmem {
 
 // The group's block (bx, by) as the lattice array holds it: interior, top and
 // bottom rim rows, left and right rim columns (the corners are not used).
+// One byte per site: 16-byte pieces; packed (d.bits 4 or 2): groups of 4
+// sites, unpacked into the tile.
 template <int NT>
 __device__ __forceinline__ void own_stage(const LatticeDesc& d, uint8_t* tile, int bx, int by) {
-  const int L = d.L, pitch = d.pitch, x0 = bx * kUniB, y0 = by * kUniB;
-  for (int i = threadIdx.x; i < (kUniB + 2) * 4; i += NT) {
-    const int r = (i >> 2) - 1, q = i & 3;
-    tile_row16(tile, r, 16 * q,
-               __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0) + q));
+  const int L = d.L, pitch = d.pitch, bits = d.bits, x0 = bx * kUniB, y0 = by * kUniB;
+  if (bits == 8) {
+    for (int i = threadIdx.x; i < (kUniB + 2) * 4; i += NT) {
+      const int r = (i >> 2) - 1, q = i & 3;
+      tile_row16(tile, r, 16 * q,
+                 __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0) + q));
+    }
+  } else {
+    for (int i = threadIdx.x; i < (kUniB + 2) * (kUniB / 4); i += NT) {
+      const int r = i / (kUniB / 4) - 1, k = i % (kUniB / 4);
+      const uint32_t raw = load_group(d.lat + (size_t)wrap(y0 + r, d.H) * pitch, x0 + 4 * k, bits);
+      *reinterpret_cast<uint32_t*>(tile + tidx(r, 4 * k, kUniSP)) = unpack4(raw, bits);
+    }
   }
   const int xl = wrap(x0 - 1, L), xr = wrap(x0 + kUniB, L);
   for (int i = threadIdx.x; i < 2 * kUniB; i += NT) {
-    const int r = i & (kUniB - 1), right = i >= kUniB;
-    tile[tidx(r, right ? kUniB : -1, kUniSP)] = __ldcg(d.lat + (size_t)(y0 + r) * pitch + (right ? xr : xl));
+    const int r = i & (kUniB - 1), right = i >= kUniB, gx = right ? xr : xl;
+    const uint8_t* row = d.lat + (size_t)(y0 + r) * pitch;
+    tile[tidx(r, right ? kUniB : -1, kUniSP)] =
+        bits == 8 ? __ldcg(row + gx) : (uint8_t)(unpack4(load_group(row, gx & ~3, bits), bits) >> (8 * (gx & 3)));
   }
 }
 
@@ -1123,12 +1135,23 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) persistent_own_kernel(P
       }
       __syncthreads();
     }
-    for (int i = tid; i < 4 * kUniB * 4; i += NT) {
-      const int c = i >> 8, r = (i >> 2) & (kUniB - 1), q = i & 3;
-      const int x0 = (2 * gx + (c & 1)) * kUniB, y0 = (2 * gy + (c >> 1)) * kUniB;
-      const uint2* src = reinterpret_cast<const uint2*>(sm.tile[c] + tidx(r, 16 * q, kUniSP));
-      const uint2 u0 = src[0], u1 = src[1];
-      reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(u0.x, u0.y, u1.x, u1.y);
+    if (d.bits == 8) {
+      for (int i = tid; i < 4 * kUniB * 4; i += NT) {
+        const int c = i >> 8, r = (i >> 2) & (kUniB - 1), q = i & 3;
+        const int x0 = (2 * gx + (c & 1)) * kUniB, y0 = (2 * gy + (c >> 1)) * kUniB;
+        const uint2* src = reinterpret_cast<const uint2*>(sm.tile[c] + tidx(r, 16 * q, kUniSP));
+        const uint2 u0 = src[0], u1 = src[1];
+        reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(u0.x, u0.y, u1.x, u1.y);
+      }
+    } else {
+      // packed: whole groups of 4 sites (a block starts on a group boundary,
+      // so no group is shared with another block)
+      for (int i = tid; i < 4 * kUniB * (kUniB / 4); i += NT) {
+        const int c = i >> 10, r = (i >> 4) & (kUniB - 1), k = i & 15;
+        const int x0 = (2 * gx + (c & 1)) * kUniB, y0 = (2 * gy + (c >> 1)) * kUniB;
+        const uint32_t v = *reinterpret_cast<const uint32_t*>(sm.tile[c] + tidx(r, 4 * k, kUniSP));
+        store_group(d.lat + (size_t)(y0 + r) * pitch, x0 + 4 * k, d.bits, pack4(v, d.bits));
+      }
     }
   }
   // The last CTA to leave publishes the MCS number.

@@ -29,10 +29,10 @@ def _built():
                                              (100, None, 8, "persistent_kernel"),
                                              (256, 128, 8, "persistent_own_kernel"),
                                              (200, 128, 8, "persistent_kernel"),
-                                             (256, None, 2, "persistent_kernel"),
+                                             (256, None, 2, "persistent_own_kernel"),
                                              (6400, None, 8, "persistent_kernel")])
 def test_owner_kernel_choice(L, H, bits, expect):
-    """Uniform lattices (squares and rectangles) of one byte per site whose
+    """Uniform lattices (squares and rectangles, any bits per site) whose
     (L/128)(H/128) groups the device holds at once; the others run the flag
     kernel (200 x 128: generic partition; 6400: 2500 groups, more CTAs of 128
     threads than 152 SMs can hold)."""

@@ -26,16 +26,17 @@ def _decode(raw: np.ndarray, L: int, bits: int) -> np.ndarray:
     return np.stack(fields, axis=-1).reshape(raw.shape[0], -1)[:, :L].astype(np.uint8)
 
 
-@pytest.mark.parametrize("persistent", [1, 3, 0], ids=["persistent", "persistent-flags", "phase"])
+@pytest.mark.parametrize("persistent", [1, 3, 5, 0], ids=["persistent", "persistent-flags", "persistent-owner",
+                                                          "phase"])
 @pytest.mark.parametrize("bits,S,K", [(2, 3, (1,)), (4, 5, (1, 2)), (4, 3, (1,))])
-@pytest.mark.parametrize("L,H", [(128, 128), (256, 256), (100, 100), (131, 131), (128, 200), (200, 64)])
+@pytest.mark.parametrize("L,H", [(128, 128), (256, 256), (100, 100), (131, 131), (128, 200), (200, 64), (384, 512)])
 def test_packed_parity(L, H, bits, S, K, persistent):
     seed = 7000 + L + 3 * H + bits
     D = O.circulant(S, K)
     X = 2.0 + L / 64
     g = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.2, persistent=persistent, log_every=2, H=H,
                   bits_per_site=bits)
-    assert g.update_kernel in ("persistent_kernel", "phase_kernel", "resident_kernel")
+    assert g.update_kernel in ("persistent_kernel", "phase_kernel", "resident_kernel", "persistent_own_kernel")
     o = O.init(L, S, 0.2, seed, H=H)
     assert np.array_equal(g.snapshot(), o)
     m = 0
@@ -139,3 +140,27 @@ def test_packed_benchmark_size():
     _, la = a.counts_log()
     _, lb = b.counts_log()
     assert np.array_equal(la, lb)
+
+
+@pytest.mark.parametrize("bits", [2, 4])
+def test_packed_block_owners_L1024(bits):
+    """Block owners on a packed lattice (the default at L = 1024): the tiles
+    are unpacked once at launch start and packed once at the end; several
+    launches, counts at every log point, the device buffer in the packed
+    layout."""
+    torch = pytest.importorskip("torch")
+    S, L, seed, X = 3, 1024, 31 + bits, 6.0
+    D = O.circulant(S, (1,))
+    buf = torch.zeros(E.lattice_bytes(L, L, bits), dtype=torch.uint8, device="cuda")
+    g = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.25, log_every=3, bits_per_site=bits, device_buffer=buf)
+    assert g.update_kernel == "persistent_own_kernel"
+    o = O.init(L, S, 0.25, seed)
+    g.run(4).run(3)
+    o7, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 7)
+    assert np.array_equal(g.snapshot(), o7)
+    g.sync()
+    raw = g.as_tensor().cpu().numpy()
+    assert np.array_equal(_decode(raw, L, bits), o7)
+    _, log = g.counts_log()
+    _, olog, _ = O.run_observed(o, D, 1.0, 1.0, X, seed, 7, log_every=3)
+    assert np.array_equal(log, olog)
