@@ -383,22 +383,27 @@ void escg_server_destroy(escg_server_t* s);
  *
  * Runs n_mcs Monte Carlo steps (schedule version 1, exactly as escg_run)
  * from absolute MCS number mcs_begin on the caller's device lattice
- * d_lattice (L rows of escg_lattice_pitch(L) bytes, values 0..S, updated in
- * place), then, if d_counts_out is not NULL, writes the species counts
- * (S+1 uint64 values, device memory) of the final lattice there.  Inputs and
- * outputs are the caller's; the library allocates nothing, neither device
- * nor pinned memory.  Its scratch state (run state, block epochs, partition
- * and transition tables) lives in one fixed 64 KiB device array that every
- * GPU loading the library keeps until the process exits; L is therefore
- * limited to 8..4096 (larger lattices are rejected with ESCG_EINVAL and a
- * message).  Every call clears and rewrites that array, so calls whose work
- * overlaps on the GPU (from several host threads or streams) race and must
- * be serialised by the caller.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  digraph and rates are host memory read during
- * the call; cuda_stream may be NULL (the legacy default stream).  Returns
- * when the work has finished; ESCG_ETIMEOUT if a bounded device-side wait
- * gave up.  No counts log, no stop at extinction. */
+ * d_lattice (L rows of escg_lattice_pitch(L) bytes, 16-byte aligned, values
+ * 0..S, updated in place), then, if d_counts_out is not NULL, writes the
+ * species counts (S+1 uint64 values, device memory, 8-byte aligned) of the
+ * final lattice there.  Inputs and outputs are the caller's; the library
+ * allocates nothing, neither device nor pinned memory.  Its scratch state
+ * (run state, block epochs, transition table) lives in one fixed 64 KiB
+ * device array that every GPU loading the library keeps until the process
+ * exits; L is therefore limited to 8..4096 (larger lattices are rejected
+ * with ESCG_EINVAL and a message).  Every call clears and rewrites that
+ * array, so calls whose work overlaps on the GPU (from several host threads
+ * or streams) race and must be serialised by the caller.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  digraph and rates are host
+ * memory read during the call; cuda_stream may be NULL (the legacy default
+ * stream).  Arguments are checked on the host before any device work
+ * (ESCG_EINVAL: NULL or misaligned buffers, L or S out of range, a bad
+ * digraph or rates, mcs_begin + n_mcs >= 2^31); the lattice's values are
+ * checked on the device before the first step, and a value outside 0..S
+ * fails the call with ESCG_EINVAL, the lattice unchanged.  Returns when the
+ * work has finished; ESCG_ETIMEOUT if a bounded device-side wait gave up.
+ * No counts log, no stop at extinction. */
 int escg_run_noalloc(uint8_t* d_lattice, int32_t L, int32_t S, const uint8_t* digraph,
                      const escg_rates* rates, uint64_t seed, uint64_t mcs_begin, uint64_t n_mcs,
                      uint64_t* d_counts_out, void* cuda_stream);

@@ -6,7 +6,7 @@
 // service that pre-reserves all GPU memory at start-up), and loops where a
 // cudaMalloc/cudaFree would synchronise the device or is forbidden.  For them
 // this entry point keeps all the scratch state the persistent kernel needs --
-// run state, block epochs, partition and transition tables -- in one
+// run state, block epochs and the transition table -- in one
 // file-scope device array of fixed size, which every GPU that loads the
 // library holds until the process exits.
 #include <cmath>
@@ -18,94 +18,43 @@
 
 namespace escg_impl {
 
-// Scratch layout (bytes): RunState | epochs | partition tables | transitions.
+// Scratch layout (bytes): RunState | block epochs | transition table.  The
+// kernels find block spans and fine segments in closed form (AxisGeom in the
+// kernel parameters), so no partition tables are kept.
 constexpr int kNoallocMaxL = 4096;
 constexpr size_t kNoallocScratchBytes = 64 * 1024;
 constexpr size_t kNoallocStateBytes = (sizeof(RunState) + 255) / 256 * 256;
-constexpr int kNoallocMaxP = 2 * ((kNoallocMaxL + 64) / 128);      // 64
-constexpr int kNoallocMaxGQ = kNoallocMaxL / 2;                     // fine segments per axis
+constexpr int kNoallocMaxP = 2 * ((kNoallocMaxL + 64) / 128);      // 64 coarse blocks per axis
 constexpr size_t kNoallocDoneOff = kNoallocStateBytes;
-constexpr size_t kNoallocTabOff = kNoallocDoneOff + 4 * (size_t)kNoallocMaxP * kNoallocMaxP;
-constexpr size_t kNoallocTransOff =
-    kNoallocTabOff + 4 * (size_t)((kNoallocMaxP + 1) * 2 + kNoallocMaxGQ + 1 + 63) / 64 * 64;
-static_assert(kNoallocTransOff + 4 * kTransWords <= kNoallocScratchBytes, "scratch too small");
+constexpr size_t kNoallocDoneBytes = 4 * (size_t)kNoallocMaxP * kNoallocMaxP;
+constexpr size_t kNoallocTransOff = (kNoallocDoneOff + kNoallocDoneBytes + 255) / 256 * 256;
+constexpr size_t kNoallocTransBytes = 4 * (size_t)kTransWords;
+static_assert(kNoallocTransOff >= kNoallocDoneOff + kNoallocDoneBytes, "epochs overlap the transition table");
+static_assert(kNoallocTransOff + kNoallocTransBytes <= kNoallocScratchBytes, "scratch too small");
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocScratchBytes];
 
+// Set-up of one call, passed by value in the kernel parameters (2 KB): the
+// transition table comes from the host builder that every other entry point
+// uses (build_transitions), so there is one copy of the rule.
 struct NoallocSetup {
-  int32_t L, S;
   uint32_t mcs_begin;
-  uint8_t digraph[kMaxStates * kMaxStates];
+  int32_t n_blocks;                // P * P
+  uint32_t trans[kTransWords];
 };
 
-__device__ __forceinline__ void nsplit(int n, int parts, int32_t* start) {
-  const int q = n / parts, r = n % parts;
-  start[0] = 0;
-  for (int k = 0; k < parts; ++k) start[k + 1] = start[k] + q + (k < r ? 1 : 0);
-}
-
-// One CTA: clears the run state, sets every block epoch to mcs_begin, and
-// writes the schedule-v1 partition tables and the Alg. 3 transition table
-// of this call into the scratch array.
-__global__ void noalloc_setup_kernel(uint8_t* scratch, NoallocSetup a) {
+// One CTA: clears the run state, sets every block epoch to mcs_begin and
+// copies the transition table into the scratch array.
+__global__ void noalloc_setup_kernel(uint8_t* scratch, const __grid_constant__ NoallocSetup a) {
   RunState* st = reinterpret_cast<RunState*>(scratch);
-  const int L = a.L, h = (L + 64) / 128, P = 2 * (h < 1 ? 1 : h);
   uint32_t* done = reinterpret_cast<uint32_t*>(scratch + kNoallocDoneOff);
   uint32_t* words = reinterpret_cast<uint32_t*>(scratch);
+  uint32_t* tr = reinterpret_cast<uint32_t*>(scratch + kNoallocTransOff);
   for (int i = threadIdx.x; i < (int)(sizeof(RunState) / 4); i += blockDim.x) words[i] = 0;
-  for (int i = threadIdx.x; i < P * P; i += blockDim.x) done[i] = a.mcs_begin;
-  if (threadIdx.x == 0) {
-    st->mcs = a.mcs_begin;
-    int32_t* cs = reinterpret_cast<int32_t*>(scratch + kNoallocTabOff);
-    nsplit(L, P, cs);
-    int GQ = 0;
-    for (int k = 0; k < P; ++k) GQ += 2 * ((cs[k + 1] - cs[k]) / 4);
-    int32_t* fs = cs + (P + 1);
-    int32_t* fc = fs + (GQ + 1);
-    int g = 0;
-    for (int k = 0; k < P; ++k) {
-      const int w = cs[k + 1] - cs[k], Q = 2 * (w / 4);
-      fc[k] = g;
-      const int q0 = w / Q, r0 = w % Q;
-      int x = cs[k];
-      for (int q = 0; q < Q; ++q) {
-        fs[g + q] = x;
-        x += q0 + (q < r0 ? 1 : 0);
-      }
-      g += Q;
-    }
-    fs[GQ] = L;
-    fc[P] = GQ;
-    const int S = a.S, s1 = S + 1;
-    uint8_t* tr = scratch + kNoallocTransOff;
-    // every edge certain: interaction thresholds 2^32 (stored as 0xFFFFFFFF)
-    uint32_t* thr = reinterpret_cast<uint32_t*>(tr) + kTransPairs;
-    for (int k = 0; k < s1 * s1; ++k) thr[k] = 0xFFFFFFFFu;
-    for (int act = 0; act < 4; ++act)
-      for (int x = 0; x < s1; ++x)
-        for (int y = 0; y < s1; ++y) {
-          const bool xy = x && y && a.digraph[(x - 1) * S + (y - 1)];
-          const bool yx = x && y && a.digraph[(y - 1) * S + (x - 1)];
-          int nx = x, ny = y;
-          if (x != y) {
-            if (act == 0) {
-              nx = y;
-              ny = x;
-            } else if (act == 1) {
-              if (xy)
-                ny = 0;
-              else if (yx)
-                nx = 0;
-            } else if (act == 2) {
-              if (y == 0)
-                ny = x;
-              else if (x == 0)
-                nx = y;
-            }
-          }
-          tr[(x * s1 + y) * 4 + act] = (uint8_t)(nx | (ny << 4));
-        }
-  }
+  for (int i = threadIdx.x; i < a.n_blocks; i += blockDim.x) done[i] = a.mcs_begin;
+  for (int i = threadIdx.x; i < kTransWords; i += blockDim.x) tr[i] = a.trans[i];
+  __syncthreads();
+  if (threadIdx.x == 0) st->mcs = a.mcs_begin;
 }
 
 __global__ void noalloc_counts_kernel(const uint8_t* scratch, int S, uint64_t* out) {
@@ -153,6 +102,14 @@ extern "C" int escg_run_noalloc(uint8_t* d_lattice, int32_t L, int32_t S, const 
     set_last_error("escg_run_noalloc: NULL lattice, digraph or rates");
     return ESCG_EINVAL;
   }
+  if (reinterpret_cast<uintptr_t>(d_lattice) % 16 != 0) {
+    set_last_error("escg_run_noalloc: d_lattice must be 16-byte aligned (rows are read as 16-byte vectors)");
+    return ESCG_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(d_counts_out) % 8 != 0) {
+    set_last_error("escg_run_noalloc: d_counts_out must be 8-byte aligned");
+    return ESCG_EINVAL;
+  }
   if (L < 8 || L > kNoallocMaxL) {
     set_last_error("escg_run_noalloc: L=%d outside [8, %d] (the fixed scratch array holds at most "
                    "that size)", L, kNoallocMaxL);
@@ -173,7 +130,8 @@ extern "C" int escg_run_noalloc(uint8_t* d_lattice, int32_t L, int32_t S, const 
     set_last_error("escg_run_noalloc: rates must be finite, >= 0 and not all zero");
     return ESCG_EINVAL;
   }
-  if (mcs_begin + n_mcs >= 0x80000000ull) {
+  // written so that no sum can wrap around 2^64
+  if (mcs_begin >= 0x80000000ull || n_mcs >= 0x80000000ull - mcs_begin) {
     set_last_error("escg_run_noalloc: MCS numbers must stay below 2^31");
     return ESCG_EINVAL;
   }
@@ -195,14 +153,10 @@ extern "C" int escg_run_noalloc(uint8_t* d_lattice, int32_t L, int32_t S, const 
   d.pitch = escg_lattice_pitch(L);
   d.P = P;
   d.GQ = GQ;
-  d.cs = reinterpret_cast<const int32_t*>(scratch + kNoallocTabOff);
-  d.fs = d.cs + (P + 1);
-  d.fc = d.fs + (GQ + 1);
+  d.cs = d.fs = d.fc = nullptr;   // partition in closed form only (d.ax, d.ay)
   d.H = L;   // square
   d.Py = P;
-  d.csy = d.cs;
-  d.fsy = d.fs;
-  d.fcy = d.fc;
+  d.csy = d.fsy = d.fcy = nullptr;
   d.ax = make_axis_geom(L, P);
   d.ay = d.ax;
   d.bits = 8;
@@ -218,18 +172,23 @@ extern "C" int escg_run_noalloc(uint8_t* d_lattice, int32_t L, int32_t S, const 
   d.tx = tx >> 32 ? 0xFFFFFFFFu : (uint32_t)tx;
   d.txi = txi >> 32 ? 0xFFFFFFFFu : (uint32_t)txi;
   d.S = S;
+  d.nbh = 4;
+  d.reflect = 0;
   d.uniform64 = (L % 64 == 0 && L / 64 == P && d.pitch % 16 == 0) ? 1 : 0;
   fill_perm24(d.perm24);
 
   NoallocSetup su;
   std::memset(&su, 0, sizeof su);
-  su.L = L;
-  su.S = S;
   su.mcs_begin = (uint32_t)mcs_begin;
-  std::memcpy(su.digraph, digraph, (size_t)S * S);
+  su.n_blocks = P * P;
+  build_transitions(S, digraph, nullptr, tx, txi, su.trans);
   noalloc_setup_kernel<<<1, 256, 0, stream>>>(scratch, su);
   cudaError_t e = cudaGetLastError();
   RunState* st = reinterpret_cast<RunState*>(scratch);
+  // Every byte of the caller's lattice must be a state 0..S (the transition
+  // table is indexed by the pair); otherwise the run state stops, so that
+  // the kernels below leave the lattice alone, and the call fails.
+  if (e == cudaSuccess) e = launch_validate(d, &st->error, kErrBadValue, &st->stopped, stream);
   const int grid_max = persistent_grid(dev, d.uniform64 != 0);
   const uint64_t per_mcs = (uint64_t)P * P;
   const uint64_t max_chunk = ((1ull << 31) - (uint64_t)grid_max) / per_mcs;
@@ -267,6 +226,10 @@ extern "C" int escg_run_noalloc(uint8_t* d_lattice, int32_t L, int32_t S, const 
   if (e != cudaSuccess) {
     set_last_error("escg_run_noalloc: %s", cudaGetErrorString(e));
     return ESCG_ECUDA;
+  }
+  if (err_word & kErrBadValue) {
+    set_last_error("escg_run_noalloc: the lattice holds a value outside 0..S=%d; it was left unchanged", S);
+    return ESCG_EINVAL;
   }
   if (err_word & kErrTimeout) {
     set_last_error("escg_run_noalloc: a bounded device-side wait timed out");

@@ -147,3 +147,23 @@ def test_create_rejects_bad_options(lib, L, S, fields, msg):
     reaches a kernel."""
     assert not _create_ex(lib, L, S, **fields)
     assert msg in lib.escg_last_error().decode()
+
+
+@pytest.mark.parametrize("ptr,counts,L,mcs_begin,n_mcs,msg", [
+    (0x1001, None, 64, 0, 1, "16-byte aligned"),
+    (0x1000, 0x2004, 64, 0, 1, "8-byte aligned"),
+    (0x1000, None, 4097, 0, 1, "4096"),
+    (0x1000, None, 64, 1, 2**64 - 1, "2^31"),
+    (0x1000, None, 64, 2**31, 0, "2^31"),
+    (0x1000, None, 64, 2**31 - 5, 5, "2^31"),
+])
+def test_noalloc_rejects_bad_arguments_before_any_device_work(lib, ptr, counts, L, mcs_begin, n_mcs, msg):
+    """escg_run_noalloc checks its arguments on the host first, so a
+    misaligned buffer or an MCS range that would pass 2^31 (or wrap around
+    2^64) never reaches a kernel (none of these touch the pointers)."""
+    D = np.ascontiguousarray(O.circulant(3, [1]), dtype=np.uint8)
+    r = _lib.Rates(1.0, 1.0, 1.0)
+    rc = lib.escg_run_noalloc(C.c_void_p(ptr), L, 3, D.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(r), 1,
+                              mcs_begin, n_mcs, C.c_void_p(counts) if counts else None, None)
+    assert rc == _lib.ESCG_EINVAL
+    assert msg in lib.escg_last_error().decode()
