@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libescg.so")
-SOURCES = ["escg_kernels.cu", "escg_api.cu", "escg_diag.cu", "escg_batch.cu", "escg_noalloc.cu"]
+SOURCES = ["escg_kernels.cu", "escg_api.cu", "escg_diag.cu", "escg_batch.cu", "escg_noalloc.cu", "escg_owner.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -50,6 +50,9 @@ namespace {
   } while (0)
 
 constexpr uint32_t kDefaultSpinLimit = 2000000;  // polls of ~1 us: a few seconds
+// Largest number of generic block-owner CTAs per SM that persistent = 1
+// accepts.
+constexpr int kGownDefaultPerSM = 2;
 
 // Schedule v1 partition of one axis (both axes are identical).
 struct Partition {
@@ -244,6 +247,9 @@ struct escg {
   bool use_own = false;          // block-owner kernel (uniform, square, one byte per site)
   int own_dyn = 0;               // its shared-memory padding
   int own_threads = 0;           // and CTA size
+  bool use_gown = false;         // block owners on a generic partition
+  GownConfig gown{};
+  size_t ob_words = 0;           // boundary-record words allocated (all blocks)
   CUtensorMap tmap{};
   uint32_t spin_limit = kDefaultSpinLimit;
   int stall_block = -1;
@@ -361,10 +367,7 @@ int reset_state(escg* h, uint64_t mcs, bool validate = false) {
   // Boundary records left by an earlier run carry epochs the new one may wait
   // for (a lattice restored at an MCS the handle has run through before):
   // epoch 0 never matches a wait, which always expects an epoch >= 1.
-  if (h->d_ob)
-    CUDA_TRY(cudaMemsetAsync(h->d_ob, 0,
-                             (size_t)h->part.P * h->part_y.P * kRecordWords * sizeof(unsigned long long),
-                             h->stream));
+  if (h->d_ob) CUDA_TRY(cudaMemsetAsync(h->d_ob, 0, h->ob_words * sizeof(unsigned long long), h->stream));
   h->log_num0_host = num0;
   h->mcs_enq = mcs;
   h->failed = false;
@@ -710,6 +713,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
       set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
       return fail(ESCG_ENOMEM);
     }
+    h->ob_words = words;
     h->use_ll = true;
     h->grid = persistent_ll_grid(h->device);
   }
@@ -731,11 +735,31 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
           set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
           return fail(ESCG_ENOMEM);
         }
+        h->ob_words = words;
       }
       h->use_own = true;
       h->own_dyn = dyn;
       h->own_threads = nt;
       h->use_ll = false;
+    }
+  }
+  // Block owners on a generic partition (von Neumann rule, periodic or
+  // reflecting, any bits per site): on request (5), and by default (1) from
+  // 2 x 2 groups of blocks while the grid needs at most kGownDefaultPerSM
+  // CTAs per SM.  Needs the device to hold one CTA per group at once.
+  if (!d.uniform64 && d.nbh == 4 &&
+      (o.persistent == 5 || (o.persistent == 1 && (p.P / 2) * (py.P / 2) >= 2))) {
+    GownConfig cfg{};
+    if (persistent_gown_config(d, h->device, &cfg) > 0 &&
+        (o.persistent == 5 || cfg.ctas_per_sm <= kGownDefaultPerSM)) {
+      const size_t words = (size_t)p.P * py.P * kGRecordWords;
+      if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
+        set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
+        return fail(ESCG_ENOMEM);
+      }
+      h->ob_words = words;
+      h->use_gown = true;
+      h->gown = cfg;
     }
   }
   // Whole-lattice residency: on request (4), and by default (1) for a generic
@@ -744,8 +768,10 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   // generic visits (tied at L = 200, slower beyond; the mailbox kernel is
   // faster for the uniform L = 128).
   if ((o.persistent == 4 || (o.persistent == 1 && !d.uniform64 && p.P == 2 && py.P == 2)) &&
-      resident_fits(d, h->device))
+      resident_fits(d, h->device)) {
     h->use_resident = true;
+    h->use_gown = false;
+  }
   if (o.ctas_per_sm > 0) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -820,6 +846,8 @@ int escg_run(escg_t* h, uint64_t n_mcs) {
         CUDA_TRY(launch_resident(a, h->stream));
       } else if (h->use_own) {
         CUDA_TRY(launch_persistent_own(a, h->own_dyn, h->own_threads, h->stream));
+      } else if (h->use_gown) {
+        CUDA_TRY(launch_persistent_gown(a, h->gown, h->stream));
       } else if (h->use_tma) {
         TmaArgs ta{};
         ta.map = h->tmap;
@@ -1103,6 +1131,7 @@ const char* escg_update_kernel(escg_t* h) {
   if (!h->opt.persistent) return "phase_kernel";
   if (h->use_resident) return "resident_kernel";
   if (h->use_own) return "persistent_own_kernel";
+  if (h->use_gown) return "persistent_gown_kernel";
   if (h->use_tma) return "persistent_tma_kernel";
   return h->use_ll ? "persistent_ll_kernel" : "persistent_kernel";
 }

@@ -113,6 +113,26 @@ int persistent_ll_grid(int device);
 // leaves, or 0 when the device cannot hold the whole grid.
 int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int* threads, int* ctas_per_sm);
 cudaError_t launch_persistent_own(const PersistentArgs& a, int dyn_bytes, int threads, cudaStream_t stream);
+// Block owners on any partition of the von Neumann rule (escg_owner.cu):
+// periodic or reflecting, squares and rectangles, any bits per site; blocks
+// of at most kMaxBlock sites with fine segments of 2 or 3 sites.  Records of
+// kGRecordWords words per block (4 sides x 2 lines x 32 word slots); the
+// grid of (P/2)(Py/2) CTAs must be resident at once.
+constexpr int kGRecordWords = 256;
+struct GownConfig {
+  int dyn_bytes;     // dynamic shared memory: 4 tiles, the drawn words, padding
+  int threads;       // 256 or 512 (one quad per thread)
+  int ctas_per_sm;
+  int tile_stride;   // bytes per tile in dynamic shared memory
+};
+struct GownArgs {
+  PersistentArgs p;
+  int32_t tile_stride;
+};
+// Grid size (0: this lattice or device cannot run the kernel) and launch
+// configuration.
+int persistent_gown_config(const LatticeDesc& d, int device, GownConfig* cfg);
+cudaError_t launch_persistent_gown(const PersistentArgs& a, const GownConfig& cfg, cudaStream_t stream);
 // Completes the lattice array after a mailbox launch that ended at MCS
 // m_end: every edge cell of a block that a neighbour's visit wrote last (in
 // MCS m_end - 1) takes the value from that neighbour's record.  Does nothing

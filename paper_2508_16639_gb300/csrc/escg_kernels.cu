@@ -24,21 +24,9 @@
 #include "escg_resident.cuh"
 #include "escg_internal.h"
 #include "escg_tma.cuh"
+#include "escg_sync.cuh"
 
 namespace escg_impl {
-
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
-  return *reinterpret_cast<const volatile uint32_t*>(p);
-}
 
 // ---------------------------------------------------------------------------
 // One thread per group of 4 sites (a 32-bit word, 16-bit word or byte of
@@ -155,25 +143,6 @@ __global__ void __launch_bounds__(256) count_kernel(LatticeDesc d, RunState* st)
   __syncthreads();
   if ((int)threadIdx.x <= d.S && part[threadIdx.x])
     atomicAdd(&st->cur[threadIdx.x], (unsigned long long)part[threadIdx.x]);
-}
-
-// Writes the log entry of MCS m_end from counts c[0..S]; stasis check.
-__device__ void write_log_entry(RunState* st, LogBuffers lb, int S, uint32_t m_end, uint32_t log_every,
-                                const unsigned long long* c, int stop_at_extinction) {
-  const uint32_t idx = m_end / log_every - st->log_num0;
-  const uint32_t slot = idx % (uint32_t)kLogCap;
-  int alive = 0;
-  for (int v = 0; v < kMaxStates; ++v) {
-    const unsigned long long x = (v <= S) ? c[v] : 0ull;
-    lb.counts[(size_t)slot * kMaxStates + v] = x;
-    if (v >= 1 && v <= S && x > 0) ++alive;
-  }
-  lb.mcs[slot] = m_end;
-  atomicMax(&st->n_log, idx + 1u);
-  if (stop_at_extinction && alive <= 1) {
-    st->mcs = m_end;
-    st->stopped = 1;
-  }
 }
 
 __global__ void finalize_kernel(RunState* st, int S, LogBuffers lb, uint32_t m_end, uint32_t log_every,
@@ -399,18 +368,6 @@ constexpr int kLLConsumers = 256, kLLThreads = kLLConsumers + 32;
 // 4 CTAs of 9 warps per SM (56 registers); 5 (40 registers, with spills)
 // was measured slower at L = 3200.
 constexpr int kLLMinBlocks = 4;
-
-__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_word(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void bar_named(uint32_t id, uint32_t n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
 
 // Tile index of position pos (0..63) of line (side, part) of a uniform block.
 __device__ __forceinline__ int line_tidx(int side, int part, int pos) {

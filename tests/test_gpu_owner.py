@@ -26,16 +26,16 @@ def _built():
 @pytest.mark.parametrize("L,H,bits,expect", [(128, None, 8, "persistent_own_kernel"),
                                              (1024, None, 8, "persistent_own_kernel"),
                                              (3200, None, 8, "persistent_own_kernel"),
-                                             (100, None, 8, "persistent_kernel"),
+                                             (100, None, 8, "persistent_gown_kernel"),
                                              (256, 128, 8, "persistent_own_kernel"),
-                                             (200, 128, 8, "persistent_kernel"),
+                                             (200, 128, 8, "persistent_gown_kernel"),
                                              (256, None, 2, "persistent_own_kernel"),
                                              (6400, None, 8, "persistent_kernel")])
 def test_owner_kernel_choice(L, H, bits, expect):
     """Uniform lattices (squares and rectangles, any bits per site) whose
-    (L/128)(H/128) groups the device holds at once; the others run the flag
-    kernel (200 x 128: generic partition; 6400: 2500 groups, more CTAs of 128
-    threads than 152 SMs can hold)."""
+    (L/128)(H/128) groups the device holds at once run the uniform owner
+    kernel, generic partitions (100; 200 x 128) the generic one; 6400 (2500
+    groups, more CTAs of 128 threads than 152 SMs can hold) the flag kernel."""
     g = E.Lattice(L, 3, E.circulant(3, [1]), (1.0, 1.0, 1.0), 5, p_empty=0.25, persistent=5, H=H,
                   bits_per_site=bits)
     assert g.update_kernel == expect

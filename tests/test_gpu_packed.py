@@ -36,7 +36,8 @@ def test_packed_parity(L, H, bits, S, K, persistent):
     X = 2.0 + L / 64
     g = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.2, persistent=persistent, log_every=2, H=H,
                   bits_per_site=bits)
-    assert g.update_kernel in ("persistent_kernel", "phase_kernel", "resident_kernel", "persistent_own_kernel")
+    assert g.update_kernel in ("persistent_kernel", "phase_kernel", "resident_kernel", "persistent_own_kernel",
+                               "persistent_gown_kernel")
     o = O.init(L, S, 0.2, seed, H=H)
     assert np.array_equal(g.snapshot(), o)
     m = 0

@@ -121,11 +121,12 @@ def test_rect_large_properties():
 
 
 @pytest.mark.parametrize("L,H,expect", [(384, 768, "persistent_own_kernel"), (1024, 256, "persistent_own_kernel"),
-                                        (256, 128, "persistent_kernel"), (200, 384, "persistent_kernel")])
+                                        (256, 128, "persistent_kernel"), (200, 384, "persistent_gown_kernel")])
 def test_rect_default_kernel(L, H, expect):
     """persistent = 1 runs block owners on uniform rectangles from 3 x 3
     groups of 2 x 2 blocks (384 x 768: 3 x 6 groups; 1024 x 256: 8 x 2),
-    the flag kernel on smaller or generic ones."""
+    the flag kernel on smaller ones, the generic block owners on generic
+    ones (200 x 384: 2 x 3 groups)."""
     g = E.Lattice(L, 3, E.circulant(3, [1]), (1.0, 1.0, 2.0), 9, p_empty=0.25, H=H)
     assert g.update_kernel == expect
     g.run(4)

@@ -103,14 +103,15 @@ def test_resident_fallback_for_large_lattices():
 
 @pytest.mark.parametrize("L,H,expect", [(100, 100, "resident_kernel"), (64, 150, "resident_kernel"),
                                         (128, 128, "persistent_ll_kernel"), (384, 384, "persistent_own_kernel"),
-                                        (200, 200, "persistent_kernel"),
+                                        (200, 200, "persistent_gown_kernel"),
                                         (2048, 2048, "persistent_own_kernel"), (2816, 2816, "persistent_kernel"),
                                         (256, 128, "persistent_kernel")])
 def test_default_kernel_choice(L, H, expect):
     """persistent = 1 picks residency for generic 2 x 2-block partitions,
+    the generic block owners for larger generic ones (200: 2 x 2 groups),
     for uniform square ones the mailbox kernel below 3 x 3 groups of blocks
     (128), block owners up to 3 owner CTAs per SM (384; 2048: 256 groups),
-    the flag kernel beyond (2816: 484 groups) and for rectangles."""
+    the flag kernel beyond (2816: 484 groups) and for small rectangles."""
     D = O.circulant(3, (1,))
     g = E.Lattice(L, 3, D, (1.0, 1.0, 2.0), 11, p_empty=0.2, H=H)
     assert g.update_kernel == expect

@@ -16,7 +16,8 @@ def _built():
     build()
 
 
-@pytest.mark.parametrize("persistent", [1, 3, 2, 0], ids=["persistent", "persistent-flags", "persistent-tma", "phase"])
+@pytest.mark.parametrize("persistent", [1, 3, 2, 5, 0],
+                         ids=["persistent", "persistent-flags", "persistent-tma", "persistent-owner", "phase"])
 @pytest.mark.parametrize("nbh,reflect", [(8, False), (4, True), (8, True)], ids=["moore", "reflect", "moore-reflect"])
 @pytest.mark.parametrize("L", [64, 128, 131, 256])
 def test_variant_parity(L, nbh, reflect, persistent):
