@@ -52,7 +52,7 @@ namespace {
 constexpr uint32_t kDefaultSpinLimit = 2000000;  // polls of ~1 us: a few seconds
 // Largest number of generic block-owner CTAs per SM that persistent = 1
 // accepts.
-constexpr int kGownDefaultPerSM = 2;
+constexpr int kGownDefaultPerSM = 3;
 
 // Schedule v1 partition of one axis (both axes are identical).
 struct Partition {

@@ -19,10 +19,16 @@
 //    bottom lines have bw cells, its left and right lines bh; a record line
 //    has kGLineWords word slots of 4 cells each.
 //  * Random words drawn ahead.  Philox depends on (seed, sub-block, MCS,
-//    attempt) only, not on the lattice, so once a visit has published its
-//    records the CTA draws every word of its next visit into shared memory
-//    while the neighbours run.  A fine phase then holds only the dependent
-//    chain of its longest sub-block's attempts (9 for a 3 x 3 sub-block).
+//    attempt) only, not on the lattice, so a visit draws every word of its
+//    four fine phases into shared memory while its record polls are in
+//    flight, and each thread moves its sub-block's words into registers
+//    before stepping it.  A fine phase then holds only the dependent chain of
+//    its longest sub-block's attempts (9 for a 3 x 3 sub-block).
+//  * Quads handed out all-2 x 2 first (the batch kernel's order), so that the
+//    warps whose lanes step only 4 attempts per phase are not held to the 6
+//    or 9 of a lane at the block's leading rows or columns.
+//  * Each owned block's geometry and neighbour ids worked out once per
+//    launch (no divisions in a visit).
 //  * A reflecting boundary: a side on the lattice edge has no neighbour;
 //    nothing is polled or placed across it, and no diagonal block writes a
 //    rim end beyond it.
@@ -43,12 +49,6 @@ constexpr int kGLineWords = 32;         // word slots per record line (a line of
 static_assert(kGRecordWords == 4 * 2 * kGLineWords, "record layout");
 constexpr int kGSlots = 9;              // attempts of the largest sub-block (3 x 3)
 
-struct GownSmem {
-  uint32_t trans[kTransWords];
-  uint32_t hist[kMaxStates];
-  uint32_t forder;   // fine order of the next visit
-  uint32_t abort;
-};
 
 // Geometry of one coarse block's visit.
 struct GBlock {
@@ -56,6 +56,7 @@ struct GBlock {
   int sp;          // tile pitch
   int hx, nq;      // quads per row, quads
   uint32_t inv_hx;
+  QuadMap qm;      // quad order: the all-2 x 2 quads first
 };
 
 __device__ __forceinline__ GBlock gblock(const LatticeDesc& d, int bx, int by) {
@@ -66,7 +67,48 @@ __device__ __forceinline__ GBlock gblock(const LatticeDesc& d, int bx, int by) {
   b.hx = b.X.Q >> 1;
   b.nq = b.hx * (b.Y.Q >> 1);
   b.inv_hx = (65536u + (uint32_t)b.hx - 1u) / (uint32_t)b.hx;
+  b.qm = quad_map(b.X, b.Y);
   return b;
+}
+
+// One owned block, worked out once per launch: its geometry, block id, the
+// ids of its 4 edge neighbours (side 0 top, 1 bottom, 2 left, 3 right) and
+// 4 diagonal neighbours (0 up-left, 1 up-right, 2 down-left, 3 down-right),
+// the heights of the block rows above and below and the widths of the block
+// columns left and right (the rim-end positions in the diagonals' records),
+// and which sides have a neighbour (all, unless the boundary reflects).
+struct GColour {
+  GBlock g;
+  int32_t id;
+  int32_t nbr[4];
+  int32_t diag[4];
+  int32_t h_up, h_down, w_left, w_right;
+  int32_t ex[4];
+};
+
+__device__ __forceinline__ void gcolour_init(const LatticeDesc& d, int bx, int by, GColour& c) {
+  const int P = d.P, Py = d.Py;
+  const int xl = bx == 0 ? P - 1 : bx - 1, xr = bx == P - 1 ? 0 : bx + 1;
+  const int yu = by == 0 ? Py - 1 : by - 1, yd = by == Py - 1 ? 0 : by + 1;
+  c.g = gblock(d, bx, by);
+  c.id = by * P + bx;
+  c.nbr[0] = yu * P + bx;
+  c.nbr[1] = yd * P + bx;
+  c.nbr[2] = by * P + xl;
+  c.nbr[3] = by * P + xr;
+  c.diag[0] = yu * P + xl;
+  c.diag[1] = yu * P + xr;
+  c.diag[2] = yd * P + xl;
+  c.diag[3] = yd * P + xr;
+  c.h_up = block_span(d.ay, yu).w;
+  c.h_down = block_span(d.ay, yd).w;
+  c.w_left = block_span(d.ax, xl).w;
+  c.w_right = block_span(d.ax, xr).w;
+  const bool refl = d.reflect != 0;
+  c.ex[0] = !refl || by > 0;
+  c.ex[1] = !refl || by < Py - 1;
+  c.ex[2] = !refl || bx > 0;
+  c.ex[3] = !refl || bx < P - 1;
 }
 
 // Tile index of position pos of line (side, part) of a bw x bh block.
@@ -76,13 +118,13 @@ __device__ __forceinline__ int gline_tidx(int s, int part, int pos, int bw, int 
   return (s < 2) ? tidx(fixed, pos, sp) : tidx(pos, fixed, sp);
 }
 
-// Whether side s of block (bx, by) has a neighbour (always, unless the
-// boundary reflects and the side lies on the lattice edge).
-template <bool REFLECT>
-__device__ __forceinline__ bool side_exists(const LatticeDesc& d, int bx, int by, int s) {
-  if (!REFLECT) return true;
-  return s == 0 ? by > 0 : s == 1 ? by < d.Py - 1 : s == 2 ? bx > 0 : bx < d.P - 1;
-}
+struct GownSmem {
+  GColour col[4];    // the owned block of each colour
+  uint32_t trans[kTransWords];
+  uint32_t hist[kMaxStates];
+  uint32_t forder;   // fine order of the current visit
+  uint32_t abort;
+};
 
 // The block's tile as the lattice array holds it: interior, top and bottom
 // rim rows, left and right rim columns (not the corners; nothing beyond a
@@ -112,25 +154,37 @@ __device__ __forceinline__ void gown_stage(const LatticeDesc& d, uint8_t* tile, 
 
 // Every Philox word of the visit of block g in MCS m, by quad and fine
 // colour: W[(colour * kGSlots + t) * NT + q] is the word of attempt t of the
-// quad's sub-block of that colour (t < its cell count).
+// quad's sub-block of that colour (t < its cell count).  Thread i draws the
+// words of colour i mod 4 for the quads i/4 + k NT/4, k = 0..3: the sub-blocks
+// with 3 x 3 cells (three Philox calls) sit at the block's leading corner,
+// and this spreads them over different threads, each with four independent
+// draws in flight.
 template <int NT>
-__device__ __forceinline__ void gown_words(const LatticeDesc& d, const GBlock& g, uint32_t m, uint32_t* W) {
-  for (int q = threadIdx.x; q < g.nq; q += NT) {
-    const int qy = (int)(((uint32_t)q * g.inv_hx) >> 16), qx = q - qy * g.hx;
+__device__ __forceinline__ void gown_words(const LatticeDesc& d, const GBlock& g, uint32_t m,
+                                           uint32_t* __restrict__ W) {
+  const int c = threadIdx.x & 3;
+  uint32_t gid[4];
+  int nk[4], q[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int fx = 2 * qx + (c & 1), fy = 2 * qy + (c >> 1);
-      const int nk = seg_width(g.X, fx) * seg_width(g.Y, fy);
-      const uint32_t gid = (uint32_t)(g.Y.f0 + fy) * (uint32_t)d.GQ + (uint32_t)(g.X.f0 + fx);
-      uint32_t* w = W + (c * kGSlots) * NT + q;
+  for (int k = 0; k < 4; ++k) {
+    q[k] = (int)(threadIdx.x >> 2) + k * (NT / 4);
+    int qx, qy;
+    quad_at(g.qm, q[k] < g.nq ? q[k] : 0, qx, qy);
+    const int fx = 2 * qx + (c & 1), fy = 2 * qy + (c >> 1);
+    nk[k] = q[k] < g.nq ? seg_width(g.X, fx) * seg_width(g.Y, fy) : 0;
+    gid[k] = (uint32_t)(g.Y.f0 + fy) * (uint32_t)d.GQ + (uint32_t)(g.X.f0 + fx);
+  }
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        if (4 * j >= nk) break;
-        const uint4 x = philox10_rk(make_uint4((uint32_t)j, gid, m, kTagStep), d.rk);
-        w[(4 * j) * NT] = x.x;
-        if (4 * j + 1 < nk) w[(4 * j + 1) * NT] = x.y;
-        if (4 * j + 2 < nk) w[(4 * j + 2) * NT] = x.z;
-        if (4 * j + 3 < nk) w[(4 * j + 3) * NT] = x.w;
+  for (int j = 0; j < 3; ++j) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (4 * j < nk[k]) {
+        const uint4 x = philox10_rk(make_uint4((uint32_t)j, gid[k], m, kTagStep), d.rk);
+        uint32_t* w = W + (c * kGSlots + 4 * j) * NT + q[k];
+        w[0] = x.x;
+        if (4 * j + 1 < nk[k]) w[NT] = x.y;
+        if (4 * j + 2 < nk[k]) w[2 * NT] = x.z;
+        if (4 * j + 3 < nk[k]) w[3 * NT] = x.w;
       }
     }
   }
@@ -140,29 +194,36 @@ __device__ __forceinline__ void gown_words(const LatticeDesc& d, const GBlock& g
 // ord), each ending with a CTA barrier.
 template <int NT, bool REFLECT>
 __device__ __forceinline__ void gown_fine_phases(const LatticeDesc& d, const GBlock& g, uint8_t* tile,
-                                                 uint32_t ord, const uint8_t* trans, const uint32_t* W) {
+                                                 uint32_t ord, const uint8_t* trans,
+                                                 const uint32_t* __restrict__ W) {
   const uint32_t s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
   const int sp = g.sp;
 #pragma unroll 1
   for (int fi = 0; fi < 4; ++fi) {
     const int fcol = order_at(ord, fi), cx = fcol & 1, cy = fcol >> 1;
     for (int q = threadIdx.x; q < g.nq; q += NT) {
-      const int qy = (int)(((uint32_t)q * g.inv_hx) >> 16), qx = q - qy * g.hx;
+      int qx, qy;
+      quad_at(g.qm, q, qx, qy);
       const int fx = 2 * qx + cx, fy = 2 * qy + cy;
-      const int sx = seg_start(g.X, fx), wx = seg_width(g.X, fx);
-      const int sy = seg_start(g.Y, fy), wy = seg_width(g.Y, fy);
+      const int sx = seg_start(g.X, fx), sy = seg_start(g.Y, fy);
+      const int base = tidx(sy, sx, sp);
+      // the sub-block's words into registers first: the tile stores of one
+      // attempt must not hold up the word loads of the next
+      const uint32_t* __restrict__ w = W + (fcol * kGSlots) * NT + q;
+      const int wx = seg_width(g.X, fx), wy = seg_width(g.Y, fy);
       const uint32_t nk = (uint32_t)(wx * wy), n4 = 4u * nk;
       const uint32_t inv_wx = wx == 2 ? 32768u : 21846u;   // ceil(65536 / wx), widths 2 and 3
-      const int base = tidx(sy, sx, sp);
-      const uint32_t* w = W + (fcol * kGSlots) * NT + q;
+      uint32_t wv[kGSlots];
+#pragma unroll
+      for (int t = 0; t < kGSlots; ++t) wv[t] = (uint32_t)t < nk ? w[t * NT] : 0u;
 #pragma unroll
       for (int t = 0; t < kGSlots; ++t) {
         if ((uint32_t)t < nk) {
           if (REFLECT)
-            attempt_variant(tile, trans, w[t * NT], n4, 2, base, wx, inv_wx, sp, tx, txi, s1, true,
+            attempt_variant(tile, trans, wv[t], n4, 2, base, wx, inv_wx, sp, tx, txi, s1, true,
                             g.Y.s0 + sy, g.X.s0 + sx, d.H, d.L);
           else
-            attempt(tile, trans, w[t * NT], n4, base, wx, inv_wx, sp, tx, txi, s1);
+            attempt(tile, trans, wv[t], n4, base, wx, inv_wx, sp, tx, txi, s1);
         }
       }
     }
@@ -220,7 +281,7 @@ __device__ __forceinline__ void gown_store(const LatticeDesc& d, const uint8_t* 
 }
 
 template <int NT, bool REFLECT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(const __grid_constant__ GownArgs ga) {
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) persistent_gown_kernel(const __grid_constant__ GownArgs ga) {
   extern __shared__ __align__(16) uint8_t gdyn[];
   __shared__ GownSmem sm;
   const PersistentArgs& a = ga.p;
@@ -234,11 +295,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
   const bool run = !ld_volatile(&st->stopped);
   if (run) {
     load_trans(d, sm.trans);
-    const int P = d.P, Py = d.Py, half = P >> 1;
-    const uint32_t nb = (uint32_t)(P * Py);
+    const int P = d.P, half = P >> 1;
+    const uint32_t nb = (uint32_t)(P * d.Py);
     const int gx = (int)blockIdx.x % half, gy = (int)blockIdx.x / half;
-    for (int c = 0; c < 4; ++c)
-      gown_stage<NT>(d, gdyn + c * tstride, gblock(d, 2 * gx + (c & 1), 2 * gy + (c >> 1)));
+    if (tid < 4) gcolour_init(d, 2 * gx + (tid & 1), 2 * gy + (tid >> 1), sm.col[tid]);
+    if (tid == 0) sm.abort = 0;
+    __syncthreads();
+    for (int c = 0; c < 4; ++c) gown_stage<NT>(d, gdyn + c * tstride, sm.col[c].g);
     const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
     const uint32_t m_end = a.m_begin + a.n_mcs;
     uint32_t ordp = colour_order(philox10(make_uint4(0u, 0u, a.m_begin - 1u, kTagOrder), d.key0, d.key1).x,
@@ -246,13 +309,21 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
     uint32_t ord = colour_order(philox10(make_uint4(0u, 0u, a.m_begin, kTagOrder), d.key0, d.key1).x, d.perm24);
     uint32_t ord_next = colour_order(philox10(make_uint4(0u, 0u, a.m_begin + 1u, kTagOrder), d.key0, d.key1).x,
                                      d.perm24);
-    {  // words and fine order of the first visit
-      const int c0 = order_at(ord, 0), bx = 2 * gx + (c0 & 1), by = 2 * gy + (c0 >> 1);
-      gown_words<NT>(d, gblock(d, bx, by), a.m_begin, W);
-      if (tid == 0) sm.forder = fine_order(d, bx, by, a.m_begin);
-    }
-    if (tid == 0) sm.abort = 0;
-    __syncthreads();
+    // the polling role of this thread: warp w < 8 polls side s = w & 3, part
+    // w >> 2 of the edge neighbour's record of the opposite side (one word per
+    // lane); lanes 24 and 25 of warps 0..3 also a diagonal neighbour's
+    // rim-end word, dl = 2 s + (lane & 1): dl 0..3 the ends of the top and
+    // bottom rim rows, 4..7 those of the left and right rim columns
+    const bool poller = warp < 8;
+    const int s = warp & 3, part = (warp >> 2) & 1;
+    const int dl = 2 * s + (lane & 1);
+    const int ddx = (dl == 0 || dl == 2 || dl == 4 || dl == 5) ? -1 : 1;
+    const int ddy = (dl == 0 || dl == 1 || dl == 4 || dl == 6) ? -1 : 1;
+    const int oside = (dl < 4) ? (ddx < 0 ? 2 : 3) : (ddy < 0 ? 0 : 1);
+    const int dq = (ddy > 0 ? 2 : 0) + (ddx > 0 ? 1 : 0);            // diagonal index
+    const int drec = (dl < 4) ? (ddx < 0 ? 3 : 2) : (ddy < 0 ? 1 : 0);  // its record side
+    const bool isd = poller && part == 0 && (lane == 24 || lane == 25);
+    const int o0 = (s < 2) ? 2 : 0, o1 = (s < 2) ? 3 : 1;   // other-axis sides at the two line ends
     bool quit = false;
     for (uint32_t m = a.m_begin; m < m_end && !quit; ++m) {
       if (m != a.m_begin) {
@@ -263,9 +334,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
       for (int k = 0; k < 4; ++k) {
         if (tid < kMaxStates) sm.hist[tid] = 0;
         const int colour = order_at(ord, k);
-        const int bx = 2 * gx + (colour & 1), by = 2 * gy + (colour >> 1);
-        const int X = by * P + bx;
-        const GBlock g = gblock(d, bx, by);
+        const GColour& C = sm.col[colour];
+        // a register copy: tile stores (bytes) could otherwise alias it and
+        // force reloads inside the fine phases
+        const GBlock g = C.g;
         const int bw = g.X.w, bh = g.Y.w, sp = g.sp;
         uint8_t* tile = gdyn + colour * tstride;
         const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1), sD = slot_of(ord, colour ^ 3);
@@ -279,36 +351,24 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
         const bool first = (m == a.m_begin);
         const int kV = first && sV > k ? -1 : kV0, kH = first && sH > k ? -1 : kH0;
         const int kD = first && sD > k ? -1 : kD0, kXp = first ? 3 : slot_of(ordp, colour);
-        // warp w < 8 polls side s = w & 3, part w >> 2 of the edge neighbour's
-        // record of the opposite side (one word per lane); lanes 24 and 25 of
-        // warps 0..3 also a diagonal neighbour's rim-end word, dl = 2 s +
-        // (lane & 1): dl 0..3 the ends of the top and bottom rim rows, 4..7
-        // those of the left and right rim columns
-        const bool poller = warp < 8;
-        const int s = warp & 3, part = (warp >> 2) & 1;
         const int len = (s < 2) ? bw : bh, nwd = (len + 3) >> 2;
-        const bool exs = side_exists<REFLECT>(d, bx, by, s);
-        const int nx = (s == 2) ? (bx + P - 1) % P : (s == 3) ? (bx + 1) % P : bx;
-        const int ny = (s == 0) ? (by + Py - 1) % Py : (s == 1) ? (by + 1) % Py : by;
+        const bool exs = C.ex[s] != 0;
         const uint32_t e = (s < 2) ? eV : eH;
-        const unsigned long long* p = ob + ((size_t)(ny * P + nx) * 4 + (s ^ 1)) * (2 * kLW) + part * kLW + lane;
-        const int dl = 2 * s + (lane & 1);
-        const int ddx = (dl == 0 || dl == 2 || dl == 4 || dl == 5) ? -1 : 1;
-        const int ddy = (dl == 0 || dl == 1 || dl == 4 || dl == 6) ? -1 : 1;
-        const int oside = (dl < 4) ? (ddx < 0 ? 2 : 3) : (ddy < 0 ? 0 : 1);
-        const bool isd = poller && part == 0 && (lane == 24 || lane == 25);
-        const bool dex = exs && side_exists<REFLECT>(d, bx, by, oside);
-        const int dbx = (bx + P + ddx) % P, dby = (by + Py + ddy) % Py;
-        const int drec = (dl < 4) ? (ddx < 0 ? 3 : 2) : (ddy < 0 ? 1 : 0);
-        const int dpos = (dl < 4) ? (ddy < 0 ? block_span(d.ay, dby).w - 1 : 0)
-                                  : (ddx < 0 ? block_span(d.ax, dbx).w - 1 : 0);
-        const unsigned long long* pd =
-            ob + ((size_t)(dby * P + dbx) * 4 + drec) * (2 * kLW) + kLW + (dpos >> 2);
-        bool got = !poller || !exs || lane >= nwd || (first && ((s < 2) ? sV : sH) > k);
+        const unsigned long long* p = ob + ((size_t)C.nbr[s] * 4 + (s ^ 1)) * (2 * kLW) + part * kLW + lane;
+        const bool dex = exs && C.ex[oside] != 0;
+        const int dpos = (dl < 4) ? (ddy < 0 ? C.h_up - 1 : 0) : (ddx < 0 ? C.w_left - 1 : 0);
+        const unsigned long long* pd = ob + ((size_t)C.diag[dq] * 4 + drec) * (2 * kLW) + kLW + (dpos >> 2);
+        const bool skip_s = first && ((s < 2) ? sV : sH) > k;   // that neighbour has not visited yet
+        bool got = !poller || !exs || lane >= nwd || skip_s;
         bool got_d = !isd || !dex || (first && sD > k);
         unsigned long long word = 0, dword = 0;
         if (!got) word = ld_word(p);
         if (!got_d) dword = ld_word(pd);
+        // while those loads are in flight: every random word and the fine
+        // order of this visit (the words of the previous visit are no longer
+        // read: its last fine phase ended with a barrier)
+        gown_words<NT>(d, g, m, W);
+        if (tid == NT - 1) sm.forder = fine_order(d, 2 * gx + (colour & 1), 2 * gy + (colour >> 1), m);
         bool failed = false;
         uint32_t spins = 0;
         for (;;) {
@@ -336,8 +396,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
           // that is the block itself, the tile already holds it
           const int xp = 1 - part;
           const int kS = (s < 2) ? kV : kH, kO = (s < 2) ? kH : kV;
-          const int o0 = (s < 2) ? 2 : 0, o1 = (s < 2) ? 3 : 1;   // other-axis sides at the two ends
-          if (lane < nwd && !(first && ((s < 2) ? sV : sH) > k)) {
+          if (lane < nwd && !skip_s) {
             const uint32_t data = (uint32_t)word;
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
@@ -345,9 +404,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
               if (pos >= len) break;
               int beat = kXp;
               if (pos == 0 || pos == len - 1) {
-                const bool ex_o = side_exists<REFLECT>(d, bx, by, pos == 0 ? o0 : o1);
-                const int other = ex_o ? (xp == 0 ? kO : kD) : -1;
-                beat = max(beat, other);
+                const bool ex_o = C.ex[pos == 0 ? o0 : o1] != 0;
+                beat = max(beat, ex_o ? (xp == 0 ? kO : kD) : -1);
               }
               if (kS > beat) tile[gline_tidx(s, xp, pos, bw, bh, sp)] = (uint8_t)(data >> (8 * jj));
             }
@@ -364,14 +422,15 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
           break;
         }
         gown_fine_phases<NT, REFLECT>(d, g, tile, sm.forder, trans, W);
-        if (poller && exs && lane < nwd && X != a.stall_block) {
+        if (poller && exs && lane < nwd && C.id != a.stall_block) {
           uint32_t bytes = 0;
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
             const int pos = 4 * lane + jj;
             if (pos < len) bytes |= (uint32_t)tile[gline_tidx(s, part, pos, bw, bh, sp)] << (8 * jj);
           }
-          st_word(ob + ((size_t)X * 4 + s) * (2 * kLW) + part * kLW + lane, ((unsigned long long)(m + 1u) << 32) | bytes);
+          st_word(ob + ((size_t)C.id * 4 + s) * (2 * kLW) + part * kLW + lane,
+                  ((unsigned long long)(m + 1u) << 32) | bytes);
         }
         if (a.fuse_counts && ((m + 1u) % a.log_every) == 0u) {
           count_tile_generic(tile, sp, kColOff, bw, bh, sm.hist, NT >> 5, k, sV, sH, sD);
@@ -391,20 +450,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
             }
           }
         }
-        // the words and fine order of the next visit, drawn while the
-        // neighbours run theirs (the words of this visit are no longer read:
-        // its last fine phase ended with a barrier)
-        {
-          const uint32_t mn = k < 3 ? m : m + 1u;
-          if (mn < m_end) {
-            const int cn = order_at(k < 3 ? ord : ord_next, (k + 1) & 3);
-            const int bxn = 2 * gx + (cn & 1), byn = 2 * gy + (cn >> 1);
-            gown_words<NT>(d, gblock(d, bxn, byn), mn, W);
-            if (tid == 0) sm.forder = fine_order(d, bxn, byn, mn);
-          }
-        }
-        // the next visit's placement must not overtake this visit's record
-        // reads and counts, nor its fine phases the words drawn above
+        // the next visit's placement and words must not overtake this visit's
+        // record reads and counts
         __syncthreads();
       }
     }
@@ -421,14 +468,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
       bool need[kPer];
 #pragma unroll
       for (int j = 0; j < kPer; ++j) {
-        const int i = tid + j * NT, c = i >> 7, s = (i >> 5) & 3, w = i & 31;
-        const int bx = 2 * gx + (c & 1), by = 2 * gy + (c >> 1);
-        const int len = (s < 2) ? block_span(d.ax, bx).w : block_span(d.ay, by).w;
-        const int nx = (s == 2) ? (bx + P - 1) % P : (s == 3) ? (bx + 1) % P : bx;
-        const int ny = (s == 0) ? (by + Py - 1) % Py : (s == 1) ? (by + 1) % Py : by;
-        need[j] = 4 * w < len && side_exists<REFLECT>(d, bx, by, s) &&
-                  slot_of(ord, (s < 2) ? c ^ 2 : c ^ 1) > slot_of(ord, c);
-        wp[j] = ob + ((size_t)(ny * P + nx) * 4 + (s ^ 1)) * (2 * kLW) + kLW + w;
+        const int i = tid + j * NT, c = i >> 7, si = (i >> 5) & 3, w = i & 31;
+        const GColour& C = sm.col[c];
+        const int len = (si < 2) ? C.g.X.w : C.g.Y.w;
+        need[j] = 4 * w < len && C.ex[si] != 0 && slot_of(ord, (si < 2) ? c ^ 2 : c ^ 1) > slot_of(ord, c);
+        wp[j] = ob + ((size_t)C.nbr[si] * 4 + (si ^ 1)) * (2 * kLW) + kLW + w;
         wv[j] = need[j] ? ld_word(wp[j]) : 0ull;
       }
       bool failed = false;
@@ -457,29 +501,27 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) persistent_gown_kernel(
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
           if (!need[j]) continue;
-          const int i = tid + j * NT, c = i >> 7, s = (i >> 5) & 3, w = i & 31;
-          const int bx = 2 * gx + (c & 1), by = 2 * gy + (c >> 1);
-          const int bw = block_span(d.ax, bx).w, bh = block_span(d.ay, by).w;
-          const int len = (s < 2) ? bw : bh, sp = tile_pitch(bw);
-          const int kX = slot_of(ord, c), kS = slot_of(ord, (s < 2) ? c ^ 2 : c ^ 1);
-          const int kO = slot_of(ord, (s < 2) ? c ^ 1 : c ^ 2);
-          const int o0 = (s < 2) ? 2 : 0, o1 = (s < 2) ? 3 : 1;
+          const int i = tid + j * NT, c = i >> 7, si = (i >> 5) & 3, w = i & 31;
+          const GColour& C = sm.col[c];
+          const int bw = C.g.X.w, bh = C.g.Y.w;
+          const int len = (si < 2) ? bw : bh;
+          const int kX = slot_of(ord, c), kS = slot_of(ord, (si < 2) ? c ^ 2 : c ^ 1);
+          const int kO = slot_of(ord, (si < 2) ? c ^ 1 : c ^ 2);
+          const int e0 = (si < 2) ? 2 : 0, e1 = (si < 2) ? 3 : 1;
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
             const int pos = 4 * w + jj;
             if (pos >= len) break;
             int beat = kX;
-            if (pos == 0 || pos == len - 1)
-              beat = max(beat, side_exists<REFLECT>(d, bx, by, pos == 0 ? o0 : o1) ? kO : -1);
+            if (pos == 0 || pos == len - 1) beat = max(beat, C.ex[pos == 0 ? e0 : e1] ? kO : -1);
             if (kS > beat)
-              gdyn[c * tstride + gline_tidx(s, 0, pos, bw, bh, sp)] = (uint8_t)((uint32_t)wv[j] >> (8 * jj));
+              gdyn[c * tstride + gline_tidx(si, 0, pos, bw, bh, C.g.sp)] = (uint8_t)((uint32_t)wv[j] >> (8 * jj));
           }
         }
       }
       __syncthreads();
     }
-    for (int c = 0; c < 4; ++c)
-      gown_store<NT>(d, gdyn + c * tstride, gblock(d, 2 * gx + (c & 1), 2 * gy + (c >> 1)));
+    for (int c = 0; c < 4; ++c) gown_store<NT>(d, gdyn + c * tstride, sm.col[c].g);
   }
   // The last CTA to leave publishes the MCS number.
   __syncthreads();

@@ -71,14 +71,14 @@ def test_gown_parity_every_mcs(case):
 
 @pytest.mark.parametrize("L,H,expect", [(200, None, "persistent_gown_kernel"), (333, None, "persistent_gown_kernel"),
                                         (800, None, "persistent_gown_kernel"), (1000, None, "persistent_gown_kernel"),
-                                        (2200, None, "persistent_gown_kernel"), (2300, None, "persistent_kernel"),
+                                        (2700, None, "persistent_gown_kernel"), (3000, None, "persistent_kernel"),
                                         (100, None, "resident_kernel"), (200, 384, "persistent_gown_kernel"),
-                                        (3200, 1600, "persistent_kernel")])
+                                        (3200, 1600, "persistent_gown_kernel"), (6400, 1600, "persistent_kernel")])
 def test_gown_default_choice(L, H, expect):
     """persistent = 1 runs the generic block owners from two groups of 2 x 2
-    blocks while the grid needs at most 2 CTAs per SM (2200: 289 groups);
-    beyond, the flag kernel (2300: 324 groups; 3200 x 1600: 325); one group
-    (P = 2): whole-lattice residency."""
+    blocks while the grid needs at most 3 CTAs per SM (2700: 441 groups;
+    3200 x 1600: 325); beyond, the flag kernel (3000: 529 groups; 6400 x
+    1600: 650); one group (P = 2): whole-lattice residency."""
     g = E.Lattice(L, 3, E.circulant(3, [1]), (1.0, 1.0, 2.0), 9, p_empty=0.25, H=H)
     assert g.update_kernel == expect
     g.close()
