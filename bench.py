@@ -91,6 +91,7 @@ def _parse():
     ap.add_argument("--mobility", type=float, default=1e-4)
     ap.add_argument("--mcs-per-step", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-rs-seconds", type=float, default=8.0)
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="time budget of the reference arm's timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -101,10 +102,13 @@ def _parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-replicas", type=int, default=1024)
     ap.add_argument("--ensemble-baseline-sample", type=int, default=16)
+    ap.add_argument("--ensemble-cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-park", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-sizes", action="store_true")
+    ap.add_argument("--no-mobility", action="store_true")
+    ap.add_argument("--mobility-steps", type=int, default=200)
     ap.add_argument("--size-steps", type=int, default=100)
     ap.add_argument("--no-packed", action="store_true")
     ap.add_argument("--packed-steps", type=int, default=100)
@@ -112,7 +116,8 @@ def _parse():
     ap.add_argument("--park-per-point", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rate", type=float, default=200.0,
-                    help="mean Poisson arrival rate (requests/s); ~ the measured capacity")
+                    help="mean Poisson arrival rate (requests/s) of the first serving run")
+    ap.add_argument("--serve-saturated-requests", type=int, default=4000)
     return ap.parse_args()
 
 
@@ -189,6 +194,103 @@ def _cpu_oracle_rate(w, seconds: float):
             return done * w.L * w.L / el, done, el
 
 
+def _hbm_peak():
+    """The driver's measured HBM copy bandwidth (MEASURED_PEAKS.json), else
+    the profiling recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback (6.8 TB/s, one earlier GB300 measurement)"
+
+
+def _cpu_info():
+    """(CPU model, logical cores) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return model, os.cpu_count()
+
+
+def _cpu_rs_rate(w, seconds: float):
+    """Random-sequential oracle (Alg. 3 + Alg. 4, single thread) on the same
+    initial lattice: whole MCS until `seconds` have passed."""
+    import oracle as O
+    X = O.exchange_from_mobility(w.mobility, w.L * w.L)
+    D = O.circulant(w.S, w.K)
+    lat = O.init(w.L, w.S, w.p_empty, w.seed)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        lat = O.rs_run(lat, D, w.interact, w.reproduce, X, w.seed, 1, mcs_begin=done)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return done * w.L * w.L / el, done, el
+
+
+def _oracle_ensemble_worker(job):
+    """One host core: the schedule-v1 replay oracle on its share of the
+    ensemble's replicas, in order, each to extinction or its budget in
+    chunks of 10 MCS, until `seconds` have passed.  Returns (site-updates,
+    runs finished, seconds)."""
+    reps, seconds = job
+    import oracle as O
+    t0 = time.perf_counter()
+    upd, fin = 0, 0
+    for r in reps:
+        L, S = r["L"], r["S"]
+        X = O.exchange_from_mobility(r["mobility"], L * L)
+        D = O.circulant(S, r["K"])
+        lat = O.init(L, S, r["p_empty"], r["seed"])
+        m, finished = 0, False
+        while not finished:
+            n = min(10, r["max_mcs"] - m)
+            lat, _, mend = O.run_observed(lat, D, r["interact"], r["reproduce"], X, r["seed"], n, log_every=10,
+                                          stop_at_extinction=True, mcs_begin=m)
+            upd += (mend - m) * L * L
+            finished = mend < m + n or mend >= r["max_mcs"]
+            m = mend
+            if time.perf_counter() - t0 >= seconds:
+                break
+        fin += int(finished)
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return upd, fin, time.perf_counter() - t0
+
+
+def _oracle_ensemble_rate(reps, seconds: float, mean_updates_per_run: float):
+    """The ensemble on every host core: one oracle process per core (spawned,
+    so that no CUDA state is inherited), replicas dealt round-robin, a
+    bounded wall time.  Runs/s = aggregate site-updates/s divided by the
+    mean site-updates of a run of this ensemble (from the GPU run, whose
+    runs are the same)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    jobs = [(reps[k::cores], seconds) for k in range(cores)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_ensemble_worker, jobs)
+    wall = time.perf_counter() - t0
+    upd = sum(r[0] for r in res)
+    fin = sum(r[1] for r in res)
+    rate = upd / max(r[2] for r in res)
+    return {"value": rate / mean_updates_per_run, "unit": "runs/s", "cores": cores, "kind": "oracle",
+            "site_updates_per_s": rate, "runs_finished_in_sample": fin, "wall_s": wall,
+            "sample": f"schedule-v1 replay oracle, one process per core over the ensemble's replicas "
+                      f"(round-robin), {seconds:g} s each; runs/s = site-updates/s / mean site-updates of "
+                      f"a run ({mean_updates_per_run:.3g})"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -239,29 +341,66 @@ def _config(w, mcs_per_step):
             "parallelism": "replicas (one independent lattice per GPU)"}
 
 
-def _ensemble(args, rank):
+def _ensemble(args, rank, world, dist):
     """Batched ensemble: independent replicas (L uniform on {64,100,200,400},
     RPS/RPSLS, M log-uniform on [1e-5, 1e-3]) each to extinction or 10^4 MCS
-    in shared persistent launches; beside it, a sample of the same runs one
-    at a time through the single-lattice path."""
+    in shared persistent launches, the replicas dealt round-robin over the
+    ranks; beside it, a sample of the same runs as per-run launches (one
+    single-lattice handle per run, each on its own stream, all in flight at
+    once) and the CPU oracle on every host core."""
     import numpy as np
+    import torch
+    from paper_2508_16639_gb300 import Lattice, circulant, replicas as R
     from paper_2508_16639_gb300 import workloads as W
-    from paper_2508_16639_gb300.ensemble import run_batch, run_one_at_a_time
-    reps = W.ensemble(args.ensemble_replicas, seed=1 + rank)
+    from paper_2508_16639_gb300.ensemble import run_batch
+    from paper_2508_16639_gb300.serve import request_spec
+    reps_all = W.ensemble(args.ensemble_replicas, seed=1)
+    reps = R.shard(reps_all, rank, world)
+    if dist is not None:
+        dist.barrier()
     out, mcs, ext = run_batch(reps)
+    secs = R.max_over_ranks(out["seconds"], dist, device="cuda")
+    out["runs"] = len(reps_all)
+    out["runs_per_s"] = len(reps_all) / secs
+    out["site_updates_per_s"] = R.sum_over_ranks(out["site_updates_per_s"] * out["seconds"], dist,
+                                                 device="cuda") / secs
+    out["seconds"] = secs
+    # per-run launches: the sample's runs as concurrent single-lattice handles
     sample_idx = np.random.default_rng(0).choice(len(reps), min(args.ensemble_baseline_sample, len(reps)),
                                                  replace=False)
-    base, mcs1 = run_one_at_a_time([reps[i] for i in sample_idx])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = []
+    for i in sample_idx:
+        sp = request_spec(reps[i])
+        g = Lattice(sp["L"], sp["S"], circulant(sp["S"], reps[i]["K"]), sp["rates"], sp["seed"],
+                    p_empty=sp["p_empty"], log_every=10, stop_at_extinction=sp["stop_at_extinction"],
+                    stream=torch.cuda.Stream())
+        g.run(sp["max_mcs"])
+        hs.append(g)
+    for g in hs:
+        g.sync()
+    el = time.perf_counter() - t0
+    mcs1 = np.array([g.mcs for g in hs])
+    for g in hs:
+        g.close()
+    base = {"runs": len(sample_idx), "seconds": el, "runs_per_s": len(sample_idx) / el,
+            "sample": f"{len(sample_idx)} of the same runs, one single-lattice handle per run, each on its own "
+                      "stream, all enqueued before the first is waited for (creation included)",
+            "identical_mcs": bool(np.array_equal(mcs1, mcs[sample_idx]))}
+    out["per_run_launches"] = base
+    out["speedup_vs_per_run"] = out["runs_per_s"] / world / base["runs_per_s"]   # per GPU
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_run = out["site_updates_per_s"] * secs / len(reps_all)
+        out["cpu_baseline"] = _oracle_ensemble_rate(reps_all, args.ensemble_cpu_seconds, per_run)
     out["metric"] = "ensemble runs/s"
-    out["config"] = {"workload": f"{len(reps)} replicas, L in {{64,100,200,400}}, S in {{3,5}}, "
-                                 "M log-uniform [1e-5,1e-3], to extinction or 10^4 MCS, log every 10 MCS"}
-    out["per_run_launches"] = dict(base, sample=f"{len(sample_idx)} of the same runs, one at a time",
-                                   identical_mcs=bool(np.array_equal(mcs1, mcs[sample_idx])))
-    out["speedup_vs_per_run"] = out["runs_per_s"] / base["runs_per_s"]
+    out["config"] = {"workload": f"{len(reps_all)} replicas, L in {{64,100,200,400}}, S in {{3,5}}, "
+                                 "M log-uniform [1e-5,1e-3], to extinction or 10^4 MCS, log every 10 MCS",
+                     "ranks": world, "split": "round-robin over ranks (replicas.shard)"}
     return out
 
 
-def _park(args, rank):
+def _park(args, rank, world, dist):
     """Probabilistic-dominance ensemble (the Park, Chen and Szolnoki model the
     paper replicates): L = 100, 8 species, edge probabilities (alpha, beta,
     gamma = 1), no mobility, L^2 MCS or until one species is left; reports
@@ -270,9 +409,11 @@ def _park(args, rank):
     import numpy as np
     from paper_2508_16639_gb300 import workloads as W
     from paper_2508_16639_gb300 import Batch
-    specs = W.park_ensemble(per_point=args.park_per_point)
-    for sp in specs:
-        sp["seed"] += 1000003 * rank
+    from paper_2508_16639_gb300 import replicas as R
+    specs_all = W.park_ensemble(per_point=args.park_per_point)
+    specs = R.shard(specs_all, rank, world)
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     b = Batch([{k: v for k, v in sp.items() if k != "point"} for sp in specs], log_every=10)
     t1 = time.perf_counter()
@@ -285,12 +426,14 @@ def _park(args, rank):
         n = int((c[1:9] > 0).sum())
         surv.setdefault(key, np.zeros(9, dtype=int))[n] += 1
     site_updates = float(sum(int(m) * sp["L"] ** 2 for m, sp in zip(mcs, specs)))
-    out = {"metric": "probabilistic-dominance ensemble runs/s", "runs": len(specs),
-           "seconds": t2 - t1, "setup_seconds": t1 - t0, "runs_per_s": len(specs) / (t2 - t1),
-           "site_updates_per_s": site_updates / (t2 - t1), "threads": b.threads, "launches": b.launches,
+    secs = R.max_over_ranks(t2 - t1, dist, device="cuda")
+    out = {"metric": "probabilistic-dominance ensemble runs/s", "runs": len(specs_all),
+           "seconds": secs, "setup_seconds": t1 - t0, "runs_per_s": len(specs_all) / secs,
+           "site_updates_per_s": R.sum_over_ranks(site_updates, dist, device="cuda") / secs,
+           "threads": b.threads, "launches": b.launches,
            "mean_mcs": float(np.mean(mcs)),
            "surviving_species_histogram": {k: v.tolist() for k, v in sorted(surv.items())},
-           "config": {"workload": f"{len(specs)} replicas: L=100, 8 species beating the next 3 with "
+           "config": {"workload": f"{len(specs_all)} replicas: L=100, 8 species beating the next 3 with "
                                   "probabilities (alpha, beta, 1), alpha, beta in {0.2,0.5,0.8}, "
                                   "I=P=1, no mobility, to one species or L^2 MCS"}}
     b.close()
@@ -342,6 +485,46 @@ def _variants(args, rank, w):
                                  "rect_<columns>x<rows>: the same N = L*L as a rectangle; "
                                  f"{c2.name}: S=5 C(5,{{1,2}}), p_empty {c2.p_empty}, M {c2.mobility:g}",
                      "steps": args.variant_steps}
+    return out
+
+
+def _mobility_points(args, rank, w):
+    """The benchmark lattice (L = 3200, RPS with empty sites) at the other two
+    mobilities of the workload, M = 1e-5 and 1e-3 (exchange 2MN: 99.0 % and
+    99.9 % of attempts), timed as the main measurement: device time per 10-MCS
+    step, L2 flushed before each step."""
+    import torch
+    import paper_2508_16639_gb300 as E
+    from paper_2508_16639_gb300 import replicas as R
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for M in (1e-5, 1e-3):
+        wm = _workload(M, w.L)
+        N = wm.L * wm.L
+        X = E.exchange_from_mobility(M, N)
+        stream = torch.cuda.Stream()
+        g = E.Lattice(wm.L, wm.S, E.circulant(wm.S, wm.K), (wm.interact, wm.reproduce, X),
+                      R.replica_seed(wm.seed, rank), p_empty=wm.p_empty, log_every=wm.log_every, stream=stream,
+                      time_kernels=True)
+        for _ in range(3):
+            g.run(10)
+        g.sync()
+        g.kernel_time(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.mobility_steps)]
+        for a, b in ev:
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            a.record(stream)
+            g.run(10)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        kms, kn = g.kernel_time()
+        out[wm.name] = {"site_updates_per_s": 10 * N / (ms * 1e-3), "ms_per_10_mcs": ms,
+                        "kernel_ms_per_launch": kms / max(1, kn), "exchange": X, "kernel": g.update_kernel}
+        g.close()
+    out["config"] = {"workload": f"{w.name} at M = 1e-5 and 1e-3", "steps": args.mobility_steps}
     return out
 
 
@@ -422,18 +605,45 @@ def _packed(args, rank, w):
     return out
 
 
-def _serving(args, rank):
-    """Serving: Poisson arrivals of run requests (L log-uniform [50,1600],
-    S in {3,5}, budgets log-uniform 10^2-10^4 MCS, half stop at extinction),
-    continuous batching with admission by free device memory."""
+def _serve_shard(args, rank, world, dist, rate, n):
+    """One request stream at mean rate `rate` (requests/s over all ranks),
+    its requests dealt round-robin over the ranks; runs/s over all ranks and
+    latency percentiles over every request."""
+    import numpy as np
+    from paper_2508_16639_gb300 import replicas as R
     from paper_2508_16639_gb300 import workloads as W
     from paper_2508_16639_gb300.serve import serve
-    reqs = W.request_stream(n=args.serve_requests, seed=2 + rank, rate_per_s=args.serve_rate)
+    reqs = R.shard(W.request_stream(n=n, seed=2, rate_per_s=rate), rank, world)
+    if dist is not None:
+        dist.barrier()
     out = serve(reqs, arena_bytes=4 << 30, max_slots=4096, chunks_per_step=4)
+    lat = np.asarray(out.pop("latencies_s"))
+    secs = R.max_over_ranks(out["seconds"], dist, device="cuda")
+    if dist is not None:
+        parts = [None] * world
+        dist.all_gather_object(parts, lat.tolist())
+        lat = np.concatenate([np.asarray(p) for p in parts])
+    out.update(runs=int(lat.size), seconds=secs, runs_per_s=lat.size / secs,
+               p50_latency_s=float(np.percentile(lat, 50)), p99_latency_s=float(np.percentile(lat, 99)),
+               mean_latency_s=float(lat.mean()), offered_rate_per_s=rate)
+    return out
+
+
+def _serving(args, rank, world, dist):
+    """Serving: Poisson arrivals of run requests (L log-uniform [50,1600],
+    S in {3,5}, budgets log-uniform 10^2-10^4 MCS, half stop at extinction),
+    continuous batching with admission by free device memory; at the default
+    offered rate and at twice the rate the first run sustained (above
+    capacity: the queue grows, and runs/s is the capacity)."""
+    out = _serve_shard(args, rank, world, dist, args.serve_rate, args.serve_requests)
+    sat_rate = 2.0 * out["runs_per_s"]
+    out["saturated"] = _serve_shard(args, rank, world, dist, sat_rate, args.serve_saturated_requests)
     out["metric"] = "served runs/s and p50/p99 latency (arrival to result)"
-    out["config"] = {"workload": f"{len(reqs)} requests, Poisson rate {args.serve_rate}/s, "
-                                 "L log-uniform [50,1600], S in {3,5}, budget log-uniform [1e2,1e4] MCS, "
-                                 "50% stop at extinction", "arena_bytes": 4 << 30, "max_slots": 4096}
+    out["config"] = {"workload": f"{args.serve_requests} requests, Poisson rate {args.serve_rate}/s "
+                                 f"(saturated: {args.serve_saturated_requests} requests at twice the sustained "
+                                 "runs/s), L log-uniform [50,1600], S in {3,5}, budget log-uniform [1e2,1e4] MCS, "
+                                 "50% stop at extinction", "arena_bytes": 4 << 30, "max_slots": 4096,
+                     "ranks": world, "split": "round-robin over ranks (replicas.shard)"}
     return out
 
 
@@ -496,28 +706,46 @@ def main():
     attempts = K * mps * N * world
     value = attempts / (ms * 1e-3)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel.  Integer issue binds (the lattice is
+    # L2-resident): achieved = the 24 algorithmic integer instructions of an
+    # attempt x attempts per launch / the launch's event-timed duration;
+    # peak = the measured throughput of a probe running exactly that
+    # instruction mix (escg_diag_alg_throughput) per SM per clock x SMs x the
+    # maximum SM clock.  Bandwidth, as a second view: the algorithmic tile
+    # traffic (2 B per attempt) against the measured L2-resident copy
+    # bandwidth and the driver's measured HBM copy bandwidth.
+    alg_s, alg_sm_clk = E.alg_throughput()
     ops_s, ops_sm_clk = E.int_throughput()
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
-    lanes = 64 if ops_sm_clk < 96 else 128
     sm_max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = sms * lanes * sm_max_mhz * 1e6  # integer instructions/s
+    peak = sms * alg_sm_clk * sm_max_mhz * 1e6  # instructions of the step's mix per second
     per_launch_attempts = mps * N  # one persistent launch = one 10-MCS chunk
     avg_launch_s = (kernel_ms * 1e-3) / max(1, kernel_n)
     achieved = per_launch_attempts * ALG_INT_INSTR_PER_ATTEMPT / avg_launch_s
     traffic = (NCU_TRAFFIC["bytes_per_launch"]
                if (NCU_TRAFFIC["sources_sha1"] == _sources_sha1() and g.update_kernel == NCU_TRAFFIC["kernel"]
                    and w.L == NCU_TRAFFIC["L"] and mps == NCU_TRAFFIC["mcs_per_launch"]) else None)
+    tile_gbs = 2.0 * per_launch_attempts / avg_launch_s / 1e9
+    l2_peak = E.l2_copy_gbs(N, 200)
+    hbm_peak, hbm_src = _hbm_peak()
     roofline = {"bound": "alu", "kernel": g.update_kernel,
                 "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tinstr/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "alg_int_instr_per_attempt": ALG_INT_INSTR_PER_ATTEMPT,
                 "attempts_per_launch": per_launch_attempts,
                 "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": kernel_n,
-                "peak_derivation": f"{sms} SMs x {lanes} int32 lanes x {sm_max_mhz:.0f} MHz",
-                "probe_int_instr_per_s": ops_s, "probe_int_instr_per_sm_clk": ops_sm_clk,
-                "l2_lattice_gbs": 2.0 * per_launch_attempts / avg_launch_s / 1e9}
+                "peak_derivation": f"{sms} SMs x {alg_sm_clk:.1f} instructions of the step's mix per SM per clock "
+                                   f"(measured probe) x {sm_max_mhz:.0f} MHz",
+                "probe_alg_instr_per_s": alg_s, "probe_alg_instr_per_sm_clk": alg_sm_clk,
+                "probe_philox_pair_instr_per_sm_clk": ops_sm_clk,
+                "issue_ceiling": {"peak": sms * 128 * sm_max_mhz * 1e6 / 1e12, "unit": "Tinstr/s",
+                                  "frac_alg": achieved / (sms * 128 * sm_max_mhz * 1e6),
+                                  "note": "4 schedulers x 32 lanes per SM per clock; algorithmic instructions"},
+                "l2": {"achieved_gbs": tile_gbs, "peak_gbs": l2_peak, "frac": tile_gbs / l2_peak,
+                       "peak_source": f"measured: copy between two L2-resident {N / 1e6:.2f} MB buffers"},
+                "hbm": {"achieved_gbs": tile_gbs, "peak_gbs": hbm_peak, "frac": tile_gbs / hbm_peak,
+                        "peak_source": hbm_src}}
 
     e2e = None
     if not args.no_e2e:
@@ -564,15 +792,9 @@ def main():
                "sync": {"value": K * mps * N * world / el_sync, "ms_per_step": 1e3 * el_sync / K,
                         "api": "escg_step_host on one handle (restore + run + snapshot + counts)"}}
 
-    ensemble = None
-    if not args.no_ensemble:
-        ensemble = _ensemble(args, rank)
-    serving = None
-    if not args.no_serving:
-        serving = _serving(args, rank)
-    park = None
-    if not args.no_park:
-        park = _park(args, rank)
+    mobility = None
+    if not args.no_mobility:
+        mobility = _mobility_points(args, rank, w)
     packed = None
     if not args.no_packed:
         packed = _packed(args, rank, w)
@@ -582,24 +804,40 @@ def main():
     sizes = None
     if not args.no_sizes:
         sizes = _sizes(args, rank, w)
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = _ensemble(args, rank, world, dist)
+    serving = None
+    if not args.no_serving:
+        serving = _serving(args, rank, world, dist)
+    park = None
+    if not args.no_park:
+        park = _park(args, rank, world, dist)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, nmcs, el = _cpu_oracle_rate(w, args.cpu_seconds)
+        rs_rate, rs_mcs, rs_el = _cpu_rs_rate(w, args.cpu_rs_seconds)
+        model, ncpu = _cpu_info()
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"schedule-v1 replay oracle, first {nmcs} MCS of the L={w.L} lattice "
-                         f"({el:.1f} s, single thread)"}
+                         f"({el:.1f} s, single thread)",
+               "cpu_model": model, "nproc": ncpu,
+               "random_sequential": {"value": rs_rate, "unit": UNIT, "cores": 1,
+                                     "sample": f"random-sequential oracle (Alg. 3 + Alg. 4), first {rs_mcs} MCS "
+                                               f"of the same lattice ({rs_el:.1f} s, single thread)"}}
 
     if rank == 0:
+        # the sections with their own metrics last (ensemble, serving, park)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": _config(w, mps), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks,
-                "ensemble": ensemble, "serving": serving, "park": park, "variants": variants, "packed": packed,
-                "sizes": sizes,
                 "context": {"paper_cuda_ms_L3200_site_updates_per_s": 2.45e8,
-                            "paper_hardware": "RTX A2000 (not a target)"}}
+                            "paper_hardware": "RTX A2000 (not a target)"},
+                "mobility": mobility, "variants": variants, "packed": packed, "sizes": sizes,
+                "ensemble": ensemble, "serving": serving, "park": park}
         print(json.dumps(line), flush=True)
     g.close()
     if dist is not None:

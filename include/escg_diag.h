@@ -24,6 +24,24 @@ extern "C" {
  * Allocates and frees a small device buffer; synchronises. */
 int escg_diag_int_throughput(double* ops_per_s, double* ops_per_sm_clk);
 
+/* The same kind of probe for the instruction mix of one elementary step:
+ * 24 integer instructions per step (a quarter of a Philox4x32-10 call --
+ * 5 wide multiplies and 5 three-input XORs -- and the cell and neighbour
+ * offsets, action select, table index and unpacking: 2 byte permutes,
+ * 4 shifts, 3 adds, 2 compares, 1 select, 1 multiply-add, 1 and).
+ * *alg_per_s: instructions of that mix per second (the denominator of the
+ * Monte Carlo kernels' integer roofline, which counts the same 24 per
+ * attempt); *alg_per_sm_clk (may be NULL) per SM per SM clock.  Allocates
+ * and frees a small device buffer; synchronises. */
+int escg_diag_alg_throughput(double* alg_per_s, double* alg_per_sm_clk);
+
+/* Device-to-device copy bandwidth between two buffers of `bytes` each that
+ * stay in L2 (16-byte vectors, loads through L2 as the Monte Carlo kernels'
+ * tile loads): one launch copying the buffer reps times, after a warm-up
+ * launch of three copies; *gbs = bytes read + bytes written per second /
+ * 1e9.  Allocates and frees the two buffers; synchronises. */
+int escg_diag_l2_copy(size_t bytes, int reps, double* gbs);
+
 /* Test hook: the next persistent launches of h never publish the epoch of
  * coarse block `block` (0 <= block < P*P), so its neighbours' waits run out
  * after `spin_limit` polls; escg_sync then returns ESCG_ETIMEOUT and the

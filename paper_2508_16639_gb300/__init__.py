@@ -46,6 +46,22 @@ def int_throughput():
     return float(a.value), float(b.value)
 
 
+def alg_throughput():
+    """Measured throughput of the elementary step's integer-instruction mix
+    (24 per step): (instructions/s, instructions per SM per clock)."""
+    a, b = C.c_double(), C.c_double()
+    check(load().escg_diag_alg_throughput(C.byref(a), C.byref(b)))
+    return float(a.value), float(b.value)
+
+
+def l2_copy_gbs(nbytes: int, reps: int = 200) -> float:
+    """Device copy bandwidth (read + write GB/s) between two L2-resident
+    buffers of nbytes each."""
+    g = C.c_double()
+    check(load().escg_diag_l2_copy(nbytes, reps, C.byref(g)))
+    return float(g.value)
+
+
 def lattice_pitch(L: int, bits_per_site: int = 8) -> int:
     return int(load().escg_lattice_pitch_ex(L, bits_per_site))
 

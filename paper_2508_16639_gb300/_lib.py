@@ -109,6 +109,8 @@ SIGNATURES = {
     "escg_debug_stall_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint32]),
     "escg_coarse_blocks": (C.c_int32, [C.c_void_p]),
     "escg_update_kernel": (C.c_char_p, [C.c_void_p]),
+    "escg_diag_alg_throughput": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "escg_diag_l2_copy": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_double)]),
 }
 
 _lib = None

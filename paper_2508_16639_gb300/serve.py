@@ -58,6 +58,6 @@ def serve(requests, server: Server | None = None, time_scale: float = 1.0, **ser
     lat = np.array([latency[i] for i in range(n)])
     return {"runs": n, "seconds": total, "runs_per_s": n / total, "steps": steps,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "mean_latency_s": float(lat.mean()),
+            "mean_latency_s": float(lat.mean()), "latencies_s": lat.tolist(),
             "site_updates": float(sum(done_mcs[i] * requests[i]["L"] ** 2 for i in range(n))),
             "threads": srv.threads}

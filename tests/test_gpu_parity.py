@@ -302,6 +302,15 @@ def test_kernel_timing_counts_launches():
     assert E.int_throughput()[0] > 1e12
 
 
+def test_roofline_probes():
+    """The denominators of the bench's rooflines: the step's instruction mix
+    runs at a positive rate of at most the 128-per-SM-per-clock issue ceiling,
+    and an L2-resident copy moves more than a few TB/s."""
+    alg, per_sm_clk = E.alg_throughput()
+    assert alg > 1e12 and 0 < per_sm_clk <= 128.5
+    assert E.l2_copy_gbs(8 << 20, 20) > 1000.0
+
+
 def test_restore_rejects_values_outside_states():
     L, S = 40, 3
     g = E.Lattice(L, S, E.circulant(S, [1]), (1.0, 1.0, 1.0), 3, p_empty=0.25)

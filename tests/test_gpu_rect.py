@@ -100,16 +100,16 @@ def test_rect_device_buffer_and_bad_height():
 
 
 def test_rect_large_properties():
-    """3200 x 1600 (a strip of the 3200 x 3200 benchmark lattice): the flag
-    kernel matches the oracle's replay after the first MCS, it and one
-    launch per coarse phase agree bit for bit after 20 MCS, and the logged
-    counts sum to N = L*H."""
+    """3200 x 1600 (a strip of the 3200 x 3200 benchmark lattice): the default
+    kernel (generic block owners: 1600 is not a multiple of 128) matches the
+    oracle's replay after the first MCS, it and one launch per coarse phase
+    agree bit for bit after 20 MCS, and the logged counts sum to N = L*H."""
     S, L, H, seed = 3, 3200, 1600, 2508
     D = O.circulant(S, (1,))
     X = 2.0 * 1e-4 * L * H
     a = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.25, persistent=1, H=H)
     b = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.25, persistent=0, H=H)
-    assert a.update_kernel == "persistent_kernel"
+    assert a.update_kernel == "persistent_gown_kernel"
     a.run(1)
     o, _ = O.replay_run(O.init(L, S, 0.25, seed, H=H), D, 1.0, 1.0, X, seed, 1)
     assert np.array_equal(a.snapshot(), o)
