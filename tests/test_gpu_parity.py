@@ -133,12 +133,14 @@ def test_cfg2_rpsls_L800_every_mcs():
 @pytest.mark.parametrize("M", [1e-5, 1e-4, 1e-3])
 def test_cfg3_L3200_full_size(M):
     """Full-size lattice in the benchmark's launch configuration (persistent
-    kernel, chunks ending at log points every 10 MCS)."""
+    kernel, chunks ending at log points every 10 MCS), checked at MCS 1, 2,
+    10 and 100 (M = 1e-4; about 35 s of replay oracle) and 1, 3, 10 (the two
+    other mobilities)."""
     w = W.CFG3[M]
     X = _x(w.L, w.mobility, w.exchange)
     g, o, D = _pair(w.L, w.S, w.K, w.p_empty, w.interact, w.reproduce, X, w.seed,
                     log_every=w.log_every)
-    checkpoints = [1, 2, 10] if M == 1e-4 else [1, 3]
+    checkpoints = [1, 2, 10, 100] if M == 1e-4 else [1, 3, 10]
     m = 0
     for c in checkpoints:
         g.run(c - m)
@@ -146,8 +148,8 @@ def test_cfg3_L3200_full_size(M):
         m = c
         assert np.array_equal(g.snapshot(), o), (M, c)
     ms, log = g.counts_log()
-    assert list(ms) == [k for k in (0, 10) if k <= m]
-    assert np.array_equal(log[-1] if m == 10 else O.counts(o, w.S), O.counts(o, w.S))
+    assert list(ms) == list(range(0, m + 1, 10))
+    assert np.array_equal(log[-1], O.counts(o, w.S))
 
 
 def test_counts_log_matches_oracle():

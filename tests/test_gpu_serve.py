@@ -62,6 +62,41 @@ def test_served_runs_match_single_runs(arena_mb, max_slots):
     assert srv.stats() == (0, 0, 0)
 
 
+def test_served_runs_match_the_replay_oracle():
+    """A served mix -- small runs and three at L = 1000 .. 1600 from the top of
+    the serving workload's range -- against the schedule-v1 replay oracle run
+    by itself: MCS reached (stasis or budget), counts and lattice."""
+    import oracle as O
+    small = _reqs(10, seed=21, L_range=(50, 300), budget=(20, 120))
+    big = _reqs(3, seed=22, L_range=(1000, 1600), budget=(20, 30))
+    reqs = small[:5] + big + small[5:]
+    srv = E.Server(arena_bytes=256 << 20, max_slots=16, keep_lattice=True, chunks_per_step=2)
+    ids = {}
+    for k in range(0, len(reqs), 4):
+        for r in reqs[k:k + 4]:
+            ids[srv.submit(request_spec(r))] = r
+        srv.step()
+    done = set()
+    for _ in range(10000):
+        done.update(srv.poll())
+        if len(done) == len(reqs):
+            break
+        srv.step()
+    assert len(done) == len(reqs)
+    assert max(r["L"] for r in reqs) >= 1000
+    for rid, r in ids.items():
+        sp = request_spec(r)
+        D = O.circulant(sp["S"], r["K"])
+        I, P, X = sp["rates"]
+        lat, log, mend = O.run_observed(O.init(sp["L"], sp["S"], sp["p_empty"], sp["seed"]), D, I, P, X,
+                                        sp["seed"], sp["max_mcs"], log_every=10,
+                                        stop_at_extinction=sp["stop_at_extinction"])
+        mcs, ext, cnt, glat = srv.result(rid, lattice=True)
+        assert mcs == mend, rid
+        assert np.array_equal(glat, lat), rid
+        assert np.array_equal(cnt[:sp["S"] + 1], log[-1]), rid
+
+
 def test_serve_loop_reports_latency():
     reqs = _reqs(40, seed=9, L_range=(50, 200), budget=(20, 100))
     out = serve(reqs, time_scale=0.05, arena_bytes=64 << 20, max_slots=32, chunks_per_step=2)
