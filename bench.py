@@ -99,6 +99,9 @@ def _parse():
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--L", type=int, default=3200, help="lattice side (3200 is the benchmark)")
+    ap.add_argument("--workload", choices=["rps", "rpsls-L800"], default="rps",
+                    help="rps: the benchmark's RPS lattice (side --L, mobility --mobility); rpsls-L800: the RPSLS "
+                         "workload (L = 800, p_empty 0.2, M = 1e-4) for profiling its kernel")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-replicas", type=int, default=1024)
     ap.add_argument("--ensemble-baseline-sample", type=int, default=16)
@@ -666,7 +669,11 @@ def main():
     __graft_entry__.build()
     import paper_2508_16639_gb300 as E
 
-    w = _workload(args.mobility, args.L)
+    if args.workload == "rpsls-L800":
+        from paper_2508_16639_gb300 import workloads as W
+        w = W.CFG2
+    else:
+        w = _workload(args.mobility, args.L)
     N = w.L * w.L
     X = E.exchange_from_mobility(w.mobility, N)
     stream = torch.cuda.Stream()
