@@ -532,22 +532,24 @@ def _mobility_points(args, rank, w):
 
 
 def _sizes(args, rank, w):
-    """Latency-bound sizes: the benchmark's workload (RPS with empty sites,
-    M = 1e-4) on smaller square lattices, each with the kernel persistent = 1
-    picks for it (the boundary mailbox at L = 128, block owners from 384 to
-    2688, the flag kernel beyond): device time per 10-MCS step, L2 flushed
-    before each step."""
+    """Latency-bound and mid sizes: the benchmark's workload (RPS with empty
+    sites, M = 1e-4) on L x L lattices from 128 to 3200 (uniform and generic
+    partitions), each timed with every fixed launch mode (flag 3, TMA 2,
+    block owners 5, mailbox 6), the default size rule (1) and the
+    autotuner's choice (1 with autotune): device time per 10-MCS step, L2
+    flushed before each step.  tuned_vs_best: the tuned time over the best
+    fixed mode's."""
     import torch
     import paper_2508_16639_gb300 as E
     from paper_2508_16639_gb300 import replicas as R
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    out = {}
-    for Lc in (128, 512, 1024, 1536, 2048, 2560):
+
+    def timed(Lc, **kw):
         N = Lc * Lc
         X = E.exchange_from_mobility(w.mobility, N)
         stream = torch.cuda.Stream()
         g = E.Lattice(Lc, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X), R.replica_seed(w.seed, rank),
-                      p_empty=w.p_empty, log_every=w.log_every, stream=stream)
+                      p_empty=w.p_empty, log_every=w.log_every, stream=stream, **kw)
         for _ in range(3):
             g.run(10)
         g.sync()
@@ -561,11 +563,26 @@ def _sizes(args, rank, w):
             b.record(stream)
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
-        out[f"L{Lc}"] = {"site_updates_per_s": 10 * N / (ms * 1e-3), "us_per_mcs": ms * 100.0,
-                         "kernel": g.update_kernel}
+        res = {"us_per_mcs": ms * 100.0, "site_updates_per_s": 10 * N / (ms * 1e-3), "kernel": g.update_kernel}
+        if kw.get("autotune"):
+            mode, ctas, _, n = g.autotune_result
+            res.update(mode=mode, ctas_per_sm=ctas, configurations_timed=n)
         g.close()
-    out["config"] = {"workload": f"{w.name} workload on L x L lattices, default kernel choice",
-                     "steps": args.size_steps}
+        return res
+
+    out = {}
+    for Lc in (128, 512, 800, 1024, 1536, 2048, 2200, 2560, 3200):
+        fixed = {f"mode{m}": timed(Lc, persistent=m) for m in (3, 2, 5, 6)}
+        best = min(v["us_per_mcs"] for v in fixed.values())
+        default = timed(Lc)
+        tuned = timed(Lc, autotune=True)
+        out[f"L{Lc}"] = {"default": default, "tuned": tuned, "fixed": fixed,
+                         "tuned_vs_best": tuned["us_per_mcs"] / best,
+                         "default_vs_best": default["us_per_mcs"] / best,
+                         # the headline's own fields: the default choice
+                         "us_per_mcs": default["us_per_mcs"], "kernel": default["kernel"]}
+    out["config"] = {"workload": f"{w.name} workload on L x L lattices; modes that a lattice cannot run fall back "
+                                 "to the flag kernel", "steps": args.size_steps}
     return out
 
 

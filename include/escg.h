@@ -156,6 +156,17 @@ typedef struct {
                                     use).  Results are identical for all three;
                                     the device buffer is H rows of
                                     escg_lattice_pitch_ex(L, b) bytes.        */
+    int32_t autotune;            /* 1 (with persistent = 1): on the first
+                                    handle of its (device, L, H, S,
+                                    bits_per_site, neighbourhood, boundary),
+                                    time every distinct launch mode and CTA
+                                    count on a copy of the initial lattice
+                                    (10 MCS of warm-up, 20 timed) and keep the
+                                    fastest, cached for the process; later
+                                    handles of that key take the cached
+                                    choice.  Physical mapping only: results
+                                    are those of every mode.  0: the size rule
+                                    of persistent = 1 (default).             */
 } escg_options;
 
 typedef struct escg escg_t;
@@ -314,8 +325,11 @@ int32_t escg_batch_active(escg_batch_t* b);
 /* Copies replica i's lattice (L*L bytes) to host memory.  Synchronises. */
 int escg_batch_snapshot(escg_batch_t* b, int32_t i, uint8_t* host_out);
 
-/* CTA size in use (after autotuning) and kernel launches so far. */
+/* CTA size in use (after autotuning: the first chunks time the chunk kernel
+ * at 64, 128 and 256 threads, TMA-staged and plain, and keep the fastest),
+ * whether the TMA-staged chunk kernel is in use, and kernel launches so far. */
 int32_t escg_batch_threads(escg_batch_t* b);
+int32_t escg_batch_uses_tma(escg_batch_t* b);
 uint64_t escg_batch_launch_count(escg_batch_t* b);
 
 void escg_batch_destroy(escg_batch_t* b);
@@ -371,6 +385,7 @@ int escg_server_result(escg_server_t* s, int64_t id, uint64_t* mcs_out, int32_t*
 /* Runs resident, runs queued, arena bytes in use. */
 int escg_server_stats(escg_server_t* s, int32_t* resident, int32_t* queued, uint64_t* bytes_in_use);
 int32_t escg_server_threads(escg_server_t* s);
+int32_t escg_server_uses_tma(escg_server_t* s);
 uint64_t escg_server_launch_count(escg_server_t* s);
 void escg_server_destroy(escg_server_t* s);
 

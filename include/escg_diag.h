@@ -49,6 +49,14 @@ int escg_diag_l2_copy(size_t bytes, int reps, double* gbs);
  * spin_limit 0 restores the default limit. */
 int escg_debug_stall_block(escg_t* h, int32_t block, uint32_t spin_limit);
 
+/* The autotuner's choice for a handle created with escg_options.autotune:
+ * the launch mode (escg_options.persistent) and CTAs per SM it runs with,
+ * the winner's device time per MCS, and how many distinct configurations
+ * were timed (0: the choice came from the process's cache).  ESCG_ESTATE for
+ * a handle created without autotune. */
+int escg_autotune_result(escg_t* h, int32_t* persistent, int32_t* ctas_per_sm, double* ms_per_mcs,
+                         int32_t* candidates);
+
 /* Coarse blocks per axis (P) of the handle's schedule-v1 partition. */
 int32_t escg_coarse_blocks(escg_t* h);
 

@@ -83,8 +83,11 @@ class Lattice:
     warp, 6 with boundary records (mailbox), 4 the whole
     lattice resident in one CTA's shared memory (small lattices; larger ones
     run as 3), 5 one CTA per 2x2 group of blocks with its tiles resident
-    (L and H multiples of 128; others run as 3), 0 one
-    launch per coarse phase -- all bit-identical.  dominance_prob: optional S x S edge
+    (any partition of the von Neumann rule whose grid the device holds;
+    others run as 3), 0 one launch per coarse phase -- all bit-identical.
+    autotune: with persistent = 1, time the distinct launch modes and CTA
+    counts on the first handle of its size and rule and keep the fastest
+    (cached for the process; see autotune_result).  dominance_prob: optional S x S edge
     probabilities (Park, Chen and Szolnoki's probabilistic dominance);
     neighbourhood 4 or 8 (Moore) and reflecting_boundary: the paper's rule
     variants.  H: rows (default L).  bits_per_site: device storage, 8 (one
@@ -94,7 +97,7 @@ class Lattice:
                  log_every: int = 10, stop_at_extinction: bool = False, persistent: int = 1,
                  stream=None, device_buffer=None, time_kernels: bool = False, ctas_per_sm: int = 0,
                  dominance_prob=None, neighbourhood: int = 4, reflecting_boundary: bool = False,
-                 H: int = None, bits_per_site: int = 8):
+                 H: int = None, bits_per_site: int = 8, autotune: bool = False):
         lib = load()
         self.L, self.S = int(L), int(S)
         self.H = self.L if H is None else int(H)
@@ -112,6 +115,7 @@ class Lattice:
         opt.reflecting_boundary = int(bool(reflecting_boundary))
         opt.height = self.H
         opt.bits_per_site = int(bits_per_site)
+        opt.autotune = int(bool(autotune))
         self.bits_per_site = int(bits_per_site)
         if dominance_prob is not None:
             Pd = np.ascontiguousarray(np.asarray(dominance_prob, dtype=np.float64).reshape(S, S))
@@ -219,6 +223,16 @@ class Lattice:
         ms, n = C.c_double(), C.c_uint64()
         check(load().escg_kernel_time(self._h, C.byref(ms), C.byref(n), int(bool(reset))))
         return float(ms.value), int(n.value)
+
+    @property
+    def autotune_result(self):
+        """(launch mode, CTAs per SM, ms per MCS, configurations timed) of a
+        handle created with autotune=True; 0 configurations timed means the
+        choice came from the process's cache."""
+        mode, ctas, n = C.c_int32(), C.c_int32(), C.c_int32()
+        ms = C.c_double()
+        check(load().escg_autotune_result(self._h, C.byref(mode), C.byref(ctas), C.byref(ms), C.byref(n)))
+        return int(mode.value), int(ctas.value), float(ms.value), int(n.value)
 
     def debug_stall_block(self, block: int, spin_limit: int = 0):
         """Test hook: never publish the epoch of one coarse block so that the
@@ -354,6 +368,10 @@ class Batch:
         return int(load().escg_batch_threads(self._h))
 
     @property
+    def uses_tma(self) -> bool:
+        return bool(load().escg_batch_uses_tma(self._h))
+
+    @property
     def launches(self) -> int:
         return int(load().escg_batch_launch_count(self._h))
 
@@ -436,6 +454,10 @@ class Server:
     @property
     def threads(self) -> int:
         return int(load().escg_server_threads(self._h))
+
+    @property
+    def uses_tma(self) -> bool:
+        return bool(load().escg_server_uses_tma(self._h))
 
     @property
     def launches(self) -> int:

@@ -26,7 +26,7 @@ class Options(C.Structure):
                 ("device_lattice", C.c_void_p), ("time_kernels", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("dominance_prob", C.POINTER(C.c_double)),
                 ("neighbourhood", C.c_int32), ("reflecting_boundary", C.c_int32),
-                ("height", C.c_int32), ("bits_per_site", C.c_int32)]
+                ("height", C.c_int32), ("bits_per_site", C.c_int32), ("autotune", C.c_int32)]
 
 
 class ReplicaSpec(C.Structure):
@@ -91,6 +91,7 @@ SIGNATURES = {
     "escg_batch_active": (C.c_int32, [C.c_void_p]),
     "escg_batch_snapshot": (C.c_int, [C.c_void_p, C.c_int32, _u8p]),
     "escg_batch_threads": (C.c_int32, [C.c_void_p]),
+    "escg_batch_uses_tma": (C.c_int32, [C.c_void_p]),
     "escg_batch_launch_count": (C.c_uint64, [C.c_void_p]),
     "escg_batch_destroy": (None, [C.c_void_p]),
     "escg_server_default_options": (None, [C.POINTER(ServerOptions)]),
@@ -102,6 +103,7 @@ SIGNATURES = {
     "escg_server_stats": (C.c_int, [C.c_void_p, _i32p, _i32p, _u64p]),
     "escg_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
     "escg_server_threads": (C.c_int32, [C.c_void_p]),
+    "escg_server_uses_tma": (C.c_int32, [C.c_void_p]),
     "escg_server_launch_count": (C.c_uint64, [C.c_void_p]),
     "escg_server_destroy": (None, [C.c_void_p]),
     # include/escg_diag.h
@@ -110,6 +112,8 @@ SIGNATURES = {
     "escg_coarse_blocks": (C.c_int32, [C.c_void_p]),
     "escg_update_kernel": (C.c_char_p, [C.c_void_p]),
     "escg_diag_alg_throughput": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "escg_autotune_result": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
     "escg_diag_l2_copy": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_double)]),
 }
 

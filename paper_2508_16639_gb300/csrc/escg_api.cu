@@ -8,7 +8,9 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -248,6 +250,9 @@ struct escg {
   int own_dyn = 0;               // its shared-memory padding
   int own_threads = 0;           // and CTA size
   bool use_gown = false;         // block owners on a generic partition
+  int tuned_mode = 0, tuned_ctas = 0;   // autotuner's choice (launch mode, CTAs per SM)
+  double tuned_ms_per_mcs = 0.0;
+  int tuned_candidates = 0;      // configurations timed (0: taken from the cache)
   GownConfig gown{};
   size_t ob_words = 0;           // boundary-record words allocated (all blocks)
   CUtensorMap tmap{};
@@ -410,6 +415,110 @@ void free_handle(escg* h) {
   delete h;
 }
 
+// Boundary records of at least `words` words (zeroed by the next reset).
+int ensure_records(escg* h, size_t words) {
+  if (h->ob_words >= words) return ESCG_OK;
+  cudaFree(h->d_ob);
+  h->d_ob = nullptr;
+  h->ob_words = 0;
+  if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
+    set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
+    return ESCG_ENOMEM;
+  }
+  h->ob_words = words;
+  return ESCG_OK;
+}
+
+// Picks the lattice-update kernel for launch mode `persistent` (escg_options)
+// and the CTAs per SM of the ticketed kernels (0: as many as fit), from the
+// partition, the storage and the device's occupancy.  Physical mapping only:
+// every choice gives the same lattices.
+int select_kernel(escg* h, int persistent, int ctas_per_sm) {
+  LatticeDesc& d = h->desc;
+  const Partition& p = h->part;
+  const Partition& py = h->part_y;
+  const int L = h->L, H = h->H;
+  h->use_tma = h->use_ll = h->use_own = h->use_gown = h->use_resident = false;
+  h->own_dyn = h->own_threads = 0;
+  h->gown = GownConfig{};
+  h->grid = persistent_grid(h->device, d.uniform64 != 0);
+  // the TMA and mailbox kernels are written for square lattices of one byte
+  // per site; the flag kernel takes rectangular and packed ones in both
+  // geometries
+  const bool square = (H == L) && h->bits == 8;
+  if (d.uniform64 && square && persistent == 2) {
+    if (!make_tensor_map(&h->tmap, h->lattice, L, h->pitch)) {
+      set_err("cuTensorMapEncodeTiled failed for L=%d", L);
+      return ESCG_ECUDA;
+    }
+    h->use_tma = true;
+    h->grid = persistent_tma_grid(h->device);
+  }
+  // The mailbox kernel shortens every hop of the colour-phase chain but
+  // binds each CTA's next item one visit early.  Measured (GB300, 608 CTAs):
+  // faster than the flag kernel while a coarse phase has at most half as
+  // many blocks as there are CTAs (L <= 2048: 10-25 %), slower with 576 or
+  // 625 blocks per phase (L = 3072, 3200: 3-5 %), where the flag kernel keeps
+  // items unbound until a CTA is free.  It runs on request (6) and by default
+  // where the block owners below cannot.
+  if (d.uniform64 && square && (persistent == 1 || persistent == 6) &&
+      (persistent == 6 || 2 * (p.P * p.P / 4) <= persistent_ll_grid(h->device))) {
+    if (ensure_records(h, (size_t)p.P * p.P * kRecordWords) != ESCG_OK) return ESCG_ENOMEM;
+    h->use_ll = true;
+    h->grid = persistent_ll_grid(h->device);
+  }
+  // Block owners: on request (5), and by default (1) from 3 x 3 groups of
+  // blocks while the grid needs at most 3 CTAs per SM -- measured (GB300, µs
+  // per MCS, mailbox or flag kernel vs owners): L = 384 15.4 vs 14.1, 512
+  // 15.9 vs 14.4, 1024 18.2 vs 13.0, 1536 20.0 vs 12.4, 2048 19.7 vs 15.1,
+  // 2560 23.3 vs 19.5; tied at L = 256 and at 4 per SM (3072); slower at
+  // L = 128 (13.3 vs 14.0) and from 5 per SM (3200: 25.5 vs 29.2), where every
+  // CTA of an SM is in the same colour phase at once and the flag kernel's
+  // free binding keeps the SMs busier.  Needs the device to hold one CTA per
+  // 2x2 group of blocks at once.
+  if (d.uniform64 && (persistent == 5 || (persistent == 1 && (p.P / 2) * (py.P / 2) >= 9))) {
+    int dyn = 0, nt = 0, per_sm = 0;
+    if (persistent_own_config(d, h->device, &dyn, &nt, &per_sm) > 0 && (persistent == 5 || per_sm <= 3)) {
+      if (ensure_records(h, (size_t)p.P * py.P * kRecordWords) != ESCG_OK) return ESCG_ENOMEM;
+      h->use_own = true;
+      h->own_dyn = dyn;
+      h->own_threads = nt;
+      h->use_ll = false;
+    }
+  }
+  // Block owners on a generic partition (von Neumann rule, periodic or
+  // reflecting, any bits per site): on request (5), and by default (1) from
+  // 2 x 2 groups of blocks while the grid needs at most kGownDefaultPerSM
+  // CTAs per SM.  Needs the device to hold one CTA per group at once.
+  if (!d.uniform64 && d.nbh == 4 &&
+      (persistent == 5 || (persistent == 1 && (p.P / 2) * (py.P / 2) >= 2))) {
+    GownConfig cfg{};
+    if (persistent_gown_config(d, h->device, &cfg) > 0 &&
+        (persistent == 5 || cfg.ctas_per_sm <= kGownDefaultPerSM)) {
+      if (ensure_records(h, (size_t)p.P * py.P * kGRecordWords) != ESCG_OK) return ESCG_ENOMEM;
+      h->use_gown = true;
+      h->gown = cfg;
+    }
+  }
+  // Whole-lattice residency: on request (4), and by default (1) for a generic
+  // partition with 2 x 2 coarse blocks (L, H < 192 and not 128), where it was
+  // measured 1.4-2.2x faster than the flag kernel's dependency chain of
+  // generic visits (tied at L = 200, slower beyond; the mailbox kernel is
+  // faster for the uniform L = 128).
+  if ((persistent == 4 || (persistent == 1 && !d.uniform64 && p.P == 2 && py.P == 2)) &&
+      resident_fits(d, h->device)) {
+    h->use_resident = true;
+    h->use_gown = false;
+  }
+  if (ctas_per_sm > 0) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (sms * ctas_per_sm < h->grid) h->grid = sms * ctas_per_sm;
+  }
+
+  return ESCG_OK;
+}
+
 int check_inputs(int32_t L, int32_t S, const uint8_t* D, const escg_rates* rates) {
   if (L < 8 || L > 16384) {
     set_err("L=%d out of range [8, 16384]", L);
@@ -494,6 +603,10 @@ int escg_circulant(int32_t S, const int32_t* K, int32_t nK, uint8_t* D) {
   return ESCG_OK;
 }
 
+}  // extern "C"
+static int autotune(escg* h);
+extern "C" {
+
 escg_t* escg_create(int32_t L, int32_t S, const uint8_t* digraph, const escg_rates* rates, uint64_t seed) {
   escg_options o;
   escg_default_options(&o);
@@ -540,6 +653,10 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   }
   if (reinterpret_cast<uintptr_t>(o.device_lattice) % 16 != 0) {
     set_err("device_lattice must be 16-byte aligned (rows are read as 16-byte vectors)");
+    return nullptr;
+  }
+  if (o.autotune != 0 && o.autotune != 1) {
+    set_err("autotune must be 0 or 1 (got %d)", o.autotune);
     return nullptr;
   }
   if (o.persistent < 0 || o.persistent > 6) {
@@ -686,97 +803,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   d.reflect = o.reflecting_boundary;
   // the uniform kernels implement the von Neumann, periodic rule only
   d.uniform64 = (uni && h->pitch % 16 == 0 && d.nbh == 4 && !d.reflect) ? 1 : 0;
-  h->grid = persistent_grid(h->device, d.uniform64 != 0);
-  // the TMA and mailbox kernels are written for square lattices of one byte
-  // per site; the flag kernel takes rectangular and packed ones in both
-  // geometries
-  const bool square = (H == L) && h->bits == 8;
-  if (d.uniform64 && square && o.persistent == 2) {
-    if (!make_tensor_map(&h->tmap, h->lattice, L, h->pitch)) {
-      set_err("cuTensorMapEncodeTiled failed for L=%d", L);
-      return fail(ESCG_ECUDA);
-    }
-    h->use_tma = true;
-    h->grid = persistent_tma_grid(h->device);
-  }
-  // The mailbox kernel shortens every hop of the colour-phase chain but
-  // binds each CTA's next item one visit early.  Measured (GB300, 608 CTAs):
-  // faster than the flag kernel while a coarse phase has at most half as
-  // many blocks as there are CTAs (L <= 2048: 10-25 %), slower with 576 or
-  // 625 blocks per phase (L = 3072, 3200: 3-5 %), where the flag kernel keeps
-  // items unbound until a CTA is free.  It runs on request (6) and by default
-  // where the block owners below cannot.
-  if (d.uniform64 && square && (o.persistent == 1 || o.persistent == 6) &&
-      (o.persistent == 6 || 2 * (p.P * p.P / 4) <= persistent_ll_grid(h->device))) {
-    const size_t words = (size_t)p.P * p.P * kRecordWords;
-    if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
-      set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
-      return fail(ESCG_ENOMEM);
-    }
-    h->ob_words = words;
-    h->use_ll = true;
-    h->grid = persistent_ll_grid(h->device);
-  }
-  // Block owners: on request (5), and by default (1) from 3 x 3 groups of
-  // blocks while the grid needs at most 3 CTAs per SM -- measured (GB300, µs
-  // per MCS, mailbox or flag kernel vs owners): L = 384 15.4 vs 14.1, 512
-  // 15.9 vs 14.4, 1024 18.2 vs 13.0, 1536 20.0 vs 12.4, 2048 19.7 vs 15.1,
-  // 2560 23.3 vs 19.5; tied at L = 256 and at 4 per SM (3072); slower at
-  // L = 128 (13.3 vs 14.0) and from 5 per SM (3200: 25.5 vs 29.2), where every
-  // CTA of an SM is in the same colour phase at once and the flag kernel's
-  // free binding keeps the SMs busier.  Needs the device to hold one CTA per
-  // 2x2 group of blocks at once.
-  if (d.uniform64 && (o.persistent == 5 || (o.persistent == 1 && (p.P / 2) * (py.P / 2) >= 9))) {
-    int dyn = 0, nt = 0, per_sm = 0;
-    if (persistent_own_config(d, h->device, &dyn, &nt, &per_sm) > 0 && (o.persistent == 5 || per_sm <= 3)) {
-      if (!h->d_ob) {
-        const size_t words = (size_t)p.P * py.P * kRecordWords;
-        if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
-          set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
-          return fail(ESCG_ENOMEM);
-        }
-        h->ob_words = words;
-      }
-      h->use_own = true;
-      h->own_dyn = dyn;
-      h->own_threads = nt;
-      h->use_ll = false;
-    }
-  }
-  // Block owners on a generic partition (von Neumann rule, periodic or
-  // reflecting, any bits per site): on request (5), and by default (1) from
-  // 2 x 2 groups of blocks while the grid needs at most kGownDefaultPerSM
-  // CTAs per SM.  Needs the device to hold one CTA per group at once.
-  if (!d.uniform64 && d.nbh == 4 &&
-      (o.persistent == 5 || (o.persistent == 1 && (p.P / 2) * (py.P / 2) >= 2))) {
-    GownConfig cfg{};
-    if (persistent_gown_config(d, h->device, &cfg) > 0 &&
-        (o.persistent == 5 || cfg.ctas_per_sm <= kGownDefaultPerSM)) {
-      const size_t words = (size_t)p.P * py.P * kGRecordWords;
-      if (cudaMalloc(&h->d_ob, words * sizeof(unsigned long long)) != cudaSuccess) {
-        set_err("cudaMalloc of %zu boundary-record bytes failed", words * sizeof(unsigned long long));
-        return fail(ESCG_ENOMEM);
-      }
-      h->ob_words = words;
-      h->use_gown = true;
-      h->gown = cfg;
-    }
-  }
-  // Whole-lattice residency: on request (4), and by default (1) for a generic
-  // partition with 2 x 2 coarse blocks (L, H < 192 and not 128), where it was
-  // measured 1.4-2.2x faster than the flag kernel's dependency chain of
-  // generic visits (tied at L = 200, slower beyond; the mailbox kernel is
-  // faster for the uniform L = 128).
-  if ((o.persistent == 4 || (o.persistent == 1 && !d.uniform64 && p.P == 2 && py.P == 2)) &&
-      resident_fits(d, h->device)) {
-    h->use_resident = true;
-    h->use_gown = false;
-  }
-  if (o.ctas_per_sm > 0) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    if (sms * o.ctas_per_sm < h->grid) h->grid = sms * o.ctas_per_sm;
-  }
+  if (select_kernel(h, o.persistent, o.ctas_per_sm) != ESCG_OK) return fail(ESCG_ENOMEM);
 
   if (launch_init(d, h->T_empty, h->stream) != cudaSuccess) {
     set_err("init kernel launch failed");
@@ -788,6 +815,7 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
     set_err("initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(ESCG_ECUDA);
   }
+  if (o.autotune && o.persistent == 1 && autotune(h) != ESCG_OK) return fail(ESCG_ECUDA);
   return h;
 }
 
@@ -1139,3 +1167,146 @@ const char* escg_update_kernel(escg_t* h) {
 void escg_destroy(escg_t* h) { free_handle(h); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner.  Every launch mode and CTA count gives the same lattice, so the
+// fastest is a measured, result-neutral choice.  On the first handle of a
+// (device, L, H, S, bits per site, rule) the candidates are timed on a
+// scratch copy of the initial lattice -- 10 MCS to warm up, then 20 MCS
+// between two CUDA events -- and the winner is cached for the process; the
+// handle then starts from its initial lattice at MCS 0 as if just created.
+namespace {
+
+struct TuneKey {
+  int dev, L, H, S, bits, nbh, reflect;
+  bool operator<(const TuneKey& o) const {
+    const int a[7] = {dev, L, H, S, bits, nbh, reflect}, b[7] = {o.dev, o.L, o.H, o.S, o.bits, o.nbh, o.reflect};
+    for (int i = 0; i < 7; ++i)
+      if (a[i] != b[i]) return a[i] < b[i];
+    return false;
+  }
+};
+struct TuneVal {
+  int mode, ctas;
+  double ms_per_mcs;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+// What a selection runs, for dropping candidates that duplicate another.
+std::string kernel_signature(escg* h) {
+  char buf[128];
+  snprintf(buf, sizeof buf, "%s/%d/%d/%d", escg_update_kernel(h), h->grid, h->own_threads, h->gown.threads);
+  return buf;
+}
+
+// Device time of 20 MCS of the current selection from the scratch lattice
+// (after 10 MCS of warm-up), or a negative value if a wait timed out.
+int tune_time(escg* h, const uint8_t* scratch, size_t nbytes, double* ms) {
+  CUDA_TRY(cudaMemcpyAsync(h->lattice, scratch, nbytes, cudaMemcpyDeviceToDevice, h->stream));
+  int rc = reset_state(h, 0);
+  if (rc == ESCG_OK) rc = escg_run(h, 10);
+  if (rc != ESCG_OK) return rc;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  cudaEventRecord(e0, h->stream);
+  rc = escg_run(h, 20);
+  cudaEventRecord(e1, h->stream);
+  if (rc == ESCG_OK) rc = escg_sync(h);
+  float t = 0.f;
+  if (rc == ESCG_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = ESCG_ECUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = rc == ESCG_OK ? (double)t : -1.0;
+  return rc == ESCG_ETIMEOUT ? ESCG_OK : rc;   // a timed-out candidate only loses
+}
+
+}  // namespace
+
+static int autotune(escg* h) {
+  const TuneKey key{h->device, h->L, h->H, h->S, h->bits, h->desc.nbh, h->desc.reflect};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it != g_tune.end()) {
+    h->tuned_mode = it->second.mode;
+    h->tuned_ctas = it->second.ctas;
+    h->tuned_ms_per_mcs = it->second.ms_per_mcs;
+    h->tuned_candidates = 0;
+    return select_kernel(h, it->second.mode, it->second.ctas);
+  }
+  const size_t nbytes = escg_lattice_bytes_ex(h->L, h->H, h->bits);
+  uint8_t* scratch = nullptr;
+  if (cudaMalloc(&scratch, nbytes) != cudaSuccess) {
+    set_err("autotune: cudaMalloc of a %zu-byte scratch lattice failed", nbytes);
+    return ESCG_ENOMEM;
+  }
+  CUDA_TRY(cudaMemcpyAsync(scratch, h->lattice, nbytes, cudaMemcpyDeviceToDevice, h->stream));
+  const int saved_timing = h->opt.time_kernels, saved_stop = h->opt.stop_at_extinction;
+  h->opt.time_kernels = 0;
+  h->opt.stop_at_extinction = 0;
+  // (launch mode, CTAs per SM of the ticketed kernels): the default rule,
+  // the flag kernel at 4, 3 and 2 CTAs per SM, the mailbox kernel at 4 and 3,
+  // the TMA-staged flag kernel, the block owners, whole-lattice residency;
+  // modes a lattice cannot run fall back to one already listed and are
+  // dropped as duplicates
+  const int cand[][2] = {{1, 0}, {3, 0}, {3, 3}, {3, 2}, {6, 0}, {6, 3}, {2, 0}, {5, 0}, {4, 0}};
+  std::vector<std::string> seen;
+  int best_mode = 1, best_ctas = 0, n = 0, rc = ESCG_OK;
+  double best = -1.0;
+  for (const auto& c : cand) {
+    rc = select_kernel(h, c[0], c[1]);
+    if (rc != ESCG_OK) break;
+    const std::string sig = kernel_signature(h);
+    bool dup = false;
+    for (const auto& x : seen) dup = dup || x == sig;
+    if (dup) continue;
+    seen.push_back(sig);
+    double ms = -1.0;
+    rc = tune_time(h, scratch, nbytes, &ms);
+    if (rc != ESCG_OK) break;
+    ++n;
+    if (ms >= 0.0 && (best < 0.0 || ms < best)) {
+      best = ms;
+      best_mode = c[0];
+      best_ctas = c[1];
+    }
+  }
+  h->opt.time_kernels = saved_timing;
+  h->opt.stop_at_extinction = saved_stop;
+  if (rc == ESCG_OK) rc = select_kernel(h, best_mode, best_ctas);
+  if (rc == ESCG_OK) {
+    cudaError_t e = cudaMemcpyAsync(h->lattice, scratch, nbytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) rc = reset_state(h, 0);
+    if (e == cudaSuccess && rc == ESCG_OK) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      set_err("autotune: restoring the initial lattice failed: %s", cudaGetErrorString(e));
+      rc = ESCG_ECUDA;
+    }
+  }
+  cudaFree(scratch);
+  if (rc != ESCG_OK) return rc;
+  h->tuned_mode = best_mode;
+  h->tuned_ctas = best_ctas;
+  h->tuned_ms_per_mcs = best / 20.0;
+  h->tuned_candidates = n;
+  g_tune[key] = TuneVal{best_mode, best_ctas, best / 20.0};
+  return ESCG_OK;
+}
+
+extern "C" int escg_autotune_result(escg_t* h, int32_t* persistent, int32_t* ctas_per_sm, double* ms_per_mcs,
+                                    int32_t* candidates) {
+  if (!h) {
+    set_err("NULL handle");
+    return ESCG_EINVAL;
+  }
+  if (!h->opt.autotune) {
+    set_err("the handle was not created with autotune");
+    return ESCG_ESTATE;
+  }
+  if (persistent) *persistent = h->tuned_mode;
+  if (ctas_per_sm) *ctas_per_sm = h->tuned_ctas;
+  if (ms_per_mcs) *ms_per_mcs = h->tuned_ms_per_mcs;
+  if (candidates) *candidates = h->tuned_candidates;
+  return ESCG_OK;
+}

@@ -1170,32 +1170,40 @@ int engine_chunk(Engine* e, int threads) {
   return ESCG_OK;
 }
 
-// Online autotuning of the CTA size: one chunk per candidate, timed with
-// events; the physical mapping never changes the results.
+// Online autotuning of the chunk kernel: its CTA size (64, 128, 256 consumer
+// threads) and its staging (the warp-specialised TMA kernel or the plain
+// one), one chunk per candidate, timed with events; the physical mapping
+// never changes the results, so the tuning chunks are ordinary chunks of the
+// run.
 int engine_autotune(Engine* e, uint64_t* chunks_left) {
   const int cand[3] = {64, 128, 256};
   float best = 1e30f;
   int best_t = 256;
-  for (int c = 0; c < 3 && *chunks_left > 0; ++c) {
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, e->stream);
-    const int rc = engine_chunk(e, cand[c]);
-    cudaEventRecord(e1, e->stream);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (rc != ESCG_OK) return rc;
-    --*chunks_left;
-    if (ms < best) {
-      best = ms;
-      best_t = cand[c];
+  bool best_tma = true;
+  for (int m = 0; m < 2; ++m)
+    for (int c = 0; c < 3 && *chunks_left > 0; ++c) {
+      e->tma = (m == 0);
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, e->stream);
+      const int rc = engine_chunk(e, cand[c]);
+      cudaEventRecord(e1, e->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (rc != ESCG_OK) return rc;
+      --*chunks_left;
+      if (ms < best) {
+        best = ms;
+        best_t = cand[c];
+        best_tma = e->tma;
+      }
     }
-  }
   e->threads = best_t;
+  e->tma = best_tma;
   return ESCG_OK;
 }
 
@@ -1390,6 +1398,7 @@ int escg_batch_snapshot(escg_batch_t* b, int32_t i, uint8_t* host_out) {
 }
 
 int32_t escg_batch_threads(escg_batch_t* b) { return b ? b->e.threads : 0; }
+int32_t escg_batch_uses_tma(escg_batch_t* b) { return b ? (int32_t)b->e.tma : 0; }
 uint64_t escg_batch_launch_count(escg_batch_t* b) { return b ? b->e.launches : 0; }
 
 void escg_batch_destroy(escg_batch_t* b) {
@@ -1647,6 +1656,7 @@ int escg_server_stats(escg_server_t* s, int32_t* resident, int32_t* queued, uint
 }
 
 int32_t escg_server_threads(escg_server_t* s) { return s ? s->e.threads : 0; }
+int32_t escg_server_uses_tma(escg_server_t* s) { return s ? (int32_t)s->e.tma : 0; }
 uint64_t escg_server_launch_count(escg_server_t* s) { return s ? s->e.launches : 0; }
 
 void escg_server_destroy(escg_server_t* s) {
