@@ -365,6 +365,50 @@ __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0,
   }
 }
 
+// Piece t (0..255) of a uniform one-byte-per-site tile: a 16-byte quarter
+// row of the interior and, for t < 8, of the top / bottom rim rows, for
+// t >= 128 one cell of the left / right rim columns.  load_tile_uni and
+// store_tile_uni run piece threadIdx.x; CTAs of fewer threads run several.
+__device__ __forceinline__ void load_piece_uni(const LatticeDesc& d, int x0, int y0, uint8_t* tile, int t) {
+  const int L = d.L, pitch = d.pitch;
+  {  // interior: 64 rows x 4 x 16 bytes, one 16-byte load per piece
+    const int r = t >> 2, q = t & 3;
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q);
+    uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    dst[0] = make_uint2(v.x, v.y);
+    dst[1] = make_uint2(v.z, v.w);
+  }
+  if (t < 8) {  // top / bottom rim rows
+    const int r = (t < 4) ? -1 : kUniB, q = t & 3;
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0) + q);
+    uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    dst[0] = make_uint2(v.x, v.y);
+    dst[1] = make_uint2(v.z, v.w);
+  } else if (t >= 128) {  // left / right rim columns
+    const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
+    tile[tidx(r, c, kUniSP)] = __ldcg(d.lat + (size_t)(y0 + r) * pitch + wrap(x0 + c, L));
+  }
+}
+
+__device__ __forceinline__ void store_piece_uni(const LatticeDesc& d, int x0, int y0, const uint8_t* tile, int t) {
+  const int L = d.L, pitch = d.pitch;
+  {
+    const int r = t >> 2, q = t & 3;
+    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    const uint2 a = src[0], b = src[1];
+    reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
+  }
+  if (t < 8) {
+    const int r = (t < 4) ? -1 : kUniB, q = t & 3;
+    const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
+    const uint2 a = src[0], b = src[1];
+    reinterpret_cast<uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
+  } else if (t >= 128) {
+    const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
+    d.lat[(size_t)(y0 + r) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, kUniSP)];
+  }
+}
+
 // Uniform staging: 64 x 64 interior (64 rows of 16 + 16 + 16 + 16 sites,
 // one quarter row per thread), the top and bottom rim rows, and the left and
 // right rim columns (threads 128..255, one site each).  Packed lattices: a
@@ -376,23 +420,7 @@ __device__ __forceinline__ uint32_t load_tile_uni(const LatticeDesc& d, int x0, 
   const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = PACKED ? d.bits : 8;
   uint32_t rim_raw = 0;
   if (bits == 8) {
-    {  // interior: 64 rows x 4 x 16 bytes, one 16-byte load per thread
-      const int r = t >> 2, q = t & 3;
-      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q);
-      uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
-      dst[0] = make_uint2(v.x, v.y);
-      dst[1] = make_uint2(v.z, v.w);
-    }
-    if (t < 8) {  // top / bottom rim rows
-      const int r = (t < 4) ? -1 : kUniB, q = t & 3;
-      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0) + q);
-      uint2* dst = reinterpret_cast<uint2*>(tile + tidx(r, 16 * q, kUniSP));
-      dst[0] = make_uint2(v.x, v.y);
-      dst[1] = make_uint2(v.z, v.w);
-    } else if (t >= 128) {  // left / right rim columns
-      const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
-      tile[tidx(r, c, kUniSP)] = __ldcg(d.lat + (size_t)(y0 + r) * pitch + wrap(x0 + c, L));
-    }
+    load_piece_uni(d, x0, y0, tile, t);
     return rim_raw;
   }
   // packed: 16 sites = 32 bits (2 bits per site) or 64 bits (4 bits)
@@ -432,21 +460,7 @@ __device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int
                                                uint32_t rim_raw) {
   const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = PACKED ? d.bits : 8;
   if (bits == 8) {
-    {
-      const int r = t >> 2, q = t & 3;
-      const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
-      const uint2 a = src[0], b = src[1];
-      reinterpret_cast<uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
-    }
-    if (t < 8) {
-      const int r = (t < 4) ? -1 : kUniB, q = t & 3;
-      const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
-      const uint2 a = src[0], b = src[1];
-      reinterpret_cast<uint4*>(d.lat + (size_t)wrap(y0 + r, d.H) * pitch + x0)[q] = make_uint4(a.x, a.y, b.x, b.y);
-    } else if (t >= 128) {
-      const int k = t - 128, c = (k < 64) ? -1 : kUniB, r = k & 63;
-      d.lat[(size_t)(y0 + r) * pitch + wrap(x0 + c, L)] = tile[tidx(r, c, kUniSP)];
-    }
+    store_piece_uni(d, x0, y0, tile, t);
     return;
   }
   auto quarter = [&](int r, int gy, int q) {

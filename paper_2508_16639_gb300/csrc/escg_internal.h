@@ -83,12 +83,16 @@ struct PersistentArgs {
   int32_t stall_block;   // test hook: never publish this block's epoch (-1: off)
   unsigned long long* ob;  // boundary records of the mailbox kernel ([P*P][4][32]), else null
   int32_t fuse_counts;     // 1: counts of log points fused into the visits; 0: the host counts
+  int32_t threads;         // flag kernel on uniform one-byte lattices: 128 (two quads per
+                           // thread, up to 8 CTAs per SM) or 0 / 256 (one quad per thread)
 };
 // MCS [m_begin, m_begin + n_mcs) in one persistent dataflow launch, counts
 // of log points fused in.
 cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream);
 // Occupancy-derived grid size of the persistent kernel for a lattice.
 int persistent_grid(int device, bool uniform);
+// The same for the 128-thread build of the uniform flag kernel (up to 8 per SM).
+int persistent_grid128(int device);
 
 // Whole-lattice residency: one CTA runs MCS [m_begin, m_begin + n_mcs) with
 // the lattice in shared memory (counts of log points written in-kernel).

@@ -193,9 +193,17 @@ constexpr int kPersistentThreads = 256;
 constexpr int kUniMinBlocks = 4;
 constexpr int kUniLaunchPerSM = 4;
 
-template <bool UNI, bool PACKED = false>
-__global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
+__device__ __forceinline__ void own_fine_phases(const LatticeDesc& d, int bx, int by, uint32_t m, uint8_t* tile,
+                                                uint32_t ord, const uint8_t* trans);
+
+// NT = 256: one quad (2 x 2 sub-blocks) per thread, up to 4 CTAs per SM;
+// NT = 128 (uniform, one byte per site): two quads per thread stepped
+// pairwise (own_fine_phases), up to 8 CTAs per SM -- twice the visits in
+// flight per SM for the same number of threads.
+template <bool UNI, bool PACKED = false, int NT = kPersistentThreads>
+__global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
     persistent_kernel(PersistentArgs a) {
+  static_assert(NT == kPersistentThreads || (NT == 128 && UNI && !PACKED), "128-thread CTAs: uniform bytes only");
   __shared__ VisitSmem sm;
   __shared__ uint16_t stash[(UNI || !PACKED) ? 1 : kStashWords];
   __shared__ uint32_t s_item, s_ord, s_quit, s_abort;
@@ -274,18 +282,31 @@ __global__ void __launch_bounds__(kPersistentThreads, UNI ? kUniMinBlocks : 4)
       }
       __syncthreads();
       if (s_abort) break;  // uniform across the CTA
-      if (UNI)
+      if (NT == 128) {
+        const int x0 = bx * kUniB, y0 = by * kUniB;
+        load_piece_uni(d, x0, y0, sm.tile, tid);
+        load_piece_uni(d, x0, y0, sm.tile, tid + 128);
+        __syncthreads();
+        own_fine_phases(d, bx, by, m, sm.tile, sm.forder, reinterpret_cast<const uint8_t*>(sm.trans));
+        store_piece_uni(d, x0, y0, sm.tile, tid);
+        store_piece_uni(d, x0, y0, sm.tile, tid + 128);
+      } else if (UNI) {
         visit_uniform<false, PACKED>(d, bx, by, m, sm);
-      else
+      } else {
         visit_generic<false, PACKED>(d, bx, by, m, sm, stash);
+      }
       const bool log_point = a.fuse_counts && ((m + 1u) % a.log_every) == 0u;
       if (log_point) {
         const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1),
                   sD = slot_of(ord, colour ^ 3);
-        if (UNI)
+        if (NT == 128) {
+          count_pieces_uni<kUniSP, kColOff>(sm.tile, sm.hist, d.S, k, sV, sH, sD, tid);
+          count_pieces_uni<kUniSP, kColOff>(sm.tile, sm.hist, d.S, k, sV, sH, sD, tid + 128);
+        } else if (UNI) {
           count_visit_uni<kUniSP, kColOff>(sm.tile, sm.hist, d.S, k, sV, sH, sD);
-        else
+        } else {
           count_visit_generic(d, bx, by, sm, k, sV, sH, sD);
+        }
       }
       __syncthreads();
       if (tid == 0 && by * P + bx != a.stall_block) {
@@ -1586,7 +1607,9 @@ int persistent_tma_grid(int device) {
 }
 
 cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream) {
-  if (a.d.uniform64 && a.d.bits != 8)
+  if (a.threads == 128 && a.d.uniform64 && a.d.bits == 8)
+    persistent_kernel<true, false, 128><<<grid, 128, 0, stream>>>(a);
+  else if (a.d.uniform64 && a.d.bits != 8)
     persistent_kernel<true, true><<<grid, kPersistentThreads, 0, stream>>>(a);
   else if (a.d.uniform64)
     persistent_kernel<true, false><<<grid, kPersistentThreads, 0, stream>>>(a);
@@ -1678,6 +1701,15 @@ cudaError_t launch_ll_merge(const LatticeDesc& d, const unsigned long long* ob, 
   const uint32_t ord = d.perm24[(uint32_t)(((uint64_t)x * 24u) >> 32)];
   ll_merge_kernel<<<d.P * d.P, 256, 0, stream>>>(d, ob, st, m_end, ord);
   return cudaGetLastError();
+}
+
+int persistent_grid128(int device) {
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<true, false, 128>, 128, 0);
+  if (per_sm > 8) per_sm = 8;
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
 }
 
 int persistent_grid(int device, bool uniform) {

@@ -108,6 +108,40 @@ def test_many_mcs_per_launch(L, S, X, n, log_every, persistent):
     assert mcs == n + 3 and np.array_equal(c, O.counts(o, S))
 
 
+@pytest.mark.parametrize("L,S,ctas,log_every", [(128, 3, 8, 3), (256, 5, 6, 2), (384, 3, 8, 10), (1024, 3, 5, 10)])
+def test_flag_kernel_128_thread_ctas(L, S, ctas, log_every):
+    """The flag kernel with more than 4 CTAs per SM on a uniform one-byte
+    lattice runs its 128-thread build (two quads per thread, stepped
+    pairwise): bit-exact after every MCS, fused counts included."""
+    K = (1,) if S == 3 else (1, 2)
+    X = 2.0 + L / 64
+    seed = 515 + L
+    g, o, D = _pair(L, S, K, 0.2, 1.0, 1.0, X, seed, persistent=3, ctas_per_sm=ctas, log_every=log_every)
+    assert g.update_kernel == "persistent_kernel"
+    for m in range(4):
+        g.run(1)
+        o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 1, mcs_begin=m)
+        assert np.array_equal(g.snapshot(), o), m
+    g.run(11)
+    o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 11, mcs_begin=4)
+    assert np.array_equal(g.snapshot(), o)
+    ms, log = g.counts_log()
+    _, olog, _ = O.run_observed(O.init(L, S, 0.2, seed), D, 1.0, 1.0, X, seed, 15, log_every=log_every)
+    assert np.array_equal(log, olog)
+
+
+def test_flag_kernel_128_thread_default_on_deep_phases():
+    """L = 6400 (2500 blocks per coarse phase): persistent = 1 runs the flag
+    kernel's 128-thread build; bit-exact against the oracle after 2 MCS."""
+    L, S, seed = 6400, 3, 6400
+    X = 2.0 * 1e-4 * L * L
+    g, o, D = _pair(L, S, (1,), 0.25, 1.0, 1.0, X, seed)
+    assert g.update_kernel == "persistent_kernel"
+    g.run(2)
+    o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 2)
+    assert np.array_equal(g.snapshot(), o)
+
+
 def test_cfg1_competition_only_L64():
     w = W.CFG1
     g, o, D = _pair(w.L, w.S, w.K, w.p_empty, w.interact, w.reproduce, w.exchange, w.seed)
