@@ -445,7 +445,7 @@ int select_kernel(escg* h, int persistent, int ctas_per_sm) {
   h->use_tma = h->use_ll = h->use_own = h->use_gown = h->use_resident = false;
   h->own_dyn = h->own_threads = 0;
   h->gown = GownConfig{};
-  h->grid = persistent_grid(h->device, d.uniform64 != 0);
+  h->grid = persistent_grid(h->device, d.uniform64 != 0 || d.uniform_var != 0);
   // the TMA and mailbox kernels are written for square lattices of one byte
   // per site; the flag kernel takes rectangular and packed ones in both
   // geometries
@@ -819,8 +819,10 @@ escg_t* escg_create_ex(int32_t L, int32_t S, const uint8_t* digraph, const escg_
   for (int k = 0; k < py.GQ; ++k) uni = uni && (py.fs[k + 1] - py.fs[k] == 2);
   d.nbh = o.neighbourhood;
   d.reflect = o.reflecting_boundary;
-  // the uniform kernels implement the von Neumann, periodic rule only
+  // the uniform kernels implement the von Neumann, periodic rule; the flag
+  // kernel also the variants on 64 x 64 blocks of one byte per site
   d.uniform64 = (uni && h->pitch % 16 == 0 && d.nbh == 4 && !d.reflect) ? 1 : 0;
+  d.uniform_var = (uni && h->pitch % 16 == 0 && (d.nbh == 8 || d.reflect) && h->bits == 8) ? 1 : 0;
   if (select_kernel(h, o.persistent, o.ctas_per_sm) != ESCG_OK) return fail(ESCG_ENOMEM);
 
   if (launch_init(d, h->T_empty, h->stream) != cudaSuccess) {

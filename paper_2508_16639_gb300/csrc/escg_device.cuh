@@ -588,6 +588,76 @@ __device__ __forceinline__ void attempt_variant_2x2(uint8_t* __restrict__ tile, 
   apply_rule(tile, trans, ti, ti + dr * sp + dc, w << (2 + lg), tx, txi, s1);
 }
 
+// One elementary step on a 2 x 2 sub-block of a uniform tile under a rule
+// variant (the step of attempt_variant for n_k = 4): MOORE: p = 32 w, cell =
+// bits 31..30 of w (row, column), direction = bits 29..27 (0 up, 1 down,
+// 2 left, 3 right, 4 up-left, 5 up-right, 6 down-left, 7 down-right), u =
+// w << 5; else the von Neumann step of attempt_uni.  EDGE: the block touches
+// the edge of a reflecting lattice, and a step that would leave it is
+// mirrored ((gy, gx): lattice coordinates of the sub-block's first cell);
+// blocks away from the edge take the plain step, which is then the same.
+template <int SP, bool MOORE, bool EDGE>
+__device__ __forceinline__ void attempt_uni_var(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
+                                                uint32_t w, int base, uint32_t tx, uint32_t txi, uint32_t s1,
+                                                int gy, int gx, int H, int L) {
+  static_assert(2 * SP + 2 < 256, "offsets must fit the byte tables");
+  if (EDGE) {
+    attempt_variant_2x2(tile, trans, w, MOORE ? 3 : 2, base, SP, tx, txi, s1, true, gy, gx, H, L);
+  } else if (MOORE) {
+    // the eight neighbour offsets plus SP + 1, as bytes selected by dir ^ 4
+    // (byte 0 holds up-left's 0, so the selector's zero nibbles add nothing)
+    constexpr uint32_t kLo = 0u | (2u << 8) | ((uint32_t)(2 * SP) << 16) | ((uint32_t)(2 * SP + 2) << 24);
+    constexpr uint32_t kHi = 1u | ((uint32_t)(2 * SP + 1) << 8) | ((uint32_t)SP << 16) | ((uint32_t)(SP + 2) << 24);
+    const uint32_t dir = (w >> 27) & 7u;
+    const int ti = base + (int)(w >> 31) * SP + (int)((w >> 30) & 1u);
+    const int tj = ti - SP - 1 + (int)__byte_perm(kLo, kHi, dir ^ 4u);
+    apply_rule(tile, trans, ti, tj, w << 5, tx, txi, s1);
+  } else {
+    attempt_uni<SP>(tile, trans, w, base, tx, txi, s1);
+  }
+}
+
+// The four fine colour phases of a uniform visit under a rule variant
+// (threads 0..255, a CTA barrier after each).
+template <bool MOORE, bool EDGE>
+__device__ __forceinline__ void fine_phases_var(const LatticeDesc& d, int bx, int by, uint32_t m, uint8_t* tile,
+                                                uint32_t ord, const uint8_t* trans) {
+  const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
+  const uint32_t s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
+  const uint32_t GQ = (uint32_t)d.GQ;
+  const uint32_t g00 = (uint32_t)(by * (kUniB / 2) + 2 * qy) * GQ + (uint32_t)(bx * (kUniB / 2) + 2 * qx);
+  const int base00 = tidx(4 * qy, 4 * qx, kUniSP);
+  const int gy00 = by * kUniB + 4 * qy, gx00 = bx * kUniB + 4 * qx;
+#pragma unroll
+  for (int fi = 0; fi < 4; ++fi) {
+    const uint32_t fcol = (ord >> (2 * fi)) & 3u, cx = fcol & 1u, cy = fcol >> 1;
+    const uint32_t g = g00 + cy * GQ + cx;
+    const int base = base00 + (int)(cy * (2 * kUniSP) + 2 * cx);
+    const int gy = gy00 + 2 * (int)cy, gx = gx00 + 2 * (int)cx;
+    const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
+    attempt_uni_var<kUniSP, MOORE, EDGE>(tile, trans, x.x, base, tx, txi, s1, gy, gx, d.H, d.L);
+    attempt_uni_var<kUniSP, MOORE, EDGE>(tile, trans, x.y, base, tx, txi, s1, gy, gx, d.H, d.L);
+    attempt_uni_var<kUniSP, MOORE, EDGE>(tile, trans, x.z, base, tx, txi, s1, gy, gx, d.H, d.L);
+    attempt_uni_var<kUniSP, MOORE, EDGE>(tile, trans, x.w, base, tx, txi, s1, gy, gx, d.H, d.L);
+    __syncthreads();
+  }
+}
+
+// The four corner cells of a uniform tile (the Moore rule's diagonal
+// neighbours), pieces t = 8..11 of the one-byte staging; corners beyond a
+// reflecting edge are loaded wrapped and never stepped into, so writing them
+// back leaves their (inactive) block unchanged.
+__device__ __forceinline__ void corner_uni(const LatticeDesc& d, int x0, int y0, uint8_t* tile, int t, bool store) {
+  if (t < 8 || t >= 12) return;
+  const int r = (t & 1) ? kUniB : -1, c = (t & 2) ? kUniB : -1;
+  uint8_t* cell = d.lat + (size_t)wrap(y0 + r, d.H) * d.pitch + wrap(x0 + c, d.L);
+  if (store)
+    *cell = tile[tidx(r, c, kUniSP)];
+  else
+    tile[tidx(r, c, kUniSP)] = __ldcg(cell);
+}
+
+
 // Order in which a visit hands out the quads (2 x 2 groups of fine
 // sub-blocks) of a block: first the rx x ry regular ones (columns qx >= irx,
 // rows qy >= iry, all four sub-blocks 2 x 2), then the rows qy < iry, then

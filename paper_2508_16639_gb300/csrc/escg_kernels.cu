@@ -200,10 +200,13 @@ __device__ __forceinline__ void own_fine_phases(const LatticeDesc& d, int bx, in
 // NT = 128 (uniform, one byte per site): two quads per thread stepped
 // pairwise (own_fine_phases), up to 8 CTAs per SM -- twice the visits in
 // flight per SM for the same number of threads.
-template <bool UNI, bool PACKED = false, int NT = kPersistentThreads>
+// VAR (uniform geometry, one byte per site): a rule variant on 64 x 64
+// blocks -- bit 0 a reflecting boundary, bit 1 the Moore neighbourhood.
+template <bool UNI, bool PACKED = false, int NT = kPersistentThreads, int VAR = 0>
 __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
     persistent_kernel(PersistentArgs a) {
   static_assert(NT == kPersistentThreads || (NT == 128 && UNI && !PACKED), "128-thread CTAs: uniform bytes only");
+  static_assert(VAR == 0 || (UNI && !PACKED && NT == kPersistentThreads), "variants: uniform bytes, 256 threads");
   __shared__ VisitSmem sm;
   __shared__ uint16_t stash[(UNI || !PACKED) ? 1 : kStashWords];
   __shared__ uint32_t s_item, s_ord, s_quit, s_abort;
@@ -282,7 +285,20 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
       }
       __syncthreads();
       if (s_abort) break;  // uniform across the CTA
-      if (NT == 128) {
+      if (VAR != 0) {
+        const int x0 = bx * kUniB, y0 = by * kUniB;
+        load_piece_uni(d, x0, y0, sm.tile, tid);
+        if (VAR & 2) corner_uni(d, x0, y0, sm.tile, tid, false);
+        __syncthreads();
+        const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
+        const bool edge = (VAR & 1) && (bx == 0 || bx == P - 1 || by == 0 || by == Py - 1);
+        if (edge)
+          fine_phases_var<(VAR & 2) != 0, true>(d, bx, by, m, sm.tile, sm.forder, trans);
+        else
+          fine_phases_var<(VAR & 2) != 0, false>(d, bx, by, m, sm.tile, sm.forder, trans);
+        store_piece_uni(d, x0, y0, sm.tile, tid);
+        if (VAR & 2) corner_uni(d, x0, y0, sm.tile, tid, true);
+      } else if (NT == 128) {
         const int x0 = bx * kUniB, y0 = by * kUniB;
         load_piece_uni(d, x0, y0, sm.tile, tid);
         load_piece_uni(d, x0, y0, sm.tile, tid + 128);
@@ -1607,7 +1623,15 @@ int persistent_tma_grid(int device) {
 }
 
 cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream) {
-  if (a.threads == 128 && a.d.uniform64 && a.d.bits == 8)
+  if (a.d.uniform_var) {
+    const int var = (a.d.nbh == 8 ? 2 : 0) | (a.d.reflect ? 1 : 0);
+    if (var == 1)
+      persistent_kernel<true, false, kPersistentThreads, 1><<<grid, kPersistentThreads, 0, stream>>>(a);
+    else if (var == 2)
+      persistent_kernel<true, false, kPersistentThreads, 2><<<grid, kPersistentThreads, 0, stream>>>(a);
+    else
+      persistent_kernel<true, false, kPersistentThreads, 3><<<grid, kPersistentThreads, 0, stream>>>(a);
+  } else if (a.threads == 128 && a.d.uniform64 && a.d.bits == 8)
     persistent_kernel<true, false, 128><<<grid, 128, 0, stream>>>(a);
   else if (a.d.uniform64 && a.d.bits != 8)
     persistent_kernel<true, true><<<grid, kPersistentThreads, 0, stream>>>(a);

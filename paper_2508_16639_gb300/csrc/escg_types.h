@@ -82,6 +82,9 @@ struct LatticeDesc {
   int32_t bits;         // bits per site in `lat`: 8 (one byte) or 4, 2 (packed
                         // rows: site c at bits [c*bits, (c+1)*bits), little endian)
   uint8_t perm24[24];   // the 24 colour orders, lexicographic (4 x 2 bits)
+  int32_t uniform_var;  // all blocks 64x64 with 2x2 sub-blocks, one byte per site,
+                        // and a rule variant (Moore and/or reflecting): the flag
+                        // kernel's uniform variant visit
 };
 
 // Fills perm24 with the 24 orders of the colours {0,1,2,3} in lexicographic

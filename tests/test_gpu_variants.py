@@ -56,3 +56,22 @@ def test_bad_variant_is_rejected():
     D = O.circulant(3, (1,))
     with pytest.raises(E.EscgError):
         E.Lattice(64, 3, D, (1.0, 1.0, 1.0), 1, neighbourhood=6)
+
+
+@pytest.mark.parametrize("nbh,reflect", [(8, False), (4, True), (8, True)], ids=["moore", "reflect", "moore-reflect"])
+def test_uniform_variant_visit_full_size(nbh, reflect):
+    """The benchmark lattice (L = 3200, 64 x 64 blocks) under the rule
+    variants runs the flag kernel's uniform variant visit (the Moore step
+    from a byte-permute offset table, the mirror only in blocks on the
+    lattice edge); bit-exact against the replay oracle after MCS 1 and 2."""
+    L, S, seed = 3200, 3, 3200 + nbh + int(reflect)
+    D = O.circulant(S, (1,))
+    X = 2.0 * 1e-4 * L * L
+    g = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.25, persistent=3, neighbourhood=nbh,
+                  reflecting_boundary=reflect)
+    o = O.init(L, S, 0.25, seed)
+    for m in range(2):
+        g.run(1)
+        o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 1, mcs_begin=m, neighbourhood=nbh, reflect=reflect)
+        got = g.snapshot()
+        assert np.array_equal(got, o), f"after MCS {m + 1}: {int((got != o).sum())} sites differ"
