@@ -75,3 +75,22 @@ def test_uniform_variant_visit_full_size(nbh, reflect):
         o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 1, mcs_begin=m, neighbourhood=nbh, reflect=reflect)
         got = g.snapshot()
         assert np.array_equal(got, o), f"after MCS {m + 1}: {int((got != o).sum())} sites differ"
+
+
+@pytest.mark.parametrize("nbh,reflect", [(4, False), (8, True)], ids=["vonneumann", "moore-reflect"])
+def test_deep_generic_visit_full_size(nbh, reflect):
+    """L = 4800 (a generic partition of 38 x 38 groups, too many for the block
+    owners; 1444 blocks per coarse phase, over two waves of flag-kernel CTAs):
+    the flag kernel's generic visit, bit-exact against the replay oracle after
+    MCS 1 and 2."""
+    L, S, seed = 4800, 3, 4800 + nbh
+    D = O.circulant(S, (1,))
+    X = 2.0 * 1e-4 * L * L
+    g = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.25, neighbourhood=nbh, reflecting_boundary=reflect)
+    assert g.update_kernel == "persistent_kernel"
+    o = O.init(L, S, 0.25, seed)
+    for m in range(2):
+        g.run(1)
+        o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 1, mcs_begin=m, neighbourhood=nbh, reflect=reflect)
+        got = g.snapshot()
+        assert np.array_equal(got, o), f"after MCS {m + 1}: {int((got != o).sum())} sites differ"
