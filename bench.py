@@ -99,6 +99,9 @@ def _parse():
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--L", type=int, default=3200, help="lattice side (3200 is the benchmark)")
+    ap.add_argument("--neighbourhood", type=int, default=4, choices=[4, 8],
+                    help="rule of the main measurement (8: Moore), for profiling the variant builds")
+    ap.add_argument("--reflect", action="store_true", help="reflecting boundary for the main measurement")
     ap.add_argument("--workload", choices=["rps", "rpsls-L800"], default="rps",
                     help="rps: the benchmark's RPS lattice (side --L, mobility --mobility); rpsls-L800: the RPSLS "
                          "workload (L = 800, p_empty 0.2, M = 1e-4) for profiling its kernel")
@@ -696,7 +699,8 @@ def main():
     stream = torch.cuda.Stream()
     g = E.Lattice(w.L, w.S, E.circulant(w.S, w.K), (w.interact, w.reproduce, X), R.replica_seed(w.seed, rank),
                   p_empty=w.p_empty, log_every=w.log_every, stream=stream, time_kernels=True,
-                  persistent=args.persistent, ctas_per_sm=args.ctas_per_sm)
+                  persistent=args.persistent, ctas_per_sm=args.ctas_per_sm, neighbourhood=args.neighbourhood,
+                  reflecting_boundary=args.reflect)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     K, Wm, mps = args.steps, args.warmup, args.mcs_per_step
 
@@ -862,6 +866,8 @@ def main():
                             "paper_hardware": "RTX A2000 (not a target)"},
                 "mobility": mobility, "variants": variants, "packed": packed, "sizes": sizes,
                 "ensemble": ensemble, "serving": serving, "park": park}
+        if args.neighbourhood != 4 or args.reflect:
+            line["config"].update(neighbourhood=args.neighbourhood, reflecting_boundary=bool(args.reflect))
         print(json.dumps(line), flush=True)
     g.close()
     if dist is not None:

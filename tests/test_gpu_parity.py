@@ -397,3 +397,24 @@ def test_async_host_steps_on_two_handles():
     a.step_host_async(bad, 0, 5, outs[0], cnts[0])
     with pytest.raises(E.EscgError):
         a.step_host_wait()
+
+
+@pytest.mark.parametrize("bits", [8, 2])
+def test_maximum_size_lattice(bits):
+    """The largest lattice the boundary takes (L = 16384, 268 M sites; the
+    byte lattice runs the flag kernel's 128-thread build, the packed one the
+    256-thread build): bit-exact against the replay oracle after one MCS, and
+    the counts add up to N."""
+    L, S, seed = 16384, 3, 16384 + bits
+    D = O.circulant(S, (1,))
+    X = 2.0 * 1e-4 * L * L
+    g = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.25, bits_per_site=bits)
+    o = O.init(L, S, 0.25, seed)
+    assert np.array_equal(g.snapshot(), o)
+    g.run(1)
+    o, att = O.replay_run(o, D, 1.0, 1.0, X, seed, 1)
+    assert att == L * L
+    assert np.array_equal(g.snapshot(), o)
+    c, m = g.counts()
+    assert m == 1 and int(c.sum()) == L * L and np.array_equal(c, O.counts(o, S))
+    g.close()
