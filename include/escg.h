@@ -382,6 +382,14 @@ int escg_server_poll(escg_server_t* s, int64_t* ids_out, int32_t cap, int32_t* n
 int escg_server_result(escg_server_t* s, int64_t id, uint64_t* mcs_out, int32_t* extinct_out,
                        uint64_t* counts16_out, uint8_t* lattice_out);
 
+/* Host-clock times of a finished run, in seconds since the server was
+ * created: when it was submitted, when a step admitted it to a slot, and when
+ * the step that retired it had synchronised (queue wait = admitted -
+ * submitted; in service = finished - admitted, whole steps of
+ * chunks_per_step * log_every MCS).  A run cancelled while queued has
+ * admitted = finished.  ESCG_ESTATE if the run has not finished. */
+int escg_server_timing(escg_server_t* s, int64_t id, double* submitted_s, double* admitted_s, double* finished_s);
+
 /* Runs resident, runs queued, arena bytes in use. */
 int escg_server_stats(escg_server_t* s, int32_t* resident, int32_t* queued, uint64_t* bytes_in_use);
 int32_t escg_server_threads(escg_server_t* s);

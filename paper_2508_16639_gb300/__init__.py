@@ -446,6 +446,13 @@ class Server:
                                         _u8(lat) if lattice else None))
         return int(mcs.value), bool(ext.value), cnt, lat
 
+    def timing(self, rid: int):
+        """(submitted, admitted, finished) host-clock seconds of a finished run
+        since the server was created."""
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        check(load().escg_server_timing(self._h, int(rid), C.byref(a), C.byref(b), C.byref(c)))
+        return float(a.value), float(b.value), float(c.value)
+
     def stats(self):
         r, q, b = C.c_int32(), C.c_int32(), C.c_uint64()
         check(load().escg_server_stats(self._h, C.byref(r), C.byref(q), C.byref(b)))

@@ -104,6 +104,8 @@ SIGNATURES = {
     "escg_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
     "escg_server_threads": (C.c_int32, [C.c_void_p]),
     "escg_server_uses_tma": (C.c_int32, [C.c_void_p]),
+    "escg_server_timing": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
     "escg_server_launch_count": (C.c_uint64, [C.c_void_p]),
     "escg_server_destroy": (None, [C.c_void_p]),
     # include/escg_diag.h

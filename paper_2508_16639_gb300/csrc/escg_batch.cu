@@ -24,6 +24,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -1415,6 +1416,7 @@ namespace {
 
 struct Request {
   int64_t id = 0;
+  double submitted_s = 0.0;       // host clock, seconds since the server was created
   escg_replica_spec spec{};
   std::vector<uint8_t> digraph;   // owned copies
   std::vector<double> prob;
@@ -1424,6 +1426,7 @@ struct Request {
 struct Result {
   uint64_t mcs = 0;
   int32_t extinct = 0;
+  double submitted_s = 0.0, admitted_s = 0.0, finished_s = 0.0;   // host clock (see escg_server_timing)
   uint64_t counts[kMaxStates] = {};
   std::vector<uint8_t> lattice;
 };
@@ -1441,6 +1444,11 @@ struct escg_server {
   std::vector<int64_t> finished;     // not yet polled
   int64_t next_id = 0;
   int resident = 0;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  std::vector<double> slot_submitted, slot_admitted;   // of the run resident in each slot
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
 };
 
 extern "C" {
@@ -1476,6 +1484,8 @@ escg_server_t* escg_server_create(const escg_server_options* opt) {
   }
   s->slot_req.assign(s->opt.max_slots, -1);
   s->slot_L.assign(s->opt.max_slots, 0);
+  s->slot_submitted.assign(s->opt.max_slots, 0.0);
+  s->slot_admitted.assign(s->opt.max_slots, 0.0);
   for (int i = s->opt.max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
   return s;
 }
@@ -1493,6 +1503,7 @@ int64_t escg_server_submit(escg_server_t* s, const escg_replica_spec* spec) {
     return ESCG_ENOMEM;
   }
   r.spec = *spec;
+  r.submitted_s = s->now();
   r.digraph.assign(spec->digraph, spec->digraph + spec->S * spec->S);
   if (spec->dominance_prob) r.prob.assign(spec->dominance_prob, spec->dominance_prob + spec->S * spec->S);
   s->queue.push_back(std::move(r));
@@ -1514,6 +1525,8 @@ int escg_server_step(escg_server_t* s, int32_t* finished_out) {
     s->free_slots.pop_back();
     s->slot_req[slot] = r.id;
     s->slot_L[slot] = r.spec.L;
+    s->slot_submitted[slot] = r.submitted_s;
+    s->slot_admitted[slot] = s->now();
     s->resident++;
     s->queue.pop_front();
   }
@@ -1538,6 +1551,9 @@ int escg_server_step(escg_server_t* s, int32_t* finished_out) {
       res.mcs = x.mcs;
       res.extinct = (int32_t)x.stopped;
       for (int v = 0; v < kMaxStates; ++v) res.counts[v] = x.counts[v];
+      res.submitted_s = s->slot_submitted[slot];
+      res.admitted_s = s->slot_admitted[slot];
+      res.finished_s = s->now();
       if (s->opt.keep_lattice) {
         const LatticeDesc& d = s->e.h_slots[slot].d;
         res.lattice.resize((size_t)d.L * d.L);
@@ -1566,8 +1582,11 @@ int escg_server_cancel(escg_server_t* s, int64_t id) {
   // still queued: drop it; its result is the run not started (MCS 0)
   for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
     if (it->id != id) continue;
+    Result res;
+    res.submitted_s = it->submitted_s;
+    res.admitted_s = res.finished_s = s->now();
     s->queue.erase(it);
-    s->results[id] = Result{};
+    s->results[id] = std::move(res);
     s->finished.push_back(id);
     return ESCG_OK;
   }
@@ -1598,6 +1617,9 @@ int escg_server_cancel(escg_server_t* s, int64_t id) {
   res.mcs = x.mcs;
   res.extinct = (int32_t)x.stopped;
   for (int v = 0; v < kMaxStates; ++v) res.counts[v] = x.counts[v];
+  res.submitted_s = s->slot_submitted[slot];
+  res.admitted_s = s->slot_admitted[slot];
+  res.finished_s = s->now();
   if (s->opt.keep_lattice) {
     const LatticeDesc& d = s->e.h_slots[slot].d;
     res.lattice.resize((size_t)d.L * d.L);
@@ -1644,6 +1666,19 @@ int escg_server_result(escg_server_t* s, int64_t id, uint64_t* mcs_out, int32_t*
     }
     std::memcpy(lattice_out, r.lattice.data(), r.lattice.size());
   }
+  return ESCG_OK;
+}
+
+int escg_server_timing(escg_server_t* s, int64_t id, double* submitted_s, double* admitted_s, double* finished_s) {
+  if (!s) return ESCG_EINVAL;
+  auto it = s->results.find(id);
+  if (it == s->results.end()) {
+    set_last_error("run %lld has not finished", (long long)id);
+    return ESCG_ESTATE;
+  }
+  if (submitted_s) *submitted_s = it->second.submitted_s;
+  if (admitted_s) *admitted_s = it->second.admitted_s;
+  if (finished_s) *finished_s = it->second.finished_s;
   return ESCG_OK;
 }
 

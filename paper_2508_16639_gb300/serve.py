@@ -3,7 +3,8 @@
 `serve()` replays a stream of run requests in real time: each request is
 submitted to the server when its (scaled) arrival time has passed, the
 server is stepped while it holds work, and a request's latency is measured
-from its arrival to the step that retires it.  The loop itself is host-side
+from its arrival to the step that retires it, split into the wait in the
+queue and the time in service (escg_server_timing).  The loop itself is host-side
 orchestration; admission, execution and retirement happen in libescg.
 """
 from __future__ import annotations
@@ -31,6 +32,7 @@ def serve(requests, server: Server | None = None, time_scale: float = 1.0, **ser
     arrival = {}
     latency = {}
     done_mcs = {}
+    parts = {}   # request -> (queue wait, in service), seconds on the server's clock
     nxt = 0
     n = len(requests)
     steps = 0
@@ -54,10 +56,19 @@ def serve(requests, server: Server | None = None, time_scale: float = 1.0, **ser
             i, t_arr = arrival[rid]
             latency[i] = t_done - t_arr
             done_mcs[i] = srv.result(rid)[0]
+            t_sub, t_adm, t_fin = srv.timing(rid)
+            parts[i] = (t_adm - t_sub, t_fin - t_adm)
     total = time.perf_counter() - t0
     lat = np.array([latency[i] for i in range(n)])
+    pr = np.array([parts[i] for i in range(n)])
+    breakdown = {f"{name}_{q}_s": float(np.percentile(pr[:, k], p))
+                 for k, name in enumerate(("queue", "service")) for q, p in (("p50", 50), ("p99", 99))}
     return {"runs": n, "seconds": total, "runs_per_s": n / total, "steps": steps,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_latency_s": float(lat.mean()), "latencies_s": lat.tolist(),
             "site_updates": float(sum(done_mcs[i] * requests[i]["L"] ** 2 for i in range(n))),
-            "threads": srv.threads}
+            "threads": srv.threads,
+            # arrival to result = (at most one step until submission) + queue
+            # wait (submission to admission) + service (admission to the step
+            # that retires the run)
+            "latency_breakdown": breakdown}

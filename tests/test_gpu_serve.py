@@ -102,6 +102,9 @@ def test_serve_loop_reports_latency():
     out = serve(reqs, time_scale=0.05, arena_bytes=64 << 20, max_slots=32, chunks_per_step=2)
     assert out["runs"] == 40 and out["runs_per_s"] > 0
     assert 0 < out["p50_latency_s"] <= out["p99_latency_s"]
+    b = out["latency_breakdown"]
+    assert 0 <= b["queue_p50_s"] <= b["queue_p99_s"] and 0 < b["service_p50_s"] <= b["service_p99_s"]
+    assert b["service_p99_s"] <= out["p99_latency_s"] + 1e-6
 
 
 def test_submit_rejects_runs_larger_than_the_arena():
