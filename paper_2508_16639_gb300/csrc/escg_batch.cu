@@ -403,6 +403,10 @@ constexpr int kBSP = 144, kBRows = kMaxBlock + 2;
 constexpr uint32_t kBBoxBytes = (uint32_t)(kBSP * kBRows);   // 14112
 constexpr int kBTileStride = 14208;                          // 128-byte multiple
 constexpr uint32_t kBMbarLimit = 1u << 26;
+// Suspending waits of the warp-specialised chunk kernel: hint and bound
+// (about 4 s at 2 GHz, the order of the flag waits' spin limit).
+constexpr uint32_t kBMbarHintNs = 2000;
+constexpr long long kBMbarMaxCycles = 8000000000ll;
 
 struct BItem {
   uint32_t m, ord, forder, quit;
@@ -453,7 +457,7 @@ __device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t
         m = a.states[slot].mcs + i;
         if (m < a.slots[slot].max_mcs) break;
       }
-      if (!mbar_wait(&sm.empty[b], (use & 1u) ^ 1u, kBMbarLimit)) {
+      if (!mbar_wait_sleep(&sm.empty[b], (use & 1u) ^ 1u, kBMbarHintNs, kBMbarMaxCycles)) {
         btma_fail(ctl);
         quit = 1;
       }
@@ -550,9 +554,9 @@ __device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t
       fence_proxy_async_smem();   // the consumers' accesses of this tile precede the TMA's
       mbar_arrive_expect_tx(&sm.tma[b], kBBoxBytes);
       tma_load_2d(sm.tile[b], ta.maps + slot, xal, y0 - 1, &sm.tma[b]);
-      if (!mbar_wait(&sm.tma[b], use & 1u, kBMbarLimit)) {
+      if (!mbar_wait_sleep(&sm.tma[b], use & 1u, kBMbarHintNs, kBMbarMaxCycles)) {
         btma_fail(ctl);
-        mbar_wait(&sm.tma[b], use & 1u, kBMbarLimit);   // no copy left in flight
+        mbar_wait_sleep(&sm.tma[b], use & 1u, kBMbarHintNs, kBMbarMaxCycles);   // no copy left in flight
         ok = 0;
       }
     }
@@ -594,7 +598,7 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
   for (uint32_t n = 0;; ++n) {
     const int b = (int)(n & 1u);
     const uint32_t use = n >> 1;
-    if (!mbar_wait(&sm.full[b], use & 1u, kBMbarLimit)) {
+    if (!mbar_wait_sleep(&sm.full[b], use & 1u, kBMbarHintNs, kBMbarMaxCycles)) {
       if (tid == 0) btma_fail(ctl);
       return;
     }

@@ -1176,6 +1176,10 @@ constexpr uint32_t kTmaBoxBytes = (uint32_t)(kTmaSP * kTmaRows);   // 7392
 constexpr int kTmaTileStride = 7424;                               // 128-byte multiple
 constexpr int kTmaConsumers = 256, kTmaThreads = kTmaConsumers + 32;
 constexpr uint32_t kMbarLimit = 1u << 26;
+// The consumers' wait for a staged tile suspends (hint) instead of spinning,
+// bounded by about 4 s of SM clock.
+constexpr uint32_t kMbarHintNs = 2000;
+constexpr long long kMbarMaxCycles = 8000000000ll;
 // Work items a producer holds (9 lanes poll each).  Measured at L = 3200: a
 // window of 3 was slower than 1 -- dispatching a newer ready item delays the
 // globally oldest one behind a whole visit and lengthens the critical path.
@@ -1396,7 +1400,7 @@ __device__ void tma_consumer(const TmaArgs& a, TmaSmem& sm) {
   for (uint32_t n = 0;; ++n) {
     const int b = (int)(n & 1u);
     const uint32_t use = n >> 1;
-    if (!mbar_wait(&sm.full[b], use & 1u, kMbarLimit)) {
+    if (!mbar_wait_sleep(&sm.full[b], use & 1u, kMbarHintNs, kMbarMaxCycles)) {
       if (t == 0) tma_fail(st);
       break;
     }

@@ -59,6 +59,33 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
+// The same test with a suspend-time hint: while the phase is incomplete the
+// thread may be suspended for up to hint_ns nanoseconds instead of returning
+// at once, so that a waiting warp stops taking issue slots from the warps
+// that work.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits with suspend hints, bounded by elapsed SM clock cycles (early
+// wake-ups cannot shorten the bound); false on timeout.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns,
+                                                long long max_cycles) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait_hint(bar, parity, hint_ns)) return true;
+    if (clock64() - t0 > max_cycles) return false;
+  }
+}
+
 // Orders this thread's earlier generic-proxy accesses of global memory
 // (including data other CTAs published and this thread acquired) before its
 // later async-proxy (TMA) accesses.
