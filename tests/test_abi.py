@@ -140,6 +140,7 @@ def _create_ex(lib, L, S, **fields):
     (64, 3, dict(reflecting_boundary=2), "neighbourhood"),
     (64, 3, dict(device_lattice=0x1001), "aligned"),
     (64, 3, dict(p_empty=1.5), "p_empty"),
+    (64, 3, dict(autotune=2), "autotune"),
 ])
 def test_create_rejects_bad_options(lib, L, S, fields, msg):
     """Options are checked on the host before any device work, so an invalid
