@@ -252,7 +252,7 @@ struct escg {
   bool use_own = false;          // block-owner kernel (uniform, square, one byte per site)
   int own_dyn = 0;               // its shared-memory padding
   int own_threads = 0;           // and CTA size
-  int flag_threads = 256;        // CTA size of the flag kernel (128: uniform bytes, > 4 CTAs per SM)
+  int flag_threads = 256;        // CTA size of the flag kernel (128: uniform geometry, > 4 CTAs per SM)
   bool use_gown = false;         // block owners on a generic partition
   int tuned_mode = 0, tuned_ctas = 0;   // autotuner's choice (launch mode, CTAs per SM)
   double tuned_ms_per_mcs = 0.0;
@@ -514,8 +514,8 @@ int select_kernel(escg* h, int persistent, int ctas_per_sm) {
     h->use_resident = true;
     h->use_gown = false;
   }
-  // The flag kernel on a uniform one-byte lattice with more than 4 CTAs per
-  // SM requested, or by default (1) with at least kFlag128Ratio times as many
+  // The flag kernel on a uniform lattice (any bits per site) with more than
+  // 4 CTAs per SM requested, or by default (1) with at least kFlag128Ratio times as many
   // blocks per coarse phase as 256-thread CTAs: the 128-thread build (two
   // quads per thread), up to 8 per SM.  Measured (µs per MCS, 4 x 256 vs
   // 8 x 128 threads per SM): L = 2048 21.7 vs 26.7, 3200 25.5 vs 32.8 (5 x 128:
@@ -524,7 +524,7 @@ int select_kernel(escg* h, int persistent, int ctas_per_sm) {
   h->flag_threads = 256;
   const bool flag = !h->use_tma && !h->use_ll && !h->use_own && !h->use_gown && !h->use_resident;
   const bool deep = persistent == 1 && (int64_t)p.P * py.P / 4 >= (int64_t)kFlag128Ratio * h->grid;
-  if (flag && (ctas_per_sm > 4 || deep) && d.uniform64 && h->bits == 8) {
+  if (flag && (ctas_per_sm > 4 || deep) && d.uniform64) {
     h->flag_threads = 128;
     h->grid = persistent_grid128(h->device);
   }

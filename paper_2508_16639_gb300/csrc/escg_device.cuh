@@ -409,21 +409,16 @@ __device__ __forceinline__ void store_piece_uni(const LatticeDesc& d, int x0, in
   }
 }
 
-// Uniform staging: 64 x 64 interior (64 rows of 16 + 16 + 16 + 16 sites,
-// one quarter row per thread), the top and bottom rim rows, and the left and
-// right rim columns (threads 128..255, one site each).  Packed lattices: a
-// quarter row is one 32-bit (2 bits per site) or 64-bit (4 bits) load, and
-// a rim-column site comes with its group of 4, which the thread keeps
-// (returned, then passed to store_tile_uni) to write the group back whole.
-template <bool PACKED = false>
-__device__ __forceinline__ uint32_t load_tile_uni(const LatticeDesc& d, int x0, int y0, uint8_t* tile) {
-  const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = PACKED ? d.bits : 8;
-  uint32_t rim_raw = 0;
-  if (bits == 8) {
-    load_piece_uni(d, x0, y0, tile, t);
-    return rim_raw;
-  }
-  // packed: 16 sites = 32 bits (2 bits per site) or 64 bits (4 bits)
+// Piece t (0..255) of a uniform tile on a packed lattice (2 or 4 bits per
+// site), the same pieces as load_piece_uni: a quarter row is one 32-bit
+// (2 bits) or 64-bit (4 bits) load, and a rim-column site comes with its
+// group of 4, which is returned (0 for the other pieces) for
+// store_piece_uni_packed to write the group back whole.  The other three
+// sites of that group belong to the neighbouring block, which no visit
+// updates while this one runs.
+__device__ __forceinline__ uint32_t load_piece_uni_packed(const LatticeDesc& d, int x0, int y0, uint8_t* tile,
+                                                          int t, int bits) {
+  const int L = d.L, pitch = d.pitch;
   auto quarter = [&](int r, int gy, int q) {
     const uint8_t* row = d.lat + (size_t)gy * pitch;
     uint32_t lo, hi;
@@ -442,6 +437,7 @@ __device__ __forceinline__ uint32_t load_tile_uni(const LatticeDesc& d, int x0, 
     dst[0] = make_uint2(unpack4(lo, bits), unpack4(lo >> sh, bits));
     dst[1] = make_uint2(unpack4(hi, bits), unpack4(hi >> sh, bits));
   };
+  uint32_t rim_raw = 0;
   quarter(t >> 2, y0 + (t >> 2), t & 3);
   if (t < 8) {
     const int r = (t < 4) ? -1 : kUniB;
@@ -455,14 +451,11 @@ __device__ __forceinline__ uint32_t load_tile_uni(const LatticeDesc& d, int x0, 
   return rim_raw;
 }
 
-template <bool PACKED = false>
-__device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int y0, const uint8_t* tile,
-                                               uint32_t rim_raw) {
-  const int L = d.L, pitch = d.pitch, t = threadIdx.x, bits = PACKED ? d.bits : 8;
-  if (bits == 8) {
-    store_piece_uni(d, x0, y0, tile, t);
-    return;
-  }
+// Writes back piece t as load_piece_uni_packed loaded it; rim_raw is the
+// group that call returned for the same piece.
+__device__ __forceinline__ void store_piece_uni_packed(const LatticeDesc& d, int x0, int y0, const uint8_t* tile,
+                                                       int t, int bits, uint32_t rim_raw) {
+  const int L = d.L, pitch = d.pitch;
   auto quarter = [&](int r, int gy, int q) {
     uint8_t* row = d.lat + (size_t)gy * pitch;
     const uint2* src = reinterpret_cast<const uint2*>(tile + tidx(r, 16 * q, kUniSP));
@@ -486,6 +479,30 @@ __device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int
                        ((uint32_t)tile[tidx(r, c, kUniSP)] << (8 * e));
     store_group(d.lat + (size_t)(y0 + r) * pitch, gx & ~3, bits, pack4(u, bits));
   }
+}
+
+// Uniform staging: 64 x 64 interior (64 rows of 16 + 16 + 16 + 16 sites,
+// one quarter row per thread), the top and bottom rim rows, and the left and
+// right rim columns (threads 128..255, one site each), piece threadIdx.x.
+// Packed lattices: the returned rim group goes back to store_tile_uni.
+template <bool PACKED = false>
+__device__ __forceinline__ uint32_t load_tile_uni(const LatticeDesc& d, int x0, int y0, uint8_t* tile) {
+  const int t = threadIdx.x, bits = PACKED ? d.bits : 8;
+  if (bits == 8) {
+    load_piece_uni(d, x0, y0, tile, t);
+    return 0;
+  }
+  return load_piece_uni_packed(d, x0, y0, tile, t, bits);
+}
+
+template <bool PACKED = false>
+__device__ __forceinline__ void store_tile_uni(const LatticeDesc& d, int x0, int y0, const uint8_t* tile,
+                                               uint32_t rim_raw) {
+  const int t = threadIdx.x, bits = PACKED ? d.bits : 8;
+  if (bits == 8)
+    store_piece_uni(d, x0, y0, tile, t);
+  else
+    store_piece_uni_packed(d, x0, y0, tile, t, bits, rim_raw);
 }
 
 // Loads the transition table (built on the host) and the fine order.

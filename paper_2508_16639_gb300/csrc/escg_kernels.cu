@@ -197,15 +197,15 @@ __device__ __forceinline__ void own_fine_phases(const LatticeDesc& d, int bx, in
                                                 uint32_t ord, const uint8_t* trans);
 
 // NT = 256: one quad (2 x 2 sub-blocks) per thread, up to 4 CTAs per SM;
-// NT = 128 (uniform, one byte per site): two quads per thread stepped
-// pairwise (own_fine_phases), up to 8 CTAs per SM -- twice the visits in
-// flight per SM for the same number of threads.
+// NT = 128 (uniform geometry, any bits per site): two quads per thread
+// stepped pairwise (own_fine_phases), up to 8 CTAs per SM -- twice the
+// visits in flight per SM for the same number of threads.
 // VAR (uniform geometry, one byte per site): a rule variant on 64 x 64
 // blocks -- bit 0 a reflecting boundary, bit 1 the Moore neighbourhood.
 template <bool UNI, bool PACKED = false, int NT = kPersistentThreads, int VAR = 0>
 __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
     persistent_kernel(PersistentArgs a) {
-  static_assert(NT == kPersistentThreads || (NT == 128 && UNI && !PACKED), "128-thread CTAs: uniform bytes only");
+  static_assert(NT == kPersistentThreads || (NT == 128 && UNI), "128-thread CTAs: uniform geometry only");
   static_assert(VAR == 0 || (UNI && !PACKED && NT == kPersistentThreads), "variants: uniform bytes, 256 threads");
   __shared__ VisitSmem sm;
   __shared__ uint16_t stash[(UNI || !PACKED) ? 1 : kStashWords];
@@ -300,12 +300,23 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
         if (VAR & 2) corner_uni(d, x0, y0, sm.tile, tid, true);
       } else if (NT == 128) {
         const int x0 = bx * kUniB, y0 = by * kUniB;
-        load_piece_uni(d, x0, y0, sm.tile, tid);
-        load_piece_uni(d, x0, y0, sm.tile, tid + 128);
+        uint32_t rim_raw = 0;   // packed: the rim group of piece tid + 128
+        if (PACKED) {
+          load_piece_uni_packed(d, x0, y0, sm.tile, tid, d.bits);
+          rim_raw = load_piece_uni_packed(d, x0, y0, sm.tile, tid + 128, d.bits);
+        } else {
+          load_piece_uni(d, x0, y0, sm.tile, tid);
+          load_piece_uni(d, x0, y0, sm.tile, tid + 128);
+        }
         __syncthreads();
         own_fine_phases(d, bx, by, m, sm.tile, sm.forder, reinterpret_cast<const uint8_t*>(sm.trans));
-        store_piece_uni(d, x0, y0, sm.tile, tid);
-        store_piece_uni(d, x0, y0, sm.tile, tid + 128);
+        if (PACKED) {
+          store_piece_uni_packed(d, x0, y0, sm.tile, tid, d.bits, 0u);
+          store_piece_uni_packed(d, x0, y0, sm.tile, tid + 128, d.bits, rim_raw);
+        } else {
+          store_piece_uni(d, x0, y0, sm.tile, tid);
+          store_piece_uni(d, x0, y0, sm.tile, tid + 128);
+        }
       } else if (UNI) {
         visit_uniform<false, PACKED>(d, bx, by, m, sm);
       } else {
@@ -1637,6 +1648,8 @@ cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t st
       persistent_kernel<true, false, kPersistentThreads, 3><<<grid, kPersistentThreads, 0, stream>>>(a);
   } else if (a.threads == 128 && a.d.uniform64 && a.d.bits == 8)
     persistent_kernel<true, false, 128><<<grid, 128, 0, stream>>>(a);
+  else if (a.threads == 128 && a.d.uniform64)
+    persistent_kernel<true, true, 128><<<grid, 128, 0, stream>>>(a);
   else if (a.d.uniform64 && a.d.bits != 8)
     persistent_kernel<true, true><<<grid, kPersistentThreads, 0, stream>>>(a);
   else if (a.d.uniform64)
@@ -1734,7 +1747,12 @@ cudaError_t launch_ll_merge(const LatticeDesc& d, const unsigned long long* ob, 
 int persistent_grid128(int device) {
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  // the same grid for one byte and for 2 or 4 bits per site: the fewer CTAs
+  // of the two builds that an SM holds
+  int per_sm_packed = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<true, false, 128>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_packed, persistent_kernel<true, true, 128>, 128, 0);
+  if (per_sm_packed < per_sm) per_sm = per_sm_packed;
   if (per_sm > 8) per_sm = 8;
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;

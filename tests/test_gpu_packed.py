@@ -165,3 +165,50 @@ def test_packed_block_owners_L1024(bits):
     _, log = g.counts_log()
     _, olog, _ = O.run_observed(o, D, 1.0, 1.0, X, seed, 7, log_every=3)
     assert np.array_equal(log, olog)
+
+
+@pytest.mark.parametrize("bits,S,K", [(2, 3, (1,)), (4, 5, (1, 2))])
+@pytest.mark.parametrize("L,ctas", [(128, 8), (384, 6), (1024, 8)])
+def test_packed_flag_kernel_128_thread_ctas(L, ctas, bits, S, K):
+    """The flag kernel's 128-thread build on a packed lattice (more than 4
+    CTAs per SM requested): each thread stages and writes back two pieces of
+    the tile, one of them a rim-column site merged into its packed group of
+    4; bit-exact after every MCS and at every log point."""
+    seed = 9100 + L + bits
+    D = O.circulant(S, K)
+    X = 2.0 + L / 64
+    g = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.2, persistent=3, ctas_per_sm=ctas, log_every=2,
+                  bits_per_site=bits)
+    assert g.update_kernel == "persistent_kernel"
+    o = O.init(L, S, 0.2, seed)
+    for m in range(3):
+        g.run(1)
+        o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 1, mcs_begin=m)
+        assert np.array_equal(g.snapshot(), o), m
+    g.run(5)
+    o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 5, mcs_begin=3)
+    assert np.array_equal(g.snapshot(), o)
+    _, log = g.counts_log()
+    _, olog, _ = O.run_observed(O.init(L, S, 0.2, seed), D, 1.0, 1.0, X, seed, 8, log_every=2)
+    assert np.array_equal(log, olog)
+
+
+@pytest.mark.parametrize("bits", [2, 4])
+def test_packed_flag_kernel_128_thread_default_L6400(bits):
+    """L = 6400 (2500 blocks per coarse phase) on a packed lattice: the
+    default selection runs the flag kernel's 128-thread build; bit-exact
+    against the oracle after 2 MCS and equal to the one-byte lattice after 6."""
+    L, S, seed = 6400, 3, 6400 + bits
+    D = O.circulant(S, (1,))
+    X = 2.0 * 1e-4 * L * L
+    g = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.25, bits_per_site=bits)
+    assert g.update_kernel == "persistent_kernel"
+    g.run(2)
+    o, _ = O.replay_run(O.init(L, S, 0.25, seed), D, 1.0, 1.0, X, seed, 2)
+    assert np.array_equal(g.snapshot(), o)
+    b = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.25)
+    g.run(4)
+    b.run(6)
+    assert np.array_equal(g.snapshot(), b.snapshot())
+    g.close()
+    b.close()

@@ -401,10 +401,9 @@ def test_async_host_steps_on_two_handles():
 
 @pytest.mark.parametrize("bits", [8, 2])
 def test_maximum_size_lattice(bits):
-    """The largest lattice the boundary takes (L = 16384, 268 M sites; the
-    byte lattice runs the flag kernel's 128-thread build, the packed one the
-    256-thread build): bit-exact against the replay oracle after one MCS, and
-    the counts add up to N."""
+    """The largest lattice the boundary takes (L = 16384, 268 M sites; both
+    run the flag kernel's 128-thread build): bit-exact against the replay
+    oracle after one MCS, and the counts add up to N."""
     L, S, seed = 16384, 3, 16384 + bits
     D = O.circulant(S, (1,))
     X = 2.0 * 1e-4 * L * L
