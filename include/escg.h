@@ -113,7 +113,11 @@ typedef struct {
                                     CUDA events on the handle's stream (read
                                     back with escg_kernel_time)               */
     int32_t ctas_per_sm;         /* persistent CTAs per SM (0: as many as fit);
-                                    physical mapping only, results unchanged  */
+                                    for the block owners (one CTA per group of
+                                    2x2 blocks) the least packing: at least
+                                    this many per SM, leaving the other SMs to
+                                    other streams; physical mapping only,
+                                    results unchanged                         */
     const double* dominance_prob;/* optional S*S row-major edge probabilities
                                     (Park, Chen and Szolnoki's probabilistic
                                     dominance, the paper's section "Park,

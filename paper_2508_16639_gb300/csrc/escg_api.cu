@@ -482,7 +482,8 @@ int select_kernel(escg* h, int persistent, int ctas_per_sm) {
   // 2x2 group of blocks at once.
   if (d.uniform64 && (persistent == 5 || (persistent == 1 && (p.P / 2) * (py.P / 2) >= 9))) {
     int dyn = 0, nt = 0, per_sm = 0;
-    if (persistent_own_config(d, h->device, &dyn, &nt, &per_sm) > 0 && (persistent == 5 || per_sm <= 3)) {
+    if (persistent_own_config(d, h->device, &dyn, &nt, &per_sm, ctas_per_sm) > 0 &&
+        (persistent == 5 || per_sm <= 3)) {
       if (ensure_records(h, (size_t)p.P * py.P * kRecordWords) != ESCG_OK) return ESCG_ENOMEM;
       h->use_own = true;
       h->own_dyn = dyn;
@@ -497,7 +498,7 @@ int select_kernel(escg* h, int persistent, int ctas_per_sm) {
   if (!d.uniform64 && d.nbh == 4 &&
       (persistent == 5 || (persistent == 1 && (p.P / 2) * (py.P / 2) >= 2))) {
     GownConfig cfg{};
-    if (persistent_gown_config(d, h->device, &cfg) > 0 &&
+    if (persistent_gown_config(d, h->device, &cfg, ctas_per_sm) > 0 &&
         (persistent == 5 || cfg.ctas_per_sm <= kGownDefaultPerSM)) {
       if (ensure_records(h, (size_t)p.P * py.P * kGRecordWords) != ESCG_OK) return ESCG_ENOMEM;
       h->use_gown = true;

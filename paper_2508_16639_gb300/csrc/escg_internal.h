@@ -114,8 +114,11 @@ int persistent_ll_grid(int device);
 // All (P/2)(Py/2) CTAs must be resident at once: persistent_own_config returns
 // the grid size, the CTA size (128 or 256 threads), the shared-memory
 // padding that spreads the grid over the SMs and the CTAs per SM that
-// leaves, or 0 when the device cannot hold the whole grid.
-int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int* threads, int* ctas_per_sm);
+// leaves, or 0 when the device cannot hold the whole grid.  min_per_sm > 0
+// packs at least that many CTAs per SM (fewer SMs, the rest left to other
+// streams' kernels).
+int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int* threads, int* ctas_per_sm,
+                          int min_per_sm = 0);
 cudaError_t launch_persistent_own(const PersistentArgs& a, int dyn_bytes, int threads, cudaStream_t stream);
 // Block owners on any partition of the von Neumann rule (escg_owner.cu):
 // periodic or reflecting, squares and rectangles, any bits per site; blocks
@@ -134,8 +137,8 @@ struct GownArgs {
   int32_t tile_stride;
 };
 // Grid size (0: this lattice or device cannot run the kernel) and launch
-// configuration.
-int persistent_gown_config(const LatticeDesc& d, int device, GownConfig* cfg);
+// configuration; min_per_sm as for persistent_own_config.
+int persistent_gown_config(const LatticeDesc& d, int device, GownConfig* cfg, int min_per_sm = 0);
 cudaError_t launch_persistent_gown(const PersistentArgs& a, const GownConfig& cfg, cudaStream_t stream);
 // Completes the lattice array after a mailbox launch that ended at MCS
 // m_end: every edge cell of a block that a neighbour's visit wrote last (in

@@ -1699,7 +1699,8 @@ static int own_padding(int per_sm, int smem_sm, int reserved, int optin) {
   }
 }
 
-int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int* threads, int* ctas_per_sm) {
+int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int* threads, int* ctas_per_sm,
+                          int min_per_sm) {
   const int groups = (d.P / 2) * (d.Py / 2);
   int sms = 0, smem_sm = 0, reserved = 0, optin = 0, coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
@@ -1711,7 +1712,8 @@ int persistent_own_config(const LatticeDesc& d, int device, int* dyn_bytes, int*
   if (sms <= 0) return 0;
   // the padding spreads the grid over all SMs: at most ceil(groups / SMs)
   // CTAs per SM
-  const int per_sm = (groups + sms - 1) / sms;
+  int per_sm = (groups + sms - 1) / sms;
+  if (per_sm < min_per_sm) per_sm = min_per_sm;
   // 256 threads while 4 fit an SM (54 registers); beyond, 128 (a 256-thread
   // build for 5 per SM, held to 48 registers, was measured slower)
   const int nt = per_sm <= 4 ? 256 : 128;

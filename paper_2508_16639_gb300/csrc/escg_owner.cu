@@ -557,7 +557,7 @@ static int gown_padding(int per_sm, int smem_sm, int reserved, int optin, int ne
   }
 }
 
-int persistent_gown_config(const LatticeDesc& d, int device, GownConfig* cfg) {
+int persistent_gown_config(const LatticeDesc& d, int device, GownConfig* cfg, int min_per_sm) {
   if (d.nbh != 4 || d.P < 2 || d.Py < 2) return 0;
   // widest block and its fine segments on each axis
   auto axis_ok = [](const AxisGeom& g, int* wmax, int* qmax) {
@@ -586,7 +586,8 @@ int persistent_gown_config(const LatticeDesc& d, int device, GownConfig* cfg) {
   if (sms <= 0) return 0;
   const int tile_bytes = ((wy + 2) * (((kColOff + wx + 1) + 15) & ~15) + 15) & ~15;
   const int need_dyn = 4 * tile_bytes + 4 * kGSlots * nt * (int)sizeof(uint32_t);
-  const int per_sm = (groups + sms - 1) / sms;
+  int per_sm = (groups + sms - 1) / sms;
+  if (per_sm < min_per_sm) per_sm = min_per_sm;
   const bool refl = d.reflect != 0;
   int dyn;
   if (nt == 256)

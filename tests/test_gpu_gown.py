@@ -188,3 +188,26 @@ def test_gown_bounded_wait_times_out_with_status():
     g.run(2)
     o, _ = O.replay_run(ref, O.circulant(S, [1]), 1.0, 1.0, 1.0, 3, 2)
     assert np.array_equal(g.snapshot(), o)
+
+
+@pytest.mark.parametrize("L,per_sm", [(400, 3), (800, 2), (1024, 4), (1024, 8)])
+def test_owners_packed_per_sm_concurrent_handles(L, per_sm):
+    """Block owners with a packing request (at least per_sm CTAs per SM, the
+    other SMs left free): three handles on their own streams, each
+    bit-exact against the replay oracle after 5 MCS (generic owners at
+    L = 400 and 800, uniform owners at 1024, 128-thread CTAs at 8 per SM)."""
+    torch = pytest.importorskip("torch")
+    S, X = 3, 3.0
+    D = E.circulant(S, [1])
+    hs = [E.Lattice(L, S, D, (1.0, 1.0, X), 300 + i, p_empty=0.25, persistent=5, ctas_per_sm=per_sm,
+                    stream=torch.cuda.Stream()) for i in range(3)]
+    expect = "persistent_own_kernel" if L % 128 == 0 else "persistent_gown_kernel"
+    assert all(h.update_kernel == expect for h in hs)
+    for h in hs:
+        h.run(2)
+    for h in hs:
+        h.run(3)
+    for i, h in enumerate(hs):
+        o, _ = O.replay_run(O.init(L, S, 0.25, 300 + i), O.circulant(S, [1]), 1.0, 1.0, X, 300 + i, 5)
+        assert np.array_equal(h.snapshot(), o), i
+        h.close()
