@@ -365,6 +365,88 @@ __device__ __forceinline__ void store_tile_generic(const LatticeDesc& d, int x0,
   }
 }
 
+// Generic tiles of one-byte lattices are staged in aligned 8-byte groups.
+// The tile's column origin depends on the block, origin = 8 + (x0 mod 8), so
+// that every lattice column that is a multiple of 8 sits on an 8-byte
+// boundary of the tile; the row pitch round_up(bw + 23, 16) holds the groups
+// from the one with the left rim column to the one with the right rim
+// column.  The sites these groups bring in beyond the rim columns, and the
+// corners, belong to the block's eight neighbours, which no visit updates
+// while this one runs, and lie at least a block width (32 sites or more)
+// away from every other block's tile; the fine phases never reach them, so
+// they go back to the lattice as they came.  Row padding beyond column L is
+// neither needed nor written: the lattice's last group of a row is written
+// back one byte at a time.
+__device__ __forceinline__ int gen_origin(int x0) { return 8 + (x0 & 7); }
+__device__ __forceinline__ int gen_pitch(int bw) { return (bw + 23 + 15) & ~15; }
+
+// Rows r = -1 .. bh of a generic tile, two per warp and pass (16 lanes per
+// row, one 8-byte group per lane); the periodic rim columns of the blocks at
+// the lattice's left and right edges come as single bytes.  The loads of
+// kPass passes are issued before any of them is written to the tile.
+__device__ __forceinline__ void load_tile_aligned(const LatticeDesc& d, int x0, int y0, int bw, int bh,
+                                                  uint8_t* tile, int sp, int origin) {
+  constexpr int kPass = 5;
+  const int L = d.L, lane = threadIdx.x & 31, l16 = lane & 15, nw = blockDim.x >> 5;
+  const int g_lo = max(x0 - 1, 0) >> 3, g_hi = min(x0 + bw, L - 1) >> 3;
+  const bool act = l16 <= g_hi - g_lo;
+  const int gcol = (g_lo + l16) * 8, tcol = origin + gcol - x0;
+  const bool wrap_l = !d.reflect && x0 == 0 && l16 == 0;
+  const bool wrap_r = !d.reflect && x0 + bw == L && l16 == g_hi - g_lo;
+  for (int r0 = 2 * (int)(threadIdx.x >> 5) + (lane >> 4) - 1; r0 <= bh; r0 += 2 * nw * kPass) {
+    uint2 v[kPass];
+    uint8_t wl[kPass], wr[kPass];
+#pragma unroll
+    for (int i = 0; i < kPass; ++i) {
+      const int r = r0 + 2 * nw * i;
+      const int gy = r <= bh ? tile_row_gy(d, y0, r) : -1;
+      v[i] = make_uint2(0u, 0u);
+      wl[i] = wr[i] = 0;
+      if (!act || gy < 0) continue;
+      const uint8_t* row = d.lat + (size_t)gy * d.pitch;
+      v[i] = __ldcg(reinterpret_cast<const uint2*>(row + gcol));
+      if (wrap_l) wl[i] = __ldcg(row + L - 1);
+      if (wrap_r) wr[i] = __ldcg(row);
+    }
+#pragma unroll
+    for (int i = 0; i < kPass; ++i) {
+      const int r = r0 + 2 * nw * i;
+      if (!act || r > bh || tile_row_gy(d, y0, r) < 0) continue;
+      uint8_t* trow = tile + (r + 1) * sp;
+      *reinterpret_cast<uint2*>(trow + tcol) = v[i];
+      if (wrap_l) trow[origin - 1] = wl[i];
+      if (wrap_r) trow[origin + bw] = wr[i];
+    }
+  }
+}
+
+// Writes back what load_tile_aligned staged.
+__device__ __forceinline__ void store_tile_aligned(const LatticeDesc& d, int x0, int y0, int bw, int bh,
+                                                   const uint8_t* tile, int sp, int origin) {
+  const int L = d.L, lane = threadIdx.x & 31, l16 = lane & 15, nw = blockDim.x >> 5;
+  const int g_lo = max(x0 - 1, 0) >> 3, g_hi = min(x0 + bw, L - 1) >> 3;
+  const bool act = l16 <= g_hi - g_lo;
+  const int gcol = (g_lo + l16) * 8, tcol = origin + gcol - x0;
+  const bool wrap_l = !d.reflect && x0 == 0 && l16 == 0;
+  const bool wrap_r = !d.reflect && x0 + bw == L && l16 == g_hi - g_lo;
+  for (int r = 2 * (int)(threadIdx.x >> 5) + (lane >> 4) - 1; r <= bh; r += 2 * nw) {
+    const int gy = tile_row_gy(d, y0, r);
+    if (!act || gy < 0) continue;
+    uint8_t* row = d.lat + (size_t)gy * d.pitch;
+    const uint8_t* trow = tile + (r + 1) * sp;
+    const uint2 v = *reinterpret_cast<const uint2*>(trow + tcol);
+    if (gcol + 8 <= L) {
+      *reinterpret_cast<uint2*>(row + gcol) = v;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (gcol + e < L) row[gcol + e] = (uint8_t)(((e < 4) ? v.x : v.y) >> (8 * (e & 3)));
+    }
+    if (wrap_l) row[L - 1] = trow[origin - 1];
+    if (wrap_r) row[0] = trow[origin + bw];
+  }
+}
+
 // Piece t (0..255) of a uniform one-byte-per-site tile: a 16-byte quarter
 // row of the interior and, for t < 8, of the top / bottom rim rows, for
 // t >= 128 one cell of the left / right rim columns.  load_tile_uni and
@@ -729,10 +811,15 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
                                               VisitSmem& sm, uint16_t* stash = nullptr) {
   const BlockSpan X = block_span(d.ax, bx), Y = block_span(d.ay, by);
   const int x0 = X.s0, bw = X.w, y0 = Y.s0, bh = Y.w;
-  const int sp = tile_pitch(bw);
+  // packed lattices: the byte staging with the stash; one byte per site:
+  // aligned 8-byte groups
+  const int sp = PACKED ? tile_pitch(bw) : gen_pitch(bw), org = PACKED ? kColOff : gen_origin(x0);
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (OWN_FORDER && tid == 0) sm.forder = fine_order(d, bx, by, m);
-  load_tile_generic<PACKED>(d, x0, y0, bw, bh, sm.tile, sp, stash);
+  if (PACKED)
+    load_tile_generic<true>(d, x0, y0, bw, bh, sm.tile, sp, stash);
+  else
+    load_tile_aligned(d, x0, y0, bw, bh, sm.tile, sp, org);
   __syncthreads();
   const uint32_t s1 = (uint32_t)d.S + 1u;
   const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans);
@@ -759,7 +846,7 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
       const uint32_t g = (uint32_t)(Y.f0 + fy) * (uint32_t)d.GQ + (uint32_t)(X.f0 + fx);
       // ceil(65536 / wx) for the fine widths 2, 3, 4
       const uint32_t inv_wx = wx == 2 ? 32768u : (wx == 3 ? 21846u : 16384u);
-      const int base = tidx(sy, sx, sp);
+      const int base = (sy + 1) * sp + sx + org;
       for (uint32_t j = 0; 4u * j < nk; ++j) {
         const uint4 x = philox10_rk(make_uint4(j, g, m, kTagStep), d.rk);
         const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
@@ -776,7 +863,10 @@ __device__ __forceinline__ void visit_generic(const LatticeDesc& d, int bx, int 
     }
     __syncthreads();
   }
-  store_tile_generic<PACKED>(d, x0, y0, bw, bh, sm.tile, sp, stash);
+  if (PACKED)
+    store_tile_generic<true>(d, x0, y0, bw, bh, sm.tile, sp, stash);
+  else
+    store_tile_aligned(d, x0, y0, bw, bh, sm.tile, sp, org);
 }
 
 // ---------------------------------------------------------------------------
@@ -943,10 +1033,14 @@ __device__ __forceinline__ void count_tile_generic(const uint8_t* tile, int sp, 
   }
 }
 
+// The tile as visit_generic<.., PACKED> left it.
+template <bool PACKED = false>
 __device__ __forceinline__ void count_visit_generic(const LatticeDesc& d, int bx, int by, VisitSmem& sm,
                                                     int k, int sV, int sH, int sD) {
-  const int bw = block_span(d.ax, bx).w, bh = block_span(d.ay, by).w;
-  count_tile_generic(sm.tile, tile_pitch(bw), kColOff, bw, bh, sm.hist, blockDim.x >> 5, k, sV, sH, sD);
+  const BlockSpan X = block_span(d.ax, bx);
+  const int bw = X.w, bh = block_span(d.ay, by).w;
+  const int sp = PACKED ? tile_pitch(bw) : gen_pitch(bw), org = PACKED ? kColOff : gen_origin(X.s0);
+  count_tile_generic(sm.tile, sp, org, bw, bh, sm.hist, blockDim.x >> 5, k, sV, sH, sD);
 }
 
 }  // namespace escg_impl

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
         } else if (UNI) {
           count_visit_uni<kUniSP, kColOff>(sm.tile, sm.hist, d.S, k, sV, sH, sD);
         } else {
-          count_visit_generic(d, bx, by, sm, k, sV, sH, sD);
+          count_visit_generic<PACKED>(d, bx, by, sm, k, sV, sH, sD);
         }
       }
       __syncthreads();

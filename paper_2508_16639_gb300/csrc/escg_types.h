@@ -14,7 +14,7 @@ constexpr uint32_t kTagInit = 1, kTagOrder = 2, kTagFineOrder = 3, kTagStep = 4;
 // interior (keeps interior rows 8-byte aligned), and the largest tile pitch.
 constexpr int kMaxBlock = 96;
 constexpr int kColOff = 8;
-constexpr int kMaxTilePitch = 112;   // round_up(kColOff + kMaxBlock + 1, 16)
+constexpr int kMaxTilePitch = 128;   // round_up(kMaxBlock + 23, 16): the aligned generic tile
 constexpr int kMaxTileRows = kMaxBlock + 2;
 constexpr int kMaxFine = kMaxBlock / 2;  // fine segments per block axis
 constexpr int kMaxStates = 16;           // S <= 15
