@@ -436,7 +436,7 @@ def _park(args, rank, world, dist):
     out = {"metric": "probabilistic-dominance ensemble runs/s", "runs": len(specs_all),
            "seconds": secs, "setup_seconds": t1 - t0, "runs_per_s": len(specs_all) / secs,
            "site_updates_per_s": R.sum_over_ranks(site_updates, dist, device="cuda") / secs,
-           "threads": b.threads, "launches": b.launches,
+           "threads": b.threads, "staging": "tma" if b.uses_tma else "plain", "launches": b.launches,
            "mean_mcs": float(np.mean(mcs)),
            "surviving_species_histogram": {k: v.tolist() for k, v in sorted(surv.items())},
            "config": {"workload": f"{len(specs_all)} replicas: L=100, 8 species beating the next 3 with "

@@ -28,7 +28,7 @@ def run_batch(reps, log_every: int = 10, threads: int = 0, use_graph: bool = Tru
         bins[key] = (k + int(e), n + 1)
     out = {"runs": len(reps), "seconds": t2 - t1, "setup_seconds": t1 - t0,
            "runs_per_s": len(reps) / (t2 - t1), "site_updates_per_s": site_updates / (t2 - t1),
-           "threads": b.threads, "launches": b.launches,
+           "threads": b.threads, "staging": "tma" if b.uses_tma else "plain", "launches": b.launches,
            "extinct_fraction": float(np.mean(ext)),
            "extinction_by_bin": {k: round(a / n, 4) for k, (a, n) in sorted(bins.items())},
            "mean_mcs": float(np.mean(mcs))}

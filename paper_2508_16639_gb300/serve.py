@@ -67,7 +67,7 @@ def serve(requests, server: Server | None = None, time_scale: float = 1.0, **ser
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
             "mean_latency_s": float(lat.mean()), "latencies_s": lat.tolist(),
             "site_updates": float(sum(done_mcs[i] * requests[i]["L"] ** 2 for i in range(n))),
-            "threads": srv.threads,
+            "threads": srv.threads, "staging": "tma" if srv.uses_tma else "plain",
             # arrival to result = (at most one step until submission) + queue
             # wait (submission to admission) + service (admission to the step
             # that retires the run)
