@@ -585,6 +585,49 @@ __device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t
   }
 }
 
+// Write-back of a TMA-staged tile (lattice column xal + t at tile column t,
+// xal = x0 - xoff a multiple of 16) by the CONS consumer threads: two rows
+// per warp and pass, 16 lanes per row, one aligned 8-byte group per lane --
+// the interior rows and the rim rows that the box read from the lattice
+// whole (sites beyond the rims and the corners included, which belong to the
+// block's eight neighbours, idle during the visit, and go back as the box
+// read them), the lattice's last group of a row byte by byte (no row
+// padding written); a wrapped rim row (placed beside the box, the block's
+// columns only) byte by byte over those columns, and the wrapped rim-column
+// cells of the interior rows one byte each.
+template <int CONS>
+__device__ __forceinline__ void btma_store(const LatticeDesc& d, int x0, int y0, int bw, int bh, int bx, int by,
+                                           const uint8_t* tile, int xoff) {
+  const int L = d.L, P = d.P, lane = threadIdx.x & 31, l16 = lane & 15;
+  const int g_lo = max(x0 - 1, 0) >> 3, g_hi = min(x0 + bw, L - 1) >> 3;
+  const bool act = l16 <= g_hi - g_lo;
+  const int gcol = (g_lo + l16) * 8, tcol = gcol - (x0 - xoff);
+  const bool wrap_top = by == 0, wrap_bot = by == P - 1;
+  const bool wl = x0 == 0 && l16 == 0, wr = x0 + bw == L && l16 == g_hi - g_lo;
+  if (!act) return;
+  for (int r = 2 * (int)(threadIdx.x >> 5) + (lane >> 4) - 1; r <= bh; r += 2 * (CONS / 32)) {
+    const bool wrapped = (r < 0 && wrap_top) || (r >= bh && wrap_bot);
+    const int gy = r < 0 ? (wrap_top ? L - 1 : y0 - 1) : (r >= bh ? (wrap_bot ? 0 : y0 + bh) : y0 + r);
+    uint8_t* row = d.lat + (size_t)gy * d.pitch;
+    const uint8_t* trow = tile + (r + 1) * kBSP;
+    const uint2 v = *reinterpret_cast<const uint2*>(trow + tcol);
+    if (!wrapped && gcol + 8 <= L) {
+      *reinterpret_cast<uint2*>(row + gcol) = v;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int c = gcol + e;
+        if (c < L && (!wrapped || (c >= x0 && c < x0 + bw)))
+          row[c] = (uint8_t)(((e < 4) ? v.x : v.y) >> (8 * (e & 3)));
+      }
+    }
+    if (r >= 0 && r < bh) {
+      if (wl) row[L - 1] = trow[xoff - 1];
+      if (wr) row[0] = trow[xoff + bw];
+    }
+  }
+}
+
 template <int CONS>
 __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
   const BatchArgs& a = ta.a;
@@ -665,8 +708,8 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
       const int sV = slot_of(ord, colour ^ 2), sH = slot_of(ord, colour ^ 1), sD = slot_of(ord, colour ^ 3);
       count_tile_generic(tile, kBSP, xoff, bw, bh, sm.hist, CONS / 32, k, sV, sH, sD);
     }
-    // write back block interior and rim strips (never the corners), by rows
-    store_tile_generic(d, it.x0, it.y0, bw, bh, tile, kBSP, nullptr, xoff, CONS / 32);
+    // write back the block interior and rim strips
+    btma_store<CONS>(d, it.x0, it.y0, bw, bh, it.bx, it.by, tile, xoff);
     bar_sync_consumers(CONS);
     const int P = d.P, slot = it.slot, bx = it.bx, by = it.by;
     if (log_point) {
