@@ -402,7 +402,6 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64)) batch_residen
 constexpr int kBSP = 144, kBRows = kMaxBlock + 2;
 constexpr uint32_t kBBoxBytes = (uint32_t)(kBSP * kBRows);   // 14112
 constexpr int kBTileStride = 14208;                          // 128-byte multiple
-constexpr uint32_t kBMbarLimit = 1u << 26;
 // Suspending waits of the warp-specialised chunk kernel: hint and bound
 // (about 4 s at 2 GHz, the order of the flag waits' spin limit).
 constexpr uint32_t kBMbarHintNs = 2000;
