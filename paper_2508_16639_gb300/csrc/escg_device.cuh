@@ -100,6 +100,62 @@ __device__ __forceinline__ void apply_rule(uint8_t* __restrict__ tile, const uin
   }
 }
 
+// apply_rule on a pair already read from the tile (a at ti, b at tj).
+__device__ __forceinline__ void apply_rule_ab(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
+                                              int ti, int tj, uint32_t a, uint32_t b, uint32_t u, uint32_t tx,
+                                              uint32_t txi, uint32_t s1) {
+  if (u < tx) {
+    tile[ti] = (uint8_t)b;
+    tile[tj] = (uint8_t)a;
+  } else {
+    const uint32_t pair = a * s1 + b;
+    const uint32_t tp = reinterpret_cast<const uint32_t*>(trans)[kTransPairs + pair];
+    const uint32_t act = (u >= txi) ? 2u : (u < tp ? 1u : 3u);
+    const uint32_t nn = trans[pair * 4u + act];
+    tile[ti] = (uint8_t)(nn & 15u);
+    tile[tj] = (uint8_t)(nn >> 4);
+  }
+}
+
+// The cell and neighbour tile indices and the action draw of attempt()'s
+// step (w, n4 = 4 * cells, base, wx, inv_wx, sp as there).
+__device__ __forceinline__ void locate(uint32_t w, uint32_t n4, int base, int wx, uint32_t inv_wx, int sp,
+                                       int& ti, int& tj, uint32_t& u) {
+  const uint32_t hi = __umulhi(w, n4);
+  u = w * n4;
+  const uint32_t site = hi >> 2, dir = hi & 3u;
+  const uint32_t r = (site * inv_wx) >> 16;
+  const uint32_t c = site - r * (uint32_t)wx;
+  ti = base + (int)r * sp + (int)c;
+  const int mag = (dir & 2u) ? 1 : sp;
+  tj = ti + ((dir & 1u) ? mag : -mag);
+}
+
+// The steps of a generic sub-block from the words wv[] in registers, each step's cell and neighbour located while the previous
+// step's pair is read (the locating arithmetic sits ahead of the branch of
+// the previous step's rule instead of behind it).
+// Steps t < n run (n <= N).
+template <int N>
+__device__ __forceinline__ void attempts_ahead(uint8_t* __restrict__ tile, const uint8_t* __restrict__ trans,
+                                               const uint32_t* wv, uint32_t n, uint32_t n4, int base, int wx,
+                                               uint32_t inv_wx, int sp, uint32_t tx, uint32_t txi, uint32_t s1) {
+  int ti, tj;
+  uint32_t u;
+  locate(wv[0], n4, base, wx, inv_wx, sp, ti, tj, u);
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    if ((uint32_t)t >= n) break;
+    const uint32_t a = tile[ti], b = tile[tj];
+    int ti2 = 0, tj2 = 0;
+    uint32_t u2 = 0;
+    if (t + 1 < N) locate(wv[t + 1], n4, base, wx, inv_wx, sp, ti2, tj2, u2);
+    apply_rule_ab(tile, trans, ti, tj, a, b, u, tx, txi, s1);
+    ti = ti2;
+    tj = tj2;
+    u = u2;
+  }
+}
+
 // One elementary step (Alg. 3) of a generic sub-block.  w: the attempt's
 // 32-bit Philox word; n4 = 4 * cells of the sub-block; base: tile index of
 // the sub-block's first cell; wx: its width; inv_wx = ceil(65536 / wx).

@@ -216,15 +216,14 @@ __device__ __forceinline__ void gown_fine_phases(const LatticeDesc& d, const GBl
       uint32_t wv[kGSlots];
 #pragma unroll
       for (int t = 0; t < kGSlots; ++t) wv[t] = (uint32_t)t < nk ? w[t * NT] : 0u;
+      if (REFLECT) {
 #pragma unroll
-      for (int t = 0; t < kGSlots; ++t) {
-        if ((uint32_t)t < nk) {
-          if (REFLECT)
+        for (int t = 0; t < kGSlots; ++t)
+          if ((uint32_t)t < nk)
             attempt_variant(tile, trans, wv[t], n4, 2, base, wx, inv_wx, sp, tx, txi, s1, true,
                             g.Y.s0 + sy, g.X.s0 + sx, d.H, d.L);
-          else
-            attempt(tile, trans, wv[t], n4, base, wx, inv_wx, sp, tx, txi, s1);
-        }
+      } else {
+        attempts_ahead<kGSlots>(tile, trans, wv, nk, n4, base, wx, inv_wx, sp, tx, txi, s1);
       }
     }
     __syncthreads();
