@@ -572,8 +572,7 @@ int persistent_gown_config(const LatticeDesc& d, int device, GownConfig* cfg, in
   int wx = 0, qx = 0, wy = 0, qy = 0;
   if (!axis_ok(d.ax, &wx, &qx) || !axis_ok(d.ay, &wy, &qy)) return 0;
   const int nq = (qx / 2) * (qy / 2);
-  const int nt = nq <= 256 ? 256 : (nq <= 512 ? 512 : 0);
-  if (nt == 0) return 0;
+  if (nq > 512) return 0;
   const int groups = (d.P / 2) * (d.Py / 2);
   int sms = 0, smem_sm = 0, reserved = 0, optin = 0, coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
@@ -583,10 +582,14 @@ int persistent_gown_config(const LatticeDesc& d, int device, GownConfig* cfg, in
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (sms <= 0) return 0;
-  const int tile_bytes = ((wy + 2) * (((kColOff + wx + 1) + 15) & ~15) + 15) & ~15;
-  const int need_dyn = 4 * tile_bytes + 4 * kGSlots * nt * (int)sizeof(uint32_t);
   int per_sm = (groups + sms - 1) / sms;
   if (per_sm < min_per_sm) per_sm = min_per_sm;
+  // one thread per quad (256 or 512); 512 also for blocks of up to 256
+  // quads when each SM holds one CTA: the visit's words are then drawn by
+  // twice the threads, two quads' worth each instead of four
+  const int nt = (nq > 256 || per_sm == 1) ? 512 : 256;
+  const int tile_bytes = ((wy + 2) * (((kColOff + wx + 1) + 15) & ~15) + 15) & ~15;
+  const int need_dyn = 4 * tile_bytes + 4 * kGSlots * nt * (int)sizeof(uint32_t);
   const bool refl = d.reflect != 0;
   int dyn;
   if (nt == 256)
