@@ -131,6 +131,7 @@ struct GownConfig {
   int threads;       // 256 or 512 (one quad per thread)
   int ctas_per_sm;
   int tile_stride;   // bytes per tile in dynamic shared memory
+  int prefetch;      // 512 threads, half of them drawing the next visit's words
 };
 struct GownArgs {
   PersistentArgs p;

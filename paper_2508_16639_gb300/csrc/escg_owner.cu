@@ -154,20 +154,21 @@ __device__ __forceinline__ void gown_stage(const LatticeDesc& d, uint8_t* tile, 
 
 // Every Philox word of the visit of block g in MCS m, by quad and fine
 // colour: W[(colour * kGSlots + t) * NT + q] is the word of attempt t of the
-// quad's sub-block of that colour (t < its cell count).  Thread i draws the
-// words of colour i mod 4 for the quads i/4 + k NT/4, k = 0..3: the sub-blocks
+// quad's sub-block of that colour (t < its cell count).  Thread i (of NT
+// drawing threads, i = t here) draws the words of colour i mod 4 for the
+// quads i/4 + k NT/4, k = 0..3: the sub-blocks
 // with 3 x 3 cells (three Philox calls) sit at the block's leading corner,
 // and this spreads them over different threads, each with four independent
 // draws in flight.
 template <int NT>
 __device__ __forceinline__ void gown_words(const LatticeDesc& d, const GBlock& g, uint32_t m,
-                                           uint32_t* __restrict__ W) {
-  const int c = threadIdx.x & 3;
+                                           uint32_t* __restrict__ W, int t) {
+  const int c = t & 3;
   uint32_t gid[4];
   int nk[4], q[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    q[k] = (int)(threadIdx.x >> 2) + k * (NT / 4);
+    q[k] = (t >> 2) + k * (NT / 4);
     int qx, qy;
     quad_at(g.qm, q[k] < g.nq ? q[k] : 0, qx, qy);
     const int fx = 2 * qx + (c & 1), fy = 2 * qy + (c >> 1);
@@ -191,8 +192,9 @@ __device__ __forceinline__ void gown_words(const LatticeDesc& d, const GBlock& g
 }
 
 // The four fine colour phases of a visit from the drawn words (fine order
-// ord), each ending with a CTA barrier.
-template <int NT, bool REFLECT>
+// ord), run by threads 0 .. NT - 1, each ending with a barrier: the CTA's
+// (BAR = false) or named barrier 1 over those NT threads (BAR = true).
+template <int NT, bool REFLECT, bool BAR = false>
 __device__ __forceinline__ void gown_fine_phases(const LatticeDesc& d, const GBlock& g, uint8_t* tile,
                                                  uint32_t ord, const uint8_t* trans,
                                                  const uint32_t* __restrict__ W) {
@@ -226,7 +228,10 @@ __device__ __forceinline__ void gown_fine_phases(const LatticeDesc& d, const GBl
         attempts_ahead<kGSlots>(tile, trans, wv, nk, n4, base, wx, inv_wx, sp, tx, txi, s1);
       }
     }
-    __syncthreads();
+    if (BAR)
+      asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    else
+      __syncthreads();
   }
 }
 
@@ -279,8 +284,16 @@ __device__ __forceinline__ void gown_store(const LatticeDesc& d, const uint8_t* 
   }
 }
 
-template <int NT, bool REFLECT>
+// PREF (512 threads, blocks of at most 256 quads): threads 0..255 run the
+// fine phases, synchronised by named barrier 1 (executed by exactly those
+// 256 threads -- warps 0..7 -- four times per visit, so its count of 256
+// always completes), while threads 256..511 draw the next visit's words
+// into the other half of a double buffer; a CTA barrier joins them after
+// the fine phases.  The first visit of a launch draws its own words.
+template <int NT, bool REFLECT, bool PREF>
 __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) persistent_gown_kernel(const __grid_constant__ GownArgs ga) {
+  static_assert(!PREF || NT == 512, "word prefetch: 512-thread CTAs");
+  constexpr int kHalf = NT / 2;   // PREF: the fine-phase threads and the drawing threads
   extern __shared__ __align__(16) uint8_t gdyn[];
   __shared__ GownSmem sm;
   const PersistentArgs& a = ga.p;
@@ -290,6 +303,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) persistent_gown_kernel(
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tstride = ga.tile_stride;
   uint32_t* W = reinterpret_cast<uint32_t*>(gdyn + 4 * tstride);
+  // PREF: the double buffer, half b at W + b * 4 * kGSlots * kHalf
+  auto Wb = [W](uint32_t b) { return W + (b & 1u) * (uint32_t)(4 * kGSlots * kHalf); };
   constexpr int kLW = kGLineWords;
   const bool run = !ld_volatile(&st->stopped);
   if (run) {
@@ -324,6 +339,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) persistent_gown_kernel(
     const bool isd = poller && part == 0 && (lane == 24 || lane == 25);
     const int o0 = (s < 2) ? 2 : 0, o1 = (s < 2) ? 3 : 1;   // other-axis sides at the two line ends
     bool quit = false;
+    uint32_t v = 0;   // visits so far in this launch
+    if (PREF && tid < kHalf) gown_words<kHalf>(d, sm.col[order_at(ord, 0)].g, a.m_begin, Wb(0u), tid);
     for (uint32_t m = a.m_begin; m < m_end && !quit; ++m) {
       if (m != a.m_begin) {
         ordp = ord;
@@ -366,7 +383,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) persistent_gown_kernel(
         // while those loads are in flight: every random word and the fine
         // order of this visit (the words of the previous visit are no longer
         // read: its last fine phase ended with a barrier)
-        gown_words<NT>(d, g, m, W);
+        if (!PREF) gown_words<NT>(d, g, m, W, tid);
         if (tid == NT - 1) sm.forder = fine_order(d, 2 * gx + (colour & 1), 2 * gy + (colour >> 1), m);
         bool failed = false;
         uint32_t spins = 0;
@@ -420,7 +437,22 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) persistent_gown_kernel(
           quit = true;
           break;
         }
-        gown_fine_phases<NT, REFLECT>(d, g, tile, sm.forder, trans, W);
+        if (PREF) {
+          if (tid < kHalf) {
+            gown_fine_phases<kHalf, REFLECT, true>(d, g, tile, sm.forder, trans, Wb(v));
+          } else {
+            // the next visit: slot k + 1 of this MCS, else slot 0 of the next
+            const uint32_t mn = k < 3 ? m : m + 1u;
+            if (mn < m_end) {
+              const GBlock gn = sm.col[order_at(k < 3 ? ord : ord_next, (k + 1) & 3)].g;
+              gown_words<kHalf>(d, gn, mn, Wb(v + 1u), tid - kHalf);
+            }
+          }
+          __syncthreads();
+        } else {
+          gown_fine_phases<NT, REFLECT>(d, g, tile, sm.forder, trans, W);
+        }
+        ++v;
         if (poller && exs && lane < nwd && C.id != a.stall_block) {
           uint32_t bytes = 0;
 #pragma unroll
@@ -535,9 +567,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) persistent_gown_kernel(
 }
 
 // ---------------------------------------------------------------------------
-template <int NT, bool REFLECT>
+template <int NT, bool REFLECT, bool PREF>
 static int gown_padding(int per_sm, int smem_sm, int reserved, int optin, int need_dyn) {
-  const void* fn = reinterpret_cast<const void*>(&persistent_gown_kernel<NT, REFLECT>);
+  const void* fn = reinterpret_cast<const void*>(&persistent_gown_kernel<NT, REFLECT, PREF>);
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return -1;
   const int stat = (int)fa.sharedSizeBytes;
@@ -592,17 +624,25 @@ int persistent_gown_config(const LatticeDesc& d, int device, GownConfig* cfg, in
   const int need_dyn = 4 * tile_bytes + 4 * kGSlots * nt * (int)sizeof(uint32_t);
   const bool refl = d.reflect != 0;
   int dyn;
+  // 512 threads on blocks of at most 256 quads: the upper half draws the
+  // next visit's words during the fine phases (the two buffers take the
+  // space of one 512-thread buffer)
+  const bool pref = nt == 512 && nq <= 256;
   if (nt == 256)
-    dyn = refl ? gown_padding<256, true>(per_sm, smem_sm, reserved, optin, need_dyn)
-               : gown_padding<256, false>(per_sm, smem_sm, reserved, optin, need_dyn);
+    dyn = refl ? gown_padding<256, true, false>(per_sm, smem_sm, reserved, optin, need_dyn)
+               : gown_padding<256, false, false>(per_sm, smem_sm, reserved, optin, need_dyn);
+  else if (pref)
+    dyn = refl ? gown_padding<512, true, true>(per_sm, smem_sm, reserved, optin, need_dyn)
+               : gown_padding<512, false, true>(per_sm, smem_sm, reserved, optin, need_dyn);
   else
-    dyn = refl ? gown_padding<512, true>(per_sm, smem_sm, reserved, optin, need_dyn)
-               : gown_padding<512, false>(per_sm, smem_sm, reserved, optin, need_dyn);
+    dyn = refl ? gown_padding<512, true, false>(per_sm, smem_sm, reserved, optin, need_dyn)
+               : gown_padding<512, false, false>(per_sm, smem_sm, reserved, optin, need_dyn);
   if (dyn < 0) return 0;
   cfg->dyn_bytes = dyn;
   cfg->threads = nt;
   cfg->ctas_per_sm = per_sm;
   cfg->tile_stride = tile_bytes;
+  cfg->prefetch = pref ? 1 : 0;
   return groups;
 }
 
@@ -617,11 +657,14 @@ cudaError_t launch_persistent_gown(const PersistentArgs& a, const GownConfig& cf
   const bool refl = a.d.reflect != 0;
   const void* fn;
   if (cfg.threads == 256)
-    fn = refl ? reinterpret_cast<const void*>(&persistent_gown_kernel<256, true>)
-              : reinterpret_cast<const void*>(&persistent_gown_kernel<256, false>);
+    fn = refl ? reinterpret_cast<const void*>(&persistent_gown_kernel<256, true, false>)
+              : reinterpret_cast<const void*>(&persistent_gown_kernel<256, false, false>);
+  else if (cfg.prefetch)
+    fn = refl ? reinterpret_cast<const void*>(&persistent_gown_kernel<512, true, true>)
+              : reinterpret_cast<const void*>(&persistent_gown_kernel<512, false, true>);
   else
-    fn = refl ? reinterpret_cast<const void*>(&persistent_gown_kernel<512, true>)
-              : reinterpret_cast<const void*>(&persistent_gown_kernel<512, false>);
+    fn = refl ? reinterpret_cast<const void*>(&persistent_gown_kernel<512, true, false>)
+              : reinterpret_cast<const void*>(&persistent_gown_kernel<512, false, false>);
   return cudaLaunchCooperativeKernel(fn, dim3(groups), dim3(cfg.threads), params, (size_t)cfg.dyn_bytes, stream);
 }
 
