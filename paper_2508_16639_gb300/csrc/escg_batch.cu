@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(THREADS) batch_kernel(BatchArgs a) {
       const uint32_t* flag = sd.done + ny * P + nx;
       uint32_t spins = 0;
       while (b_ld_acquire(flag) < need) {
-        if (b_ld_volatile(&ctl->abort)) {
+        if ((spins & 15u) == 15u && b_ld_volatile(&ctl->abort)) {
           s_abort = 1;
           break;
         }
@@ -518,7 +518,7 @@ __device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t
       const uint32_t* flag = sd.done + ny * P + nx;
       uint32_t spins = 0;
       while (b_ld_acquire(flag) < need) {
-        if (b_ld_volatile(&ctl->abort)) {
+        if ((spins & 15u) == 15u && b_ld_volatile(&ctl->abort)) {
           fail = 1;
           break;
         }

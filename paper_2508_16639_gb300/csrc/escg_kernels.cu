@@ -270,7 +270,8 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
         const uint32_t* flag = a.done + ny * P + nx;
         uint32_t spins = 0;
         while (ld_acquire(flag) < need) {
-          if (ld_volatile(&st->abort)) {
+          // the abort flag every 16th round, not between every two polls
+          if ((spins & 15u) == 15u && ld_volatile(&st->abort)) {
             s_abort = 1;
             break;
           }
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(kLLThreads, kLLMinBlocks) persistent_ll_kernel
             if (!got) got = (uint32_t)((word = ld_word(p)) >> 32) == e;
             if (!got_own) got_own = (uint32_t)((own = ld_word(q)) >> 32) == m;
             if (got && got_own) break;
-            if (ld_volatile(&st->abort)) {
+            if ((spins & 15u) == 15u && ld_volatile(&st->abort)) {
               failed = true;
               break;
             }
@@ -626,7 +627,7 @@ __global__ void __launch_bounds__(kLLThreads, kLLMinBlocks) persistent_ll_kernel
           const unsigned long long* p = ob + ((size_t)(ny * P + nx) * 4 + rec) * 32 + 16 + (pos >> 2);
           uint32_t spins = 0;
           while (!(first && sD > k) && (uint32_t)((word = ld_word(p)) >> 32) != eD) {
-            if (ld_volatile(&st->abort)) {
+            if ((spins & 15u) == 15u && ld_volatile(&st->abort)) {
               failed = true;
               break;
             }
@@ -1003,7 +1004,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 4) persistent_own_kernel(P
           if (!got) got = (uint32_t)(word >> 32) == e;
           if (!got_d) got_d = (uint32_t)(dword >> 32) == eD;
           if (got && got_d) break;
-          if (ld_volatile(&st->abort)) {
+          if ((spins & 15u) == 15u && ld_volatile(&st->abort)) {
             failed = true;
             break;
           }

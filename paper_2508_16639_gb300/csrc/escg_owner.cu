@@ -391,7 +391,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) persistent_gown_kernel(
           if (!got) got = (uint32_t)(word >> 32) == e;
           if (!got_d) got_d = (uint32_t)(dword >> 32) == eD;
           if (got && got_d) break;
-          if (ld_volatile(&st->abort)) {
+          // the abort flag every 16th round: a read of it in every round would
+          // put a second L2 round trip between two polls
+          if ((spins & 15u) == 15u && ld_volatile(&st->abort)) {
             failed = true;
             break;
           }
