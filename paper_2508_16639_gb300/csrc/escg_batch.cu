@@ -36,6 +36,7 @@
 #include "escg_device.cuh"
 #include "escg_internal.h"
 #include "escg_resident.cuh"
+#include "escg_rule8.cuh"
 #include "escg_tma.cuh"
 
 namespace escg_impl {
@@ -415,7 +416,7 @@ struct BItem {
 
 struct BatchTmaSmem {
   alignas(128) uint8_t tile[2][kBTileStride];
-  uint32_t trans[2][kTransWords];
+  uint2 trans2[2][kTransPairs];   // the replica's transition table, one 8-byte entry per pair (rule8)
   SlotDesc sd[2];
   BItem item[2];
   alignas(8) uint64_t full[2], empty[2], tma[2];
@@ -499,14 +500,7 @@ __device__ void btma_producer(const BatchTmaArgs& ta, BatchTmaSmem& sm, uint64_t
     BItem& it = sm.item[b];
     for (int q = lane; q <= Qx; q += 32) it.fsx[q] = (int16_t)seg_start(X, q);
     for (int q = lane; q <= Qy; q += 32) it.fsy[q] = (int16_t)seg_start(Y, q);
-    {
-      const int nt = (d.S + 1) * (d.S + 1);
-      const uint32_t* tr = reinterpret_cast<const uint32_t*>(d.trans);
-      for (int w = lane; w < nt; w += 32) {
-        sm.trans[b][w] = tr[w];
-        sm.trans[b][kTransPairs + w] = tr[kTransPairs + w];
-      }
-    }
+    fill_trans8(sm.trans2[b], d.trans, d.S, lane, 32);
     // wait until the 8 neighbours (and the block itself) have completed
     // every visit that precedes this one in schedule order
     uint32_t fail = 0;
@@ -649,7 +643,7 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
     const SlotDesc& sd = sm.sd[b];
     const LatticeDesc& d = sd.d;
     uint8_t* tile = sm.tile[b];
-    const uint8_t* trans = reinterpret_cast<const uint8_t*>(sm.trans[b]);
+    const uint2* t2 = sm.trans2[b];
     const uint32_t m = it.m, ord = it.ord, s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
     const int xoff = it.xoff, bw = it.bw, bh = it.bh, nquads = (it.Qx >> 1) * (it.Qy >> 1);
     // regular (all 2 x 2) quads first, as in visit_generic
@@ -680,10 +674,10 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
           const uint32_t g = (uint32_t)(it.fy0 + fy) * (uint32_t)d.GQ + (uint32_t)(it.fx0 + fx);
           const int base = (sy + 1) * kBSP + xoff + sx;
           const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
-          attempt_2x2(tile, trans, x.x, base, kBSP, tx, txi, s1);
-          attempt_2x2(tile, trans, x.y, base, kBSP, tx, txi, s1);
-          attempt_2x2(tile, trans, x.z, base, kBSP, tx, txi, s1);
-          attempt_2x2(tile, trans, x.w, base, kBSP, tx, txi, s1);
+          attempt8_2x2(tile, t2, x.x, base, kBSP, tx, txi, s1);
+          attempt8_2x2(tile, t2, x.y, base, kBSP, tx, txi, s1);
+          attempt8_2x2(tile, t2, x.z, base, kBSP, tx, txi, s1);
+          attempt8_2x2(tile, t2, x.w, base, kBSP, tx, txi, s1);
           continue;
         }
         const uint32_t nk = (uint32_t)(wx * wy), n4 = 4u * nk;
@@ -696,7 +690,7 @@ __device__ void btma_consumer(const BatchTmaArgs& ta, BatchTmaSmem& sm) {
           const uint32_t wv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e)
-            if (4u * jj + (uint32_t)e < nk) attempt(tile, trans, wv[e], n4, base, wx, inv_wx, kBSP, tx, txi, s1);
+            if (4u * jj + (uint32_t)e < nk) attempt8(tile, t2, wv[e], n4, base, wx, inv_wx, kBSP, tx, txi, s1);
         }
       }
       bar_sync_consumers(CONS);

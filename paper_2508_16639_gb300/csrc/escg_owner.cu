@@ -41,6 +41,7 @@
 // single-copy-atomic 64-bit store.
 #include "escg_device.cuh"
 #include "escg_internal.h"
+#include "escg_rule8.cuh"
 #include "escg_sync.cuh"
 
 namespace escg_impl {
@@ -121,7 +122,7 @@ __device__ __forceinline__ int gline_tidx(int s, int part, int pos, int bw, int 
 struct GownSmem {
   GColour col[4];    // the owned block of each colour
   uint32_t trans[kTransWords];
-  uint2 trans2[kTransPairs];   // the same table, one 8-byte entry per pair (gown_rule)
+  uint2 trans2[kTransPairs];   // the same table, one 8-byte entry per pair (rule8)
   uint32_t hist[kMaxStates];
   uint32_t forder;   // fine order of the current visit
   uint32_t abort;
@@ -192,49 +193,6 @@ __device__ __forceinline__ void gown_words(const LatticeDesc& d, const GBlock& g
   }
 }
 
-// The transition table of one pair as one 8-byte shared-memory entry: .x the
-// four new pairs (byte act: action act, as the table's first half), .y the
-// pair's interaction threshold (its second half), so that a step off the
-// exchange path reads one entry instead of two dependent words.
-__device__ __forceinline__ void gown_rule(uint8_t* __restrict__ tile, const uint2* __restrict__ t2, int ti, int tj,
-                                          uint32_t a, uint32_t b, uint32_t u, uint32_t tx, uint32_t txi,
-                                          uint32_t s1) {
-  if (u < tx) {
-    tile[ti] = (uint8_t)b;
-    tile[tj] = (uint8_t)a;
-  } else {
-    const uint2 e = t2[a * s1 + b];
-    const uint32_t act = (u >= txi) ? 2u : (u < e.y ? 1u : 3u);
-    const uint32_t nn = e.x >> (8u * act);
-    tile[ti] = (uint8_t)(nn & 15u);
-    tile[tj] = (uint8_t)((nn >> 4) & 15u);
-  }
-}
-
-// attempts_ahead on the interleaved table: steps t < n of a sub-block from
-// the words wv[], each step's cell and neighbour located while the previous
-// step's pair is read.
-template <int N>
-__device__ __forceinline__ void gown_attempts(uint8_t* __restrict__ tile, const uint2* __restrict__ t2,
-                                              const uint32_t* wv, uint32_t n, uint32_t n4, int base, int wx,
-                                              uint32_t inv_wx, int sp, uint32_t tx, uint32_t txi, uint32_t s1) {
-  int ti, tj;
-  uint32_t u;
-  locate(wv[0], n4, base, wx, inv_wx, sp, ti, tj, u);
-#pragma unroll
-  for (int t = 0; t < N; ++t) {
-    if ((uint32_t)t >= n) break;
-    const uint32_t a = tile[ti], b = tile[tj];
-    int ti2 = 0, tj2 = 0;
-    uint32_t u2 = 0;
-    if (t + 1 < N) locate(wv[t + 1], n4, base, wx, inv_wx, sp, ti2, tj2, u2);
-    gown_rule(tile, t2, ti, tj, a, b, u, tx, txi, s1);
-    ti = ti2;
-    tj = tj2;
-    u = u2;
-  }
-}
-
 // The four fine colour phases of a visit from the drawn words (fine order
 // ord), run by threads 0 .. NT - 1, each ending with a barrier: the CTA's
 // (BAR = false) or named barrier 1 over those NT threads (BAR = true).
@@ -269,7 +227,7 @@ __device__ __forceinline__ void gown_fine_phases(const LatticeDesc& d, const GBl
             attempt_variant(tile, trans, wv[t], n4, 2, base, wx, inv_wx, sp, tx, txi, s1, true,
                             g.Y.s0 + sy, g.X.s0 + sx, d.H, d.L);
       } else {
-        gown_attempts<kGSlots>(tile, t2, wv, nk, n4, base, wx, inv_wx, sp, tx, txi, s1);
+        attempts8_ahead<kGSlots>(tile, t2, wv, nk, n4, base, wx, inv_wx, sp, tx, txi, s1);
       }
     }
     if (BAR)
@@ -353,10 +311,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 1) persistent_gown_kernel(
   const bool run = !ld_volatile(&st->stopped);
   if (run) {
     load_trans(d, sm.trans);
-    {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(d.trans);
-      for (int k = tid; k < (d.S + 1) * (d.S + 1); k += NT) sm.trans2[k] = make_uint2(src[k], src[kTransPairs + k]);
-    }
+    fill_trans8(sm.trans2, d.trans, d.S, tid, NT);
     const int P = d.P, half = P >> 1;
     const uint32_t nb = (uint32_t)(P * d.Py);
     const int gx = (int)blockIdx.x % half, gy = (int)blockIdx.x / half;
