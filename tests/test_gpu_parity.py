@@ -417,3 +417,34 @@ def test_maximum_size_lattice(bits):
     c, m = g.counts()
     assert m == 1 and int(c.sum()) == L * L and np.array_equal(c, O.counts(o, S))
     g.close()
+
+
+@pytest.mark.parametrize("persistent", [3, 0, 5], ids=["flags", "phase", "owners"])
+@pytest.mark.parametrize("L,H,reflect", [(131, 131, False), (100, 100, False), (300, 140, False),
+                                         (131, 137, True)])
+def test_generic_staging_leaves_row_padding(L, H, reflect, persistent):
+    """Generic partitions whose rows end mid-way through an 8-byte group
+    (the flag and phase kernels' aligned tile staging reads whole groups;
+    the block owners write back single sites at the row ends): the lattice
+    stays bit-exact against the oracle after every MCS and the row padding
+    beyond column L of the caller's device buffer is never written."""
+    torch = pytest.importorskip("torch")
+    S, seed, X = 3, 4100 + L + H, 2.5
+    D = O.circulant(S, (1,))
+    pitch = E.lattice_pitch(L)
+    buf = torch.zeros(E.lattice_bytes(L, H), dtype=torch.uint8, device="cuda")
+    g = E.Lattice(L, S, D, (1.0, 1.0, X), seed, p_empty=0.25, persistent=persistent, H=H,
+                  reflecting_boundary=reflect, device_buffer=buf)
+    g.sync()
+    view = buf.view(H, pitch)
+    view[:, L:] = 0xAB
+    torch.cuda.synchronize()
+    o = O.init(L, S, 0.25, seed, H=H)
+    for m in range(4):
+        g.run(1)
+        o, _ = O.replay_run(o, D, 1.0, 1.0, X, seed, 1, mcs_begin=m, reflect=reflect)
+        assert np.array_equal(g.snapshot(), o), m
+    g.sync()
+    pad = view[:, L:].cpu().numpy()
+    assert (pad == 0xAB).all(), int((pad != 0xAB).sum())
+    g.close()
