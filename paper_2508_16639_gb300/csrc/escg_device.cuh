@@ -117,6 +117,25 @@ __device__ __forceinline__ void apply_rule_ab(uint8_t* __restrict__ tile, const 
   }
 }
 
+// apply_rule_ab on a transition table kept in shared memory as one 8-byte
+// entry per pair (LatticeDesc::trans with its two halves interleaved: .x the
+// four new pairs, byte `act` for action act; .y the pair's interaction
+// threshold), so that a step off the exchange path reads one entry instead of
+// two dependent words (a at ti, b at tj; u the action draw).
+__device__ __forceinline__ void rule8(uint8_t* __restrict__ tile, const uint2* __restrict__ t2, int ti, int tj,
+                                      uint32_t a, uint32_t b, uint32_t u, uint32_t tx, uint32_t txi, uint32_t s1) {
+  if (u < tx) {
+    tile[ti] = (uint8_t)b;
+    tile[tj] = (uint8_t)a;
+  } else {
+    const uint2 e = t2[a * s1 + b];
+    const uint32_t act = (u >= txi) ? 2u : (u < e.y ? 1u : 3u);
+    const uint32_t nn = e.x >> (8u * act);
+    tile[ti] = (uint8_t)(nn & 15u);
+    tile[tj] = (uint8_t)((nn >> 4) & 15u);
+  }
+}
+
 // The cell and neighbour tile indices and the action draw of attempt()'s
 // step (w, n4 = 4 * cells, base, wx, inv_wx, sp as there).
 __device__ __forceinline__ void locate(uint32_t w, uint32_t n4, int base, int wx, uint32_t inv_wx, int sp,
@@ -260,6 +279,17 @@ __device__ __forceinline__ void attempt_uni(uint8_t* __restrict__ tile, const ui
   const int ti = base + (int)__byte_perm(kTi, 0u, w >> 30);
   const int tj = ti - SP + (int)__byte_perm(kTj, 0u, (w >> 28) & 3u);
   apply_rule(tile, trans, ti, tj, w << 4, tx, txi, s1);
+}
+
+// attempt_uni on the 8-byte-entry table (rule8).
+template <int SP>
+__device__ __forceinline__ void attempt_uni8(uint8_t* __restrict__ tile, const uint2* __restrict__ t2, uint32_t w,
+                                             int base, uint32_t tx, uint32_t txi, uint32_t s1) {
+  constexpr uint32_t kTi = 0u | (1u << 8) | ((uint32_t)SP << 16) | ((uint32_t)(SP + 1) << 24);
+  constexpr uint32_t kTj = 0u | ((uint32_t)(2 * SP) << 8) | ((uint32_t)(SP - 1) << 16) | ((uint32_t)(SP + 1) << 24);
+  const int ti = base + (int)__byte_perm(kTi, 0u, w >> 30);
+  const int tj = ti - SP + (int)__byte_perm(kTj, 0u, (w >> 28) & 3u);
+  rule8(tile, t2, ti, tj, tile[ti], tile[tj], w << 4, tx, txi, s1);
 }
 
 template <int SP, int COFF>
@@ -666,9 +696,12 @@ __device__ __forceinline__ uint32_t fine_order(const LatticeDesc& d, int bx, int
 // (bx, by), MCS m, fine order ord), run by threads 0..255; each phase ends
 // with a barrier: __syncthreads() when BAR_N == 0, else named barrier
 // BAR_ID over BAR_N threads (the threads of the visit).
-template <int BAR_ID = 0, int BAR_N = 0>
+// X0: the words of the first fine phase are given (xw0, drawn by the caller
+// beforehand), else drawn here like the others.
+// T8: trans holds the 8-byte-entry table (rule8) instead.
+template <int BAR_ID = 0, int BAR_N = 0, bool X0 = false, bool T8 = false>
 __device__ __forceinline__ void fine_phases_tile(const LatticeDesc& d, int bx, int by, uint32_t m, uint8_t* tile,
-                                                 uint32_t ord, const uint8_t* trans) {
+                                                 uint32_t ord, const uint8_t* trans, uint4 xw0 = uint4{}) {
   const int t = threadIdx.x, qx = t & 15, qy = t >> 4;
   const uint32_t s1 = (uint32_t)d.S + 1u, tx = d.tx, txi = d.txi;
   // sub-block (2 qx + cx, 2 qy + cy) of the quad: global index g00 + cy*GQ + cx,
@@ -681,11 +714,19 @@ __device__ __forceinline__ void fine_phases_tile(const LatticeDesc& d, int bx, i
     const uint32_t fcol = (ord >> (2 * fi)) & 3u, cx = fcol & 1u, cy = fcol >> 1;
     const uint32_t g = g00 + cy * GQ + cx;
     const int base = base00 + (int)(cy * (2 * kUniSP) + 2 * cx);
-    const uint4 x = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
-    attempt_uni<kUniSP>(tile, trans, x.x, base, tx, txi, s1);
-    attempt_uni<kUniSP>(tile, trans, x.y, base, tx, txi, s1);
-    attempt_uni<kUniSP>(tile, trans, x.z, base, tx, txi, s1);
-    attempt_uni<kUniSP>(tile, trans, x.w, base, tx, txi, s1);
+    const uint4 x = (X0 && fi == 0) ? xw0 : philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
+    if (T8) {
+      const uint2* t2 = reinterpret_cast<const uint2*>(trans);
+      attempt_uni8<kUniSP>(tile, t2, x.x, base, tx, txi, s1);
+      attempt_uni8<kUniSP>(tile, t2, x.y, base, tx, txi, s1);
+      attempt_uni8<kUniSP>(tile, t2, x.z, base, tx, txi, s1);
+      attempt_uni8<kUniSP>(tile, t2, x.w, base, tx, txi, s1);
+    } else {
+      attempt_uni<kUniSP>(tile, trans, x.x, base, tx, txi, s1);
+      attempt_uni<kUniSP>(tile, trans, x.y, base, tx, txi, s1);
+      attempt_uni<kUniSP>(tile, trans, x.z, base, tx, txi, s1);
+      attempt_uni<kUniSP>(tile, trans, x.w, base, tx, txi, s1);
+    }
     if (BAR_N)
       asm volatile("bar.sync %0, %1;" ::"n"(BAR_ID), "n"(BAR_N) : "memory");
     else
@@ -710,6 +751,51 @@ __device__ __forceinline__ void visit_uniform(const LatticeDesc& d, int bx, int 
   __syncthreads();
   fine_phases_uni(d, bx, by, m, sm);
   store_tile_uni<PACKED>(d, x0, y0, sm.tile, rim_raw);
+}
+
+// visit_uniform on a one-byte lattice with the caller's fine order in
+// sm.forder, whose first fine phase draws its Philox words while the tile's
+// loads are in flight: the words depend on the schedule only, so they are
+// ready when the tile is, and that phase's draw leaves the visit's path
+// (L = 3200: 25.84 -> 25.43 us per MCS).  Drawing the second phase's words
+// too (into shared memory) measured 25.95, all four 26.88.
+template <bool T8 = false>
+__device__ __forceinline__ void visit_uniform_x0(const LatticeDesc& d, int bx, int by, uint32_t m,
+                                                 VisitSmem& sm) {
+  const int x0 = bx * kUniB, y0 = by * kUniB, t = threadIdx.x, L = d.L, pitch = d.pitch;
+  // the loads of load_piece_uni, issued first
+  const int r = t >> 2, q = t & 3;
+  const uint4 v = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)(y0 + r) * pitch + x0) + q);
+  const int rr = (t < 4) ? -1 : kUniB;
+  const int k = t - 128, cc = (k < 64) ? -1 : kUniB, rc = k & 63;
+  uint4 vr = make_uint4(0u, 0u, 0u, 0u);
+  uint8_t vc = 0;
+  if (t < 8)
+    vr = __ldcg(reinterpret_cast<const uint4*>(d.lat + (size_t)wrap(y0 + rr, d.H) * pitch + x0) + q);
+  else if (t >= 128)
+    vc = __ldcg(d.lat + (size_t)(y0 + rc) * pitch + wrap(x0 + cc, L));
+  // the first fine phase's words (fine_phases_tile's sub-block g of that phase)
+  const uint32_t ord = sm.forder, fcol = ord & 3u;
+  const int qx = t & 15, qy = t >> 4;
+  const uint32_t GQ = (uint32_t)d.GQ;
+  const uint32_t g = (uint32_t)(by * (kUniB / 2) + 2 * qy + (int)(fcol >> 1)) * GQ +
+                     (uint32_t)(bx * (kUniB / 2) + 2 * qx + (int)(fcol & 1u));
+  const uint4 xw0 = philox10_rk(make_uint4(0u, g, m, kTagStep), d.rk);
+  {
+    uint2* dst = reinterpret_cast<uint2*>(sm.tile + tidx(r, 16 * q, kUniSP));
+    dst[0] = make_uint2(v.x, v.y);
+    dst[1] = make_uint2(v.z, v.w);
+  }
+  if (t < 8) {
+    uint2* dst = reinterpret_cast<uint2*>(sm.tile + tidx(rr, 16 * q, kUniSP));
+    dst[0] = make_uint2(vr.x, vr.y);
+    dst[1] = make_uint2(vr.z, vr.w);
+  } else if (t >= 128) {
+    sm.tile[tidx(rc, cc, kUniSP)] = vc;
+  }
+  __syncthreads();
+  fine_phases_tile<0, 0, true, T8>(d, bx, by, m, sm.tile, ord, reinterpret_cast<const uint8_t*>(sm.trans), xw0);
+  store_tile_uni<false>(d, x0, y0, sm.tile, 0u);
 }
 
 // The step of attempt() for a 2 x 2 sub-block (n_k = 4: p = 16 w, so the

@@ -85,6 +85,9 @@ struct PersistentArgs {
   int32_t fuse_counts;     // 1: counts of log points fused into the visits; 0: the host counts
   int32_t threads;         // flag kernel on uniform one-byte lattices: 128 (two quads per
                            // thread, up to 8 CTAs per SM) or 0 / 256 (one quad per thread)
+  // div_rcp32 of the ticket decode's divisors (blocks per MCS, blocks per
+  // coarse phase, half the blocks per row); filled in by launch_persistent
+  uint32_t rcp_nb, rcp_per, rcp_half;
 };
 // MCS [m_begin, m_begin + n_mcs) in one persistent dataflow launch, counts
 // of log points fused in.

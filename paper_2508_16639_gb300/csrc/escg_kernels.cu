@@ -210,6 +210,13 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
   __shared__ VisitSmem sm;
   __shared__ uint16_t stash[(UNI || !PACKED) ? 1 : kStashWords];
   __shared__ uint32_t s_item, s_ord, s_quit, s_abort;
+  // Ticket decode by host-computed reciprocals (div_by_rcp) and neighbour
+  // indices by a compare-and-wrap instead of the device's division and
+  // modulo: measured 1.8 % faster on generic lattices (L = 4800) and 0.9 %
+  // in the 128-thread build (L = 6400), but 0.8 % slower in the 256-thread
+  // uniform build at L = 3200 beside its early first-phase draw
+  // (visit_uniform_x0), which keeps the plain decode.
+  constexpr bool kFastDecode = !(UNI && !PACKED && NT == kPersistentThreads && VAR == 0);
   const LatticeDesc& d = a.d;
   RunState* st = a.st;
   const int tid = threadIdx.x;
@@ -239,7 +246,8 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
         s_item = t;
         uint32_t quit = ((uint64_t)t >= total) || ab_next;
         if (!quit) {
-          const uint32_t m = a.m_begin + t / nb;
+          uint32_t r_unused;
+          const uint32_t m = a.m_begin + (kFastDecode ? div_by_rcp(t, nb, a.rcp_nb, r_unused) : t / nb);
           if (m != c_m) {
             c_m = m;
             c_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
@@ -253,18 +261,31 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
       __syncthreads();
       if (s_quit) break;
       const uint32_t t = s_item, ord = s_ord;
-      const uint32_t mi = t / nb, rem = t - mi * nb;
+      uint32_t mi, rem, kk, j, jx, jy;
+      if (kFastDecode) {
+        mi = div_by_rcp(t, nb, a.rcp_nb, rem);
+        kk = div_by_rcp(rem, per, a.rcp_per, j);
+        jy = div_by_rcp(j, (uint32_t)half, a.rcp_half, jx);
+      } else {
+        mi = t / nb;
+        rem = t - mi * nb;
+        kk = rem / per;
+        j = rem - kk * per;
+        jy = j / (uint32_t)half;
+        jx = j - jy * (uint32_t)half;
+      }
       const uint32_t m = a.m_begin + mi;
-      const int k = (int)(rem / per), j = (int)(rem - (uint32_t)k * per);
+      const int k = (int)kk;
       const int colour = order_at(ord, k);
-      const int bx = 2 * (j % half) + (colour & 1), by = 2 * (j / half) + (colour >> 1);
+      const int bx = 2 * (int)jx + (colour & 1), by = 2 * (int)jy + (colour >> 1);
       // Wait until the 8 neighbours (and the block itself) have completed
       // every visit that precedes this one in schedule order; meanwhile
       // warp 1 draws the block's fine colour order.
       if (tid == kTicketThread) sm.forder = fine_order(d, bx, by, m);
       if (tid < 9) {
         const int dx = tid % 3 - 1, dy = tid / 3 - 1;
-        const int nx = (bx + dx + P) % P, ny = (by + dy + Py) % Py;
+        const int nx = kFastDecode ? wrap(bx + dx, P) : (bx + dx + P) % P;
+        const int ny = kFastDecode ? wrap(by + dy, Py) : (by + dy + Py) % Py;
         const int ncol = colour ^ ((dx & 1) | ((dy & 1) << 1));
         const uint32_t need = (tid == 4) ? m : (slot_of(ord, ncol) < k ? m + 1u : m);
         const uint32_t* flag = a.done + ny * P + nx;
@@ -319,7 +340,10 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
           store_piece_uni(d, x0, y0, sm.tile, tid + 128);
         }
       } else if (UNI) {
-        visit_uniform<false, PACKED>(d, bx, by, m, sm);
+        if (PACKED)
+          visit_uniform<false, PACKED>(d, bx, by, m, sm);
+        else
+          visit_uniform_x0(d, bx, by, m, sm);
       } else {
         visit_generic<false, PACKED>(d, bx, by, m, sm, stash);
       }
@@ -1638,7 +1662,12 @@ int persistent_tma_grid(int device) {
   return sms * per_sm;
 }
 
-cudaError_t launch_persistent(const PersistentArgs& a, int grid, cudaStream_t stream) {
+cudaError_t launch_persistent(const PersistentArgs& args, int grid, cudaStream_t stream) {
+  PersistentArgs a = args;
+  const uint32_t nb = (uint32_t)(a.d.P * a.d.Py);
+  a.rcp_nb = div_rcp32(nb);
+  a.rcp_per = div_rcp32(nb >> 2);
+  a.rcp_half = div_rcp32((uint32_t)(a.d.P >> 1));
   if (a.d.uniform_var) {
     const int var = (a.d.nbh == 8 ? 2 : 0) | (a.d.reflect ? 1 : 0);
     if (var == 1)

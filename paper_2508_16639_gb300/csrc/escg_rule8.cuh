@@ -21,21 +21,6 @@ __device__ __forceinline__ void fill_trans8(uint2* t2, const uint8_t* trans, int
   for (int k = t0; k < (S + 1) * (S + 1); k += n) t2[k] = make_uint2(src[k], src[kTransPairs + k]);
 }
 
-// The rule on a pair already read (a at ti, b at tj; u the action draw).
-__device__ __forceinline__ void rule8(uint8_t* __restrict__ tile, const uint2* __restrict__ t2, int ti, int tj,
-                                      uint32_t a, uint32_t b, uint32_t u, uint32_t tx, uint32_t txi, uint32_t s1) {
-  if (u < tx) {
-    tile[ti] = (uint8_t)b;
-    tile[tj] = (uint8_t)a;
-  } else {
-    const uint2 e = t2[a * s1 + b];
-    const uint32_t act = (u >= txi) ? 2u : (u < e.y ? 1u : 3u);
-    const uint32_t nn = e.x >> (8u * act);
-    tile[ti] = (uint8_t)(nn & 15u);
-    tile[tj] = (uint8_t)((nn >> 4) & 15u);
-  }
-}
-
 // attempt_2x2 on the 8-byte table.
 __device__ __forceinline__ void attempt8_2x2(uint8_t* __restrict__ tile, const uint2* __restrict__ t2, uint32_t w,
                                              int base, int sp, uint32_t tx, uint32_t txi, uint32_t s1) {

@@ -23,6 +23,32 @@ constexpr int kMaxStates = 16;           // S <= 15
 constexpr int kTransPairs = kMaxStates * kMaxStates;
 constexpr int kTransWords = 2 * kTransPairs;
 
+// Division of any 32-bit n by a divisor d >= 1 known before the launch,
+// without the device's division sequence: rcp = floor(2^32 / d) (2^32 - 1
+// for d = 1) makes q = floor(n * rcp / 2^32) fall short of floor(n / d) by
+// less than n / 2^32 < 1, i.e. by 0 or 1, which one comparison of the
+// remainder corrects.
+inline uint32_t div_rcp32(uint32_t d) {
+  return d <= 1 ? 0xFFFFFFFFu : (uint32_t)((1ull << 32) / d);
+}
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline uint32_t div_by_rcp(uint32_t n, uint32_t d, uint32_t rcp, uint32_t& rem) {
+#if defined(__CUDA_ARCH__)
+  uint32_t q = __umulhi(n, rcp);
+#else
+  uint32_t q = (uint32_t)(((uint64_t)n * rcp) >> 32);
+#endif
+  uint32_t r = n - q * d;
+  if (r >= d) {
+    ++q;
+    r -= d;
+  }
+  rem = r;
+  return q;
+}
+
 // Closed form of one axis's schedule-v1 partition, so that a kernel finds a
 // block's span and its fine segments by arithmetic instead of table loads:
 // n sites split evenly into P coarse parts (the first r parts q + 1 sites
