@@ -22,9 +22,11 @@
 
 #include "escg_device.cuh"
 #include "escg_resident.cuh"
+#include "escg_rule8.cuh"
 #include "escg_internal.h"
 #include "escg_tma.cuh"
 #include "escg_sync.cuh"
+
 
 namespace escg_impl {
 
@@ -217,12 +219,26 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
   // uniform build at L = 3200 beside its early first-phase draw
   // (visit_uniform_x0), which keeps the plain decode.
   constexpr bool kFastDecode = !(UNI && !PACKED && NT == kPersistentThreads && VAR == 0);
+  // The uniform 256-thread build steps on the 8-byte-entry transition table
+  // (rule8: one shared-memory read off the exchange path; L = 3200 -0.7 %,
+  // -1.3 % at M = 1e-5 where more steps leave the exchange path).
+  constexpr bool kT8 = UNI && !PACKED && NT == kPersistentThreads && VAR == 0;
+  // Generic builds: the epoch is released by a thread of the last warp, and
+  // only warps 0 and 1 (the ticket thread and the pollers) meet at the top of
+  // the loop, behind a named barrier, so that the release's wait for the
+  // tile stores overlaps the next ticket's decode and polls (L = 4800 -2.1 %;
+  // +3.2 % in the uniform build at L = 3200, which keeps one CTA barrier).
+  constexpr bool kSplitTop = !UNI;
+  constexpr int kReleaseThread = kSplitTop ? NT - 32 : 0;
   const LatticeDesc& d = a.d;
   RunState* st = a.st;
   const int tid = threadIdx.x;
   const bool run = !ld_volatile(&st->stopped);
   if (run) {
-    load_trans(d, sm.trans);
+    if (kT8)
+      fill_trans8(reinterpret_cast<uint2*>(sm.trans), d.trans, d.S, tid, NT);
+    else
+      load_trans(d, sm.trans);
     const int P = d.P, half = P >> 1, Py = d.Py;
     const uint32_t nb = (uint32_t)(P * Py), per = nb >> 2;
     const uint64_t total = (uint64_t)a.n_mcs * nb;
@@ -258,31 +274,49 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
         s_abort = 0;
       }
       if (tid < kMaxStates) sm.hist[tid] = 0;
-      __syncthreads();
-      if (s_quit) break;
-      const uint32_t t = s_item, ord = s_ord;
-      uint32_t mi, rem, kk, j, jx, jy;
-      if (kFastDecode) {
-        mi = div_by_rcp(t, nb, a.rcp_nb, rem);
-        kk = div_by_rcp(rem, per, a.rcp_per, j);
-        jy = div_by_rcp(j, (uint32_t)half, a.rcp_half, jx);
+      // The item of ticket s_item: MCS m, coarse slot k, colour, block (bx, by).
+      uint32_t m = 0;
+      int k = 0, colour = 0, bx = 0, by = 0;
+      auto decode = [&]() {
+        const uint32_t t = s_item, ord = s_ord;
+        uint32_t mi, rem, kk, j, jx, jy;
+        if (kFastDecode) {
+          mi = div_by_rcp(t, nb, a.rcp_nb, rem);
+          kk = div_by_rcp(rem, per, a.rcp_per, j);
+          jy = div_by_rcp(j, (uint32_t)half, a.rcp_half, jx);
+        } else {
+          mi = t / nb;
+          rem = t - mi * nb;
+          kk = rem / per;
+          j = rem - kk * per;
+          jy = j / (uint32_t)half;
+          jx = j - jy * (uint32_t)half;
+        }
+        m = a.m_begin + mi;
+        k = (int)kk;
+        colour = order_at(ord, k);
+        bx = 2 * (int)jx + (colour & 1);
+        by = 2 * (int)jy + (colour >> 1);
+      };
+      if (kSplitTop) {
+        // Named barrier 1 over 64 threads: warps 0 and 1 (the condition is
+        // warp-uniform) reach it exactly once per iteration -- the loop is
+        // left only after the CTA barrier below, by every thread alike -- and
+        // no other code of this kernel uses barrier 1.
+        if (tid < 64) bar_named(1, 64);
       } else {
-        mi = t / nb;
-        rem = t - mi * nb;
-        kk = rem / per;
-        j = rem - kk * per;
-        jy = j / (uint32_t)half;
-        jx = j - jy * (uint32_t)half;
+        __syncthreads();
+        if (s_quit) break;
       }
-      const uint32_t m = a.m_begin + mi;
-      const int k = (int)kk;
-      const int colour = order_at(ord, k);
-      const int bx = 2 * (int)jx + (colour & 1), by = 2 * (int)jy + (colour >> 1);
+      const bool early = !kSplitTop || tid < 64;
+      const bool go = early && !s_quit;
+      if (go) decode();
       // Wait until the 8 neighbours (and the block itself) have completed
       // every visit that precedes this one in schedule order; meanwhile
       // warp 1 draws the block's fine colour order.
-      if (tid == kTicketThread) sm.forder = fine_order(d, bx, by, m);
-      if (tid < 9) {
+      if (go && tid == kTicketThread) sm.forder = fine_order(d, bx, by, m);
+      if (go && tid < 9) {
+        const uint32_t ord = s_ord;
         const int dx = tid % 3 - 1, dy = tid / 3 - 1;
         const int nx = kFastDecode ? wrap(bx + dx, P) : (bx + dx + P) % P;
         const int ny = kFastDecode ? wrap(by + dy, Py) : (by + dy + Py) % Py;
@@ -306,7 +340,9 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
         }
       }
       __syncthreads();
-      if (s_abort) break;  // uniform across the CTA
+      if (s_quit || s_abort) break;  // uniform across the CTA
+      if (!early) decode();
+      const uint32_t ord = s_ord;
       if (VAR != 0) {
         const int x0 = bx * kUniB, y0 = by * kUniB;
         load_piece_uni(d, x0, y0, sm.tile, tid);
@@ -343,7 +379,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
         if (PACKED)
           visit_uniform<false, PACKED>(d, bx, by, m, sm);
         else
-          visit_uniform_x0(d, bx, by, m, sm);
+          visit_uniform_x0<kT8>(d, bx, by, m, sm);
       } else {
         visit_generic<false, PACKED>(d, bx, by, m, sm, stash);
       }
@@ -361,7 +397,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
         }
       }
       __syncthreads();
-      if (tid == 0 && by * P + bx != a.stall_block) {
+      if (tid == kReleaseThread && by * P + bx != a.stall_block) {
         // st.release orders the CTA's tile stores (made before the barrier
         // above) before the new epoch; no separate fence is needed.  The
         // counts of a log point live in shared memory and are published
