@@ -28,6 +28,7 @@
 #include "escg_sync.cuh"
 
 
+
 namespace escg_impl {
 
 // ---------------------------------------------------------------------------
@@ -211,14 +212,14 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
   static_assert(VAR == 0 || (UNI && !PACKED && NT == kPersistentThreads), "variants: uniform bytes, 256 threads");
   __shared__ VisitSmem sm;
   __shared__ uint16_t stash[(UNI || !PACKED) ? 1 : kStashWords];
-  __shared__ uint32_t s_item, s_ord, s_quit, s_abort;
-  // Ticket decode by host-computed reciprocals (div_by_rcp) and neighbour
-  // indices by a compare-and-wrap instead of the device's division and
-  // modulo: measured 1.8 % faster on generic lattices (L = 4800) and 0.9 %
-  // in the 128-thread build (L = 6400), but 0.8 % slower in the 256-thread
-  // uniform build at L = 3200 beside its early first-phase draw
-  // (visit_uniform_x0), which keeps the plain decode.
-  constexpr bool kFastDecode = !(UNI && !PACKED && NT == kPersistentThreads && VAR == 0);
+  __shared__ uint32_t s_ord, s_quit, s_abort;
+  __shared__ uint4 s_dec;   // the item's (m, k, bx, by), decoded by the ticket thread
+  // Neighbour indices of the polls by a compare-and-wrap instead of the
+  // modulo (measured with the per-thread ticket decode this kernel had
+  // before: 1.8 % faster on generic lattices at L = 4800, 0.9 % in the
+  // 128-thread build at L = 6400, 0.8 % slower in the 256-thread uniform
+  // build at L = 3200, which keeps the modulo).
+  constexpr bool kCmpWrap = !(UNI && !PACKED && NT == kPersistentThreads && VAR == 0);
   // The uniform 256-thread build steps on the 8-byte-entry transition table
   // (rule8: one shared-memory read off the exchange path; L = 3200 -0.7 %,
   // -1.3 % at M = 1e-5 where more steps leave the exchange path).
@@ -259,44 +260,38 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
     for (;;) {
       if (tid == kTicketThread) {
         const uint32_t t = t_next;
-        s_item = t;
         uint32_t quit = ((uint64_t)t >= total) || ab_next;
         if (!quit) {
-          uint32_t r_unused;
-          const uint32_t m = a.m_begin + (kFastDecode ? div_by_rcp(t, nb, a.rcp_nb, r_unused) : t / nb);
+          // The ticket's item, decoded here once for the CTA with
+          // host-computed reciprocals (div_by_rcp) instead of every thread
+          // dividing by run-time counts (0.7-1.1 % faster at L = 3200, 4800
+          // and 6400): MCS m, coarse slot k, block j of that slot's colour.
+          uint32_t rem, j, jx;
+          const uint32_t m = a.m_begin + div_by_rcp(t, nb, a.rcp_nb, rem);
           if (m != c_m) {
             c_m = m;
             c_ord = colour_order(philox10(make_uint4(0u, 0u, m, kTagOrder), d.key0, d.key1).x, d.perm24);
           }
           s_ord = c_ord;
+          const uint32_t kk = div_by_rcp(rem, per, a.rcp_per, j);
+          const uint32_t jy = div_by_rcp(j, (uint32_t)half, a.rcp_half, jx);
+          const uint32_t col = (uint32_t)order_at(c_ord, (int)kk);
+          s_dec = make_uint4(m, kk, 2u * jx + (col & 1u), 2u * jy + (col >> 1));
         }
         s_quit = quit;
         s_abort = 0;
       }
       if (tid < kMaxStates) sm.hist[tid] = 0;
-      // The item of ticket s_item: MCS m, coarse slot k, colour, block (bx, by).
+      // The ticket's item (s_dec): MCS m, coarse slot k, colour, block (bx, by).
       uint32_t m = 0;
       int k = 0, colour = 0, bx = 0, by = 0;
       auto decode = [&]() {
-        const uint32_t t = s_item, ord = s_ord;
-        uint32_t mi, rem, kk, j, jx, jy;
-        if (kFastDecode) {
-          mi = div_by_rcp(t, nb, a.rcp_nb, rem);
-          kk = div_by_rcp(rem, per, a.rcp_per, j);
-          jy = div_by_rcp(j, (uint32_t)half, a.rcp_half, jx);
-        } else {
-          mi = t / nb;
-          rem = t - mi * nb;
-          kk = rem / per;
-          j = rem - kk * per;
-          jy = j / (uint32_t)half;
-          jx = j - jy * (uint32_t)half;
-        }
-        m = a.m_begin + mi;
-        k = (int)kk;
-        colour = order_at(ord, k);
-        bx = 2 * (int)jx + (colour & 1);
-        by = 2 * (int)jy + (colour >> 1);
+        const uint4 v = s_dec;
+        m = v.x;
+        k = (int)v.y;
+        bx = (int)v.z;
+        by = (int)v.w;
+        colour = (bx & 1) | ((by & 1) << 1);
       };
       if (kSplitTop) {
         // Named barrier 1 over 64 threads: warps 0 and 1 (the condition is
@@ -318,8 +313,8 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : (UNI ? kUniMinBlocks : 4))
       if (go && tid < 9) {
         const uint32_t ord = s_ord;
         const int dx = tid % 3 - 1, dy = tid / 3 - 1;
-        const int nx = kFastDecode ? wrap(bx + dx, P) : (bx + dx + P) % P;
-        const int ny = kFastDecode ? wrap(by + dy, Py) : (by + dy + Py) % Py;
+        const int nx = kCmpWrap ? wrap(bx + dx, P) : (bx + dx + P) % P;
+        const int ny = kCmpWrap ? wrap(by + dy, Py) : (by + dy + Py) % Py;
         const int ncol = colour ^ ((dx & 1) | ((dy & 1) << 1));
         const uint32_t need = (tid == 4) ? m : (slot_of(ord, ncol) < k ? m + 1u : m);
         const uint32_t* flag = a.done + ny * P + nx;
