@@ -63,7 +63,7 @@ ALG_INT_INSTR_PER_ATTEMPT = 24
 # DRAM traffic of persistent_kernel from one ncu capture (bytes per launch of
 # a 10-MCS chunk at L = 3200), valid only for that kernel and workload and the
 # kernel sources it was taken from (hash below); None otherwise.
-NCU_TRAFFIC = {"sources_sha1": "3ec9580e902dc87a6ae7e9c1abbee6cc491d997d", "bytes_per_launch": 10302293 + 670635,
+NCU_TRAFFIC = {"sources_sha1": "f3d15f12ffa514d9d6328dec9a3d032ff0fde2ee", "bytes_per_launch": 10304768 + 817493,
                "kernel": "persistent_kernel", "L": 3200, "mcs_per_launch": 10,
                "profile": "profiles/persistent_kernel_L3200_M1e-4.md"}
 
